@@ -1,0 +1,122 @@
+"""Pins for oracle.fc (Sec. 4): polynomial exactness computed straight from the
+polynomial, blending endpoint conditions, Gram-table invariants and smoothness."""
+import numpy as np
+import pytest
+
+from oracle import fc
+from tables import gram_golden, paper_constants
+
+
+def _direct_paper_continuation(q, N, n_cont, dy):
+    """For a polynomial q of degree <= p the least-squares fits are exact, so the
+    continuation is (1-sigma) q(right wall + j dy) + sigma q(left wall - (n_cont+1-j) dy)."""
+    j = np.arange(1, n_cont + 1)
+    t = (j - 1) / (n_cont - 1)
+    s = 10 * t ** 3 - 15 * t ** 4 + 6 * t ** 5
+    yr = (N - 1) * dy + j * dy
+    yl = -(n_cont + 1 - j) * dy
+    return (1 - s) * q(yr) + s * q(yl)
+
+
+@pytest.mark.parametrize("n_match,p,n_cont", [(5, 3, 25), (10, 5, 16), (8, 4, 12)])
+def test_paper_table_exact_for_low_degree_polynomials(n_match, p, n_cont):
+    N = 40
+    dy = 1.0 / (N - 1)
+    y = np.arange(N) * dy
+    rng = np.random.default_rng(p)
+    c = rng.uniform(-1, 1, p + 1)
+    q = lambda yy: sum(c[i] * yy ** i for i in range(p + 1))
+    E = fc.paper_table(n_match, n_cont, p, fc.DIRICHLET)
+    F = fc.extend_last_axis(q(y), E)
+    np.testing.assert_allclose(F[N:], _direct_paper_continuation(q, N, n_cont, dy), rtol=0, atol=1e-10)
+
+
+def test_paper_neumann_row_exact_when_wall_slope_is_zero():
+    # q = y^2 (1-y)^2 has zero slope at both walls, so the appended Neumann row
+    # (Eq. 28) is consistent and the fit is still exact.
+    N, n_match, p, n_cont = 48, 10, 5, 12
+    dy = 1.0 / (N - 1)
+    y = np.arange(N) * dy
+    q = lambda yy: yy ** 2 * (1 - yy) ** 2
+    E = fc.paper_table(n_match, n_cont, p, fc.NEUMANN)
+    F = fc.extend_last_axis(q(y), E)
+    np.testing.assert_allclose(F[N:], _direct_paper_continuation(q, N, n_cont, dy), rtol=0, atol=1e-10)
+    # ... and with a nonzero wall slope it differs from the Dirichlet table.
+    q2 = lambda yy: yy + 0.0 * yy
+    Ed = fc.paper_table(n_match, n_cont, p, fc.DIRICHLET)
+    assert np.abs(fc.extend_last_axis(q2(y), E)[N:] - fc.extend_last_axis(q2(y), Ed)[N:]).max() > 1e-3
+
+
+def test_blend_sigma_endpoint_conditions():
+    # Eq. 26: sigma(0) = 0, sigma(1) = 1, sigma'(0) = sigma'(1) = 0.
+    want = paper_constants()["blend_sigma_endpoints"]
+    e = 1e-6
+    d0 = (fc.blend_sigma(e) - fc.blend_sigma(-e)) / (2 * e)
+    d1 = (fc.blend_sigma(1 + e) - fc.blend_sigma(1 - e)) / (2 * e)
+    np.testing.assert_allclose([fc.blend_sigma(0.0), fc.blend_sigma(1.0), d0, d1], want, atol=1e-8)
+
+
+def test_gram_table_matches_golden_file():
+    E = fc.gram_table(5, 25)
+    np.testing.assert_array_equal(E, gram_golden(5, 25))
+
+
+@pytest.mark.parametrize("n_cont", [22, 25, 28, 32])
+def test_gram_table_continues_constants_exactly(n_cont):
+    # The right blend-to-zero of 1 plus its mirror image solve the least-squares
+    # problem "1 on both fit intervals", whose exact solution is the constant 1.
+    E = gram_golden(5, n_cont)
+    # rounding of a sum of entries of size up to ~1e4
+    tol = 4e-16 * np.abs(E).sum(axis=1)
+    assert np.all(np.abs(E @ np.ones(10) - 1.0) <= tol)
+
+
+def test_gram_table_mirror_symmetry():
+    E = gram_golden(5, 25)
+    np.testing.assert_array_equal(E[:, 5:], E[::-1, :5][:, ::-1])
+
+
+def _spectral_derivative(F, dy):
+    n = F.shape[-1]
+    k = 2 * np.pi * np.fft.fftfreq(n, d=dy)
+    if n % 2 == 0:
+        k[n // 2] = 0
+    return np.real(np.fft.ifft(1j * k * np.fft.fft(F)))
+
+
+@pytest.mark.parametrize("deg", [0, 1, 2, 3, 4])
+def test_gram_extension_is_smooth_for_polynomials(deg):
+    # Degree < n_match is represented exactly by the Gram basis, so the only error
+    # of the extended line's Fourier derivative is the table's own (a few 1e-10).
+    N = 64
+    y = np.linspace(0, 1, N)
+    dy = y[1] - y[0]
+    c = np.random.default_rng(deg).uniform(-1, 1, deg + 1)
+    f = sum(c[i] * y ** i for i in range(deg + 1))
+    fp = sum(i * c[i] * y ** (i - 1) for i in range(1, deg + 1)) if deg > 0 else 0 * y
+    F = fc.extend_last_axis(f, gram_golden(5, 25))
+    err = np.abs(_spectral_derivative(F, dy)[:N] - fp).max()
+    assert err < 2e-9
+
+
+def test_gram_extension_converges_at_high_order():
+    # Paper's Sec. 4.3 example f = e^y sin(5y) + 0.5 y^3: derivative error of the
+    # FC-extended line falls like O(dy^4) (degree-4 Gram basis, derivative).
+    f = lambda y: np.exp(y) * np.sin(5 * y) + 0.5 * y ** 3
+    fp = lambda y: np.exp(y) * (np.sin(5 * y) + 5 * np.cos(5 * y)) + 1.5 * y ** 2
+    errs = []
+    for N in (64, 128, 256):
+        y = np.linspace(0, 1, N)
+        F = fc.extend_last_axis(f(y), gram_golden(5, 25))
+        errs.append(np.abs(_spectral_derivative(F, y[1] - y[0])[:N] - fp(y)).max())
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(rates > 3.7), (errs, rates)
+
+
+def test_extend2d_tensor_product_commutes():
+    E = gram_golden(5, 25)
+    f = np.random.default_rng(3).standard_normal((12, 9))
+    a = fc.extend2d(f, E, E)
+    b = fc.extend_last_axis(fc.extend_last_axis(f.T, E).T.T, E).T  # x first, then y
+    b = fc.extend_last_axis(fc.extend_last_axis(f.T, E).T, E)
+    np.testing.assert_allclose(a, b, rtol=0, atol=1e-9 * np.abs(a).max())

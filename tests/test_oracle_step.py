@@ -1,0 +1,67 @@
+"""Pins for oracle.step (Sec. 2.2, Eqs. 5-9, Sec. 6.3)."""
+import numpy as np
+import pytest
+
+from oracle import step, norms
+from paper_2606_06247_gb300 import inputs
+from tables import gram_golden, paper_constants
+
+
+def test_rk3_coefficients_are_the_printed_ones():
+    c = paper_constants()
+    np.testing.assert_allclose(step.RK3_A, c["RK3_a"], rtol=1e-15)
+    np.testing.assert_allclose(step.RK3_G, c["RK3_g"], rtol=1e-15)
+    np.testing.assert_allclose(step.RK3_Z, c["RK3_z"], rtol=1e-15)
+
+
+def _ode_error(scheme, dt, lam=-1.3, T=1.0):
+    A, G, Z = step.scheme_coefficients(scheme)
+    u = np.array([1.0])
+    Fp = np.zeros(1)
+    for _ in range(int(round(T / dt))):
+        for k in range(len(A)):
+            F = -lam * u           # du/dt = -F
+            u = step.momentum_update(u, F, Fp, 0.0, dt, A[k], G[k], Z[k])
+            Fp = F
+    return abs(u[0] - np.exp(lam * T))
+
+
+def test_rk3_is_third_order_and_fop_first_order():
+    e = [_ode_error("rk3", dt) for dt in (0.1, 0.05, 0.025)]
+    r = np.log2(np.array(e[:-1]) / np.array(e[1:]))
+    assert np.all(np.abs(r - 3) < 0.2), r
+    e = [_ode_error("fop", dt) for dt in (0.01, 0.005)]
+    assert abs(np.log2(e[0] / e[1]) - 1) < 0.1
+
+
+def _startup_series(y, t, F, nu, nterms=4001):
+    u = F / (2 * nu) * y * (1 - y)
+    for n in range(1, nterms, 2):
+        u -= 4 * F / (nu * np.pi ** 3 * n ** 3) * np.sin(n * np.pi * y) * np.exp(-nu * n * n * np.pi ** 2 * t)
+    return u
+
+
+def test_channel_startup_matches_analytic_series():
+    # Sec. 6.3 channel from rest: u(y,t) = F/(2nu) y(1-y) - sum_{n odd} 4F/(nu pi^3 n^3) sin(n pi y) e^{-nu n^2 pi^2 t}.
+    N = 32
+    E = gram_golden(5, 25)
+    p = step.Problem(nx=N, ny=N, Lx=N / (N - 1), Ly=1.0, x_walls=False, family="G4", h_over_dx=1.3,
+                     E_dir=E, E_neu=E, nu=0.1, rho=1.0, dt=1e-3, force=(0.8, 0.0), scheme="rk3").build_symbols()
+    u, v = inputs.channel_initial(N, N, seed=1)
+    u, v, phi = step.isph_steps(p, u, v, 40)
+    y = np.linspace(0, 1, N)
+    ua = np.tile(_startup_series(y, 0.04, 0.8, 0.1), (N, 1))
+    assert norms.l2_rel(u, ua) < 1e-3
+    assert np.abs(v).max() < 1e-5 and np.abs(phi).max() < 1e-4
+    assert np.all(u[:, 0] == 0) and np.all(u[:, -1] == 0) and np.all(v[:, [0, -1]] == 0)
+
+
+def test_cavity_walls_and_lid_are_imposed():
+    N = 16
+    E = gram_golden(5, 25)
+    p = step.Problem(nx=N, ny=N, Lx=1.0, Ly=1.0, x_walls=True, family="G8", h_over_dx=1.3,
+                     E_dir=E, E_neu=E, nu=1e-3, rho=1.0, dt=1e-3, u_top=1.0, scheme="rk3").build_symbols()
+    u, v = inputs.cavity_initial(N, N)
+    u, v, phi = step.isph_steps(p, u, v, 3)
+    assert np.all(u[1:-1, -1] == 1.0) and u[0, -1] == 0 and u[-1, -1] == 0
+    assert np.all(u[0, :] == 0) and np.all(v[:, 0] == 0) and np.all(np.isfinite(u))
