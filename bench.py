@@ -1,0 +1,368 @@
+"""Benchmark of the FC spectral ISPH hot path on GB300 (one JSON line).
+
+Workload: 2D lid-driven square cavity, 256 x 256 particles, walls on all four
+sides with FC(Gram) d=5, C=25 continuation in x and y (281 x 281 extended
+grid), Re = 1000 (lid velocity 1, nu = 1e-3), G8 kernel with h = 1.3 dx,
+low-storage RK3 (3 projection substeps per step), dt = 1e-3, fluid at rest at
+t = 0.  A batch of B independent instances is advanced together (device
+resident state, one CUDA graph per step).  One bench step = one RK3 ISPH step
+of every instance.  The metric is particle-updates/s = B * 256^2 * steps / s.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--batch B] [--prec f32|f64]
+  python bench.py --impl reference ...   # the FP64 CPU oracle (numpy) on the same workload
+
+Under torchrun each rank runs its own batch on its own GPU (independent
+instances, no data-path collective; weak scaling); rank 0 prints the line.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-updates/s per ISPH step, served-mixed vs plain FP64 at equal L2; p50/p99"
+N = 256
+NU, DT, LID = 1e-3, 1e-3, 1.0
+FAMILY, HDX = "G8", 1.3
+N_MATCH, N_CONT = 5, 25
+PROF_KINDS = ["col_fwd", "row_mom", "row_div", "row_grad", "row_op", "col_mom", "col_div", "col_corr", "col_out",
+              "row_ppe", "col_ppe", "other"]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--batch", type=int, default=32)
+    ap.add_argument("--prec", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--refine", type=int, default=2)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for k, nm in enumerate(names):
+                    if r[5 + k].lower().startswith("active"):
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- byte model
+def kernel_bytes(kind, nx, ny, hy, cb, batch):
+    """Algorithmic bytes one launch of each kernel kind must move (whole batch):
+    its spectra in/out at the context's complex size cb and the FP64 fields it
+    reads/writes.  Intermediates kept on chip inside the kernel do not count."""
+    S = hy * nx * cb        # one half-spectrum (rows ky < hy)
+    P = ny * nx * cb        # one PPE (DCT-y) spectrum (rows l < ny)
+    F = nx * ny * 8         # one FP64 field
+    per = {
+        "col_fwd": 2 * F + 2 * S,
+        "row_mom": 8 * S,
+        "row_div": 3 * S,
+        "row_grad": 3 * S,
+        "col_mom": 6 * S + 4 * F + 4 * F + 2 * S,
+        "col_div": S + F + P,
+        "col_corr": 2 * S + 2 * F + 2 * F + 2 * S,
+        "row_ppe": 2 * P,
+        "col_ppe": P + F + S,
+    }
+    return per.get(kind, 0) * batch
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# ---------------------------------------------------------------- CPU oracle
+class OracleCavity:
+    """The FP64 oracle (numpy) on one 256^2 cavity instance; built once, stepped on demand."""
+
+    def __init__(self, n=N):
+        import numpy as np
+        from oracle import fc as ofc
+        from oracle import step as ostep
+        self.ostep = ostep
+        E = ofc.gram_table(N_MATCH, N_CONT)
+        self.p = ostep.Problem(nx=n, ny=n, Lx=1.0, Ly=1.0, x_walls=True, family=FAMILY, h_over_dx=HDX, E_dir=E,
+                               E_neu=E, nu=NU, rho=1.0, dt=DT, u_top=LID, scheme="rk3").build_symbols()
+        self.u = np.zeros((n, n))
+        self.v = np.zeros((n, n))
+
+    def step(self):
+        t0 = time.perf_counter()
+        self.u, self.v, _ = self.ostep.isph_steps(self.p, self.u, self.v, 1)
+        return time.perf_counter() - t0
+
+
+def oracle_rate(seconds, n=N):
+    """Particle-updates/s of the oracle over >= 1 step and about `seconds` of stepping."""
+    oc = OracleCavity(n)
+    oc.step()  # first step outside the timing
+    el, steps = 0.0, 0
+    while steps == 0 or el < seconds:
+        el += oc.step()
+        steps += 1
+    return n * n * steps / el, steps, el
+
+
+def cpu_cores():
+    return os.cpu_count() or 1
+
+
+# ---------------------------------------------------------------- main (ours)
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0:
+        import __graft_entry__
+        __graft_entry__.build()
+    if ws > 1:
+        dist.barrier()
+    from paper_2606_06247_gb300 import binding as b
+
+    B = args.batch
+    dy = 1.0 / (N - 1)
+    stream = torch.cuda.current_stream()
+
+    def make(prec, refine):
+        return b.Context(N, N, 1.0, 1.0, x_walls=True, batch=B, n_match=N_MATCH, n_cont=N_CONT, family=FAMILY,
+                         h_over_dx=HDX, prec=prec, refine=refine)
+
+    def state():
+        z = torch.zeros((B, N, N), dtype=torch.float64, device=dev)
+        return [z.clone() for _ in range(5)]
+
+    prm = dict(nu=NU, rho=1.0, dt=DT, u_top=LID, scheme="rk3")
+
+    def timed(ctx, st, steps, warmup):
+        u, v, p, fu, fv = st
+        ctx.isph_step(u, v, p, fu, fv, warmup, use_graph=True, **prm)
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+        n0 = ctx.launch_count
+        with ClockSampler(local) as clk:
+            torch.cuda.synchronize()
+            ev[0].record(stream)
+            for k in range(steps):
+                ctx.isph_step(u, v, p, fu, fv, 1, use_graph=True, **prm)
+                ev[k + 1].record(stream)
+            torch.cuda.synchronize()
+        launches = ctx.launch_count - n0
+        per = [ev[k].elapsed_time(ev[k + 1]) for k in range(steps)]
+        total = ev[0].elapsed_time(ev[steps])
+        return total, per, launches, clk.summary()
+
+    # ---- headline: the chosen precision, batched, device resident
+    ctx = make(args.prec, args.refine if args.prec == "f32" else 0)
+    st = state()
+    total_ms, per_ms, launches, clocks = timed(ctx, st, args.steps, args.warmup)
+    t_max = total_ms
+    if ws > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    updates = ws * B * N * N * args.steps
+    value = updates / (t_max / 1e3)
+
+    # ---- per-kernel durations (eager launches, events on the launching stream)
+    ctx.set_profiling(True)
+    u, v, p, fu, fv = st
+    ctx.isph_step(u, v, p, fu, fv, max(2, min(args.steps, 5)), use_graph=False, **prm)
+    prof = ctx.get_profile()
+    ctx.set_profiling(False)
+    cb = 8 if args.prec == "f32" else 16
+    hy = (N + N_CONT) // 2 + 1
+    kinds = {k: dict(ms=v_[0], launches=v_[1], avg_ms=v_[0] / v_[1]) for k, v_ in prof.items()}
+    dom = max(kinds, key=lambda k: kinds[k]["ms"])
+    peaks, peak_src = load_peaks()
+    for k, d in kinds.items():
+        by = kernel_bytes(k, N, N, hy, cb, B)
+        d["alg_bytes"] = by
+        d["gbs"] = by / (d["avg_ms"] * 1e-3) / 1e9 if by else None
+    roof = {"kernel": dom, "bound": "hbm", "achieved": kinds[dom]["gbs"], "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": (kinds[dom]["gbs"] or 0) / peaks["hbm_gbs"], "traffic": None, "peak_source": peak_src + " hbm_gbs",
+            "alg_bytes_per_launch": kinds[dom]["alg_bytes"], "avg_launch_ms": kinds[dom]["avg_ms"]}
+    prof_total = sum(d["ms"] for d in kinds.values())
+    for d in kinds.values():
+        d["share"] = d["ms"] / prof_total
+
+    # ---- e2e through the C ABI with host buffers (pinned), copies inside the timed region
+    hu = torch.zeros((B, N, N), dtype=torch.float64).pin_memory()
+    hv = torch.zeros_like(hu).pin_memory()
+    hu.copy_(st[0].cpu())
+    hv.copy_(st[1].cpu())
+    e2e_steps = max(3, min(args.steps, 10))
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        u.copy_(hu, non_blocking=True)
+        v.copy_(hv, non_blocking=True)
+        ctx.isph_step(u, v, p, fu, fv, 1, use_graph=True, **prm)
+        hu.copy_(u, non_blocking=True)
+        hv.copy_(v, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    e2e = {"value": B * N * N / (e2e_ms / 1e3), "unit": "particle-updates/s",
+           "h2d_bytes_per_step": 2 * B * N * N * 8, "d2h_bytes_per_step": 2 * B * N * N * 8}
+
+    # ---- mixed vs plain FP64 on the same workload: throughput and L2 after the same steps
+    compare = None
+    if args.prec == "f32":
+        ctx64 = make("f64", 0)
+        st64 = state()
+        t64, per64, _, _ = timed(ctx64, st64, max(2, args.steps // 4), 1)
+        n64 = max(2, args.steps // 4)
+        v64 = B * N * N * n64 / (t64 / 1e3)
+        # equal-start L2: advance copies of one state with both paths
+        nsteps_cmp = 20
+        sa = state()
+        sb = state()
+        ctx.isph_step(*sa, nsteps_cmp, use_graph=True, **prm)
+        ctx64.isph_step(*sb, nsteps_cmp, use_graph=True, **prm)
+        torch.cuda.synchronize()
+        du = (sa[0] - sb[0]).double()
+        dv = (sa[1] - sb[1]).double()
+        l2 = float(torch.sqrt((du ** 2).sum() / (sb[0] ** 2).sum().clamp_min(1e-300)).item())
+        l2v = float(torch.sqrt((dv ** 2).sum() / (sb[1] ** 2).sum().clamp_min(1e-300)).item())
+        compare = {"plain_fp64_value": v64, "plain_fp64_ms_per_step": t64 / n64, "speedup_mixed_over_fp64": value / v64,
+                   "rel_l2_u_vs_fp64_after_20_steps": l2, "rel_l2_v_vs_fp64_after_20_steps": l2v,
+                   "linf_u_vs_fp64": float(du.abs().max().item())}
+
+    # ---- CPU baseline (oracle), rank 0 only
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        rate, nst, el = oracle_rate(args.cpu_seconds)
+        cpu = {"value": rate, "unit": "particle-updates/s", "cores": cpu_cores(), "kind": "oracle",
+               "sample": f"FP64 numpy oracle, 1 instance x {nst} RK3 steps of the 256^2 cavity ({el:.1f} s)"}
+
+    if rank == 0:
+        per_sorted = sorted(per_ms)
+        line = {
+            "metric": METRIC, "value": value, "unit": "particle-updates/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if args.prec == "f32" else "f64", "data": "synthetic",
+            "config": {"workload": f"lid-driven cavity {N}x{N} Re=1000, FC(Gram) d=5 C=25 on x and y, "
+                                   f"G8 h=1.3dx, RK3 dt=1e-3, batch of {B} instances", "batch": B, "nx": N, "ny": N,
+                       "precision": ("FP32 FFT/symbols, FP64 FC sums, state and PPE residual, "
+                                     f"{args.refine} refinement sweeps") if args.prec == "f32" else "FP64",
+                       "l2": f"inputs larger than L2 (state + workspace {B * N * N * 8 * 11 / 2**20:.0f} MiB)",
+                       "parallelism": f"replicas x{ws}"},
+            "latency_ms": {"p50": per_sorted[len(per_sorted) // 2], "p99": per_sorted[min(len(per_sorted) - 1, int(0.99 * len(per_sorted)))]},
+            "roofline": roof,
+            "kernels": kinds,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "compare": compare,
+        }
+        print(json.dumps(line))
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    oc = OracleCavity()
+    for _ in range(args.warmup):
+        oc.step()
+    times = [oc.step() for _ in range(args.steps)]
+    total = sum(times)
+    value = N * N * args.steps / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "particle-updates/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"lid-driven cavity {N}x{N} Re=1000, FC(Gram) d=5 C=25 on x and y, G8 h=1.3dx, "
+                                   "RK3 dt=1e-3; one instance per step (bounded sample)", "batch": 1, "nx": N, "ny": N},
+            "cpu_baseline": {"value": value, "unit": "particle-updates/s", "cores": cpu_cores(), "kind": "oracle",
+                             "sample": f"{args.steps} single-instance RK3 steps of the 256^2 cavity after {args.warmup} warm-up"},
+            "e2e": {"value": value, "unit": "particle-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

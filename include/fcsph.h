@@ -1,0 +1,188 @@
+/*
+ * fcsph.h -- C ABI of the GB300 (sm_103a) hot path of the FC-based spectral
+ * incompressible SPH scheme (Lin, Fourtakas & Rogers).
+ *
+ * One call chain per projection (sub)step (Sec. 5.2, Eqs. 5-9):
+ *   FC extension of each wall-normal line (Sec. 4, Eq. 30)
+ *   -> forward FFT over the extended periodic grid (Eqs. 11, 13)
+ *   -> multiplication by the kernel's Fourier symbol per operator (Eq. 16)
+ *      and the spectral PPE division (Eqs. 31-33)
+ *   -> inverse FFT and truncation to the physical nodes (Eq. 30).
+ *
+ * Conventions shared by every entry point
+ * --------------------------------------
+ * Grid.  y always has walls on its first and last node (dy = Ly/(ny-1)).
+ *   x is periodic (dx = Lx/nx, "channel") or has walls too (dx = Lx/(nx-1),
+ *   "cavity").  A field is a dense array f[batch][nx][ny], y contiguous,
+ *   holding `batch` independent instances of the same grid.
+ * Extended grid.  my = ny + n_cont; mx = nx (periodic x) or nx + n_cont.
+ * Pointers.  Every field pointer is a DEVICE pointer owned by the caller and
+ *   must stay valid until the work queued on the context's stream finishes.
+ *   Field element type: double when the context precision is FCSPH_F64,
+ *   float when FCSPH_F32 -- except the time-stepping state of isph_step,
+ *   which is always double.  Host pointers are marked "host".
+ * Asynchrony.  Calls enqueue work on the stream given at fcsph_create and
+ *   return; fcsph_sync waits and reports device-side errors.  No call aborts
+ *   the process and no kernel traps.
+ * Errors.  Every call returns an fcsph_status; on failure the context keeps
+ *   a message (fcsph_last_error).  Invalid arguments are rejected before any
+ *   work is queued (FCSPH_EINVAL); CUDA errors map to FCSPH_ECUDA.
+ */
+#ifndef FCSPH_H
+#define FCSPH_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FCSPH_OK = 0,
+  FCSPH_EINVAL = 1,      /* bad argument or unsupported size                 */
+  FCSPH_ENOMEM = 2,      /* device or host allocation failed                  */
+  FCSPH_ECUDA = 3,       /* a CUDA runtime call failed                        */
+  FCSPH_ETIMEOUT = 4,    /* a bounded device-side wait gave up                */
+  FCSPH_ENONFINITE = 5,  /* a non-finite value reached the time-step state    */
+  FCSPH_EUNSUPPORTED = 6 /* valid request this build does not implement       */
+} fcsph_status;
+
+enum { FCSPH_F64 = 0, FCSPH_F32 = 1 };                 /* arithmetic of FFTs and symbols */
+enum { FCSPH_FC_GRAM = 0, FCSPH_FC_PAPER = 1 };         /* FC table construction          */
+enum { FCSPH_DIRICHLET = 0, FCSPH_NEUMANN = 1 };        /* boundary data type (Sec. 4.4)  */
+enum { FCSPH_G2 = 1, FCSPH_G4 = 2, FCSPH_G6 = 3, FCSPH_G8 = 4, FCSPH_G10 = 5 }; /* Gaussian order 2n */
+enum { FCSPH_OP_W = 1u, FCSPH_OP_DX = 2u, FCSPH_OP_DY = 4u, FCSPH_OP_LAP = 8u }; /* spectral_op mask */
+enum { FCSPH_SCHEME_FOP = 0, FCSPH_SCHEME_RK3 = 1 };    /* Sec. 2.2                       */
+
+typedef struct {
+  int nx, ny;      /* physical nodes per instance (nx >= 4, ny >= 2*n_match)    */
+  double lx, ly;   /* domain lengths (see Grid above)                          */
+  int x_walls;     /* 0: x periodic; 1: walls at both x ends                   */
+  int batch;       /* independent instances per call (>= 1)                    */
+} fcsph_grid;
+
+typedef struct {
+  int variant;     /* FCSPH_FC_GRAM (default) or FCSPH_FC_PAPER                 */
+  int n_match;     /* wall-adjacent points per wall (Gram: d; paper: C, Eq. 14) */
+  int n_cont;      /* continuation points appended (Gram: C; paper: d, Eq. 21)  */
+  int poly_deg;    /* FCSPH_FC_PAPER only: fitted degree p (Eq. 16), < n_match  */
+} fcsph_fc;
+
+typedef struct {
+  int family;      /* FCSPH_G4 ... (Sec. 3.3, Appendix A)                       */
+  double h_over_dx;/* smoothing length h in units of dx                         */
+} fcsph_kernel;
+
+typedef struct {
+  int fft_prec;        /* FCSPH_F64 or FCSPH_F32                                 */
+  int ppe_refine_iters;/* extra FP64-residual / FP32-correction PPE sweeps       */
+} fcsph_precision;
+
+typedef struct fcsph_ctx fcsph_ctx;
+
+/* Time-stepping state of isph_step.  All device pointers to double arrays
+ * [batch][nx][ny], owned by the caller.  fu, fv hold F^{k-1} between RK3
+ * substeps (Eq. 5); their content on entry is ignored at the first substep. */
+typedef struct {
+  double *u, *v;   /* velocity, updated in place                              */
+  double *p;       /* out: pressure phi of the last substep (Eq. 8)           */
+  double *fu, *fv; /* scratch: F^{k-1} of Eq. 5                               */
+} fcsph_state;
+
+typedef struct {
+  double nu, rho, dt;  /* viscosity, density, time step                        */
+  double force_x, force_y; /* body force f of Eq. 1 (constant)                */
+  double u_bottom, u_top;  /* tangential wall velocity at y = 0 and y = Ly    */
+  int scheme;          /* FCSPH_SCHEME_FOP or FCSPH_SCHEME_RK3                 */
+  int use_graph;       /* 1: capture one step in a CUDA graph and replay it   */
+} fcsph_step_params;
+
+/* Create a context for one grid shape: builds the FC tables (Sec. 4; FP64,
+ * or quad precision for FC(Gram)), FFT plans and twiddles for every length
+ * the path needs, and device workspace for `grid->batch` instances.
+ *   fc_table_dir / fc_table_neu (host, nullable): caller-supplied FC tables,
+ *     row-major [n_cont][2*n_match], columns = the n_match values nearest the
+ *     y_max wall (in index order) then the n_match values nearest y = 0; NULL
+ *     builds them.  The same table serves both axes.
+ *   stream: cudaStream_t (NULL = legacy default stream).  */
+fcsph_status fcsph_create(const fcsph_grid* grid, const fcsph_fc* fc, const fcsph_kernel* kernel,
+                          const fcsph_precision* prec, const double* fc_table_dir,
+                          const double* fc_table_neu, void* stream, fcsph_ctx** out);
+fcsph_status fcsph_destroy(fcsph_ctx* ctx);
+
+/* FC table used by a context (host out, [n_cont][2*n_match] doubles). */
+fcsph_status fcsph_get_fc_table(const fcsph_ctx* ctx, int bc, double* out_host, size_t n_out);
+
+/* Build an FC table on the host without a context (Sec. 4 / Sec. 4.5).
+ * FC(Gram): the blend-to-zero trigonometric least squares solved in quad
+ * precision; paper variant: Eqs. 14-29 in FP64.  out_host: [n_cont][2*n_match]. */
+fcsph_status fcsph_fc_table(const fcsph_fc* fc, int bc, double* out_host, size_t n_out);
+
+/* Eq. 30: write the FC-extended field f_ext[batch][mx][my] of f (both of the
+ * context's element type).  Continuation along y for every x column, then
+ * (walled x) along x for every extended y row.  bc: FCSPH_DIRICHLET/NEUMANN. */
+fcsph_status fc_extend(fcsph_ctx* ctx, const void* f, void* f_ext, int bc);
+
+/* Eqs. 11/13/16: for each bit set in op_mask (in the order W, DX, DY, LAP),
+ * outs[k] receives that operator of f on the physical nodes.  outs has one
+ * device pointer per set bit.  FC with the Dirichlet (bc=0) or Neumann table. */
+fcsph_status spectral_op(fcsph_ctx* ctx, const void* f, unsigned op_mask, int bc, void* const* outs);
+
+/* div(fx, fy) = IFFT( S_x FFT(Fx) + S_y FFT(Fy) ) on the physical nodes. */
+fcsph_status spectral_div(fcsph_ctx* ctx, const void* fx, const void* fy, void* out);
+
+/* Eqs. 31-33: phi with lap(phi) = rhs under the DFT(x) x DCT-I(y) (periodic x)
+ * or DCT-I x DCT-I (walled x) diagonalisation; the (0,0) mode of phi is 0.
+ * With ppe_refine_iters > 0 (F32 contexts) each sweep forms the residual in
+ * FP64 and adds an FP32 correction.  resid_out (host, nullable): relative
+ * residual ||L phi - rhs + mean mode|| / ||rhs||, computed on the device in
+ * FP64 (synchronises the stream when non-NULL). */
+fcsph_status ppe_solve(fcsph_ctx* ctx, const void* rhs, void* phi, double* resid_out);
+
+/* Advance `nsteps` projection steps (Eqs. 5-9; FOP = 1 substep, RK3 = 3)
+ * of every instance.  Velocity uses the Dirichlet table, phi the Neumann one. */
+fcsph_status isph_step(fcsph_ctx* ctx, const fcsph_state* state, int nsteps, const fcsph_step_params* params);
+
+/* Wait for the context's stream; report device-side errors (non-finite state). */
+fcsph_status fcsph_sync(fcsph_ctx* ctx);
+
+/* Batched complex DFT of `nlines` contiguous lines of length n with the
+ * library's FFT engine (mixed radix Stockham / Bluestein), for testing the
+ * engine.  dir = -1 forward (exp(-2 pi i k m/n)), +1 inverse (unscaled).
+ * in/out: device arrays of nlines*n complex (interleaved re, im) doubles
+ * (prec FCSPH_F64) or floats (FCSPH_F32); in-place allowed. */
+fcsph_status fcsph_dft(int n, int nlines, int dir, int prec, const void* in, void* out, void* stream);
+
+/* Kernel launches this context has queued since creation (for bookkeeping). */
+long long fcsph_launch_count(const fcsph_ctx* ctx);
+
+/* Per-kernel timing with CUDA events recorded on the context's stream around
+ * every launch (eager launches only; isph_step with use_graph = 0).  Kinds:
+ * FCSPH_PROF_* below.  fcsph_get_profile synchronises the stream, returns the
+ * summed milliseconds and launch counts per kind since the last call (arrays
+ * of n_kinds entries, host) and resets them. */
+enum {
+  FCSPH_PROF_COL_FWD = 0,   /* FC (or DCT) + forward FFT of wall-normal lines     */
+  FCSPH_PROF_ROW_MOM = 1,   /* x pass: 2 spectra -> 6 (grad, lap of u and v)      */
+  FCSPH_PROF_ROW_DIV = 2,   /* x pass: 2 spectra -> divergence                    */
+  FCSPH_PROF_ROW_GRAD = 3,  /* x pass: phi spectrum -> grad phi                   */
+  FCSPH_PROF_ROW_OP = 4,    /* x pass of spectral_op / spectral_div               */
+  FCSPH_PROF_COL_MOM = 5,   /* inverse + momentum update + forward of u*, v*      */
+  FCSPH_PROF_COL_DIV = 6,   /* inverse + PPE right-hand side + DCT forward        */
+  FCSPH_PROF_COL_CORR = 7,  /* inverse + projection + forward of u, v             */
+  FCSPH_PROF_COL_OUT = 8,   /* inverse + store (spectral_op / spectral_div)       */
+  FCSPH_PROF_ROW_PPE = 9,   /* PPE x transform, division, inverse                 */
+  FCSPH_PROF_COL_PPE = 10,  /* PPE inverse DCT (+ Neumann FC forward of phi)      */
+  FCSPH_PROF_OTHER = 11,    /* fc_extend, reductions, conversions                 */
+  FCSPH_PROF_KINDS = 12
+};
+fcsph_status fcsph_set_profiling(fcsph_ctx* ctx, int on);
+fcsph_status fcsph_get_profile(fcsph_ctx* ctx, double* ms_out, long long* count_out, int n_kinds);
+
+/* Copy the last error message of ctx (or of context-free calls if ctx is NULL). */
+fcsph_status fcsph_last_error(const fcsph_ctx* ctx, char* buf, size_t n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FCSPH_H */

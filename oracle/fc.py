@@ -164,11 +164,14 @@ def fc_table(variant, n_match, n_cont, bc=DIRICHLET, p=None):
 
 
 def extend_last_axis(f, E):
-    """Append the FC continuation E @ b along the last axis (Eq. 30)."""
+    """Append the FC continuation E @ b along the last axis (Eq. 30).
+
+    The table entries reach ~1e4 while E @ b is O(|b|), so the products are
+    accumulated in extended precision (np.longdouble) and rounded once."""
     n_cont, two_m = E.shape
     m = two_m // 2
     b = np.concatenate([f[..., -m:], f[..., :m]], axis=-1)
-    cont = b @ E.T
+    cont = (b.astype(np.longdouble) @ E.T.astype(np.longdouble)).astype(np.float64)
     return np.concatenate([f, cont], axis=-1)
 
 

@@ -1,0 +1,221 @@
+"""Thin ctypes binding of libfcsph (include/fcsph.h), same names as the C ABI.
+
+Argument marshalling only: every step of the path runs in the library's CUDA
+kernels.  Device arrays are torch CUDA tensors (their data_ptr() is passed);
+the stream is torch's current CUDA stream unless given.  Importing this module
+loads libfcsph.so and raises if it has not been built -- there is no fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfcsph.so")
+
+F64, F32 = 0, 1
+FC_GRAM, FC_PAPER = 0, 1
+DIRICHLET, NEUMANN = 0, 1
+FAMILY = {"G2": 1, "G4": 2, "G6": 3, "G8": 4, "G10": 5}
+OP_W, OP_DX, OP_DY, OP_LAP = 1, 2, 4, 8
+OPS = {"W": OP_W, "DX": OP_DX, "DY": OP_DY, "LAP": OP_LAP}
+SCHEME = {"fop": 0, "rk3": 1}
+PROF_KINDS = ["col_fwd", "row_mom", "row_div", "row_grad", "row_op", "col_mom", "col_div", "col_corr", "col_out",
+              "row_ppe", "col_ppe", "other"]
+STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ENONFINITE", 6: "EUNSUPPORTED"}
+
+
+class FcsphError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"fcsph {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class fcsph_grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("lx", ctypes.c_double), ("ly", ctypes.c_double),
+                ("x_walls", ctypes.c_int), ("batch", ctypes.c_int)]
+
+
+class fcsph_fc(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int), ("n_match", ctypes.c_int), ("n_cont", ctypes.c_int), ("poly_deg", ctypes.c_int)]
+
+
+class fcsph_kernel(ctypes.Structure):
+    _fields_ = [("family", ctypes.c_int), ("h_over_dx", ctypes.c_double)]
+
+
+class fcsph_precision(ctypes.Structure):
+    _fields_ = [("fft_prec", ctypes.c_int), ("ppe_refine_iters", ctypes.c_int)]
+
+
+class fcsph_state(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_void_p) for n in ("u", "v", "p", "fu", "fv")]
+
+
+class fcsph_step_params(ctypes.Structure):
+    _fields_ = [("nu", ctypes.c_double), ("rho", ctypes.c_double), ("dt", ctypes.c_double),
+                ("force_x", ctypes.c_double), ("force_y", ctypes.c_double),
+                ("u_bottom", ctypes.c_double), ("u_top", ctypes.c_double),
+                ("scheme", ctypes.c_int), ("use_graph", ctypes.c_int)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it first (python -m paper_2606_06247_gb300.build)")
+    L = ctypes.CDLL(LIB_PATH)
+    P, I, D, U, S = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_uint, ctypes.c_size_t
+    sig = {
+        "fcsph_create": [ctypes.POINTER(fcsph_grid), ctypes.POINTER(fcsph_fc), ctypes.POINTER(fcsph_kernel),
+                         ctypes.POINTER(fcsph_precision), P, P, P, ctypes.POINTER(P)],
+        "fcsph_destroy": [P],
+        "fcsph_get_fc_table": [P, I, P, S],
+        "fcsph_fc_table": [ctypes.POINTER(fcsph_fc), I, P, S],
+        "fc_extend": [P, P, P, I],
+        "spectral_op": [P, P, U, I, P],
+        "spectral_div": [P, P, P, P],
+        "ppe_solve": [P, P, P, ctypes.POINTER(D)],
+        "isph_step": [P, ctypes.POINTER(fcsph_state), I, ctypes.POINTER(fcsph_step_params)],
+        "fcsph_sync": [P],
+        "fcsph_dft": [I, I, I, I, P, P, P],
+        "fcsph_launch_count": [P],
+        "fcsph_last_error": [P, ctypes.c_char_p, S],
+        "fcsph_set_profiling": [P, I],
+        "fcsph_get_profile": [P, P, P, I],
+    }
+    for name, args in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_longlong if name == "fcsph_launch_count" else ctypes.c_int
+    return L
+
+
+lib = _load()
+
+
+def last_error(ctx=None):
+    buf = ctypes.create_string_buffer(512)
+    lib.fcsph_last_error(ctx, buf, 512)
+    return buf.value.decode()
+
+
+def _check(st, ctx=None):
+    if st != 0:
+        raise FcsphError(st, last_error(ctx))
+
+
+def _stream(stream):
+    if stream is not None:
+        return ctypes.c_void_p(stream)
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def fc_table(variant="gram", n_match=5, n_cont=25, bc=DIRICHLET, poly_deg=0):
+    """Host-built FC table [n_cont][2*n_match] (fcsph_fc_table)."""
+    fc = fcsph_fc(FC_GRAM if variant == "gram" else FC_PAPER, n_match, n_cont, poly_deg)
+    out = np.zeros((n_cont, 2 * n_match))
+    _check(lib.fcsph_fc_table(ctypes.byref(fc), bc, out.ctypes.data_as(ctypes.c_void_p), out.size))
+    return out
+
+
+def fcsph_dft(x, direction=-1, stream=None):
+    """Batched DFT over the last axis of a complex CUDA tensor (engine test entry)."""
+    import torch
+    assert x.is_cuda and x.is_complex() and x.is_contiguous()
+    prec = F64 if x.dtype == torch.complex128 else F32
+    n = x.shape[-1]
+    out = torch.empty_like(x)
+    _check(lib.fcsph_dft(n, x.numel() // n if n else 0, direction, prec, _ptr(x), _ptr(out), _stream(stream)))
+    return out
+
+
+class Context:
+    """fcsph_create/destroy plus the per-call entry points."""
+
+    def __init__(self, nx, ny, lx, ly, x_walls=False, batch=1, n_match=5, n_cont=25, variant="gram", poly_deg=0,
+                 family="G4", h_over_dx=1.3, prec="f64", refine=0, table_dir=None, table_neu=None, stream=None):
+        self.grid = fcsph_grid(nx, ny, lx, ly, 1 if x_walls else 0, batch)
+        self.fc = fcsph_fc(FC_GRAM if variant == "gram" else FC_PAPER, n_match, n_cont, poly_deg)
+        self.kernel = fcsph_kernel(FAMILY[family], h_over_dx)
+        self.prec = fcsph_precision(F64 if prec == "f64" else F32, refine)
+        self.prec_name = prec
+        self._tabs = []
+        tp = []
+        for t in (table_dir, table_neu):
+            if t is None:
+                tp.append(None)
+            else:
+                a = np.ascontiguousarray(t, dtype=np.float64)
+                assert a.shape == (n_cont, 2 * n_match)
+                self._tabs.append(a)
+                tp.append(a.ctypes.data_as(ctypes.c_void_p))
+        self.stream = _stream(stream)
+        h = ctypes.c_void_p()
+        _check(lib.fcsph_create(ctypes.byref(self.grid), ctypes.byref(self.fc), ctypes.byref(self.kernel),
+                                ctypes.byref(self.prec), tp[0], tp[1], self.stream, ctypes.byref(h)))
+        self.h = h
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h:
+            lib.fcsph_destroy(h)
+            self.h = None
+
+    def close(self):
+        self.__del__()
+
+    def _ck(self, st):
+        _check(st, self.h)
+
+    def get_fc_table(self, bc=DIRICHLET):
+        out = np.zeros((self.fc.n_cont, 2 * self.fc.n_match))
+        self._ck(lib.fcsph_get_fc_table(self.h, bc, out.ctypes.data_as(ctypes.c_void_p), out.size))
+        return out
+
+    def fc_extend(self, f, f_ext, bc=DIRICHLET):
+        self._ck(lib.fc_extend(self.h, _ptr(f), _ptr(f_ext), bc))
+
+    def spectral_op(self, f, ops, outs, bc=DIRICHLET):
+        mask = 0
+        for o in ops:
+            mask |= OPS[o]
+        order = [o for o in ("W", "DX", "DY", "LAP") if mask & OPS[o]]
+        by_name = dict(zip(ops, outs))
+        arr = (ctypes.c_void_p * len(order))(*[by_name[o].data_ptr() for o in order])
+        self._ck(lib.spectral_op(self.h, _ptr(f), mask, bc, arr))
+
+    def spectral_div(self, fx, fy, out):
+        self._ck(lib.spectral_div(self.h, _ptr(fx), _ptr(fy), _ptr(out)))
+
+    def ppe_solve(self, rhs, phi, want_resid=False):
+        r = ctypes.c_double(0.0)
+        self._ck(lib.ppe_solve(self.h, _ptr(rhs), _ptr(phi), ctypes.byref(r) if want_resid else None))
+        return r.value if want_resid else None
+
+    def isph_step(self, u, v, p, fu, fv, nsteps, nu, rho=1.0, dt=1e-3, force=(0.0, 0.0), u_bottom=0.0, u_top=0.0,
+                  scheme="fop", use_graph=True):
+        st = fcsph_state(u.data_ptr(), v.data_ptr(), p.data_ptr(), fu.data_ptr(), fv.data_ptr())
+        prm = fcsph_step_params(nu, rho, dt, force[0], force[1], u_bottom, u_top, SCHEME[scheme], 1 if use_graph else 0)
+        self._ck(lib.isph_step(self.h, ctypes.byref(st), nsteps, ctypes.byref(prm)))
+
+    def sync(self):
+        self._ck(lib.fcsph_sync(self.h))
+
+    @property
+    def launch_count(self):
+        return lib.fcsph_launch_count(self.h)
+
+    def set_profiling(self, on=True):
+        self._ck(lib.fcsph_set_profiling(self.h, 1 if on else 0))
+
+    def get_profile(self):
+        """{kind: (total_ms, launches)} since the last call (eager launches only)."""
+        ms = np.zeros(len(PROF_KINDS))
+        cnt = np.zeros(len(PROF_KINDS), dtype=np.int64)
+        self._ck(lib.fcsph_get_profile(self.h, ms.ctypes.data_as(ctypes.c_void_p),
+                                       cnt.ctypes.data_as(ctypes.c_void_p), len(PROF_KINDS)))
+        return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(PROF_KINDS) if cnt[i] > 0}

@@ -1,0 +1,604 @@
+// C ABI of the FC spectral ISPH hot path: contexts, tables, plans, workspace
+// and the call sequences of fc_extend / spectral_op / spectral_div /
+// ppe_solve / isph_step (Sec. 5.2).  All arithmetic runs in the kernels of
+// fcsph_kernels.cu; this file only validates, allocates and sequences.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "fcsph_internal.h"
+
+using namespace fcsph;
+
+namespace {
+
+std::mutex g_err_mu;
+std::string g_err;  // context-free calls
+
+void set_global_err(const std::string& s) {
+  std::lock_guard<std::mutex> lk(g_err_mu);
+  g_err = s;
+}
+
+fcsph_status fail(fcsph_ctx* c, fcsph_status st, const std::string& msg) {
+  if (c)
+    c->err = msg;
+  else
+    set_global_err(msg);
+  return st;
+}
+
+fcsph_status cuda_fail(fcsph_ctx* c, cudaError_t e, const char* where) {
+  return fail(c, FCSPH_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define FCSPH_CK(call, where)                      \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) return cuda_fail(c, e_, where); \
+  } while (0)
+
+size_t cplx_bytes(int prec) { return prec == FCSPH_F64 ? 16 : 8; }
+
+// Upload a host pool, fill Bluestein filters with the FP64 engine, then make
+// the FP32 copy.  `fill` lists (plan, filter) pairs.
+struct Fill {
+  FftPlan P;
+  std::vector<double> re, im;
+};
+
+fcsph_status upload_pool(fcsph_ctx* c, Pool& pool, std::vector<Fill>& fills, double2** d64, float2** d32,
+                         cudaStream_t st) {
+  const size_t n = pool.re.size();
+  std::vector<double2> h(n);
+  for (size_t i = 0; i < n; ++i) h[i] = make_double2(pool.re[i], pool.im[i]);
+  FCSPH_CK(cudaMalloc((void**)d64, n * sizeof(double2)), "cudaMalloc(pool64)");
+  FCSPH_CK(cudaMalloc((void**)d32, n * sizeof(float2)), "cudaMalloc(pool32)");
+  FCSPH_CK(cudaMemcpyAsync(*d64, h.data(), n * sizeof(double2), cudaMemcpyHostToDevice, st), "pool upload");
+  for (Fill& f : fills) {
+    const int m = f.P.sub.n;
+    std::vector<double2> hb(m);
+    for (int j = 0; j < m; ++j) hb[j] = make_double2(f.re[j], f.im[j]);
+    double2* tmp = nullptr;
+    FCSPH_CK(cudaMalloc((void**)&tmp, m * sizeof(double2)), "cudaMalloc(bluestein)");
+    FCSPH_CK(cudaMemcpyAsync(tmp, hb.data(), m * sizeof(double2), cudaMemcpyHostToDevice, st), "bluestein upload");
+    FftPlan direct;
+    direct.base = f.P.sub;
+    direct.bs = 0;
+    cudaError_t e = launch_dft_lines(m, 1, -1, FCSPH_F64, tmp, tmp, st, direct, *d64);
+    if (e != cudaSuccess) {
+      cudaFree(tmp);
+      return cuda_fail(c, e, "bluestein filter");
+    }
+    FCSPH_CK(cudaMemcpyAsync(hb.data(), tmp, m * sizeof(double2), cudaMemcpyDeviceToHost, st), "bluestein download");
+    FCSPH_CK(cudaStreamSynchronize(st), "bluestein sync");
+    cudaFree(tmp);
+    for (int j = 0; j < m; ++j) h[f.P.bhat + j] = make_double2(hb[j].x / m, hb[j].y / m);
+  }
+  FCSPH_CK(cudaMemcpyAsync(*d64, h.data(), n * sizeof(double2), cudaMemcpyHostToDevice, st), "pool upload 2");
+  std::vector<float2> hf(n);
+  for (size_t i = 0; i < n; ++i) hf[i] = make_float2((float)h[i].x, (float)h[i].y);
+  FCSPH_CK(cudaMemcpyAsync(*d32, hf.data(), n * sizeof(float2), cudaMemcpyHostToDevice, st), "pool32 upload");
+  FCSPH_CK(cudaStreamSynchronize(st), "pool sync");
+  return FCSPH_OK;
+}
+
+FftPlan plan_for(int n, Pool* pool, std::vector<Fill>* fills) {
+  Fill f;
+  FftPlan P = make_plan(n, pool, &f.re, &f.im);
+  if (P.bs) {
+    f.P = P;
+    fills->push_back(f);
+  }
+  return P;
+}
+
+RowOps ops_none() {
+  RowOps o;
+  memset(&o, 0, sizeof(o));
+  return o;
+}
+
+size_t field_elems(const fcsph_ctx* c) { return (size_t)c->gd.batch * c->gd.nx * c->gd.ny; }
+
+}  // namespace
+
+ProfScope::ProfScope(fcsph_ctx* ctx, int k) : c(ctx), kind(k) {
+  if (!c || !c->prof_on) return;
+  cudaEvent_t a;
+  if (!c->ev_free.empty()) {
+    a = c->ev_free.back();
+    c->ev_free.pop_back();
+  } else if (cudaEventCreate(&a) != cudaSuccess) {
+    return;
+  }
+  if (!c->ev_free.empty()) {
+    b = c->ev_free.back();
+    c->ev_free.pop_back();
+  } else if (cudaEventCreate(&b) != cudaSuccess) {
+    c->ev_free.push_back(a);
+    b = nullptr;
+    return;
+  }
+  cudaEventRecord(a, c->stream);
+  c->pending.push_back({kind, a, b});
+}
+
+ProfScope::~ProfScope() {
+  if (b) cudaEventRecord(b, c->stream);
+}
+
+extern "C" {
+
+fcsph_status fcsph_fc_table(const fcsph_fc* fc, int bc, double* out_host, size_t n_out) {
+  if (!fc || !out_host) return fail(nullptr, FCSPH_EINVAL, "fcsph_fc_table: null argument");
+  std::vector<double> E;
+  std::string err;
+  int st = fc_table_build(fc, bc, &E, &err);
+  if (st != FCSPH_OK) return fail(nullptr, (fcsph_status)st, err);
+  if (n_out < E.size()) return fail(nullptr, FCSPH_EINVAL, "fcsph_fc_table: output too small");
+  memcpy(out_host, E.data(), E.size() * sizeof(double));
+  return FCSPH_OK;
+}
+
+fcsph_status fcsph_create(const fcsph_grid* grid, const fcsph_fc* fc, const fcsph_kernel* kernel,
+                          const fcsph_precision* prec, const double* fc_table_dir, const double* fc_table_neu,
+                          void* stream, fcsph_ctx** out) {
+  if (!grid || !fc || !kernel || !prec || !out) return fail(nullptr, FCSPH_EINVAL, "fcsph_create: null argument");
+  *out = nullptr;
+  if (grid->nx < 4 || grid->ny < 2 * fc->n_match || grid->batch < 1 || !(grid->lx > 0) || !(grid->ly > 0))
+    return fail(nullptr, FCSPH_EINVAL, "fcsph_create: need nx >= 4, ny >= 2*n_match, batch >= 1, lx, ly > 0");
+  if (grid->nx > 8192 || grid->ny > 8192)
+    return fail(nullptr, FCSPH_EINVAL, "fcsph_create: nx, ny > 8192 not supported");
+  if (kernel->family < FCSPH_G2 || kernel->family > FCSPH_G10 || !(kernel->h_over_dx >= 0))
+    return fail(nullptr, FCSPH_EINVAL, "fcsph_create: bad kernel");
+  if (prec->fft_prec != FCSPH_F64 && prec->fft_prec != FCSPH_F32)
+    return fail(nullptr, FCSPH_EINVAL, "fcsph_create: bad precision");
+  if (grid->x_walls && grid->nx < 2 * fc->n_match)
+    return fail(nullptr, FCSPH_EINVAL, "fcsph_create: walled x needs nx >= 2*n_match");
+  fcsph_ctx* c = new fcsph_ctx();
+  c->grid = *grid;
+  c->fc = *fc;
+  c->kern = *kernel;
+  c->prec = *prec;
+  c->stream = (cudaStream_t)stream;
+  for (int bc = 0; bc < 2; ++bc) {
+    const double* given = bc == 0 ? fc_table_dir : fc_table_neu;
+    if (given) {
+      c->hE[bc].assign(given, given + (size_t)fc->n_cont * 2 * fc->n_match);
+    } else {
+      std::string err;
+      int st = fc_table_build(fc, bc, &c->hE[bc], &err);
+      if (st != FCSPH_OK) {
+        delete c;
+        return fail(nullptr, (fcsph_status)st, err);
+      }
+    }
+  }
+  GridDev& g = c->gd;
+  g.nx = grid->nx;
+  g.ny = grid->ny;
+  g.batch = grid->batch;
+  g.x_walls = grid->x_walls ? 1 : 0;
+  g.n_match = fc->n_match;
+  g.n_cont = fc->n_cont;
+  g.my = g.ny + g.n_cont;
+  g.mx = g.x_walls ? g.nx + g.n_cont : g.nx;
+  g.hy = g.my / 2 + 1;
+  g.rows = g.hy > g.ny ? g.hy : g.ny;
+  g.lx = grid->lx;
+  g.ly = grid->ly;
+  g.dx = g.x_walls ? grid->lx / (g.nx - 1) : grid->lx / g.nx;
+  g.dy = grid->ly / (g.ny - 1);
+  g.h = kernel->h_over_dx * g.dx;
+  g.family = kernel->family;
+
+  Pool pool;
+  std::vector<Fill> fills;
+  c->plan_y = plan_for(g.my, &pool, &fills);
+  c->plan_x = plan_for(g.mx, &pool, &fills);
+  c->plan_py = plan_for(2 * (g.ny - 1), &pool, &fills);
+  c->plan_px = plan_for(g.x_walls ? 2 * (g.nx - 1) : g.nx, &pool, &fills);
+
+  fcsph_status st = FCSPH_OK;
+  cudaError_t e;
+#define CREATE_CK(call, where)             \
+  if ((e = (call)) != cudaSuccess) {       \
+    st = cuda_fail(c, e, where);           \
+    goto fail_out;                         \
+  }
+  {
+    st = upload_pool(c, pool, fills, &c->pool64, &c->pool32, c->stream);
+    if (st != FCSPH_OK) goto fail_out;
+    const size_t ne = (size_t)g.n_cont * 2 * g.n_match;
+    CREATE_CK(cudaMalloc((void**)&c->dE, 2 * ne * sizeof(double)), "cudaMalloc(E)");
+    CREATE_CK(cudaMemcpy(c->dE, c->hE[0].data(), ne * sizeof(double), cudaMemcpyHostToDevice), "E upload");
+    CREATE_CK(cudaMemcpy(c->dE + ne, c->hE[1].data(), ne * sizeof(double), cudaMemcpyHostToDevice), "E upload");
+    const size_t fs = (size_t)g.rows * g.nx * g.batch;
+    const size_t cb = cplx_bytes(prec->fft_prec);
+    CREATE_CK(cudaMalloc(&c->spec_in, 2 * fs * cb), "cudaMalloc(spec_in)");
+    CREATE_CK(cudaMalloc(&c->spec_out, 6 * fs * cb), "cudaMalloc(spec_out)");
+    CREATE_CK(cudaMalloc(&c->spec_ppe, fs * 16), "cudaMalloc(spec_ppe)");  // FP64-sized: refinement
+    CREATE_CK(cudaMalloc((void**)&c->work, 6 * field_elems(c) * sizeof(double)), "cudaMalloc(work)");
+    CREATE_CK(cudaMalloc((void**)&c->dred, 8 * sizeof(double)), "cudaMalloc(red)");
+    CREATE_CK(cudaMalloc((void**)&c->dstatus, sizeof(int)), "cudaMalloc(status)");
+    CREATE_CK(cudaMemset(c->dstatus, 0, sizeof(int)), "status clear");
+    CREATE_CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking), "capture stream");
+  }
+  *out = c;
+  return FCSPH_OK;
+fail_out:
+  set_global_err(c->err);
+  fcsph_destroy(c);
+  return st;
+#undef CREATE_CK
+}
+
+fcsph_status fcsph_destroy(fcsph_ctx* c) {
+  if (!c) return FCSPH_OK;
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  for (auto& p : c->pending) {
+    c->ev_free.push_back(p.a);
+    c->ev_free.push_back(p.b);
+  }
+  for (cudaEvent_t ev : c->ev_free) cudaEventDestroy(ev);
+  cudaFree(c->pool64);
+  cudaFree(c->pool32);
+  cudaFree(c->dE);
+  cudaFree(c->spec_in);
+  cudaFree(c->spec_out);
+  cudaFree(c->spec_ppe);
+  cudaFree(c->work);
+  cudaFree(c->dred);
+  cudaFree(c->dstatus);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  delete c;
+  return FCSPH_OK;
+}
+
+fcsph_status fcsph_get_fc_table(const fcsph_ctx* c, int bc, double* out_host, size_t n_out) {
+  if (!c || !out_host || (bc != 0 && bc != 1)) return fail(nullptr, FCSPH_EINVAL, "fcsph_get_fc_table: bad argument");
+  if (n_out < c->hE[bc].size()) return fail(nullptr, FCSPH_EINVAL, "fcsph_get_fc_table: output too small");
+  memcpy(out_host, c->hE[bc].data(), c->hE[bc].size() * sizeof(double));
+  return FCSPH_OK;
+}
+
+fcsph_status fc_extend(fcsph_ctx* c, const void* f, void* f_ext, int bc) {
+  if (!c || !f || !f_ext || (bc != 0 && bc != 1)) return fail(c, FCSPH_EINVAL, "fc_extend: bad argument");
+  FCSPH_CK(launch_fc_extend(c, f, f_ext, bc), "fc_extend");
+  return FCSPH_OK;
+}
+
+fcsph_status spectral_op(fcsph_ctx* c, const void* f, unsigned op_mask, int bc, void* const* outs) {
+  if (!c || !f || !outs || (bc != 0 && bc != 1)) return fail(c, FCSPH_EINVAL, "spectral_op: bad argument");
+  if (op_mask == 0 || op_mask > 15u) return fail(c, FCSPH_EINVAL, "spectral_op: op_mask must be a nonempty subset of W|DX|DY|LAP");
+  RowOps ops = ops_none();
+  ops.nin = 1;
+  const int sym[4] = {SYM_W, SYM_DX, SYM_DY, SYM_LAP};
+  for (int b = 0; b < 4; ++b)
+    if (op_mask & (1u << b)) {
+      if (!outs[ops.nout]) return fail(c, FCSPH_EINVAL, "spectral_op: null output pointer");
+      ops.nterm[ops.nout] = 1;
+      ops.field[ops.nout][0] = 0;
+      ops.op[ops.nout][0] = sym[b];
+      ops.nout++;
+    }
+  const int p = c->prec.fft_prec;
+  const void* fl[1] = {f};
+  FCSPH_CK(launch_col_fwd(c, p, 1, fl, p == FCSPH_F64, bc, c->spec_in, 0), "spectral_op fwd");
+  FCSPH_CK(launch_row_sym(c, p, c->spec_in, c->spec_out, ops, 1.0 / ((double)c->gd.mx * c->gd.my), bc, FCSPH_PROF_ROW_OP),
+           "spectral_op row");
+  FCSPH_CK(launch_col_out(c, c->spec_out, ops.nout, outs), "spectral_op inv");
+  return FCSPH_OK;
+}
+
+fcsph_status spectral_div(fcsph_ctx* c, const void* fx, const void* fy, void* out) {
+  if (!c || !fx || !fy || !out) return fail(c, FCSPH_EINVAL, "spectral_div: bad argument");
+  RowOps ops = ops_none();
+  ops.nin = 2;
+  ops.nout = 1;
+  ops.nterm[0] = 2;
+  ops.field[0][0] = 0;
+  ops.op[0][0] = SYM_DX;
+  ops.field[0][1] = 1;
+  ops.op[0][1] = SYM_DY;
+  const int p = c->prec.fft_prec;
+  const void* fl[2] = {fx, fy};
+  void* outs[1] = {out};
+  FCSPH_CK(launch_col_fwd(c, p, 2, fl, p == FCSPH_F64, FCSPH_DIRICHLET, c->spec_in, 0), "spectral_div fwd");
+  FCSPH_CK(launch_row_sym(c, p, c->spec_in, c->spec_out, ops, 1.0 / ((double)c->gd.mx * c->gd.my), FCSPH_DIRICHLET,
+                          FCSPH_PROF_ROW_OP),
+           "spectral_div row");
+  FCSPH_CK(launch_col_out(c, c->spec_out, 1, outs), "spectral_div inv");
+  return FCSPH_OK;
+}
+
+// Iterative refinement of the PPE solution phi64 (double, device) for the
+// right-hand side b64: b0 = b64 without its (0,0) transform mode (FP64), then
+// `iters` sweeps of r = b0 - L phi (FP64) and phi += solve(r) (context
+// precision).  Removing the constant mode first keeps it out of the FP32
+// corrections, whose rounding it would otherwise dominate.  The last sweep
+// optionally ends with the Neumann-FC forward transform of phi (spec_in).
+static fcsph_status ppe_refine(fcsph_ctx* c, const double* b64, double* phi64, int iters, int neumann_fwd) {
+  const int p = c->prec.fft_prec;
+  const size_t n = field_elems(c);
+  double* r = c->work + 4 * n;
+  double* b0 = c->work + 5 * n;
+  const void* bl[1] = {b64};
+  FCSPH_CK(launch_col_fwd(c, FCSPH_F64, 1, bl, 1, FCSPH_DIRICHLET, c->spec_ppe, 1), "refine project fwd");
+  FCSPH_CK(launch_row_ppe(c, FCSPH_F64, c->spec_ppe, 2), "refine project row");
+  FCSPH_CK(launch_col_ppe_inv(c, FCSPH_F64, c->spec_ppe, b0, 1, nullptr, 0, nullptr, 0, nullptr), "refine project inv");
+  for (int it = 0; it < iters; ++it) {
+    const void* pl[1] = {phi64};
+    FCSPH_CK(launch_col_fwd(c, FCSPH_F64, 1, pl, 1, FCSPH_DIRICHLET, c->spec_ppe, 1), "refine L fwd");
+    FCSPH_CK(launch_row_ppe(c, FCSPH_F64, c->spec_ppe, 1), "refine L row");
+    FCSPH_CK(launch_col_ppe_inv(c, FCSPH_F64, c->spec_ppe, r, 1, nullptr, 1, b0, 0, nullptr), "refine resid");
+    const void* rl[1] = {r};
+    FCSPH_CK(launch_col_fwd(c, p, 1, rl, 1, FCSPH_DIRICHLET, c->spec_ppe, 1), "refine fwd");
+    FCSPH_CK(launch_row_ppe(c, p, c->spec_ppe, 0), "refine row");
+    const bool last = it + 1 == iters;
+    FCSPH_CK(launch_col_ppe_inv(c, p, c->spec_ppe, phi64, 1, phi64, 2, nullptr, (neumann_fwd && last) ? 1 : 0,
+                                c->spec_in),
+             "refine add");
+  }
+  return FCSPH_OK;
+}
+
+fcsph_status ppe_solve(fcsph_ctx* c, const void* rhs, void* phi, double* resid_out) {
+  if (!c || !rhs || !phi) return fail(c, FCSPH_EINVAL, "ppe_solve: bad argument");
+  const int p = c->prec.fft_prec;
+  const size_t n = field_elems(c);
+  double* b64 = c->work + 2 * n;
+  double* phi64 = c->work + 3 * n;
+  if (p == FCSPH_F64) {
+    FCSPH_CK(cudaMemcpyAsync(b64, rhs, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream), "ppe rhs copy");
+  } else {
+    FCSPH_CK(cudaMemsetAsync(b64, 0, n * sizeof(double), c->stream), "ppe rhs clear");
+    FCSPH_CK(launch_axpy(c, b64, nullptr, (const float*)rhs, (int)n, 1.0), "ppe rhs widen");
+  }
+  const int iters = p == FCSPH_F32 ? c->prec.ppe_refine_iters : 0;
+  const void* bl[1] = {b64};
+  FCSPH_CK(launch_col_fwd(c, p, 1, bl, 1, FCSPH_DIRICHLET, c->spec_ppe, 1), "ppe fwd");
+  FCSPH_CK(launch_row_ppe(c, p, c->spec_ppe, 0), "ppe row");
+  FCSPH_CK(launch_col_ppe_inv(c, p, c->spec_ppe, iters > 0 ? (void*)phi64 : phi, iters > 0 ? 1 : (p == FCSPH_F64),
+                              phi64, 0, nullptr, 0, nullptr),
+           "ppe inv");
+  if (iters > 0) {
+    fcsph_status st = ppe_refine(c, b64, phi64, iters, 0);
+    if (st != FCSPH_OK) return st;
+    FCSPH_CK(launch_narrow(c, (float*)phi, phi64, (int)n), "ppe phi narrow");
+  }
+  if (resid_out) {
+    // r = b - L phi in FP64; its constant (0,0) part per instance is removed
+    double* r = c->work + 4 * n;
+    const void* pl[1] = {phi64};
+    FCSPH_CK(launch_col_fwd(c, FCSPH_F64, 1, pl, 1, FCSPH_DIRICHLET, c->spec_ppe, 1), "resid fwd");
+    FCSPH_CK(launch_row_ppe(c, FCSPH_F64, c->spec_ppe, 1), "resid row");
+    FCSPH_CK(launch_col_ppe_inv(c, FCSPH_F64, c->spec_ppe, r, 1, nullptr, 1, b64, 0, nullptr), "resid inv");
+    FCSPH_CK(launch_resid_norm(c, r, b64, c->dred), "resid norm");
+    double h2[2];
+    FCSPH_CK(cudaMemcpyAsync(h2, c->dred, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "resid read");
+    FCSPH_CK(cudaStreamSynchronize(c->stream), "resid sync");
+    *resid_out = h2[1] > 0 ? std::sqrt(h2[0] / h2[1]) : std::sqrt(h2[0]);
+  }
+  return FCSPH_OK;
+}
+
+// One substep (Eqs. 5-9).  Precondition: spec_in holds the Dirichlet-FC
+// forward transforms of (u, v).  Postcondition (fwd_next): the same for the
+// new (u, v).
+static fcsph_status substep(fcsph_ctx* c, const fcsph_state* s, const StepDev& sd, int fwd_next) {
+  const int p = c->prec.fft_prec;
+  const size_t n = field_elems(c);
+  double* us = c->work;
+  double* vs = c->work + n;
+  double* b = c->work + 2 * n;
+  const double scale = 1.0 / ((double)c->gd.mx * c->gd.my);
+  RowOps mom = ops_none();
+  mom.nin = 2;
+  mom.nout = 6;
+  const int opl[3] = {SYM_DX, SYM_DY, SYM_LAP};
+  for (int o = 0; o < 6; ++o) {
+    mom.nterm[o] = 1;
+    mom.field[o][0] = o / 3;
+    mom.op[o][0] = opl[o % 3];
+  }
+  FCSPH_CK(launch_row_sym(c, p, c->spec_in, c->spec_out, mom, scale, FCSPH_DIRICHLET, FCSPH_PROF_ROW_MOM), "step mom row");
+  FCSPH_CK(launch_step_mom(c, sd, c->spec_out, s->u, s->v, s->fu, s->fv, us, vs, c->spec_in), "step mom col");
+  RowOps dv = ops_none();
+  dv.nin = 2;
+  dv.nout = 1;
+  dv.nterm[0] = 2;
+  dv.field[0][0] = 0;
+  dv.op[0][0] = SYM_DX;
+  dv.field[0][1] = 1;
+  dv.op[0][1] = SYM_DY;
+  FCSPH_CK(launch_row_sym(c, p, c->spec_in, c->spec_out, dv, scale, FCSPH_DIRICHLET, FCSPH_PROF_ROW_DIV), "step div row");
+  FCSPH_CK(launch_step_div(c, sd, c->spec_out, b, c->spec_ppe), "step div col");
+  // PPE: the DCT-y forward of b is already in spec_ppe (fused above)
+  const int iters = p == FCSPH_F32 ? c->prec.ppe_refine_iters : 0;
+  FCSPH_CK(launch_row_ppe(c, p, c->spec_ppe, 0), "step ppe row");
+  FCSPH_CK(launch_col_ppe_inv(c, p, c->spec_ppe, s->p, 1, s->p, 0, nullptr, iters == 0 ? 1 : 0, c->spec_in),
+           "step ppe col");
+  if (iters > 0) {
+    fcsph_status st = ppe_refine(c, b, s->p, iters, 1);
+    if (st != FCSPH_OK) return st;
+  }
+  RowOps gr = ops_none();
+  gr.nin = 1;
+  gr.nout = 2;
+  gr.nterm[0] = gr.nterm[1] = 1;
+  gr.op[0][0] = SYM_DX;
+  gr.op[1][0] = SYM_DY;
+  FCSPH_CK(launch_row_sym(c, p, c->spec_in, c->spec_out, gr, scale, FCSPH_NEUMANN, FCSPH_PROF_ROW_GRAD), "step grad row");
+  FCSPH_CK(launch_step_corr(c, sd, c->spec_out, us, vs, s->u, s->v, fwd_next ? c->spec_in : nullptr), "step corr col");
+  return FCSPH_OK;
+}
+
+static fcsph_status one_step(fcsph_ctx* c, const fcsph_state* s, const fcsph_step_params* prm) {
+  static const double A3[3] = {8.0 / 15.0, 2.0 / 15.0, 1.0 / 3.0};
+  static const double G3[3] = {8.0 / 15.0, 5.0 / 12.0, 3.0 / 4.0};
+  static const double Z3[3] = {0.0, -17.0 / 60.0, -5.0 / 12.0};
+  const int nsub = prm->scheme == FCSPH_SCHEME_RK3 ? 3 : 1;
+  for (int k = 0; k < nsub; ++k) {
+    StepDev sd;
+    sd.nu = prm->nu;
+    sd.rho = prm->rho;
+    sd.dt = prm->dt;
+    sd.fx = prm->force_x;
+    sd.fy = prm->force_y;
+    sd.u_bottom = prm->u_bottom;
+    sd.u_top = prm->u_top;
+    if (nsub == 3) {
+      sd.a = A3[k];
+      sd.g = G3[k];
+      sd.z = Z3[k];
+    } else {
+      sd.a = 1.0;
+      sd.g = 1.0;
+      sd.z = 0.0;
+    }
+    fcsph_status st = substep(c, s, sd, 1);
+    if (st != FCSPH_OK) return st;
+  }
+  return FCSPH_OK;
+}
+
+fcsph_status isph_step(fcsph_ctx* c, const fcsph_state* s, int nsteps, const fcsph_step_params* prm) {
+  if (!c || !s || !prm || nsteps < 0) return fail(c, FCSPH_EINVAL, "isph_step: bad argument");
+  if (!s->u || !s->v || !s->p || !s->fu || !s->fv) return fail(c, FCSPH_EINVAL, "isph_step: null state pointer");
+  if (prm->scheme != FCSPH_SCHEME_FOP && prm->scheme != FCSPH_SCHEME_RK3)
+    return fail(c, FCSPH_EINVAL, "isph_step: bad scheme");
+  if (!(prm->dt > 0) || !(prm->rho > 0) || !(prm->nu >= 0)) return fail(c, FCSPH_EINVAL, "isph_step: need dt, rho > 0, nu >= 0");
+  if (nsteps == 0) return FCSPH_OK;
+  const void* uv[2] = {s->u, s->v};
+  FCSPH_CK(launch_col_fwd(c, c->prec.fft_prec, 2, uv, 1, FCSPH_DIRICHLET, c->spec_in, 0), "step initial fwd");
+  if (!prm->use_graph) {
+    for (int it = 0; it < nsteps; ++it) {
+      fcsph_status st = one_step(c, s, prm);
+      if (st != FCSPH_OK) return st;
+    }
+    return FCSPH_OK;
+  }
+  std::vector<double> key = {(double)(uintptr_t)s->u, (double)(uintptr_t)s->v, (double)(uintptr_t)s->p,
+                             (double)(uintptr_t)s->fu, (double)(uintptr_t)s->fv, prm->nu, prm->rho, prm->dt,
+                             prm->force_x, prm->force_y, prm->u_bottom, prm->u_top, (double)prm->scheme};
+  if (!c->gexec || key != c->graph_key) {
+    if (c->gexec) {
+      cudaGraphExecDestroy(c->gexec);
+      c->gexec = nullptr;
+    }
+    cudaStream_t user = c->stream;
+    const int prof = c->prof_on;
+    c->prof_on = 0;
+    c->stream = c->cap_stream;
+    FCSPH_CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeRelaxed), "begin capture");
+    const long long before = c->launches;
+    fcsph_status st = one_step(c, s, prm);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
+    c->stream = user;
+    c->prof_on = prof;
+    c->graph_kernels = c->launches - before;
+    c->launches = before;  // captured launches are counted at replay
+    if (st != FCSPH_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "end capture");
+    e = cudaGraphInstantiate(&c->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(c, e, "graph instantiate");
+    c->graph_key = key;
+  }
+  for (int it = 0; it < nsteps; ++it) FCSPH_CK(cudaGraphLaunch(c->gexec, c->stream), "graph launch");
+  c->launches += (long long)nsteps * c->graph_kernels;
+  return FCSPH_OK;
+}
+
+fcsph_status fcsph_sync(fcsph_ctx* c) {
+  if (!c) return fail(nullptr, FCSPH_EINVAL, "fcsph_sync: null context");
+  FCSPH_CK(cudaStreamSynchronize(c->stream), "sync");
+  int st = 0;
+  FCSPH_CK(cudaMemcpy(&st, c->dstatus, sizeof(int), cudaMemcpyDeviceToHost), "status read");
+  if (st & 1) {
+    cudaMemset(c->dstatus, 0, sizeof(int));
+    return fail(c, FCSPH_ENONFINITE, "non-finite value in the time-step state");
+  }
+  return FCSPH_OK;
+}
+
+fcsph_status fcsph_dft(int n, int nlines, int dir, int prec, const void* in, void* out, void* stream) {
+  if (n < 1 || n > 65536 || nlines < 0 || (dir != -1 && dir != 1) || (prec != FCSPH_F64 && prec != FCSPH_F32) || !in || !out)
+    return fail(nullptr, FCSPH_EINVAL, "fcsph_dft: bad argument");
+  if (nlines == 0) return FCSPH_OK;
+  fcsph_ctx tmp;  // only for error reporting inside helpers
+  fcsph_ctx* c = &tmp;
+  Pool pool;
+  std::vector<Fill> fills;
+  FftPlan P = plan_for(n, &pool, &fills);
+  double2* d64 = nullptr;
+  float2* d32 = nullptr;
+  cudaStream_t st = (cudaStream_t)stream;
+  fcsph_status s = upload_pool(c, pool, fills, &d64, &d32, st);
+  if (s != FCSPH_OK) {
+    cudaFree(d64);
+    cudaFree(d32);
+    return fail(nullptr, s, c->err);
+  }
+  cudaError_t e = launch_dft_lines(n, nlines, dir, prec, in, out, st, P, prec == FCSPH_F64 ? (const void*)d64 : (const void*)d32);
+  cudaError_t e2 = cudaStreamSynchronize(st);
+  cudaFree(d64);
+  cudaFree(d32);
+  if (e != cudaSuccess) return fail(nullptr, FCSPH_ECUDA, std::string("fcsph_dft: ") + cudaGetErrorString(e));
+  if (e2 != cudaSuccess) return fail(nullptr, FCSPH_ECUDA, std::string("fcsph_dft: ") + cudaGetErrorString(e2));
+  return FCSPH_OK;
+}
+
+long long fcsph_launch_count(const fcsph_ctx* c) { return c ? c->launches : -1; }
+
+fcsph_status fcsph_set_profiling(fcsph_ctx* c, int on) {
+  if (!c) return fail(nullptr, FCSPH_EINVAL, "fcsph_set_profiling: null context");
+  c->prof_on = on ? 1 : 0;
+  return FCSPH_OK;
+}
+
+fcsph_status fcsph_get_profile(fcsph_ctx* c, double* ms, long long* cnt, int nk) {
+  if (!c || !ms || !cnt || nk < 1) return fail(c, FCSPH_EINVAL, "fcsph_get_profile: bad argument");
+  FCSPH_CK(cudaStreamSynchronize(c->stream), "profile sync");
+  for (auto& p : c->pending) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, p.a, p.b) == cudaSuccess) {
+      c->prof_ms[p.kind] += t;
+      c->prof_n[p.kind] += 1;
+    }
+    c->ev_free.push_back(p.a);
+    c->ev_free.push_back(p.b);
+  }
+  c->pending.clear();
+  for (int k = 0; k < nk && k < FCSPH_PROF_KINDS; ++k) {
+    ms[k] = c->prof_ms[k];
+    cnt[k] = c->prof_n[k];
+    c->prof_ms[k] = 0;
+    c->prof_n[k] = 0;
+  }
+  return FCSPH_OK;
+}
+
+fcsph_status fcsph_last_error(const fcsph_ctx* c, char* buf, size_t n) {
+  if (!buf || n == 0) return FCSPH_EINVAL;
+  std::string s;
+  if (c) {
+    s = c->err;
+  } else {
+    std::lock_guard<std::mutex> lk(g_err_mu);
+    s = g_err;
+  }
+  snprintf(buf, n, "%s", s.c_str());
+  return FCSPH_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,157 @@
+// Internal types shared by the host table/plan builder, the C ABI layer and
+// the CUDA kernels.  Not part of the public ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/fcsph.h"
+
+namespace fcsph {
+
+constexpr int kMaxStages = 20;
+// Largest prime factor handled by a direct Stockham stage; lengths with a
+// larger prime factor go through Bluestein's chirp-z convolution.
+constexpr int kMaxDirectPrime = 31;
+
+// One Stockham decomposition n = radix[0] * radix[1] * ...; `tw` is the offset
+// (in complex elements) of the n roots exp(-2 pi i e / n), e < n, in the pool.
+struct Plan1 {
+  int n = 0;
+  int nst = 0;
+  int tw = 0;
+  int radix[kMaxStages] = {0};
+};
+
+// A length-n complex DFT: direct (bs = 0, `base` holds the stages) or
+// Bluestein (bs = 1: base.n = n; `sub` is the smooth length-m plan; `chirp`
+// holds exp(i pi j^2 / n), j < n; `bhat` holds FFT_m(b)/m of the chirp filter).
+struct FftPlan {
+  Plan1 base;
+  int bs = 0;
+  Plan1 sub;
+  int chirp = 0;
+  int bhat = 0;
+  int line_len() const { return bs ? sub.n : base.n; }  // smem line length
+};
+
+// Host-side twiddle/chirp pool (FP64 master, FP32 copy made at upload).
+struct Pool {
+  std::vector<double> re, im;
+  int add(const std::vector<double>& r, const std::vector<double>& i) {
+    int off = (int)re.size();
+    re.insert(re.end(), r.begin(), r.end());
+    im.insert(im.end(), i.begin(), i.end());
+    return off;
+  }
+};
+
+// Host builders (fcsph_tables.cpp).
+bool factor_direct(int n, Plan1* p);
+int smooth_at_least(int n);
+// Builds the plan; Bluestein filters that need an FFT are left for the caller
+// (bhat_src gets the length-m filter b in natural order, zero-padded).
+FftPlan make_plan(int n, Pool* pool, std::vector<double>* bhat_src_re, std::vector<double>* bhat_src_im);
+int fc_table_build(const fcsph_fc* fc, int bc, std::vector<double>* E, std::string* err);
+
+}  // namespace fcsph
+
+// Operator descriptors for the spectral row pass: output o is
+// sum_{t < nterm[o]} symbol(op[o][t]) * spectrum(field[o][t]).
+enum { SYM_W = 0, SYM_DX = 1, SYM_DY = 2, SYM_LAP = 3 };
+struct RowOps {
+  int nin;               // input spectra per instance
+  int nout;              // output spectra per instance
+  int nterm[6];
+  int field[6][2];
+  int op[6][2];
+};
+
+// Everything a kernel needs about the grid and the method's constants.
+struct GridDev {
+  int nx, ny, batch, x_walls;
+  int mx, my, hy;        // extended lengths, y half-spectrum rows
+  int n_match, n_cont;
+  int rows;              // spectrum rows allocated per field (max(hy, ny))
+  double dx, dy, lx, ly, h;
+  int family;
+};
+
+struct StepDev {
+  double nu, rho, dt, fx, fy, u_bottom, u_top;
+  double a, g, z;        // substep coefficients
+};
+
+struct fcsph_ctx {
+  fcsph_grid grid;
+  fcsph_fc fc;
+  fcsph_kernel kern;
+  fcsph_precision prec;
+  GridDev gd;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  fcsph::FftPlan plan_y, plan_x, plan_py, plan_px;  // FC-y, FC/periodic-x, PPE-y (DCT), PPE-x
+  double* dE = nullptr;         // device [2][n_cont][2 n_match] (Dirichlet, Neumann)
+  std::vector<double> hE[2];    // host copies
+  double2* pool64 = nullptr;
+  float2* pool32 = nullptr;
+  void* spec_in = nullptr;      // [batch][2][rows][nx] complex (T)
+  void* spec_out = nullptr;     // [batch][6][rows][nx] complex (T)
+  void* spec_ppe = nullptr;     // [batch][rows][nx] complex (T) scratch for PPE refinement
+  double* work = nullptr;       // 6 real double fields: u*, v*, b, phi_tmp, r, delta
+  void* io_tmp = nullptr;       // scratch for F32 PPE refinement (float fields)
+  double* dred = nullptr;       // reduction scratch
+  int* dstatus = nullptr;       // device status word (bit 0: non-finite state)
+  long long launches = 0;
+  std::string err;
+  // CUDA graph of one isph step, valid for `graph_key`
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<double> graph_key;
+  long long graph_kernels = 0;  // kernels in one replay of the step graph
+  // per-kind event timing (eager launches only)
+  int prof_on = 0;
+  std::vector<cudaEvent_t> ev_free;
+  struct Pending {
+    int kind;
+    cudaEvent_t a, b;
+  };
+  std::vector<Pending> pending;
+  double prof_ms[FCSPH_PROF_KINDS] = {0};
+  long long prof_n[FCSPH_PROF_KINDS] = {0};
+};
+
+// Records an event pair around one launch when profiling is on.
+struct ProfScope {
+  fcsph_ctx* c;
+  int kind;
+  cudaEvent_t b = nullptr;
+  ProfScope(fcsph_ctx* ctx, int k);
+  ~ProfScope();
+};
+
+// Kernel launchers (fcsph_kernels.cu); return cudaGetLastError().
+cudaError_t launch_fc_extend(fcsph_ctx* c, const void* f, void* fext, int bc);
+cudaError_t launch_col_fwd(fcsph_ctx* c, int prec, int nf, const void* const* fields, int fields_double, int bc,
+                           void* spec, int dct);
+cudaError_t launch_row_sym(fcsph_ctx* c, int prec, const void* spec_in, void* spec_out, const RowOps& ops,
+                           double scale, int bc, int kind);
+cudaError_t launch_col_out(fcsph_ctx* c, const void* spec, int nout, void* const* outs);
+cudaError_t launch_row_ppe(fcsph_ctx* c, int prec, void* spec, int apply);
+cudaError_t launch_col_ppe_inv(fcsph_ctx* c, int prec, const void* spec, void* phi, int phi_double, double* phi64,
+                               int mode, const double* rhs, int neumann_fwd, void* spec_fwd);
+cudaError_t launch_step_mom(fcsph_ctx* c, const StepDev& s, const void* spec6, const double* u, const double* v,
+                            double* fu, double* fv, double* us, double* vs, void* spec2);
+cudaError_t launch_step_div(fcsph_ctx* c, const StepDev& s, const void* spec1, double* b, void* spec_dct);
+cudaError_t launch_step_corr(fcsph_ctx* c, const StepDev& s, const void* spec2, const double* us, const double* vs,
+                             double* u, double* v, void* spec_next);
+cudaError_t launch_dft_lines(int n, int nlines, int dir, int prec, const void* in, void* out, cudaStream_t st,
+                             const fcsph::FftPlan& plan, const void* pool);
+// out2[0] = sum over instances of sum (r - instance mean)^2, out2[1] = sum b^2
+cudaError_t launch_resid_norm(fcsph_ctx* c, const double* r, const double* b, double* out2);
+cudaError_t launch_axpy(fcsph_ctx* c, double* y, const double* x, const float* xf, int n, double a);
+cudaError_t launch_sub(fcsph_ctx* c, double* r, const double* b, const double* lb, int n);
+cudaError_t launch_narrow(fcsph_ctx* c, float* y, const double* x, int n);

@@ -1,0 +1,969 @@
+// CUDA kernels of the FC spectral ISPH hot path (sm_103a).
+//
+// Data layout (HBM).  Real fields f[b][i][j] (j = y, contiguous).  Spectra
+// after the y transform are stored transposed, S[b][field][ky][i] (i
+// contiguous), so that the x pass reads whole rows.  The FC-extended grid is
+// never materialised in HBM on the hot path: the continuation is computed in
+// shared memory inside the transform kernels.
+//
+// Column kernels (y direction) handle 2*Pp adjacent columns of one instance:
+// two real columns are packed into one complex line (a + i b), transformed
+// together, and separated with the Hermitian split
+//   A_k = (Z_k + conj Z_{-k}) / 2,  B_k = (Z_k - conj Z_{-k}) / (2i).
+// Row kernels (x direction) handle Rr spectrum rows of one instance.
+#include <cstdio>
+#include <cstring>
+
+#include "fcsph_fft.cuh"
+#include "fcsph_internal.h"
+
+using namespace fcsph;
+
+namespace {
+
+constexpr int kThreads = 256;
+
+template <typename T> struct PoolOf;
+template <> struct PoolOf<double> { static const double2* get(const fcsph_ctx* c) { return c->pool64; } };
+template <> struct PoolOf<float> { static const float2* get(const fcsph_ctx* c) { return c->pool32; } };
+
+__device__ __forceinline__ size_t fidx(const GridDev& g, int b, int i, int j) {
+  return ((size_t)b * g.nx + i) * g.ny + j;
+}
+
+// ---------------------------------------------------------------------------
+// Compensated dot product for the FC continuation sum_m E[m] b[m]: the table
+// entries reach ~1e4 while the result is O(|b|), so each product is split
+// exactly (p + e = a*b via fma) and the terms are added with TwoSum; the
+// result is accurate to a few ulps of the result instead of ulps of the terms.
+struct Dot2 {
+  double s = 0.0, c = 0.0;
+  __device__ __forceinline__ void add(double a, double b) {
+    const double p = a * b;
+    const double e = fma(a, b, -p);
+    const double t = s + p;
+    const double bp = t - s;
+    c += (s - (t - bp)) + (p - bp) + e;
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return s + c; }
+};
+
+// ---------------------------------------------------------------------------
+// Forward transform of packed column pairs held in shared memory.
+// lines: Pp lines of stride ls, line p has column i0+2p in .x and i0+2p+1 in
+// .y for j < ny.  dct = 0: FC-extend to my with table E ([C][2d], FP64
+// accumulation) and FFT (length my); dct = 1: even extension to 2(ny-1) and
+// FFT (DCT-I, Eq. 31).  Stores the half spectrum (or the ny real DCT
+// coefficients as (c, 0)) into spec[ky][i] for this instance/field.
+template <typename T>
+__device__ void col_forward_store(typename CT<T>::t* lines, typename CT<T>::t* scratch, int Pp, int ls,
+                                  const GridDev& g, int i0, const double* __restrict__ E, const FftPlan& P,
+                                  const typename CT<T>::t* __restrict__ pool, int dct,
+                                  typename CT<T>::t* __restrict__ spec) {
+  typedef typename CT<T>::t V;
+  const int ny = g.ny;
+  if (!dct) {
+    const int C = g.n_cont, d = g.n_match;
+    for (int e = threadIdx.x; e < Pp * C; e += blockDim.x) {
+      const int p = e / C, c = e - (e / C) * C;
+      const V* L = lines + (size_t)p * ls;
+      Dot2 ax, ay;
+      const double* Er = E + c * 2 * d;
+      for (int m = 0; m < d; ++m) {
+        const V vr = L[ny - d + m];
+        const V vl = L[m];
+        ax.add(Er[m], (double)vr.x);
+        ax.add(Er[d + m], (double)vl.x);
+        ay.add(Er[m], (double)vr.y);
+        ay.add(Er[d + m], (double)vl.y);
+      }
+      lines[(size_t)p * ls + ny + c] = mk<V>(ax.value(), ay.value());
+    }
+  } else {
+    const int M = 2 * (ny - 1);
+    for (int e = threadIdx.x; e < Pp * (ny - 2); e += blockDim.x) {
+      const int p = e / (ny - 2), jj = 1 + e - (e / (ny - 2)) * (ny - 2);
+      lines[(size_t)p * ls + M - jj] = lines[(size_t)p * ls + jj];
+    }
+  }
+  __syncthreads();
+  V* R = fft_any<T, false>(lines, scratch, Pp, ls, P, pool);
+  const int n = P.base.n;
+  const int W = 2 * Pp;
+  const int nk = dct ? ny : g.hy;
+  for (int e = threadIdx.x; e < nk * W; e += blockDim.x) {
+    const int k = e / W, col = e - (e / W) * W;
+    const int i = i0 + col;
+    if (i >= g.nx) continue;
+    const V* L = R + (size_t)(col >> 1) * ls;
+    const V z = L[k];
+    const V zm = L[k == 0 ? 0 : n - k];
+    V out;
+    if (dct) {
+      out = (col & 1) ? mk<V>(0.5 * ((double)z.y + (double)zm.y), 0.0) : mk<V>(0.5 * ((double)z.x + (double)zm.x), 0.0);
+    } else if ((col & 1) == 0) {
+      out = mk<V>(0.5 * ((double)z.x + (double)zm.x), 0.5 * ((double)z.y - (double)zm.y));
+    } else {
+      out = mk<V>(0.5 * ((double)z.y + (double)zm.y), -0.5 * ((double)z.x - (double)zm.x));
+    }
+    spec[(size_t)k * g.nx + i] = out;
+  }
+}
+
+// Gathers nout half spectra (spec + o*fstride, rows ky < hy) of the column
+// pairs into full-length packed lines Z_k = A_k + i B_k and Z_{n-k} =
+// conj(A_k) + i conj(B_k); DC and Nyquist keep only the real parts.
+template <typename T>
+__device__ void col_gather_hermitian(typename CT<T>::t* lines, int Pp, int ls, const GridDev& g, int i0,
+                                     const typename CT<T>::t* __restrict__ spec, size_t fstride, int nout, int n) {
+  typedef typename CT<T>::t V;
+  const int hy = g.hy;
+  for (int e = threadIdx.x; e < nout * hy * Pp; e += blockDim.x) {
+    const int o = e / (hy * Pp);
+    const int r = e - o * hy * Pp;
+    const int k = r / Pp, p = r - (r / Pp) * Pp;
+    const int ia = i0 + 2 * p, ib = ia + 1;
+    const V* S = spec + o * fstride + (size_t)k * g.nx;
+    V A = mk<V>(0.0, 0.0), B = mk<V>(0.0, 0.0);
+    if (ia < g.nx) A = S[ia];
+    if (ib < g.nx) B = S[ib];
+    V* L = lines + ((size_t)o * Pp + p) * ls;
+    const bool self = (k == 0) || (2 * k == n);
+    if (self) {
+      L[k] = mk<V>(A.x, B.x);
+    } else {
+      L[k] = mk<V>((double)A.x - (double)B.y, (double)A.y + (double)B.x);
+      L[n - k] = mk<V>((double)A.x + (double)B.y, (double)B.x - (double)A.y);
+    }
+  }
+}
+
+// Packed DCT-I coefficient pairs (real parts of spec rows l < ny) into lines.
+template <typename T>
+__device__ void col_gather_dct(typename CT<T>::t* lines, int Pp, int ls, const GridDev& g, int i0,
+                               const typename CT<T>::t* __restrict__ spec) {
+  typedef typename CT<T>::t V;
+  const int ny = g.ny, M = 2 * (ny - 1);
+  for (int e = threadIdx.x; e < ny * Pp; e += blockDim.x) {
+    const int l = e / Pp, p = e - (e / Pp) * Pp;
+    const int ia = i0 + 2 * p, ib = ia + 1;
+    const V* S = spec + (size_t)l * g.nx;
+    const double a = ia < g.nx ? (double)S[ia].x : 0.0;
+    const double b = ib < g.nx ? (double)S[ib].x : 0.0;
+    V* L = lines + (size_t)p * ls;
+    L[l] = mk<V>(a, b);
+    if (l >= 1 && l <= ny - 2) L[M - l] = mk<V>(a, b);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Column forward: load nf real fields, FC (or DCT) + FFT, store spectra.
+template <typename T, typename U>
+__global__ void __launch_bounds__(kThreads) k_col_fwd(GridDev g, const U* __restrict__ f0, const U* __restrict__ f1,
+                                                      const double* __restrict__ E, FftPlan P,
+                                                      const typename CT<T>::t* __restrict__ pool, int dct,
+                                                      typename CT<T>::t* __restrict__ spec, size_t fstride,
+                                                      size_t bstride, int Pp, int ls) {
+  typedef typename CT<T>::t V;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* lines = reinterpret_cast<V*>(smem_raw);
+  V* scratch = lines + (size_t)Pp * ls;
+  const int b = blockIdx.z, f = blockIdx.y;
+  const int i0 = blockIdx.x * 2 * Pp;
+  const U* src = f == 0 ? f0 : f1;
+  const int W = 2 * Pp;
+  const int ny = g.ny;
+  const size_t base = ((size_t)b * g.nx + i0) * ny;
+  for (int e = threadIdx.x; e < W * ny; e += blockDim.x) {
+    const int col = e / ny, j = e - (e / ny) * ny;
+    const double v = (i0 + col < g.nx) ? (double)src[base + e] : 0.0;
+    T* L = reinterpret_cast<T*>(lines + (size_t)(col >> 1) * ls + j);
+    L[col & 1] = (T)v;
+  }
+  __syncthreads();
+  col_forward_store<T>(lines, scratch, Pp, ls, g, i0, E, P, pool, dct, spec + b * bstride + f * fstride);
+}
+
+// ---------------------------------------------------------------------------
+// Symbols (Eq. 16 reading): W_hat(s) = e^{-s} sum_{m<n} s^m/m!, s = |k|^2 h^2/4;
+// DX = i kx W_hat, DY = i ky W_hat (zero on the own-axis Nyquist line),
+// LAP = -|k|^2 W_hat, W = W_hat.  Returned as (re, im) in the compute type.
+template <typename T>
+__device__ __forceinline__ typename CT<T>::t symbol(int op, T kx, T ky, bool nyq_x, bool nyq_y, T What) {
+  typedef typename CT<T>::t V;
+  switch (op) {
+    case SYM_W: return mk<V>(What, 0.0);
+    case SYM_DX: return mk<V>(0.0, nyq_x ? (T)0 : kx * What);
+    case SYM_DY: return mk<V>(0.0, nyq_y ? (T)0 : ky * What);
+    default: return mk<V>(-(kx * kx + ky * ky) * What, 0.0);
+  }
+}
+
+template <typename T> __device__ __forceinline__ T kernel_hat(int family, T s) {
+  T acc = 1, term = 1;
+  for (int m = 1; m < family; ++m) {
+    term = term * s / (T)m;
+    acc += term;
+  }
+  return exp(-s) * acc;
+}
+
+// Row pass: for Rr rows ky of one instance: load nin input rows, FC-extend
+// in x (walled x), FFT (length mx), form each output sum_t S_t * F_t times
+// `scale`, inverse FFT, truncate to nx, store.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_row_sym(GridDev g, const typename CT<T>::t* __restrict__ sp_in,
+                                                      typename CT<T>::t* __restrict__ sp_out, size_t fstride_in,
+                                                      size_t bstride_in, size_t fstride_out, size_t bstride_out,
+                                                      RowOps ops, const double* __restrict__ E, FftPlan P,
+                                                      const typename CT<T>::t* __restrict__ pool, double scale,
+                                                      int Rr, int ls) {
+  typedef typename CT<T>::t V;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nin = ops.nin, nout = ops.nout;
+  V* A = reinterpret_cast<V*>(smem_raw);
+  V* B = A + (size_t)nin * Rr * ls;
+  V* Cq = B + (size_t)nin * Rr * ls;
+  V* D = Cq + (size_t)nout * Rr * ls;
+  const int b = blockIdx.y;
+  const int ky0 = blockIdx.x * Rr;
+  const int nx = g.nx, mx = g.mx;
+  for (int e = threadIdx.x; e < nin * Rr * nx; e += blockDim.x) {
+    const int line = e / nx, i = e - (e / nx) * nx;
+    const int f = line / Rr, r = line - (line / Rr) * Rr;
+    const int ky = ky0 + r;
+    V v = mk<V>(0.0, 0.0);
+    if (ky < g.hy) v = sp_in[b * bstride_in + f * fstride_in + (size_t)ky * nx + i];
+    A[(size_t)line * ls + i] = v;
+  }
+  __syncthreads();
+  if (g.x_walls) {
+    const int C = g.n_cont, d = g.n_match;
+    for (int e = threadIdx.x; e < nin * Rr * C; e += blockDim.x) {
+      const int line = e / C, c = e - (e / C) * C;
+      const V* L = A + (size_t)line * ls;
+      const double* Er = E + c * 2 * d;
+      Dot2 ax, ay;
+      for (int m = 0; m < d; ++m) {
+        const V vr = L[nx - d + m];
+        const V vl = L[m];
+        ax.add(Er[m], (double)vr.x);
+        ax.add(Er[d + m], (double)vl.x);
+        ay.add(Er[m], (double)vr.y);
+        ay.add(Er[d + m], (double)vl.y);
+      }
+      A[(size_t)line * ls + nx + c] = mk<V>(ax.value(), ay.value());
+    }
+    __syncthreads();
+  }
+  V* X = fft_any<T, false>(A, B, nin * Rr, ls, P, pool);
+  const T hh = (T)(g.h * g.h * 0.25);
+  const T ckx = (T)(2.0 * 3.14159265358979323846 / (mx * g.dx));
+  const T cky = (T)(2.0 * 3.14159265358979323846 / (g.my * g.dy));
+  for (int e = threadIdx.x; e < Rr * mx; e += blockDim.x) {
+    const int r = e / mx, kxi = e - (e / mx) * mx;
+    const int ky = ky0 + r;
+    const int kappa = (2 * kxi <= mx) ? kxi : kxi - mx;
+    const T kx = ckx * (T)kappa, kyw = cky * (T)ky;
+    const bool nyq_x = (mx % 2 == 0) && (2 * kxi == mx);
+    const bool nyq_y = (g.my % 2 == 0) && (2 * ky == g.my);
+    const T What = kernel_hat<T>(g.family, (kx * kx + kyw * kyw) * hh);
+    for (int o = 0; o < nout; ++o) {
+      V acc = mk<V>(0.0, 0.0);
+      for (int t = 0; t < ops.nterm[o]; ++t) {
+        const V s = symbol<T>(ops.op[o][t], kx, kyw, nyq_x, nyq_y, What);
+        acc = cadd(acc, cmul(s, X[((size_t)ops.field[o][t] * Rr + r) * ls + kxi]));
+      }
+      Cq[((size_t)o * Rr + r) * ls + kxi] = cscale(acc, (T)scale);
+    }
+  }
+  __syncthreads();
+  V* Y = fft_any<T, true>(Cq, D, nout * Rr, ls, P, pool);
+  for (int e = threadIdx.x; e < nout * Rr * nx; e += blockDim.x) {
+    const int line = e / nx, i = e - (e / nx) * nx;
+    const int o = line / Rr, r = line - (line / Rr) * Rr;
+    const int ky = ky0 + r;
+    if (ky < g.hy) sp_out[b * bstride_out + o * fstride_out + (size_t)ky * nx + i] = Y[(size_t)line * ls + i];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// PPE row pass (Eqs. 31-33): rows l < ny hold DCT-I-in-y coefficients.  x
+// periodic: FFT (length nx); walled x: DCT-I via FFT of the even extension
+// (length 2(nx-1)).  Multiply by -1/(lam_k^2 + lam_l^2) (apply = 0, (0,0) -> 0),
+// by -(lam_k^2 + lam_l^2) (apply = 1), or by 1 except 0 on the (0,0) mode
+// (apply = 2, removes the constant mode), times the inverse-transform scales,
+// transform back, store.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_row_ppe(GridDev g, typename CT<T>::t* __restrict__ spec,
+                                                      size_t bstride, FftPlan P,
+                                                      const typename CT<T>::t* __restrict__ pool, int apply, int Rr,
+                                                      int ls) {
+  typedef typename CT<T>::t V;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* A = reinterpret_cast<V*>(smem_raw);
+  V* B = A + (size_t)Rr * ls;
+  const int b = blockIdx.y;
+  const int l0 = blockIdx.x * Rr;
+  const int nx = g.nx, ny = g.ny;
+  const int n = P.base.n;  // nx or 2(nx-1)
+  for (int e = threadIdx.x; e < Rr * nx; e += blockDim.x) {
+    const int r = e / nx, i = e - (e / nx) * nx;
+    const int l = l0 + r;
+    V v = mk<V>(0.0, 0.0);
+    if (l < ny) v = spec[b * bstride + (size_t)l * nx + i];
+    A[(size_t)r * ls + i] = v;
+    if (g.x_walls && i >= 1 && i <= nx - 2) A[(size_t)r * ls + n - i] = v;
+  }
+  __syncthreads();
+  V* X = fft_any<T, false>(A, B, Rr, ls, P, pool);
+  V* O = (X == A) ? B : A;
+  const double pi = 3.14159265358979323846;
+  const double norm = 1.0 / ((double)n * 2.0 * (ny - 1));
+  const int nk = g.x_walls ? nx : n;
+  for (int e = threadIdx.x; e < Rr * nk; e += blockDim.x) {
+    const int r = e / nk, k = e - (e / nk) * nk;
+    const int l = l0 + r;
+    double lk;
+    if (g.x_walls) {
+      lk = pi * k / g.lx;
+    } else {
+      const int kappa = (2 * k <= n) ? k : k - n;
+      lk = 2.0 * pi * kappa / g.lx;
+    }
+    const double ll = pi * l / g.ly;
+    const double den = lk * lk + ll * ll;
+    double f;
+    if (apply == 1)
+      f = -den * norm;
+    else if (apply == 2)
+      f = (k == 0 && l == 0) ? 0.0 : norm;
+    else
+      f = (k == 0 && l == 0) ? 0.0 : -norm / den;
+    const V x = X[(size_t)r * ls + k];
+    const V y = mk<V>((double)x.x * f, (double)x.y * f);
+    if (g.x_walls) {
+      O[(size_t)r * ls + k] = y;
+      if (k >= 1 && k <= nx - 2) O[(size_t)r * ls + n - k] = y;
+    } else {
+      X[(size_t)r * ls + k] = y;
+    }
+  }
+  __syncthreads();
+  V* Y;
+  if (g.x_walls)
+    Y = fft_any<T, false>(O, X, Rr, ls, P, pool);  // DCT-I is its own inverse up to the folded scale
+  else
+    Y = fft_any<T, true>(X, O, Rr, ls, P, pool);
+  for (int e = threadIdx.x; e < Rr * nx; e += blockDim.x) {
+    const int r = e / nx, i = e - (e / nx) * nx;
+    const int l = l0 + r;
+    if (l < ny) spec[b * bstride + (size_t)l * nx + i] = Y[(size_t)r * ls + i];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Column inverse with epilogues.
+enum { EPI_OUT = 0, EPI_MOM = 1, EPI_DIV = 2, EPI_CORR = 3, EPI_PPE_SOLVE = 4, EPI_PPE_RESID = 5, EPI_PPE_ADD = 6 };
+
+struct EpiArgs {
+  // EPI_OUT
+  void* outs[6];
+  int out_double;
+  // step state (double)
+  const double* u;
+  const double* v;
+  double* fu;
+  double* fv;
+  double* us;
+  double* vs;
+  double* uo;
+  double* vo;
+  double* bvec;       // DIV: out b; PPE_RESID: in b
+  double* phi;        // PPE_*: out phi / residual / accumulate
+  void* phi_any;      // PPE_SOLVE in the context's I/O type when not double
+  int phi_double;
+  StepDev s;
+  // fused forward: nf fields, table, plan, output spectra, dct
+  int fwd_nf;
+  int fwd_dct;
+  const double* fwdE;
+  FftPlan fwdP;
+  void* fwd_spec;
+  size_t fwd_fstride, fwd_bstride;
+  int* status;
+};
+
+template <typename T, int EPI>
+__global__ void __launch_bounds__(kThreads) k_col_inv(GridDev g, const typename CT<T>::t* __restrict__ spec,
+                                                      size_t fstride, size_t bstride, int nout, int nlines,
+                                                      FftPlan P, const typename CT<T>::t* __restrict__ pool,
+                                                      EpiArgs ea, int Pp, int ls) {
+  typedef typename CT<T>::t V;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* Z = reinterpret_cast<V*>(smem_raw);
+  V* S = Z + (size_t)nlines * Pp * ls;
+  const int b = blockIdx.y;
+  const int i0 = blockIdx.x * 2 * Pp;
+  const int ny = g.ny;
+  const bool ppe = (EPI == EPI_PPE_SOLVE || EPI == EPI_PPE_RESID || EPI == EPI_PPE_ADD);
+  V* R;
+  if (ppe) {
+    col_gather_dct<T>(Z, Pp, ls, g, i0, spec + b * bstride);
+    __syncthreads();
+    R = fft_any<T, false>(Z, S, Pp, ls, P, pool);
+  } else {
+    col_gather_hermitian<T>(Z, Pp, ls, g, i0, spec + b * bstride, fstride, nout, P.base.n);
+    __syncthreads();
+    R = fft_any<T, true>(Z, S, nout * Pp, ls, P, pool);
+  }
+  V* F = (R == Z) ? S : Z;  // free region for the fused forward
+  const int W = 2 * Pp;
+  for (int e = threadIdx.x; e < Pp * ny; e += blockDim.x) {
+    const int p = e / ny, j = e - (e / ny) * ny;
+    double nv[2][2];  // [field][column]
+#pragma unroll
+    for (int w = 0; w < 2; ++w) {
+      const int i = i0 + 2 * p + w;
+      nv[0][w] = nv[1][w] = 0.0;
+      if (i >= g.nx) continue;
+      const size_t id = fidx(g, b, i, j);
+      double val[6];
+      for (int o = 0; o < (ppe ? 1 : nout); ++o) {
+        const V z = R[((size_t)o * Pp + p) * ls + j];
+        val[o] = (double)(w ? z.y : z.x);
+      }
+      if (EPI == EPI_OUT) {
+        for (int o = 0; o < nout; ++o) {
+          if (ea.out_double)
+            reinterpret_cast<double*>(ea.outs[o])[id] = val[o];
+          else
+            reinterpret_cast<float*>(ea.outs[o])[id] = (float)val[o];
+        }
+      } else if (EPI == EPI_MOM) {
+        const double u = ea.u[id], v = ea.v[id];
+        const double Fu = u * val[0] + v * val[1] - ea.s.nu * val[2];
+        const double Fv = u * val[3] + v * val[4] - ea.s.nu * val[5];
+        double us = u + ea.s.dt * (-ea.s.g * Fu - ea.s.z * ea.fu[id] + ea.s.a * ea.s.fx);
+        double vs = v + ea.s.dt * (-ea.s.g * Fv - ea.s.z * ea.fv[id] + ea.s.a * ea.s.fy);
+        if (j == 0) { us = ea.s.u_bottom; vs = 0.0; }
+        if (j == ny - 1) { us = ea.s.u_top; vs = 0.0; }
+        if (g.x_walls && (i == 0 || i == g.nx - 1)) { us = 0.0; vs = 0.0; }
+        ea.fu[id] = Fu;
+        ea.fv[id] = Fv;
+        ea.us[id] = us;
+        ea.vs[id] = vs;
+        if (!isfinite(us) || !isfinite(vs)) atomicOr(ea.status, 1);
+        nv[0][w] = us;
+        nv[1][w] = vs;
+      } else if (EPI == EPI_DIV) {
+        const double bb = ea.s.rho / (ea.s.a * ea.s.dt) * val[0];
+        ea.bvec[id] = bb;
+        nv[0][w] = bb;
+      } else if (EPI == EPI_CORR) {
+        const double c = ea.s.a * ea.s.dt / ea.s.rho;
+        double u = ea.us[id] - c * val[0];
+        double v = ea.vs[id] - c * val[1];
+        if (j == 0) { u = ea.s.u_bottom; v = 0.0; }
+        if (j == ny - 1) { u = ea.s.u_top; v = 0.0; }
+        if (g.x_walls && (i == 0 || i == g.nx - 1)) { u = 0.0; v = 0.0; }
+        ea.uo[id] = u;
+        ea.vo[id] = v;
+        if (!isfinite(u) || !isfinite(v)) atomicOr(ea.status, 1);
+        nv[0][w] = u;
+        nv[1][w] = v;
+      } else if (EPI == EPI_PPE_SOLVE) {
+        if (ea.phi_double)
+          reinterpret_cast<double*>(ea.phi_any)[id] = val[0];
+        else
+          reinterpret_cast<float*>(ea.phi_any)[id] = (float)val[0];
+        if (ea.phi) ea.phi[id] = val[0];
+        nv[0][w] = val[0];
+      } else if (EPI == EPI_PPE_RESID) {
+        ea.phi[id] = ea.bvec[id] - val[0];  // r = b - L phi
+      } else if (EPI == EPI_PPE_ADD) {
+        const double ph = ea.phi[id] + val[0];
+        ea.phi[id] = ph;
+        nv[0][w] = ph;
+      }
+    }
+    if (ea.fwd_nf > 0) {
+      for (int f = 0; f < ea.fwd_nf; ++f) F[(size_t)f * Pp * ls + (size_t)p * ls + j] = mk<V>(nv[f][0], nv[f][1]);
+    }
+  }
+  if (ea.fwd_nf <= 0) return;
+  __syncthreads();
+  for (int f = 0; f < ea.fwd_nf; ++f) {
+    // forward of field f uses the lines of F (f-th block) with R as scratch
+    col_forward_store<T>(F + (size_t)f * Pp * ls, R, Pp, ls, g, i0, ea.fwdE, ea.fwdP, pool, ea.fwd_dct,
+                         reinterpret_cast<V*>(ea.fwd_spec) + b * ea.fwd_bstride + f * ea.fwd_fstride);
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// fc_extend (Eq. 30) as a standalone kernel: y continuation of every column,
+// then x continuation of every extended row (walled x).
+template <typename U>
+__global__ void k_fc_extend_y(GridDev g, const U* __restrict__ f, U* __restrict__ fe, const double* __restrict__ E) {
+  const size_t total = (size_t)g.batch * g.nx * g.my;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+    const int j = (int)(t % g.my);
+    const size_t bi = t / g.my;
+    const int i = (int)(bi % g.nx);
+    const int b = (int)(bi / g.nx);
+    const U* col = f + ((size_t)b * g.nx + i) * g.ny;
+    double v;
+    if (j < g.ny) {
+      v = (double)col[j];
+    } else {
+      const int c = j - g.ny, d = g.n_match;
+      Dot2 acc;
+      for (int m = 0; m < d; ++m) {
+        acc.add(E[c * 2 * d + m], (double)col[g.ny - d + m]);
+        acc.add(E[c * 2 * d + d + m], (double)col[m]);
+      }
+      v = acc.value();
+    }
+    fe[((size_t)b * g.mx + i) * g.my + j] = (U)v;
+  }
+}
+
+template <typename U>
+__global__ void k_fc_extend_x(GridDev g, U* __restrict__ fe, const double* __restrict__ E) {
+  const int C = g.n_cont, d = g.n_match;
+  const size_t total = (size_t)g.batch * C * g.my;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+    const int j = (int)(t % g.my);
+    const size_t bc = t / g.my;
+    const int c = (int)(bc % C);
+    const int b = (int)(bc / C);
+    U* base = fe + (size_t)b * g.mx * g.my;
+    Dot2 acc;
+    for (int m = 0; m < d; ++m) {
+      acc.add(E[c * 2 * d + m], (double)base[(size_t)(g.nx - d + m) * g.my + j]);
+      acc.add(E[c * 2 * d + d + m], (double)base[(size_t)m * g.my + j]);
+    }
+    base[(size_t)(g.nx + c) * g.my + j] = (U)acc.value();
+  }
+}
+
+// Batched DFT of contiguous lines (engine test entry).
+template <typename T, bool INV>
+__global__ void __launch_bounds__(kThreads) k_dft_lines(int n, int nlines, const typename CT<T>::t* __restrict__ in,
+                                                        typename CT<T>::t* __restrict__ out, FftPlan P,
+                                                        const typename CT<T>::t* __restrict__ pool, int L, int ls) {
+  typedef typename CT<T>::t V;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* A = reinterpret_cast<V*>(smem_raw);
+  V* B = A + (size_t)L * ls;
+  const int l0 = blockIdx.x * L;
+  for (int e = threadIdx.x; e < L * n; e += blockDim.x) {
+    const int r = e / n, j = e - (e / n) * n;
+    A[(size_t)r * ls + j] = (l0 + r < nlines) ? in[(size_t)(l0 + r) * n + j] : mk<V>(0.0, 0.0);
+  }
+  __syncthreads();
+  V* Y = fft_any<T, INV>(A, B, L, ls, P, pool);
+  for (int e = threadIdx.x; e < L * n; e += blockDim.x) {
+    const int r = e / n, j = e - (e / n) * n;
+    if (l0 + r < nlines) out[(size_t)(l0 + r) * n + j] = Y[(size_t)r * ls + j];
+  }
+}
+
+// Residual diagnostics, one block per instance: out[0] += sum_b (r - mean_b(r))^2,
+// out[1] += sum_b b^2 (two passes over the instance: mean, then deviations).
+__global__ void k_resid_inst(const double* __restrict__ r, const double* __restrict__ b, size_t n_inst, double* out) {
+  __shared__ double sh[2][kThreads];
+  const double* ri = r + blockIdx.x * n_inst;
+  const double* bi = b + blockIdx.x * n_inst;
+  double s0 = 0.0;
+  for (size_t t = threadIdx.x; t < n_inst; t += blockDim.x) s0 += ri[t];
+  sh[0][threadIdx.x] = s0;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[0][threadIdx.x] += sh[0][threadIdx.x + w];
+    __syncthreads();
+  }
+  const double mean = sh[0][0] / (double)n_inst;
+  __syncthreads();
+  double d2 = 0.0, b2 = 0.0;
+  for (size_t t = threadIdx.x; t < n_inst; t += blockDim.x) {
+    const double d = ri[t] - mean;
+    d2 += d * d;
+    b2 += bi[t] * bi[t];
+  }
+  sh[0][threadIdx.x] = d2;
+  sh[1][threadIdx.x] = b2;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      sh[0][threadIdx.x] += sh[0][threadIdx.x + w];
+      sh[1][threadIdx.x] += sh[1][threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    atomicAdd(out + 0, sh[0][0]);
+    atomicAdd(out + 1, sh[1][0]);
+  }
+}
+
+__global__ void k_axpy(double* __restrict__ y, const double* __restrict__ x, const float* __restrict__ xf, size_t n,
+                       double a) {
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
+    y[t] += a * (x ? x[t] : (double)xf[t]);
+}
+
+__global__ void k_narrow(float* __restrict__ y, const double* __restrict__ x, size_t n) {
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
+    y[t] = (float)x[t];
+}
+
+__global__ void k_sub(double* __restrict__ r, const double* __restrict__ b, const double* __restrict__ lb, size_t n) {
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
+    r[t] = b[t] - lb[t];
+}
+
+// ---------------------------------------------------------------------------
+// Host-side launch helpers.
+
+size_t cbytes(int prec) { return prec == FCSPH_F64 ? sizeof(double2) : sizeof(float2); }
+
+// Largest count (>= 1, <= cap) of units fitting in `budget` bytes.
+int fit_units(size_t per_unit, size_t budget, int cap) {
+  int u = (int)(budget / per_unit);
+  if (u < 1) u = 1;
+  if (u > cap) u = cap;
+  return u;
+}
+
+constexpr size_t kSmemBudget = 96 * 1024;  // per CTA, leaves room for 2 CTAs/SM
+constexpr size_t kSmemMax = 227 * 1024;
+
+template <typename K> cudaError_t set_smem(K kernel, size_t bytes) {
+  if (bytes > kSmemMax) return cudaErrorInvalidValue;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+int col_ls(const fcsph_ctx* c) {
+  int ls = c->plan_y.line_len();
+  if (c->plan_py.line_len() > ls) ls = c->plan_py.line_len();
+  return ls;
+}
+
+}  // namespace
+
+// ===========================================================================
+// Launchers
+
+cudaError_t launch_fc_extend(fcsph_ctx* c, const void* f, void* fext, int bc) {
+  ProfScope ps(c, FCSPH_PROF_OTHER);
+  const double* E = c->dE + (bc == FCSPH_NEUMANN ? 1 : 0) * c->gd.n_cont * 2 * c->gd.n_match;
+  const int blocks = 152 * 8;
+  if (c->prec.fft_prec == FCSPH_F64) {
+    k_fc_extend_y<double><<<blocks, kThreads, 0, c->stream>>>(c->gd, (const double*)f, (double*)fext, E);
+    c->launches++;
+    if (c->gd.x_walls) {
+      k_fc_extend_x<double><<<blocks, kThreads, 0, c->stream>>>(c->gd, (double*)fext, E);
+      c->launches++;
+    }
+  } else {
+    k_fc_extend_y<float><<<blocks, kThreads, 0, c->stream>>>(c->gd, (const float*)f, (float*)fext, E);
+    c->launches++;
+    if (c->gd.x_walls) {
+      k_fc_extend_x<float><<<blocks, kThreads, 0, c->stream>>>(c->gd, (float*)fext, E);
+      c->launches++;
+    }
+  }
+  return cudaGetLastError();
+}
+
+template <typename T, typename U>
+static cudaError_t col_fwd_t(fcsph_ctx* c, int nf, const void* const* fields, int bc, void* spec, int dct) {
+  const GridDev& g = c->gd;
+  const FftPlan& P = dct ? c->plan_py : c->plan_y;
+  const int ls = col_ls(c);
+  const size_t per = 2 * (size_t)ls * sizeof(typename CT<T>::t);
+  const int Pp = fit_units(per, kSmemBudget, (g.nx + 1) / 2);
+  const size_t smem = per * Pp;
+  cudaError_t e = set_smem(k_col_fwd<T, U>, smem);
+  if (e != cudaSuccess) return e;
+  const double* E = c->dE + (bc == FCSPH_NEUMANN ? 1 : 0) * g.n_cont * 2 * g.n_match;
+  dim3 grid((g.nx + 2 * Pp - 1) / (2 * Pp), nf, g.batch);
+  const size_t fstride = (size_t)g.rows * g.nx;
+  const size_t bstride = (dct ? 1 : 2) * fstride;
+  ProfScope ps(c, FCSPH_PROF_COL_FWD);
+  k_col_fwd<T, U><<<grid, kThreads, smem, c->stream>>>(g, (const U*)fields[0], (const U*)(nf > 1 ? fields[1] : fields[0]),
+                                                       E, P, PoolOf<T>::get(c), dct, (typename CT<T>::t*)spec, fstride,
+                                                       bstride, Pp, ls);
+  c->launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_col_fwd(fcsph_ctx* c, int prec, int nf, const void* const* fields, int fields_double, int bc,
+                           void* spec, int dct) {
+  if (prec == FCSPH_F64) {
+    if (!fields_double) return cudaErrorInvalidValue;
+    return col_fwd_t<double, double>(c, nf, fields, bc, spec, dct);
+  }
+  if (fields_double) return col_fwd_t<float, double>(c, nf, fields, bc, spec, dct);
+  return col_fwd_t<float, float>(c, nf, fields, bc, spec, dct);
+}
+
+template <typename T>
+static cudaError_t row_sym_t(fcsph_ctx* c, const void* sp_in, void* sp_out, const RowOps& ops, double scale, int bc,
+                             int kind) {
+  const GridDev& g = c->gd;
+  const int ls = c->plan_x.line_len();
+  const size_t per = (size_t)(2 * ops.nin + 2 * ops.nout) * ls * sizeof(typename CT<T>::t);
+  const int Rr = fit_units(per, kSmemBudget, 8);
+  const size_t smem = per * Rr;
+  cudaError_t e = set_smem(k_row_sym<T>, smem);
+  if (e != cudaSuccess) return e;
+  const double* E = c->dE + (bc == FCSPH_NEUMANN ? 1 : 0) * g.n_cont * 2 * g.n_match;
+  const size_t fs = (size_t)g.rows * g.nx;
+  dim3 grid((g.hy + Rr - 1) / Rr, g.batch);
+  ProfScope ps(c, kind);
+  k_row_sym<T><<<grid, kThreads, smem, c->stream>>>(g, (const typename CT<T>::t*)sp_in, (typename CT<T>::t*)sp_out, fs,
+                                                    2 * fs, fs, 6 * fs, ops, E, c->plan_x, PoolOf<T>::get(c), scale, Rr,
+                                                    ls);
+  c->launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_row_sym(fcsph_ctx* c, int prec, const void* sp_in, void* sp_out, const RowOps& ops, double scale,
+                           int bc, int kind) {
+  if (prec == FCSPH_F64) return row_sym_t<double>(c, sp_in, sp_out, ops, scale, bc, kind);
+  return row_sym_t<float>(c, sp_in, sp_out, ops, scale, bc, kind);
+}
+
+template <typename T>
+static cudaError_t col_inv_common(fcsph_ctx* c, int epi, const void* spec, int nout, EpiArgs& ea) {
+  // nout inverse lines per column pair; the fused forward reuses that space
+  const GridDev& g = c->gd;
+  const int ls = col_ls(c);
+  const int lines = nout > ea.fwd_nf ? nout : (ea.fwd_nf > 0 ? ea.fwd_nf : 1);
+  const size_t per = 2 * (size_t)lines * ls * sizeof(typename CT<T>::t);
+  const int Pp = fit_units(per, kSmemBudget, (g.nx + 1) / 2);
+  const size_t smem = per * Pp;
+  const size_t fs = (size_t)g.rows * g.nx;
+  const size_t bs = (epi >= EPI_PPE_SOLVE ? 1 : 6) * fs;  // spec_ppe or spec_out
+  dim3 grid((g.nx + 2 * Pp - 1) / (2 * Pp), g.batch);
+  const FftPlan& P = epi >= EPI_PPE_SOLVE ? c->plan_py : c->plan_y;
+  const typename CT<T>::t* pool = PoolOf<T>::get(c);
+  ea.status = c->dstatus;
+  static const int kinds[7] = {FCSPH_PROF_COL_OUT, FCSPH_PROF_COL_MOM, FCSPH_PROF_COL_DIV, FCSPH_PROF_COL_CORR,
+                               FCSPH_PROF_COL_PPE, FCSPH_PROF_COL_PPE, FCSPH_PROF_COL_PPE};
+  ProfScope ps(c, kinds[epi]);
+  cudaError_t e = cudaSuccess;
+#define FCSPH_LAUNCH_INV(E_)                                                                                     \
+  case E_:                                                                                                       \
+    e = set_smem(k_col_inv<T, E_>, smem);                                                                        \
+    if (e != cudaSuccess) return e;                                                                              \
+    k_col_inv<T, E_><<<grid, kThreads, smem, c->stream>>>(g, (const typename CT<T>::t*)spec, fs, bs, nout, lines, P, \
+                                                          pool, ea, Pp, ls);                                     \
+    break;
+  switch (epi) {
+    FCSPH_LAUNCH_INV(EPI_OUT)
+    FCSPH_LAUNCH_INV(EPI_MOM)
+    FCSPH_LAUNCH_INV(EPI_DIV)
+    FCSPH_LAUNCH_INV(EPI_CORR)
+    FCSPH_LAUNCH_INV(EPI_PPE_SOLVE)
+    FCSPH_LAUNCH_INV(EPI_PPE_RESID)
+    FCSPH_LAUNCH_INV(EPI_PPE_ADD)
+    default: return cudaErrorInvalidValue;
+  }
+#undef FCSPH_LAUNCH_INV
+  c->launches++;
+  return cudaGetLastError();
+}
+
+static cudaError_t col_inv(fcsph_ctx* c, int prec, int epi, const void* spec, int nout, EpiArgs& ea) {
+  if (prec == FCSPH_F64) return col_inv_common<double>(c, epi, spec, nout, ea);
+  return col_inv_common<float>(c, epi, spec, nout, ea);
+}
+
+static EpiArgs epi_defaults() {
+  EpiArgs ea;
+  memset(&ea, 0, sizeof(ea));
+  return ea;
+}
+
+cudaError_t launch_col_out(fcsph_ctx* c, const void* spec, int nout, void* const* outs) {
+  EpiArgs ea = epi_defaults();
+  for (int o = 0; o < nout; ++o) ea.outs[o] = outs[o];
+  ea.out_double = c->prec.fft_prec == FCSPH_F64;
+  return col_inv(c, c->prec.fft_prec, EPI_OUT, spec, nout, ea);
+}
+
+template <typename T>
+static cudaError_t row_ppe_t(fcsph_ctx* c, void* spec, int apply) {
+  const GridDev& g = c->gd;
+  const int ls = c->plan_px.line_len();
+  const size_t per = 2 * (size_t)ls * sizeof(typename CT<T>::t);
+  const int Rr = fit_units(per, kSmemBudget, 16);
+  const size_t smem = per * Rr;
+  cudaError_t e = set_smem(k_row_ppe<T>, smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((g.ny + Rr - 1) / Rr, g.batch);
+  ProfScope ps(c, FCSPH_PROF_ROW_PPE);
+  k_row_ppe<T><<<grid, kThreads, smem, c->stream>>>(g, (typename CT<T>::t*)spec, (size_t)g.rows * g.nx, c->plan_px,
+                                                    PoolOf<T>::get(c), apply, Rr, ls);
+  c->launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_row_ppe(fcsph_ctx* c, int prec, void* spec, int apply) {
+  if (prec == FCSPH_F64) return row_ppe_t<double>(c, spec, apply);
+  return row_ppe_t<float>(c, spec, apply);
+}
+
+// mode: 0 solve (phi out, optional Neumann-FC forward), 1 residual r = rhs - L phi into `phi`
+// (double), 2 accumulate phi += value (double).
+cudaError_t launch_col_ppe_inv(fcsph_ctx* c, int prec, const void* spec, void* phi, int phi_double, double* phi64,
+                               int mode, const double* rhs, int neumann_fwd, void* spec_fwd) {
+  EpiArgs ea = epi_defaults();
+  int epi = EPI_PPE_SOLVE;
+  if (mode == 0) {
+    ea.phi_any = phi;
+    ea.phi_double = phi_double;
+    ea.phi = phi64;
+  } else if (mode == 1) {
+    epi = EPI_PPE_RESID;
+    ea.phi = (double*)phi;
+    ea.bvec = (double*)rhs;
+  } else {
+    epi = EPI_PPE_ADD;
+    ea.phi = (double*)phi;
+  }
+  if (neumann_fwd) {
+    ea.fwd_nf = 1;
+    ea.fwd_dct = 0;
+    ea.fwdE = c->dE + c->gd.n_cont * 2 * c->gd.n_match;
+    ea.fwdP = c->plan_y;
+    ea.fwd_spec = spec_fwd;
+    ea.fwd_fstride = (size_t)c->gd.rows * c->gd.nx;
+    ea.fwd_bstride = 2 * ea.fwd_fstride;
+  }
+  return col_inv(c, prec, epi, spec, 1, ea);
+}
+
+cudaError_t launch_step_mom(fcsph_ctx* c, const StepDev& s, const void* spec6, const double* u, const double* v,
+                            double* fu, double* fv, double* us, double* vs, void* spec2) {
+  EpiArgs ea = epi_defaults();
+  ea.u = u;
+  ea.v = v;
+  ea.fu = fu;
+  ea.fv = fv;
+  ea.us = us;
+  ea.vs = vs;
+  ea.s = s;
+  ea.fwd_nf = 2;
+  ea.fwd_dct = 0;
+  ea.fwdE = c->dE;
+  ea.fwdP = c->plan_y;
+  ea.fwd_spec = spec2;
+  ea.fwd_fstride = (size_t)c->gd.rows * c->gd.nx;
+  ea.fwd_bstride = 2 * ea.fwd_fstride;
+  return col_inv(c, c->prec.fft_prec, EPI_MOM, spec6, 6, ea);
+}
+
+cudaError_t launch_step_div(fcsph_ctx* c, const StepDev& s, const void* spec1, double* b, void* spec_dct) {
+  EpiArgs ea = epi_defaults();
+  ea.bvec = b;
+  ea.s = s;
+  ea.fwd_nf = 1;
+  ea.fwd_dct = 1;
+  ea.fwdE = c->dE;
+  ea.fwdP = c->plan_py;
+  ea.fwd_spec = spec_dct;
+  ea.fwd_fstride = (size_t)c->gd.rows * c->gd.nx;
+  ea.fwd_bstride = ea.fwd_fstride;
+  return col_inv(c, c->prec.fft_prec, EPI_DIV, spec1, 1, ea);
+}
+
+cudaError_t launch_step_corr(fcsph_ctx* c, const StepDev& s, const void* spec2, const double* us, const double* vs,
+                             double* u, double* v, void* spec_next) {
+  EpiArgs ea = epi_defaults();
+  ea.us = (double*)us;
+  ea.vs = (double*)vs;
+  ea.uo = u;
+  ea.vo = v;
+  ea.s = s;
+  if (spec_next) {
+    ea.fwd_nf = 2;
+    ea.fwd_dct = 0;
+    ea.fwdE = c->dE;
+    ea.fwdP = c->plan_y;
+    ea.fwd_spec = spec_next;
+    ea.fwd_fstride = (size_t)c->gd.rows * c->gd.nx;
+    ea.fwd_bstride = 2 * ea.fwd_fstride;
+  }
+  return col_inv(c, c->prec.fft_prec, EPI_CORR, spec2, 2, ea);
+}
+
+cudaError_t launch_dft_lines(int n, int nlines, int dir, int prec, const void* in, void* out, cudaStream_t st,
+                             const FftPlan& plan, const void* pool) {
+  const int ls = plan.line_len();
+  cudaError_t e;
+  if (prec == FCSPH_F64) {
+    const size_t per = 2 * (size_t)ls * sizeof(double2);
+    const int L = fit_units(per, kSmemBudget, 16);
+    const size_t smem = per * L;
+    const int blocks = (nlines + L - 1) / L;
+    if (dir < 0) {
+      if ((e = set_smem(k_dft_lines<double, false>, smem)) != cudaSuccess) return e;
+      k_dft_lines<double, false><<<blocks, kThreads, smem, st>>>(n, nlines, (const double2*)in, (double2*)out, plan,
+                                                                 (const double2*)pool, L, ls);
+    } else {
+      if ((e = set_smem(k_dft_lines<double, true>, smem)) != cudaSuccess) return e;
+      k_dft_lines<double, true><<<blocks, kThreads, smem, st>>>(n, nlines, (const double2*)in, (double2*)out, plan,
+                                                                (const double2*)pool, L, ls);
+    }
+  } else {
+    const size_t per = 2 * (size_t)ls * sizeof(float2);
+    const int L = fit_units(per, kSmemBudget, 16);
+    const size_t smem = per * L;
+    const int blocks = (nlines + L - 1) / L;
+    if (dir < 0) {
+      if ((e = set_smem(k_dft_lines<float, false>, smem)) != cudaSuccess) return e;
+      k_dft_lines<float, false><<<blocks, kThreads, smem, st>>>(n, nlines, (const float2*)in, (float2*)out, plan,
+                                                                (const float2*)pool, L, ls);
+    } else {
+      if ((e = set_smem(k_dft_lines<float, true>, smem)) != cudaSuccess) return e;
+      k_dft_lines<float, true><<<blocks, kThreads, smem, st>>>(n, nlines, (const float2*)in, (float2*)out, plan,
+                                                               (const float2*)pool, L, ls);
+    }
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_resid_norm(fcsph_ctx* c, const double* r, const double* b, double* out2) {
+  cudaMemsetAsync(out2, 0, 2 * sizeof(double), c->stream);
+  ProfScope ps(c, FCSPH_PROF_OTHER);
+  k_resid_inst<<<c->gd.batch, kThreads, 0, c->stream>>>(r, b, (size_t)c->gd.nx * c->gd.ny, out2);
+  c->launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_axpy(fcsph_ctx* c, double* y, const double* x, const float* xf, int n, double a) {
+  ProfScope ps(c, FCSPH_PROF_OTHER);
+  k_axpy<<<152 * 4, kThreads, 0, c->stream>>>(y, x, xf, (size_t)n, a);
+  c->launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sub(fcsph_ctx* c, double* r, const double* b, const double* lb, int n) {
+  ProfScope ps(c, FCSPH_PROF_OTHER);
+  k_sub<<<152 * 4, kThreads, 0, c->stream>>>(r, b, lb, (size_t)n);
+  c->launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_narrow(fcsph_ctx* c, float* y, const double* x, int n) {
+  ProfScope ps(c, FCSPH_PROF_OTHER);
+  k_narrow<<<152 * 4, kThreads, 0, c->stream>>>(y, x, (size_t)n);
+  c->launches++;
+  return cudaGetLastError();
+}

@@ -1,0 +1,61 @@
+"""CPU checks of the C-ABI library: it loads, exports every entry point that
+include/fcsph.h declares, rejects bad arguments, and its host-side FC table
+builder reproduces the oracle's tables (no GPU needed for these calls)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import fc as ofc
+from tables import gram_golden
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "fcsph.h")).read()
+    return sorted(set(re.findall(r"^(?:fcsph_status|long long)\s+(\w+)\s*\(", src, re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2606_06247_gb300 import build
+    build.build()
+    from paper_2606_06247_gb300 import binding
+    return binding
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert len(names) >= 13
+    for n in names:
+        assert hasattr(lib.lib, n), n
+
+
+@pytest.mark.parametrize("n_cont", [22, 24, 25, 26])
+def test_gram_table_bitwise_equal_to_oracle(lib, n_cont):
+    # both sides solve the same least squares in extended precision and round once
+    np.testing.assert_array_equal(lib.fc_table("gram", 5, n_cont), gram_golden(5, n_cont))
+
+
+@pytest.mark.parametrize("n_cont", [28, 32])
+def test_gram_table_close_to_oracle(lib, n_cont):
+    G = gram_golden(5, n_cont)
+    assert np.abs(lib.fc_table("gram", 5, n_cont) - G).max() < 1e-12 * np.abs(G).max()
+
+
+@pytest.mark.parametrize("m,p,c", [(5, 3, 25), (10, 5, 16), (8, 4, 12)])
+@pytest.mark.parametrize("bc", [0, 1])
+def test_paper_table_matches_oracle(lib, m, p, c, bc):
+    O = ofc.paper_table(m, c, p, bc)
+    assert np.abs(lib.fc_table("paper", m, c, bc, p) - O).max() < 1e-13 * np.abs(O).max()
+
+
+def test_bad_arguments_are_rejected(lib):
+    with pytest.raises(lib.FcsphError) as e:
+        lib.fc_table("gram", 1, 25)
+    assert e.value.status == 1
+    with pytest.raises(lib.FcsphError):
+        lib.fc_table("paper", 5, 25, 0, 5)  # poly_deg must be < n_match

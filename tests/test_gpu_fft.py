@@ -1,0 +1,29 @@
+"""The library's FFT engine (fcsph_dft: Stockham mixed radix + Bluestein)
+against numpy's FFT at every transform length the configurations use."""
+import numpy as np
+import pytest
+
+from gpu_common import binding, torch_cuda
+
+# extended lengths (n + 25), PPE even extensions 2(n-1), smooth variants and small edge cases
+LENGTHS = [1, 2, 3, 4, 5, 7, 8, 11, 16, 31, 37, 64, 89, 90, 96, 126, 150, 153, 254, 256, 280, 281, 510, 512,
+           537, 540, 1022, 1049, 1050, 2046]
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("n", LENGTHS)
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_dft_matches_numpy(n, prec):
+    torch = torch_cuda()
+    b = binding()
+    rng = np.random.default_rng(n)
+    nl = 7
+    x = rng.standard_normal((nl, n)) + 1j * rng.standard_normal((nl, n))
+    dt = torch.complex128 if prec == "f64" else torch.complex64
+    xd = torch.tensor(x, dtype=dt).cuda()
+    for direction in (-1, 1):
+        y = b.fcsph_dft(xd, direction).cpu().numpy()
+        ref = np.fft.fft(x, axis=-1) if direction < 0 else np.fft.ifft(x, axis=-1) * n
+        err = np.linalg.norm(y - ref) / np.linalg.norm(ref)
+        tol = 2e-15 * np.log2(max(n, 2)) * 4 if prec == "f64" else 3e-7 * np.log2(max(n, 2)) * 4
+        assert err < tol, (n, prec, direction, err)
