@@ -153,6 +153,29 @@ fcsph_status fcsph_sync(fcsph_ctx* ctx);
  * (prec FCSPH_F64) or floats (FCSPH_F32); in-place allowed. */
 fcsph_status fcsph_dft(int n, int nlines, int dir, int prec, const void* in, void* out, void* stream);
 
+/* fcsph_dft without any allocation.  For callers that cannot allocate device
+ * memory -- a CUDA graph being captured, an application whose memory pool
+ * owns all device memory, a plugin that must not touch the CUDA allocator --
+ * this variant keeps its scratch (roots of unity, Bluestein chirp and filter)
+ * in one fixed file-scope device array of FCSPH_NOALLOC_SCRATCH_BYTES per
+ * GPU instead of allocating it.  The paper has no counterpart: this is a
+ * deployment convenience, not part of the method.
+ *   Same arguments, layout and results as fcsph_dft (up to rounding of the
+ *   roots, which are computed on the device).
+ *   Limit: the scratch holds 24 bytes per pool entry; the pool has n entries
+ *   when n factors into primes <= 31, else 2m + n (Bluestein, m the smallest
+ *   2^a 3^b 5^c 7^d >= 2n - 1).  Larger n returns FCSPH_EINVAL and queues
+ *   nothing (any direct length n <= 43690 fits; Bluestein lengths up to about
+ *   8000 fit).
+ *   Set-up: the first call on each device looks up the array's device
+ *   address (cudaGetSymbolAddress) with that device current; make that first
+ *   call before any stream capture.
+ *   Sharing: all calls use the same array and every call rewrites the parts
+ *   it reads, so calls whose work overlaps on the GPU race; serialise them.
+ *   The array stays resident on every GPU that loaded the library until exit. */
+#define FCSPH_NOALLOC_SCRATCH_BYTES (1u << 20)
+fcsph_status fcsph_dft_noalloc(int n, int nlines, int dir, int prec, const void* in, void* out, void* stream);
+
 /* Kernel launches this context has queued since creation (for bookkeeping). */
 long long fcsph_launch_count(const fcsph_ctx* ctx);
 

@@ -77,6 +77,7 @@ def _load():
         "isph_step": [P, ctypes.POINTER(fcsph_state), I, ctypes.POINTER(fcsph_step_params)],
         "fcsph_sync": [P],
         "fcsph_dft": [I, I, I, I, P, P, P],
+        "fcsph_dft_noalloc": [I, I, I, I, P, P, P],
         "fcsph_launch_count": [P],
         "fcsph_last_error": [P, ctypes.c_char_p, S],
         "fcsph_set_profiling": [P, I],
@@ -130,6 +131,21 @@ def fcsph_dft(x, direction=-1, stream=None):
     n = x.shape[-1]
     out = torch.empty_like(x)
     _check(lib.fcsph_dft(n, x.numel() // n if n else 0, direction, prec, _ptr(x), _ptr(out), _stream(stream)))
+    return out
+
+
+def fcsph_dft_noalloc(x, out, direction=-1, stream=None):
+    """fcsph_dft into a caller-provided `out`, with no allocation on the library
+    side (scratch in a fixed per-device array; see include/fcsph.h)."""
+    import torch
+    assert x.is_cuda and x.is_complex() and x.is_contiguous() and out.shape == x.shape and out.dtype == x.dtype
+    prec = F64 if x.dtype == torch.complex128 else F32
+    n = x.shape[-1]
+    st = lib.fcsph_dft_noalloc(n, x.numel() // n if n else 0, direction, prec, _ptr(x), _ptr(out), _stream(stream))
+    if st == 1:
+        raise FcsphError(st, f"fcsph_dft_noalloc: length {n} needs more than the fixed scratch of "
+                             "FCSPH_NOALLOC_SCRATCH_BYTES (or bad arguments)")
+    _check(st)
     return out
 
 

@@ -30,7 +30,7 @@ def _cuda_home():
 
 
 def _sources():
-    return [os.path.join(CSRC, f) for f in ("fcsph_tables.cpp", "fcsph_api.cpp", "fcsph_kernels.cu")]
+    return [os.path.join(CSRC, f) for f in ("fcsph_tables.cpp", "fcsph_api.cpp", "fcsph_kernels.cu", "fcsph_noalloc.cu")]
 
 
 def _needs_build():
@@ -65,7 +65,7 @@ def build(force=False, verbose=False):
         if verbose and out:
             print(out)
         if "-Xptxas" in cmd:
-            with open(os.path.join(BUILD, "ptxas_info.txt"), "w") as f:
+            with open(os.path.join(BUILD, os.path.basename(cmd[-3]) + ".ptxas.txt"), "w") as f:
                 f.write(out)
     libs = ["-cudart=static"]
     if platform.machine() == "x86_64":
