@@ -4,10 +4,12 @@
 // reversal): stage s with radix R combines sub-transforms of size Ns into
 // Ns*R.  Butterfly j (< n/R) reads x[j + r n/R], r < R, twiddles input r by
 // w^{r k n/(Ns R)} (k = j mod Ns, w = exp(-2 pi i/n)), does an R-point DFT in
-// registers and writes y[(j/Ns) Ns R + k + q Ns], q < R.  Radices 2 and 4 are
-// multiplication-free; 3, 5, 7 use table roots; larger primes (up to
-// kMaxDirectPrime) use one thread per output.  Lengths with a larger prime
-// factor use Bluestein: X = conj(c) . IFFT_m( FFT_m(x conj(c)) . FFT_m(b) / m ),
+// registers and writes y[(j/Ns) Ns R + k + q Ns], q < R.  The divisions by
+// the per-stage constants n/R and Ns use precomputed multiply-shift
+// reciprocals.  Radices 2, 3, 4, 5, 7, 8 and 9 have dedicated butterflies
+// built from the constant roots of unity; other primes up to kMaxDirectPrime
+// use one thread per output.  Lengths with a larger prime factor use
+// Bluestein: X = conj(c) . IFFT_m( FFT_m(x conj(c)) . FFT_m(b) / m ),
 // c_j = exp(i pi j^2 / n), m smooth >= 2n - 1.
 #pragma once
 
@@ -57,6 +59,10 @@ template <typename V> __device__ __forceinline__ V mk(double x, double y) {
   r.y = y;
   return r;
 }
+// -i * a (forward sign) or +i * a (inverse)
+template <typename V, bool INV> __device__ __forceinline__ V rot(V a) {
+  return INV ? mk<V>(-a.y, a.x) : mk<V>(a.y, -a.x);
+}
 
 // Root e of the length-n table, conjugated for the inverse transform.
 template <typename V, bool INV> __device__ __forceinline__ V root(const V* __restrict__ tw, int e) {
@@ -65,74 +71,193 @@ template <typename V, bool INV> __device__ __forceinline__ V root(const V* __res
   return w;
 }
 
-// In-register R-point DFT, v[q] <- sum_r v[r] w_R^{r q}, w_R = root(n/R).
+__device__ __forceinline__ int fdiv(int x, const FastDiv& d) {
+  return (int)((__umulhi((unsigned)x, d.m) + (unsigned)x) >> d.l);
+}
+
+// cos(2 pi k / R) and sin(2 pi k / R) for the odd radices (k < R).
+template <int R> __device__ __forceinline__ double cosk(int k);
+template <int R> __device__ __forceinline__ double sink(int k);
+template <> __device__ __forceinline__ double cosk<3>(int k) { return k == 0 ? 1.0 : -0.5; }
+template <> __device__ __forceinline__ double sink<3>(int k) {
+  return k == 0 ? 0.0 : (k == 1 ? 0.86602540378443864676 : -0.86602540378443864676);
+}
+template <> __device__ __forceinline__ double cosk<5>(int k) {
+  const double c1 = 0.30901699437494742410, c2 = -0.80901699437494742410;
+  return k == 0 ? 1.0 : (k == 1 || k == 4) ? c1 : c2;
+}
+template <> __device__ __forceinline__ double sink<5>(int k) {
+  const double s1 = 0.95105651629515357212, s2 = 0.58778525229247312917;
+  return k == 0 ? 0.0 : k == 1 ? s1 : k == 2 ? s2 : k == 3 ? -s2 : -s1;
+}
+template <> __device__ __forceinline__ double cosk<7>(int k) {
+  const double c1 = 0.62348980185873353053, c2 = -0.22252093395631440429, c3 = -0.90096886790241912624;
+  return k == 0 ? 1.0 : (k == 1 || k == 6) ? c1 : (k == 2 || k == 5) ? c2 : c3;
+}
+template <> __device__ __forceinline__ double sink<7>(int k) {
+  const double s1 = 0.78183148246802980871, s2 = 0.97492791218182360702, s3 = 0.43388373911755812048;
+  return k == 0 ? 0.0 : k == 1 ? s1 : k == 2 ? s2 : k == 3 ? s3 : k == 4 ? -s3 : k == 5 ? -s2 : -s1;
+}
+
+// Odd prime R: y_q = x0 + sum_{r<=h} [ (x_r + x_{R-r}) cos(2 pi r q/R)
+//                                    -/+ i (x_r - x_{R-r}) sin(2 pi r q/R) ].
 template <typename T, int R, bool INV>
-__device__ __forceinline__ void dft_reg(typename CT<T>::t* v, const typename CT<T>::t* __restrict__ tw, int n) {
+__device__ __forceinline__ void dft_odd(typename CT<T>::t* v) {
   typedef typename CT<T>::t V;
-  if (R == 2) {
-    V a = v[0], b = v[1];
+  constexpr int h = (R - 1) / 2;
+  V A[h], B[h];
+#pragma unroll
+  for (int r = 1; r <= h; ++r) {
+    A[r - 1] = cadd(v[r], v[R - r]);
+    B[r - 1] = csub(v[r], v[R - r]);
+  }
+  V o[R];
+  V y0 = v[0];
+#pragma unroll
+  for (int r = 0; r < h; ++r) y0 = cadd(y0, A[r]);
+  o[0] = y0;
+#pragma unroll
+  for (int q = 1; q <= h; ++q) {
+    V re = v[0];
+    V im = mk<V>(0.0, 0.0);
+#pragma unroll
+    for (int r = 1; r <= h; ++r) {
+      const T c = (T)cosk<R>((r * q) % R);
+      const T s = (T)sink<R>((r * q) % R);
+      re.x += A[r - 1].x * c;
+      re.y += A[r - 1].y * c;
+      im.x += B[r - 1].x * s;
+      im.y += B[r - 1].y * s;
+    }
+    const V ri = rot<V, INV>(im);  // -i * im (forward)
+    o[q] = cadd(re, ri);
+    o[R - q] = csub(re, ri);
+  }
+#pragma unroll
+  for (int q = 0; q < R; ++q) v[q] = o[q];
+}
+
+template <typename T, bool INV>
+__device__ __forceinline__ void dft4(typename CT<T>::t& a0, typename CT<T>::t& a1, typename CT<T>::t& a2,
+                                     typename CT<T>::t& a3) {
+  typedef typename CT<T>::t V;
+  const V t0 = cadd(a0, a2), t1 = csub(a0, a2);
+  const V t2 = cadd(a1, a3), t3 = rot<V, INV>(csub(a1, a3));
+  a0 = cadd(t0, t2);
+  a2 = csub(t0, t2);
+  a1 = cadd(t1, t3);
+  a3 = csub(t1, t3);
+}
+
+template <typename T, bool INV>
+__device__ __forceinline__ void dft3(typename CT<T>::t& a0, typename CT<T>::t& a1, typename CT<T>::t& a2) {
+  typename CT<T>::t v[3] = {a0, a1, a2};
+  dft_odd<T, 3, INV>(v);
+  a0 = v[0];
+  a1 = v[1];
+  a2 = v[2];
+}
+
+// In-register R-point DFT, v[q] <- sum_r v[r] w_R^{r q}.
+template <typename T, int R, bool INV>
+__device__ __forceinline__ void dft_reg(typename CT<T>::t* v) {
+  typedef typename CT<T>::t V;
+  if constexpr (R == 2) {
+    const V a = v[0], b = v[1];
     v[0] = cadd(a, b);
     v[1] = csub(a, b);
-  } else if (R == 4) {
-    V t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
-    V t2 = cadd(v[1], v[3]), d = csub(v[1], v[3]);
-    // forward: -i * d ; inverse: +i * d
-    V t3 = INV ? mk<V>(-d.y, d.x) : mk<V>(d.y, -d.x);
-    v[0] = cadd(t0, t2);
-    v[2] = csub(t0, t2);
-    v[1] = cadd(t1, t3);
-    v[3] = csub(t1, t3);
-  } else {
-    V o[R];
-    const int step = n / R;
+  } else if constexpr (R == 4) {
+    dft4<T, INV>(v[0], v[1], v[2], v[3]);
+  } else if constexpr (R == 8) {
+    // even/odd split: E = DFT4(x0,x2,x4,x6), O = DFT4(x1,x3,x5,x7); y_q = E_q + w8^q O_q
+    V e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+    V o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+    dft4<T, INV>(e0, e1, e2, e3);
+    dft4<T, INV>(o0, o1, o2, o3);
+    const T h = (T)0.70710678118654752440;
+    // w8^1 = h(1 -/+ i), w8^2 = -/+ i, w8^3 = h(-1 -/+ i)
+    const V p1 = INV ? mk<V>(h * (o1.x - o1.y), h * (o1.x + o1.y)) : mk<V>(h * (o1.x + o1.y), h * (o1.y - o1.x));
+    const V p2 = rot<V, INV>(o2);
+    const V p3 = INV ? mk<V>(-h * (o3.x + o3.y), h * (o3.x - o3.y)) : mk<V>(h * (o3.y - o3.x), -h * (o3.x + o3.y));
+    v[0] = cadd(e0, o0);
+    v[4] = csub(e0, o0);
+    v[1] = cadd(e1, p1);
+    v[5] = csub(e1, p1);
+    v[2] = cadd(e2, p2);
+    v[6] = csub(e2, p2);
+    v[3] = cadd(e3, p3);
+    v[7] = csub(e3, p3);
+  } else if constexpr (R == 9) {
+    // r = 3a + b: Z_b = DFT3_a(x_{3a+b}); T_b(q1) = w9^{b q1} Z_b(q1); y_{q1+3 q2} = DFT3_b(T)(q2)
+    V z[9];
 #pragma unroll
-    for (int q = 0; q < R; ++q) {
-      V acc = v[0];
-#pragma unroll
-      for (int r = 1; r < R; ++r) acc = cadd(acc, cmul(v[r], root<V, INV>(tw, ((r * q) % R) * step)));
-      o[q] = acc;
+    for (int b = 0; b < 3; ++b) {
+      V a0 = v[b], a1 = v[b + 3], a2 = v[b + 6];
+      dft3<T, INV>(a0, a1, a2);
+      z[b] = a0;
+      z[3 + b] = a1;
+      z[6 + b] = a2;  // z[3 q1 + b]
     }
+    const T c1 = (T)0.76604444311897803520, s1 = (T)0.64278760968653932632;  // 2 pi / 9
+    const T c2 = (T)0.17364817766693034885, s2 = (T)0.98480775301220805936;  // 4 pi / 9
+    const T c4 = (T)-0.93969262078590838405, s4 = (T)0.34202014332566873304; // 8 pi / 9
+    const T sg = INV ? (T)1 : (T)-1;
+    const V w1 = mk<V>(c1, sg * s1), w2 = mk<V>(c2, sg * s2), w4 = mk<V>(c4, sg * s4);
+    z[4] = cmul(z[4], w1);  // q1 = 1, b = 1
+    z[5] = cmul(z[5], w2);  // q1 = 1, b = 2
+    z[7] = cmul(z[7], w2);  // q1 = 2, b = 1
+    z[8] = cmul(z[8], w4);  // q1 = 2, b = 2
 #pragma unroll
-    for (int q = 0; q < R; ++q) v[q] = o[q];
+    for (int q1 = 0; q1 < 3; ++q1) {
+      V a0 = z[3 * q1], a1 = z[3 * q1 + 1], a2 = z[3 * q1 + 2];
+      dft3<T, INV>(a0, a1, a2);
+      v[q1] = a0;
+      v[q1 + 3] = a1;
+      v[q1 + 6] = a2;
+    }
+  } else {
+    dft_odd<T, R, INV>(v);
   }
 }
 
 template <typename T, int R, bool INV>
 __device__ void stage_reg(const typename CT<T>::t* __restrict__ src, typename CT<T>::t* __restrict__ dst, int nl,
-                          int ls, int n, int Ns, const typename CT<T>::t* __restrict__ tw) {
+                          int ls, int n, int Ns, const FastDiv& dnb, const FastDiv& dns,
+                          const typename CT<T>::t* __restrict__ tw) {
   typedef typename CT<T>::t V;
   const int nb = n / R;
   const int s = n / (Ns * R);
   for (int t = threadIdx.x; t < nl * nb; t += blockDim.x) {
-    const int line = t / nb;
+    const int line = fdiv(t, dnb);
     const int j = t - line * nb;
-    const int k = j % Ns;
+    const int g = fdiv(j, dns);
+    const int k = j - g * Ns;
     const V* in = src + (size_t)line * ls;
     V v[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-      V x = in[j + r * nb];
-      if (r > 0 && k > 0) x = cmul(x, root<V, INV>(tw, r * k * s));
-      v[r] = x;
-    }
-    dft_reg<T, R, INV>(v, tw, n);
-    const int base = (j / Ns) * Ns * R + k;
-    V* out = dst + (size_t)line * ls;
+    for (int r = 0; r < R; ++r) v[r] = in[j + r * nb];
+    if (k > 0) {
+      const int ks = k * s;
 #pragma unroll
-    for (int r = 0; r < R; ++r) out[base + r * Ns] = v[r];
+      for (int r = 1; r < R; ++r) v[r] = cmul(v[r], root<V, INV>(tw, r * ks));
+    }
+    dft_reg<T, R, INV>(v);
+    V* out = dst + (size_t)line * ls + g * Ns * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) out[r * Ns] = v[r];
   }
 }
 
 // Large prime radix: one thread per output element.
 template <typename T, bool INV>
 __device__ void stage_big(const typename CT<T>::t* __restrict__ src, typename CT<T>::t* __restrict__ dst, int nl,
-                          int ls, int n, int Ns, int R, const typename CT<T>::t* __restrict__ tw) {
+                          int ls, int n, int Ns, int R, const FastDiv& dn, const typename CT<T>::t* __restrict__ tw) {
   typedef typename CT<T>::t V;
   const int nb = n / R;
   const int NsR = Ns * R;
   const int s = n / NsR;
   for (int t = threadIdx.x; t < nl * n; t += blockDim.x) {
-    const int line = t / n;
+    const int line = fdiv(t, dn);
     const int o = t - line * n;
     const int g = o / NsR;
     const int mm = o - g * NsR;
@@ -163,12 +288,14 @@ __device__ typename CT<T>::t* fft_run(typename CT<T>::t* a, typename CT<T>::t* b
   for (int s = 0; s < p.nst; ++s) {
     const int R = p.radix[s];
     switch (R) {
-      case 2: stage_reg<T, 2, INV>(a, b, nl, ls, n, Ns, tw); break;
-      case 3: stage_reg<T, 3, INV>(a, b, nl, ls, n, Ns, tw); break;
-      case 4: stage_reg<T, 4, INV>(a, b, nl, ls, n, Ns, tw); break;
-      case 5: stage_reg<T, 5, INV>(a, b, nl, ls, n, Ns, tw); break;
-      case 7: stage_reg<T, 7, INV>(a, b, nl, ls, n, Ns, tw); break;
-      default: stage_big<T, INV>(a, b, nl, ls, n, Ns, R, tw); break;
+      case 2: stage_reg<T, 2, INV>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw); break;
+      case 3: stage_reg<T, 3, INV>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw); break;
+      case 4: stage_reg<T, 4, INV>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw); break;
+      case 5: stage_reg<T, 5, INV>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw); break;
+      case 7: stage_reg<T, 7, INV>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw); break;
+      case 8: stage_reg<T, 8, INV>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw); break;
+      case 9: stage_reg<T, 9, INV>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw); break;
+      default: stage_big<T, INV>(a, b, nl, ls, n, Ns, R, p.dn, tw); break;
     }
     __syncthreads();
     V* t = a;
@@ -191,7 +318,7 @@ __device__ typename CT<T>::t* fft_any(typename CT<T>::t* a, typename CT<T>::t* b
   const V* bh = pool + P.bhat;
   // a_j = x_j conj(c_j) (x conjugated first for the inverse), zero-padded to m
   for (int t = threadIdx.x; t < nl * m; t += blockDim.x) {
-    const int line = t / m;
+    const int line = fdiv(t, P.sub.dn);
     const int j = t - line * m;
     V* x = a + (size_t)line * ls + j;
     if (j < n) {
@@ -206,7 +333,7 @@ __device__ typename CT<T>::t* fft_any(typename CT<T>::t* a, typename CT<T>::t* b
   V* r = fft_run<T, false>(a, b, nl, ls, P.sub, pool + P.sub.tw);
   V* o = (r == a) ? b : a;
   for (int t = threadIdx.x; t < nl * m; t += blockDim.x) {
-    const int line = t / m;
+    const int line = fdiv(t, P.sub.dn);
     const int j = t - line * m;
     V* x = r + (size_t)line * ls + j;
     *x = cmul(*x, bh[j]);
@@ -214,7 +341,7 @@ __device__ typename CT<T>::t* fft_any(typename CT<T>::t* a, typename CT<T>::t* b
   __syncthreads();
   r = fft_run<T, true>(r, o, nl, ls, P.sub, pool + P.sub.tw);
   for (int t = threadIdx.x; t < nl * n; t += blockDim.x) {
-    const int line = t / n;
+    const int line = fdiv(t, P.base.dn);
     const int j = t - line * n;
     V* x = r + (size_t)line * ls + j;
     V v = cmulc(*x, ch[j]);

@@ -13,19 +13,51 @@
 
 namespace fcsph {
 
-constexpr int kMaxStages = 20;
+constexpr int kMaxStages = 12;
 // Largest prime factor handled by a direct Stockham stage; lengths with a
 // larger prime factor go through Bluestein's chirp-z convolution.
 constexpr int kMaxDirectPrime = 31;
 
+// Division by a fixed d (< 2^31 dividends) as (umulhi(x, m) + x) >> l.
+struct FastDiv {
+  unsigned m = 1;
+  int l = 0;
+};
+inline FastDiv make_fastdiv(unsigned d) {
+  FastDiv f;
+  int l = 0;
+  while ((1ull << l) < d) ++l;
+  f.l = l;
+  f.m = (unsigned)(((1ull << 32) * ((1ull << l) - d)) / d + 1);
+  return f;
+}
+
 // One Stockham decomposition n = radix[0] * radix[1] * ...; `tw` is the offset
 // (in complex elements) of the n roots exp(-2 pi i e / n), e < n, in the pool.
+// dnb[s], dns[s]: reciprocals of n/radix[s] and of Ns (product of the radices
+// before stage s); dn: reciprocal of n.
 struct Plan1 {
   int n = 0;
   int nst = 0;
   int tw = 0;
   int radix[kMaxStages] = {0};
+  FastDiv dnb[kMaxStages];
+  FastDiv dns[kMaxStages];
+  FastDiv dn;
 };
+// Fills n, nst, radix, dnb, dns, dn from an ordered radix list.
+inline void plan_set_radices(Plan1* p, int n, const int* rad, int nr) {
+  p->n = n;
+  p->nst = nr;
+  p->dn = make_fastdiv((unsigned)n);
+  int ns = 1;
+  for (int i = 0; i < nr; ++i) {
+    p->radix[i] = rad[i];
+    p->dnb[i] = make_fastdiv((unsigned)(n / rad[i]));
+    p->dns[i] = make_fastdiv((unsigned)ns);
+    ns *= rad[i];
+  }
+}
 
 // A length-n complex DFT: direct (bs = 0, `base` holds the stages) or
 // Bluestein (bs = 1: base.n = n; `sub` is the smooth length-m plan; `chirp`

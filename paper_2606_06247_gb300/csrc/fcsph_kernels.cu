@@ -638,6 +638,16 @@ int fit_units(size_t per_unit, size_t budget, int cap) {
   return u;
 }
 
+// Units per CTA so that `total` units spread over at least ~4 CTAs per SM
+// (152 SMs), within the shared-memory fit.
+int spread_units(int fit, long long total) {
+  const long long target = 4LL * 152;
+  long long u = (total + target - 1) / target;
+  if (u < 1) u = 1;
+  if (u > fit) u = fit;
+  return (int)u;
+}
+
 constexpr size_t kSmemBudget = 96 * 1024;  // per CTA, leaves room for 2 CTAs/SM
 constexpr size_t kSmemMax = 227 * 1024;
 
@@ -685,7 +695,7 @@ static cudaError_t col_fwd_t(fcsph_ctx* c, int nf, const void* const* fields, in
   const FftPlan& P = dct ? c->plan_py : c->plan_y;
   const int ls = col_ls(c);
   const size_t per = 2 * (size_t)ls * sizeof(typename CT<T>::t);
-  const int Pp = fit_units(per, kSmemBudget, (g.nx + 1) / 2);
+  const int Pp = spread_units(fit_units(per, kSmemBudget, (g.nx + 1) / 2), (long long)nf * g.batch * ((g.nx + 1) / 2));
   const size_t smem = per * Pp;
   cudaError_t e = set_smem(k_col_fwd<T, U>, smem);
   if (e != cudaSuccess) return e;
@@ -717,7 +727,7 @@ static cudaError_t row_sym_t(fcsph_ctx* c, const void* sp_in, void* sp_out, cons
   const GridDev& g = c->gd;
   const int ls = c->plan_x.line_len();
   const size_t per = (size_t)(2 * ops.nin + 2 * ops.nout) * ls * sizeof(typename CT<T>::t);
-  const int Rr = fit_units(per, kSmemBudget, 8);
+  const int Rr = spread_units(fit_units(per, kSmemBudget, 8), (long long)g.batch * g.hy);
   const size_t smem = per * Rr;
   cudaError_t e = set_smem(k_row_sym<T>, smem);
   if (e != cudaSuccess) return e;
@@ -732,10 +742,41 @@ static cudaError_t row_sym_t(fcsph_ctx* c, const void* sp_in, void* sp_out, cons
   return cudaGetLastError();
 }
 
-cudaError_t launch_row_sym(fcsph_ctx* c, int prec, const void* sp_in, void* sp_out, const RowOps& ops, double scale,
-                           int bc, int kind) {
+static cudaError_t row_sym_any(fcsph_ctx* c, int prec, const void* sp_in, void* sp_out, const RowOps& ops,
+                               double scale, int bc, int kind) {
   if (prec == FCSPH_F64) return row_sym_t<double>(c, sp_in, sp_out, ops, scale, bc, kind);
   return row_sym_t<float>(c, sp_in, sp_out, ops, scale, bc, kind);
+}
+
+// When one row would need more shared memory than the budget and every output
+// is a single term, the pass runs once per input field (outputs of a field
+// must be contiguous), each with its own input row and output rows.
+cudaError_t launch_row_sym(fcsph_ctx* c, int prec, const void* sp_in, void* sp_out, const RowOps& ops, double scale,
+                           int bc, int kind) {
+  const size_t cb = prec == FCSPH_F64 ? sizeof(double2) : sizeof(float2);
+  const size_t per = (size_t)(2 * ops.nin + 2 * ops.nout) * c->plan_x.line_len() * cb;
+  bool single = ops.nin > 1;
+  for (int o = 0; o < ops.nout && single; ++o) single = ops.nterm[o] == 1 && (o == 0 || ops.field[o][0] >= ops.field[o - 1][0]);
+  if (per <= kSmemBudget || !single) return row_sym_any(c, prec, sp_in, sp_out, ops, scale, bc, kind);
+  const size_t fs = (size_t)c->gd.rows * c->gd.nx * cb;
+  for (int f = 0; f < ops.nin; ++f) {
+    RowOps sub;
+    memset(&sub, 0, sizeof(sub));
+    sub.nin = 1;
+    int first = -1;
+    for (int o = 0; o < ops.nout; ++o)
+      if (ops.field[o][0] == f) {
+        if (first < 0) first = o;
+        sub.nterm[sub.nout] = 1;
+        sub.field[sub.nout][0] = 0;
+        sub.op[sub.nout][0] = ops.op[o][0];
+        sub.nout++;
+      }
+    if (sub.nout == 0) continue;
+    cudaError_t e = row_sym_any(c, prec, (const char*)sp_in + f * fs, (char*)sp_out + first * fs, sub, scale, bc, kind);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 template <typename T>
@@ -745,7 +786,7 @@ static cudaError_t col_inv_common(fcsph_ctx* c, int epi, const void* spec, int n
   const int ls = col_ls(c);
   const int lines = nout > ea.fwd_nf ? nout : (ea.fwd_nf > 0 ? ea.fwd_nf : 1);
   const size_t per = 2 * (size_t)lines * ls * sizeof(typename CT<T>::t);
-  const int Pp = fit_units(per, kSmemBudget, (g.nx + 1) / 2);
+  const int Pp = spread_units(fit_units(per, kSmemBudget, (g.nx + 1) / 2), (long long)g.batch * ((g.nx + 1) / 2));
   const size_t smem = per * Pp;
   const size_t fs = (size_t)g.rows * g.nx;
   const size_t bs = (epi >= EPI_PPE_SOLVE ? 1 : 6) * fs;  // spec_ppe or spec_out
@@ -802,7 +843,7 @@ static cudaError_t row_ppe_t(fcsph_ctx* c, void* spec, int apply) {
   const GridDev& g = c->gd;
   const int ls = c->plan_px.line_len();
   const size_t per = 2 * (size_t)ls * sizeof(typename CT<T>::t);
-  const int Rr = fit_units(per, kSmemBudget, 16);
+  const int Rr = spread_units(fit_units(per, kSmemBudget, 16), (long long)g.batch * g.ny);
   const size_t smem = per * Rr;
   cudaError_t e = set_smem(k_row_ppe<T>, smem);
   if (e != cudaSuccess) return e;

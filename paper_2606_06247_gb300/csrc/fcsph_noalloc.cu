@@ -47,37 +47,52 @@ cudaError_t scratch_address(void** out) {
   return cudaSuccess;
 }
 
-// Allocation-free plan: a Stockham factorisation with radices 4, 2, then odd
-// primes <= kMaxDirectPrime (as make_plan), else Bluestein with the smallest
+// Allocation-free plan: the Stockham factorisation of make_plan (radices 8,
+// then 4 or 2; 9, then 3; 5; 7; primes <= kMaxDirectPrime), else Bluestein with the smallest
 // 2^a 3^b 5^c 7^d >= 2n - 1.  Offsets are into a pool laid out as
 // [twiddles of the direct length | (Bluestein) chirp n | filter m].
 bool factor_fixed(int n, Plan1* p) {
-  int rad[kMaxStages];
-  int nr = 0;
-  int r = n, twos = 0;
-  while (r % 2 == 0) {
-    r /= 2;
-    ++twos;
-  }
-  while (twos >= 2) {
-    if (nr == kMaxStages) return false;
-    rad[nr++] = 4;
-    twos -= 2;
-  }
-  if (twos) {
-    if (nr == kMaxStages) return false;
-    rad[nr++] = 2;
-  }
-  for (int q = 3; r > 1; q += 2) {
+  int cnt[8] = {0};
+  int big[kMaxStages];
+  int nbig = 0;
+  int r = n;
+  for (int q = 2; q <= 7; ++q)
     while (r % q == 0) {
-      if (q > kMaxDirectPrime || nr == kMaxStages) return false;
-      rad[nr++] = q;
+      ++cnt[q];
+      r /= q;
+    }
+  for (int q = 11; r > 1; q += 2) {
+    while (r % q == 0) {
+      if (q > kMaxDirectPrime || nbig == kMaxStages) return false;
+      big[nbig++] = q;
       r /= q;
     }
   }
-  p->n = n;
-  p->nst = nr;
-  for (int i = 0; i < nr; ++i) p->radix[i] = rad[i];
+  int rad[kMaxStages];
+  int nr = 0;
+  auto push = [&](int q) {
+    if (nr == kMaxStages) return false;
+    rad[nr++] = q;
+    return true;
+  };
+  while (cnt[2] >= 3) {
+    if (!push(8)) return false;
+    cnt[2] -= 3;
+  }
+  if (cnt[2] == 2 && !push(4)) return false;
+  if (cnt[2] == 1 && !push(2)) return false;
+  while (cnt[3] >= 2) {
+    if (!push(9)) return false;
+    cnt[3] -= 2;
+  }
+  if (cnt[3] == 1 && !push(3)) return false;
+  for (int i = 0; i < cnt[5]; ++i)
+    if (!push(5)) return false;
+  for (int i = 0; i < cnt[7]; ++i)
+    if (!push(7)) return false;
+  for (int i = 0; i < nbig; ++i)
+    if (!push(big[i])) return false;
+  plan_set_radices(p, n, rad, nr);
   return true;
 }
 
@@ -97,8 +112,7 @@ bool plan_fixed(int n, FftPlan* P, int* pool_len) {
   }
   if (!factor_fixed(m, &P->sub)) return false;
   P->bs = 1;
-  P->base.n = n;
-  P->base.nst = 0;
+  plan_set_radices(&P->base, n, nullptr, 0);
   P->sub.tw = 0;
   P->chirp = m;
   P->bhat = m + n;

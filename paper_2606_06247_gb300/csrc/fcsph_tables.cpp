@@ -204,35 +204,41 @@ static void roots(int n, std::vector<double>* re, std::vector<double>* im) {
 }
 
 bool factor_direct(int n, Plan1* p) {
-  std::vector<int> pf;
+  // radix order: 8s, then a 4 or 2; 9s, then a 3; 5s; 7s; larger primes
+  int cnt[32] = {0};
+  std::vector<int> big;
   int r = n;
-  for (int q = 2; q * q <= r; ++q)
+  for (int q : {2, 3, 5, 7}) {
     while (r % q == 0) {
-      pf.push_back(q);
+      ++cnt[q];
       r /= q;
     }
-  if (r > 1) pf.push_back(r);
-  for (int q : pf)
+  }
+  for (int q = 11; q * q <= r; q += 2)
+    while (r % q == 0) {
+      big.push_back(q);
+      r /= q;
+    }
+  if (r > 1) big.push_back(r);
+  for (int q : big)
     if (q > kMaxDirectPrime) return false;
-  int twos = 0;
-  std::vector<int> odd;
-  for (int q : pf) {
-    if (q == 2)
-      ++twos;
-    else
-      odd.push_back(q);
-  }
   std::vector<int> rad;
-  while (twos >= 2) {
-    rad.push_back(4);
-    twos -= 2;
+  while (cnt[2] >= 3) {
+    rad.push_back(8);
+    cnt[2] -= 3;
   }
-  if (twos) rad.push_back(2);
-  for (int q : odd) rad.push_back(q);
+  if (cnt[2] == 2) rad.push_back(4);
+  if (cnt[2] == 1) rad.push_back(2);
+  while (cnt[3] >= 2) {
+    rad.push_back(9);
+    cnt[3] -= 2;
+  }
+  if (cnt[3] == 1) rad.push_back(3);
+  for (int i = 0; i < cnt[5]; ++i) rad.push_back(5);
+  for (int i = 0; i < cnt[7]; ++i) rad.push_back(7);
+  for (int q : big) rad.push_back(q);
   if ((int)rad.size() > kMaxStages) return false;
-  p->n = n;
-  p->nst = (int)rad.size();
-  for (int i = 0; i < p->nst; ++i) p->radix[i] = rad[i];
+  plan_set_radices(p, n, rad.data(), (int)rad.size());
   return true;
 }
 
@@ -255,8 +261,7 @@ FftPlan make_plan(int n, Pool* pool, std::vector<double>* bre, std::vector<doubl
     return P;
   }
   P.bs = 1;
-  P.base.n = n;
-  P.base.nst = 0;
+  plan_set_radices(&P.base, n, nullptr, 0);
   const int m = smooth_at_least(2 * n - 1);
   factor_direct(m, &P.sub);
   roots(m, &r, &i);

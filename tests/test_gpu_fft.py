@@ -6,8 +6,8 @@ import pytest
 from gpu_common import binding, torch_cuda
 
 # extended lengths (n + 25), PPE even extensions 2(n-1), smooth variants and small edge cases
-LENGTHS = [1, 2, 3, 4, 5, 7, 8, 11, 16, 31, 37, 64, 89, 90, 96, 126, 150, 153, 254, 256, 280, 281, 510, 512,
-           537, 540, 1022, 1049, 1050, 2046]
+LENGTHS = [1, 2, 3, 4, 5, 7, 8, 9, 11, 16, 27, 31, 37, 64, 72, 81, 89, 90, 96, 126, 150, 153, 243, 254, 256, 280,
+           281, 510, 512, 537, 540, 567, 576, 1000, 1022, 1049, 1050, 2046]
 
 
 @pytest.mark.gpu
