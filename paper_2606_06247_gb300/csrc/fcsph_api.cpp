@@ -211,6 +211,7 @@ fcsph_status fcsph_create(const fcsph_grid* grid, const fcsph_fc* fc, const fcsp
     goto fail_out;                         \
   }
   {
+    CREATE_CK(init_kernel_attributes(), "kernel attributes");
     st = upload_pool(c, pool, fills, &c->pool64, &c->pool32, c->stream);
     if (st != FCSPH_OK) goto fail_out;
     const size_t ne = (size_t)g.n_cont * 2 * g.n_match;
@@ -543,6 +544,7 @@ fcsph_status fcsph_dft(int n, int nlines, int dir, int prec, const void* in, voi
   double2* d64 = nullptr;
   float2* d32 = nullptr;
   cudaStream_t st = (cudaStream_t)stream;
+  if (init_kernel_attributes() != cudaSuccess) return fail(nullptr, FCSPH_ECUDA, "fcsph_dft: kernel attributes");
   fcsph_status s = upload_pool(c, pool, fills, &d64, &d32, st);
   if (s != FCSPH_OK) {
     cudaFree(d64);

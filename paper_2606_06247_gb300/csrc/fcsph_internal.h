@@ -165,6 +165,9 @@ struct ProfScope {
   ~ProfScope();
 };
 
+// Raises every kernel's dynamic shared-memory limit (called before any capture).
+cudaError_t init_kernel_attributes();
+
 // Kernel launchers (fcsph_kernels.cu); return cudaGetLastError().
 cudaError_t launch_fc_extend(fcsph_ctx* c, const void* f, void* fext, int bc);
 cudaError_t launch_col_fwd(fcsph_ctx* c, int prec, int nf, const void* const* fields, int fields_double, int bc,

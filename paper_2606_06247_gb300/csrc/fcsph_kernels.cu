@@ -651,9 +651,15 @@ int spread_units(int fit, long long total) {
 constexpr size_t kSmemBudget = 96 * 1024;  // per CTA, leaves room for 2 CTAs/SM
 constexpr size_t kSmemMax = 227 * 1024;
 
-template <typename K> cudaError_t set_smem(K kernel, size_t bytes) {
-  if (bytes > kSmemMax) return cudaErrorInvalidValue;
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+// Every kernel's dynamic shared-memory limit is raised once, at the first
+// context creation (init_kernel_attributes), so that no attribute call ever
+// happens while a stream is being captured; launches only check the size.
+template <typename K> cudaError_t set_smem(K, size_t bytes) {
+  return bytes > kSmemMax ? cudaErrorInvalidValue : cudaSuccess;
+}
+
+template <typename K> cudaError_t raise_smem(K kernel) {
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax);
 }
 
 int col_ls(const fcsph_ctx* c) {
@@ -666,6 +672,36 @@ int col_ls(const fcsph_ctx* c) {
 
 // ===========================================================================
 // Launchers
+
+cudaError_t init_kernel_attributes() {
+  cudaError_t e = cudaSuccess;
+#define FCSPH_RAISE(K)                           \
+  if ((e = raise_smem(K)) != cudaSuccess) return e;
+  FCSPH_RAISE((k_col_fwd<double, double>))
+  FCSPH_RAISE((k_col_fwd<float, double>))
+  FCSPH_RAISE((k_col_fwd<float, float>))
+  FCSPH_RAISE((k_row_sym<double>))
+  FCSPH_RAISE((k_row_sym<float>))
+  FCSPH_RAISE((k_row_ppe<double>))
+  FCSPH_RAISE((k_row_ppe<float>))
+  FCSPH_RAISE((k_dft_lines<double, false>))
+  FCSPH_RAISE((k_dft_lines<double, true>))
+  FCSPH_RAISE((k_dft_lines<float, false>))
+  FCSPH_RAISE((k_dft_lines<float, true>))
+#define FCSPH_RAISE_INV(T)                  \
+  FCSPH_RAISE((k_col_inv<T, EPI_OUT>))       \
+  FCSPH_RAISE((k_col_inv<T, EPI_MOM>))       \
+  FCSPH_RAISE((k_col_inv<T, EPI_DIV>))       \
+  FCSPH_RAISE((k_col_inv<T, EPI_CORR>))      \
+  FCSPH_RAISE((k_col_inv<T, EPI_PPE_SOLVE>)) \
+  FCSPH_RAISE((k_col_inv<T, EPI_PPE_RESID>)) \
+  FCSPH_RAISE((k_col_inv<T, EPI_PPE_ADD>))
+  FCSPH_RAISE_INV(double)
+  FCSPH_RAISE_INV(float)
+#undef FCSPH_RAISE_INV
+#undef FCSPH_RAISE
+  return cudaSuccess;
+}
 
 cudaError_t launch_fc_extend(fcsph_ctx* c, const void* f, void* fext, int bc) {
   ProfScope ps(c, FCSPH_PROF_OTHER);

@@ -47,13 +47,18 @@ def oracle_problem(nx, ny, x_walls, family, h_over_dx, n_cont=25, **kw):
                          E_dir=E, E_neu=E, **kw).build_symbols()
 
 
-def ulp_floor(fn, *inputs, seed=0):
-    """Relative change of fn's outputs when every input array is perturbed by
-    about one ulp (relative 2^-52, random sign): the FP64 rounding floor that
-    any evaluation of the same problem carries.  Returns a list, one per output."""
+def ulp_floor(fn, *inputs, seed=0, scale=None):
+    """Relative change of fn's outputs when every input value is moved by one
+    ulp of its magnitude (or of `scale`, the problem's value scale, when given:
+    needed for inputs that are exactly zero), random sign: the FP64 rounding
+    floor that any evaluation of the same problem carries.  One per output."""
     rng = np.random.default_rng(seed)
     base = fn(*inputs)
-    pert = [np.asarray(a) * (1.0 + 2.0 ** -52 * rng.choice([-1.0, 1.0], size=np.shape(a))) for a in inputs]
+    pert = []
+    for a in inputs:
+        a = np.asarray(a)
+        mag = np.full(a.shape, float(scale)) if scale is not None else np.abs(a)
+        pert.append(a + 2.0 ** -52 * mag * rng.choice([-1.0, 1.0], size=a.shape))
     moved = fn(*pert)
     return [rel_l2(m, b) for m, b in zip(moved, base)]
 

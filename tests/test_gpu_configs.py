@@ -1,0 +1,87 @@
+"""Parity at the workloads' own sizes: the 64 x 64 channel of the first
+configuration (100 FOP steps, full field), the lid cavity at its 64 x 64
+parity size, and the 256 x 256 lid-cavity benchmark workload in the launch
+configuration the benchmark times (batch 32, CUDA-graph replay), compared on
+two instances with the oracle."""
+import numpy as np
+import pytest
+
+from gpu_common import binding, grid_lengths, oracle_problem, parity_tol, rel_l2, to_dev, torch_cuda, ulp_floor
+from oracle import step as ostep
+from paper_2606_06247_gb300 import inputs
+
+
+def _series(y, t, F, nu, nterms=4001):
+    u = F / (2 * nu) * y * (1 - y)
+    for n in range(1, nterms, 2):
+        u -= 4 * F / (nu * np.pi ** 3 * n ** 3) * np.sin(n * np.pi * y) * np.exp(-nu * n * n * np.pi ** 2 * t)
+    return u
+
+
+@pytest.mark.gpu
+def test_channel_64_fop_100_steps_full_field():
+    torch = torch_cuda()
+    b = binding()
+    N = 64
+    lx, ly = grid_lengths(N, N, False)
+    u0, v0 = inputs.channel_initial(N, N, seed=1, sigma=1e-6)
+    ctx = b.Context(N, N, lx, ly, family="G4", h_over_dx=1.3)
+    u, v = to_dev(u0[None]), to_dev(v0[None])
+    p, fu, fv = torch.zeros_like(u), torch.zeros_like(u), torch.zeros_like(u)
+    ctx.isph_step(u, v, p, fu, fv, 100, nu=0.1, rho=1.0, dt=1e-3, force=(0.8, 0.0), scheme="fop")
+    ctx.sync()
+    prob = oracle_problem(N, N, False, "G4", 1.3, scheme="fop", nu=0.1, dt=1e-3, force=(0.8, 0.0))
+    fn = lambda a, c: ostep.isph_steps(prob, a, c, 100)
+    uo, vo, po = fn(u0, v0)
+    fl = ulp_floor(fn, u0, v0)
+    errs = [rel_l2(u[0].cpu().numpy(), uo), rel_l2(v[0].cpu().numpy(), vo), rel_l2(p[0].cpu().numpy(), po)]
+    print("channel 64^2 FOP x100 parity (u, v, p):", errs, "floor:", fl)
+    for e, f in zip(errs, fl):
+        assert e < parity_tol(f)
+    y = np.linspace(0, 1, N)
+    ua = np.tile(_series(y, 0.1, 0.8, 0.1), (N, 1))
+    assert rel_l2(u[0].cpu().numpy(), ua) < 2e-3  # FOP start-up vs the analytic series
+
+
+@pytest.mark.gpu
+def test_cavity_64_rk3_parity_size():
+    torch = torch_cuda()
+    b = binding()
+    N = 64
+    u0, v0 = inputs.cavity_initial(N, N)
+    ctx = b.Context(N, N, 1.0, 1.0, x_walls=True, family="G8", h_over_dx=1.3)
+    u, v = to_dev(u0[None]), to_dev(v0[None])
+    p, fu, fv = torch.zeros_like(u), torch.zeros_like(u), torch.zeros_like(u)
+    ctx.isph_step(u, v, p, fu, fv, 20, nu=1e-3, rho=1.0, dt=1e-3, u_top=1.0, scheme="rk3")
+    ctx.sync()
+    prob = oracle_problem(N, N, True, "G8", 1.3, scheme="rk3", nu=1e-3, dt=1e-3, u_top=1.0)
+    fn = lambda a, c: ostep.isph_steps(prob, a, c, 20)
+    uo, vo, po = fn(u0, v0)
+    fl = ulp_floor(fn, u0, v0, scale=1.0)  # fluid at rest: perturb by one ulp of the lid speed
+    errs = [rel_l2(u[0].cpu().numpy(), uo), rel_l2(v[0].cpu().numpy(), vo), rel_l2(p[0].cpu().numpy(), po)]
+    print("cavity 64^2 RK3 x20 parity (u, v, p):", errs, "floor:", fl)
+    for e, f in zip(errs, fl):
+        assert e < parity_tol(f)
+
+
+@pytest.mark.gpu
+def test_bench_workload_256_batch32_graph_sampled():
+    torch = torch_cuda()
+    b = binding()
+    N, B, steps = 256, 32, 3
+    ctx = b.Context(N, N, 1.0, 1.0, x_walls=True, batch=B, family="G8", h_over_dx=1.3)
+    init = [inputs.cavity_initial(N, N, seed=100 + k, sigma=1e-3) for k in range(B)]
+    u = to_dev(np.stack([a for a, _ in init]))
+    v = to_dev(np.stack([c for _, c in init]))
+    p, fu, fv = torch.zeros_like(u), torch.zeros_like(u), torch.zeros_like(u)
+    ctx.isph_step(u, v, p, fu, fv, steps, nu=1e-3, rho=1.0, dt=1e-3, u_top=1.0, scheme="rk3", use_graph=True)
+    ctx.sync()
+    prob = oracle_problem(N, N, True, "G8", 1.3, scheme="rk3", nu=1e-3, dt=1e-3, u_top=1.0)
+    fn = lambda a, c: ostep.isph_steps(prob, a, c, steps)
+    for k in (0, B - 1):
+        uo, vo, po = fn(*init[k])
+        fl = ulp_floor(fn, *init[k])
+        errs = [rel_l2(u[k].cpu().numpy(), uo), rel_l2(v[k].cpu().numpy(), vo), rel_l2(p[k].cpu().numpy(), po)]
+        print(f"bench workload instance {k}: parity (u, v, p) {errs} floor {fl}")
+        for e, f in zip(errs, fl):
+            assert e < parity_tol(f)
