@@ -287,7 +287,8 @@ def run_ours(args):
         d["gbs"] = by / (d["avg_ms"] * 1e-3) / 1e9 if by else None
     my, mx = N + N_CONT, N + N_CONT
     px = 2 * (N - 1)
-    split = args.prec == "f64"  # the FP64 momentum row pass runs per field (shared-memory budget)
+    # the momentum row pass runs once per field when one row set exceeds the shared-memory budget
+    split = kinds.get("row_mom", {}).get("launches", 0) > kinds.get("row_div", {}).get("launches", 0)
     for k, d in kinds.items():
         fl = kernel_flops(k, N, N, my, mx, hy, px, B, split)
         d["alg_gflop"] = fl / 1e9

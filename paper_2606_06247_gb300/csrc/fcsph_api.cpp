@@ -89,7 +89,7 @@ fcsph_status upload_pool(fcsph_ctx* c, Pool& pool, std::vector<Fill>& fills, dou
 FftPlan plan_for(int n, Pool* pool, std::vector<Fill>* fills) {
   Fill f;
   FftPlan P = make_plan(n, pool, &f.re, &f.im);
-  if (P.bs) {
+  if (P.bs || P.rd) {
     f.P = P;
     fills->push_back(f);
   }
@@ -202,6 +202,8 @@ fcsph_status fcsph_create(const fcsph_grid* grid, const fcsph_fc* fc, const fcsp
   c->plan_x = plan_for(g.mx, &pool, &fills);
   c->plan_py = plan_for(2 * (g.ny - 1), &pool, &fills);
   c->plan_px = plan_for(g.x_walls ? 2 * (g.nx - 1) : g.nx, &pool, &fills);
+  g.ex_off = pool.add(gauss_axis(g.mx, g.dx, g.h, g.mx), std::vector<double>(g.mx, 0.0));
+  g.ey_off = pool.add(gauss_axis(g.my, g.dy, g.h, g.hy), std::vector<double>(g.hy, 0.0));
 
   fcsph_status st = FCSPH_OK;
   cudaError_t e;

@@ -6,9 +6,11 @@
 // w^{r k n/(Ns R)} (k = j mod Ns, w = exp(-2 pi i/n)), does an R-point DFT in
 // registers and writes y[(j/Ns) Ns R + k + q Ns], q < R.  The divisions by
 // the per-stage constants n/R and Ns use precomputed multiply-shift
-// reciprocals.  Radices 2, 3, 4, 5, 7, 8 and 9 have dedicated butterflies
+// reciprocals.  Radices 2, 3, 4, 5, 7, 8, 9, 11, 13 and 17 have dedicated butterflies
 // built from the constant roots of unity; other primes up to kMaxDirectPrime
-// use one thread per output.  Lengths with a larger prime factor use
+// use one thread per output.  A prime length p whose p - 1 factors that way
+// uses Rader's algorithm (the DFT as a cyclic convolution of length p - 1 in
+// primitive-root order); other lengths with a larger prime factor use
 // Bluestein: X = conj(c) . IFFT_m( FFT_m(x conj(c)) . FFT_m(b) / m ),
 // c_j = exp(i pi j^2 / n), m smooth >= 2n - 1.
 #pragma once
@@ -75,28 +77,128 @@ __device__ __forceinline__ int fdiv(int x, const FastDiv& d) {
   return (int)((__umulhi((unsigned)x, d.m) + (unsigned)x) >> d.l);
 }
 
-// cos(2 pi k / R) and sin(2 pi k / R) for the odd radices (k < R).
-template <int R> __device__ __forceinline__ double cosk(int k);
-template <int R> __device__ __forceinline__ double sink(int k);
-template <> __device__ __forceinline__ double cosk<3>(int k) { return k == 0 ? 1.0 : -0.5; }
-template <> __device__ __forceinline__ double sink<3>(int k) {
-  return k == 0 ? 0.0 : (k == 1 ? 0.86602540378443864676 : -0.86602540378443864676);
+// cos(2 pi j / R) and sin(2 pi j / R), j = 1..(R-1)/2, for the odd radices;
+// cosk/sink extend them to any k by symmetry.  With unrolled loops k is a
+// compile-time constant and the switch folds to an immediate.
+template <int R> __device__ __forceinline__ double cos_tab(int j);
+template <int R> __device__ __forceinline__ double sin_tab(int j);
+template <> __device__ __forceinline__ double cos_tab<3>(int j) {
+  switch (j) {
+      case 1: return -0.4999999999999998;
+    default: return 1.0;
+  }
 }
-template <> __device__ __forceinline__ double cosk<5>(int k) {
-  const double c1 = 0.30901699437494742410, c2 = -0.80901699437494742410;
-  return k == 0 ? 1.0 : (k == 1 || k == 4) ? c1 : c2;
+template <> __device__ __forceinline__ double sin_tab<3>(int j) {
+  switch (j) {
+      case 1: return 0.8660254037844387;
+    default: return 0.0;
+  }
 }
-template <> __device__ __forceinline__ double sink<5>(int k) {
-  const double s1 = 0.95105651629515357212, s2 = 0.58778525229247312917;
-  return k == 0 ? 0.0 : k == 1 ? s1 : k == 2 ? s2 : k == 3 ? -s2 : -s1;
+template <> __device__ __forceinline__ double cos_tab<5>(int j) {
+  switch (j) {
+      case 1: return 0.30901699437494745;
+      case 2: return -0.8090169943749473;
+    default: return 1.0;
+  }
 }
-template <> __device__ __forceinline__ double cosk<7>(int k) {
-  const double c1 = 0.62348980185873353053, c2 = -0.22252093395631440429, c3 = -0.90096886790241912624;
-  return k == 0 ? 1.0 : (k == 1 || k == 6) ? c1 : (k == 2 || k == 5) ? c2 : c3;
+template <> __device__ __forceinline__ double sin_tab<5>(int j) {
+  switch (j) {
+      case 1: return 0.9510565162951535;
+      case 2: return 0.5877852522924732;
+    default: return 0.0;
+  }
 }
-template <> __device__ __forceinline__ double sink<7>(int k) {
-  const double s1 = 0.78183148246802980871, s2 = 0.97492791218182360702, s3 = 0.43388373911755812048;
-  return k == 0 ? 0.0 : k == 1 ? s1 : k == 2 ? s2 : k == 3 ? s3 : k == 4 ? -s3 : k == 5 ? -s2 : -s1;
+template <> __device__ __forceinline__ double cos_tab<7>(int j) {
+  switch (j) {
+      case 1: return 0.6234898018587336;
+      case 2: return -0.22252093395631434;
+      case 3: return -0.900968867902419;
+    default: return 1.0;
+  }
+}
+template <> __device__ __forceinline__ double sin_tab<7>(int j) {
+  switch (j) {
+      case 1: return 0.7818314824680298;
+      case 2: return 0.9749279121818236;
+      case 3: return 0.43388373911755823;
+    default: return 0.0;
+  }
+}
+template <> __device__ __forceinline__ double cos_tab<11>(int j) {
+  switch (j) {
+      case 1: return 0.8412535328311812;
+      case 2: return 0.41541501300188644;
+      case 3: return -0.142314838273285;
+      case 4: return -0.654860733945285;
+      case 5: return -0.9594929736144974;
+    default: return 1.0;
+  }
+}
+template <> __device__ __forceinline__ double sin_tab<11>(int j) {
+  switch (j) {
+      case 1: return 0.5406408174555976;
+      case 2: return 0.9096319953545183;
+      case 3: return 0.9898214418809328;
+      case 4: return 0.7557495743542583;
+      case 5: return 0.28173255684142967;
+    default: return 0.0;
+  }
+}
+template <> __device__ __forceinline__ double cos_tab<13>(int j) {
+  switch (j) {
+      case 1: return 0.8854560256532099;
+      case 2: return 0.5680647467311559;
+      case 3: return 0.120536680255323;
+      case 4: return -0.35460488704253545;
+      case 5: return -0.7485107481711012;
+      case 6: return -0.970941817426052;
+    default: return 1.0;
+  }
+}
+template <> __device__ __forceinline__ double sin_tab<13>(int j) {
+  switch (j) {
+      case 1: return 0.4647231720437685;
+      case 2: return 0.8229838658936564;
+      case 3: return 0.992708874098054;
+      case 4: return 0.9350162426854148;
+      case 5: return 0.6631226582407952;
+      case 6: return 0.23931566428755768;
+    default: return 0.0;
+  }
+}
+template <> __device__ __forceinline__ double cos_tab<17>(int j) {
+  switch (j) {
+      case 1: return 0.9324722294043558;
+      case 2: return 0.7390089172206591;
+      case 3: return 0.4457383557765383;
+      case 4: return 0.09226835946330202;
+      case 5: return -0.2736629900720829;
+      case 6: return -0.6026346363792563;
+      case 7: return -0.850217135729614;
+      case 8: return -0.9829730996839018;
+    default: return 1.0;
+  }
+}
+template <> __device__ __forceinline__ double sin_tab<17>(int j) {
+  switch (j) {
+      case 1: return 0.3612416661871529;
+      case 2: return 0.6736956436465572;
+      case 3: return 0.8951632913550623;
+      case 4: return 0.9957341762950345;
+      case 5: return 0.961825643172819;
+      case 6: return 0.7980172272802396;
+      case 7: return 0.5264321628773561;
+      case 8: return 0.18374951781657037;
+    default: return 0.0;
+  }
+}
+template <int R> __device__ __forceinline__ double cosk(int k) {
+  k %= R;
+  return k == 0 ? 1.0 : cos_tab<R>(2 * k <= R ? k : R - k);
+}
+template <int R> __device__ __forceinline__ double sink(int k) {
+  k %= R;
+  return k == 0 ? 0.0 : (2 * k <= R ? sin_tab<R>(k) : -sin_tab<R>(R - k));
 }
 
 // Odd prime R: y_q = x0 + sum_{r<=h} [ (x_r + x_{R-r}) cos(2 pi r q/R)
@@ -295,6 +397,9 @@ __device__ typename CT<T>::t* fft_run(typename CT<T>::t* a, typename CT<T>::t* b
       case 7: stage_reg<T, 7, INV>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw); break;
       case 8: stage_reg<T, 8, INV>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw); break;
       case 9: stage_reg<T, 9, INV>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw); break;
+      case 11: stage_reg<T, 11, INV>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw); break;
+      case 13: stage_reg<T, 13, INV>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw); break;
+      case 17: stage_reg<T, 17, INV>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw); break;
       default: stage_big<T, INV>(a, b, nl, ls, n, Ns, R, p.dn, tw); break;
     }
     __syncthreads();
@@ -306,11 +411,71 @@ __device__ typename CT<T>::t* fft_run(typename CT<T>::t* a, typename CT<T>::t* b
   return a;
 }
 
+// Rader transform of a prime length p = P.base.n (see FftPlan).  Slots p and
+// p + 1 of every line hold x_0 and A_0 = sum_{j>0} x_j; the Stockham stages of
+// length p - 1 never touch them.
+template <typename T, bool INV>
+__device__ typename CT<T>::t* fft_rader(typename CT<T>::t* a, typename CT<T>::t* b, int nl, int ls, const FftPlan& P,
+                                        const typename CT<T>::t* __restrict__ pool) {
+  typedef typename CT<T>::t V;
+  const int p = P.base.n;
+  const int m = p - 1;
+  const V* gi = pool + P.gidx;
+  const V* si = pool + P.sidx;
+  const V* bh = pool + P.bhat;
+  for (int t = threadIdx.x; t < nl * m; t += blockDim.x) {
+    const int line = fdiv(t, P.sub.dn);
+    const int q = t - line * m;
+    V v = a[(size_t)line * ls + (int)gi[q].x];
+    if (INV) v.y = -v.y;
+    b[(size_t)line * ls + q] = v;
+  }
+  for (int line = threadIdx.x; line < nl; line += blockDim.x) {
+    V x0 = a[(size_t)line * ls];
+    if (INV) x0.y = -x0.y;
+    a[(size_t)line * ls + p] = x0;
+    b[(size_t)line * ls + p] = x0;
+  }
+  __syncthreads();
+  V* r = fft_run<T, false>(b, a, nl, ls, P.sub, pool + P.sub.tw);
+  V* o = (r == b) ? a : b;
+  for (int t = threadIdx.x; t < nl * m; t += blockDim.x) {
+    const int line = fdiv(t, P.sub.dn);
+    const int k = t - line * m;
+    V* x = r + (size_t)line * ls + k;
+    if (k == 0) {  // A_0 = sum_{j>0} x_j, kept before the multiply overwrites it
+      r[(size_t)line * ls + p + 1] = *x;
+      o[(size_t)line * ls + p + 1] = *x;
+    }
+    *x = cmul(*x, bh[k]);
+  }
+  __syncthreads();
+  V* y = fft_run<T, true>(r, o, nl, ls, P.sub, pool + P.sub.tw);
+  V* out = (y == r) ? o : r;
+  for (int t = threadIdx.x; t < nl * m; t += blockDim.x) {
+    const int line = fdiv(t, P.sub.dn);
+    const int q = t - line * m;
+    const V* yl = y + (size_t)line * ls;
+    V v = cadd(yl[p], yl[q]);
+    if (INV) v.y = -v.y;
+    out[(size_t)line * ls + (int)si[q].x] = v;
+  }
+  for (int line = threadIdx.x; line < nl; line += blockDim.x) {
+    const V* yl = y + (size_t)line * ls;
+    V v = cadd(yl[p], yl[p + 1]);
+    if (INV) v.y = -v.y;
+    out[(size_t)line * ls] = v;
+  }
+  __syncthreads();
+  return out;
+}
+
 // Length-n DFT of nl lines (data in a[0..n) of each line; ls >= P.line_len()).
 template <typename T, bool INV>
 __device__ typename CT<T>::t* fft_any(typename CT<T>::t* a, typename CT<T>::t* b, int nl, int ls, const FftPlan& P,
                                       const typename CT<T>::t* __restrict__ pool) {
   typedef typename CT<T>::t V;
+  if (P.rd) return fft_rader<T, INV>(a, b, nl, ls, P, pool);
   if (!P.bs) return fft_run<T, INV>(a, b, nl, ls, P.base, pool + P.base.tw);
   const int n = P.base.n;
   const int m = P.sub.n;

@@ -59,16 +59,24 @@ inline void plan_set_radices(Plan1* p, int n, const int* rad, int nr) {
   }
 }
 
-// A length-n complex DFT: direct (bs = 0, `base` holds the stages) or
+// A length-n complex DFT: direct (bs = rd = 0, `base` holds the stages),
 // Bluestein (bs = 1: base.n = n; `sub` is the smooth length-m plan; `chirp`
-// holds exp(i pi j^2 / n), j < n; `bhat` holds FFT_m(b)/m of the chirp filter).
+// holds exp(i pi j^2 / n), j < n; `bhat` holds FFT_m(b)/m of the chirp
+// filter), or Rader for a prime n whose n - 1 factors directly (rd = 1: `sub`
+// has length n - 1; `gidx[q]` = g^q mod n and `sidx[q]` = g^-q mod n for a
+// primitive root g, stored as the real parts of pool entries; `bhat` holds
+// FFT_{n-1}(b)/(n-1) of b_s = exp(-2 pi i g^-s / n)).
 struct FftPlan {
   Plan1 base;
   int bs = 0;
+  int rd = 0;
   Plan1 sub;
   int chirp = 0;
   int bhat = 0;
-  int line_len() const { return bs ? sub.n : base.n; }  // smem line length
+  int gidx = 0;
+  int sidx = 0;
+  // smem line length: Rader keeps x_0 and the sum term in two extra slots
+  int line_len() const { return rd ? base.n + 2 : (bs ? sub.n : base.n); }
 };
 
 // Host-side twiddle/chirp pool (FP64 master, FP32 copy made at upload).
@@ -89,6 +97,7 @@ int smooth_at_least(int n);
 // (bhat_src gets the length-m filter b in natural order, zero-padded).
 FftPlan make_plan(int n, Pool* pool, std::vector<double>* bhat_src_re, std::vector<double>* bhat_src_im);
 int fc_table_build(const fcsph_fc* fc, int bc, std::vector<double>* E, std::string* err);
+std::vector<double> gauss_axis(int m, double d, double h, int count);
 
 }  // namespace fcsph
 
@@ -111,6 +120,9 @@ struct GridDev {
   int rows;              // spectrum rows allocated per field (max(hy, ny))
   double dx, dy, lx, ly, h;
   int family;
+  // pool offsets of exp(-kx^2 h^2/4), kx index < mx, and exp(-ky^2 h^2/4),
+  // ky < hy (real parts): the symbol's Gaussian factor is their product
+  int ex_off, ey_off;
 };
 
 struct StepDev {

@@ -200,13 +200,14 @@ __device__ __forceinline__ typename CT<T>::t symbol(int op, T kx, T ky, bool nyq
   }
 }
 
-template <typename T> __device__ __forceinline__ T kernel_hat(int family, T s) {
+// sum_{m<n} s^m / m! (n = family): W_hat = e^{-s} times this.
+template <typename T> __device__ __forceinline__ T kernel_poly(int family, T s) {
   T acc = 1, term = 1;
   for (int m = 1; m < family; ++m) {
     term = term * s / (T)m;
     acc += term;
   }
-  return exp(-s) * acc;
+  return acc;
 }
 
 // Row pass: for Rr rows ky of one instance: load nin input rows, FC-extend
@@ -268,7 +269,8 @@ __global__ void __launch_bounds__(kThreads) k_row_sym(GridDev g, const typename 
     const T kx = ckx * (T)kappa, kyw = cky * (T)ky;
     const bool nyq_x = (mx % 2 == 0) && (2 * kxi == mx);
     const bool nyq_y = (g.my % 2 == 0) && (2 * ky == g.my);
-    const T What = kernel_hat<T>(g.family, (kx * kx + kyw * kyw) * hh);
+    // e^{-s} = e^{-kx^2 h^2/4} e^{-ky^2 h^2/4} from the per-axis tables
+    const T What = pool[g.ex_off + kxi].x * pool[g.ey_off + ky].x * kernel_poly<T>(g.family, (kx * kx + kyw * kyw) * hh);
     for (int o = 0; o < nout; ++o) {
       V acc = mk<V>(0.0, 0.0);
       for (int t = 0; t < ops.nterm[o]; ++t) {
@@ -395,11 +397,13 @@ struct EpiArgs {
   int* status;
 };
 
-template <typename T, int EPI>
+// The epilogue kind is a runtime argument (uniform across the grid): one
+// instantiation per precision keeps the build small.
+template <typename T>
 __global__ void __launch_bounds__(kThreads) k_col_inv(GridDev g, const typename CT<T>::t* __restrict__ spec,
                                                       size_t fstride, size_t bstride, int nout, int nlines,
                                                       FftPlan P, const typename CT<T>::t* __restrict__ pool,
-                                                      EpiArgs ea, int Pp, int ls) {
+                                                      EpiArgs ea, int Pp, int ls, const int EPI) {
   typedef typename CT<T>::t V;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* Z = reinterpret_cast<V*>(smem_raw);
@@ -688,17 +692,8 @@ cudaError_t init_kernel_attributes() {
   FCSPH_RAISE((k_dft_lines<double, true>))
   FCSPH_RAISE((k_dft_lines<float, false>))
   FCSPH_RAISE((k_dft_lines<float, true>))
-#define FCSPH_RAISE_INV(T)                  \
-  FCSPH_RAISE((k_col_inv<T, EPI_OUT>))       \
-  FCSPH_RAISE((k_col_inv<T, EPI_MOM>))       \
-  FCSPH_RAISE((k_col_inv<T, EPI_DIV>))       \
-  FCSPH_RAISE((k_col_inv<T, EPI_CORR>))      \
-  FCSPH_RAISE((k_col_inv<T, EPI_PPE_SOLVE>)) \
-  FCSPH_RAISE((k_col_inv<T, EPI_PPE_RESID>)) \
-  FCSPH_RAISE((k_col_inv<T, EPI_PPE_ADD>))
-  FCSPH_RAISE_INV(double)
-  FCSPH_RAISE_INV(float)
-#undef FCSPH_RAISE_INV
+  FCSPH_RAISE((k_col_inv<double>))
+  FCSPH_RAISE((k_col_inv<float>))
 #undef FCSPH_RAISE
   return cudaSuccess;
 }
@@ -829,29 +824,16 @@ static cudaError_t col_inv_common(fcsph_ctx* c, int epi, const void* spec, int n
   dim3 grid((g.nx + 2 * Pp - 1) / (2 * Pp), g.batch);
   const FftPlan& P = epi >= EPI_PPE_SOLVE ? c->plan_py : c->plan_y;
   const typename CT<T>::t* pool = PoolOf<T>::get(c);
+  if (epi < EPI_OUT || epi > EPI_PPE_ADD) return cudaErrorInvalidValue;
   ea.status = c->dstatus;
   static const int kinds[7] = {FCSPH_PROF_COL_OUT, FCSPH_PROF_COL_MOM, FCSPH_PROF_COL_DIV, FCSPH_PROF_COL_CORR,
                                FCSPH_PROF_COL_PPE, FCSPH_PROF_COL_PPE, FCSPH_PROF_COL_PPE};
   ProfScope ps(c, kinds[epi]);
-  cudaError_t e = cudaSuccess;
-#define FCSPH_LAUNCH_INV(E_)                                                                                     \
-  case E_:                                                                                                       \
-    e = set_smem(k_col_inv<T, E_>, smem);                                                                        \
-    if (e != cudaSuccess) return e;                                                                              \
-    k_col_inv<T, E_><<<grid, kThreads, smem, c->stream>>>(g, (const typename CT<T>::t*)spec, fs, bs, nout, lines, P, \
-                                                          pool, ea, Pp, ls);                                     \
-    break;
-  switch (epi) {
-    FCSPH_LAUNCH_INV(EPI_OUT)
-    FCSPH_LAUNCH_INV(EPI_MOM)
-    FCSPH_LAUNCH_INV(EPI_DIV)
-    FCSPH_LAUNCH_INV(EPI_CORR)
-    FCSPH_LAUNCH_INV(EPI_PPE_SOLVE)
-    FCSPH_LAUNCH_INV(EPI_PPE_RESID)
-    FCSPH_LAUNCH_INV(EPI_PPE_ADD)
-    default: return cudaErrorInvalidValue;
-  }
-#undef FCSPH_LAUNCH_INV
+  cudaError_t e = set_smem(k_col_inv<T>, smem);
+  if (e != cudaSuccess) return e;
+  k_col_inv<T><<<grid, kThreads, smem, c->stream>>>(g, (const typename CT<T>::t*)spec, fs, bs, nout, lines, P, pool, ea,
+                                                    Pp, ls, epi);
+
   c->launches++;
   return cudaGetLastError();
 }

@@ -242,6 +242,23 @@ bool factor_direct(int n, Plan1* p) {
   return true;
 }
 
+// exp(-k^2 h^2 / 4) for the m angular wavenumbers 2 pi kappa / (m d) of an
+// m-point periodic axis (kappa signed, Nyquist positive), first `count` entries.
+std::vector<double> gauss_axis(int m, double d, double h, int count) {
+  std::vector<double> out(count);
+  for (int a = 0; a < count; ++a) {
+    const int kappa = (2 * a <= m) ? a : a - m;
+    const qreal k = 2 * QPI * (qreal)kappa / ((qreal)m * (qreal)d);
+    const qreal e = k * k * (qreal)h * (qreal)h / 4;
+#if defined(__x86_64__)
+    out[a] = (double)expq(-e);
+#else
+    out[a] = (double)expl(-e);
+#endif
+  }
+  return out;
+}
+
 int smooth_at_least(int n) {
   for (int m = n;; ++m) {
     int r = m;
@@ -251,6 +268,46 @@ int smooth_at_least(int n) {
   }
 }
 
+static bool is_prime(int n) {
+  if (n < 2) return false;
+  for (int q = 2; q * q <= n; ++q)
+    if (n % q == 0) return false;
+  return true;
+}
+
+static long long powmod(long long b, long long e, long long m) {
+  long long r = 1;
+  b %= m;
+  while (e > 0) {
+    if (e & 1) r = r * b % m;
+    b = b * b % m;
+    e >>= 1;
+  }
+  return r;
+}
+
+// Smallest primitive root of the prime p.
+static int primitive_root(int p) {
+  std::vector<int> qs;
+  int r = p - 1;
+  for (int q = 2; q * q <= r; ++q)
+    if (r % q == 0) {
+      qs.push_back(q);
+      while (r % q == 0) r /= q;
+    }
+  if (r > 1) qs.push_back(r);
+  for (int g = 2; g < p; ++g) {
+    bool ok = true;
+    for (int q : qs)
+      if (powmod(g, (p - 1) / q, p) == 1) {
+        ok = false;
+        break;
+      }
+    if (ok) return g;
+  }
+  return 1;
+}
+
 FftPlan make_plan(int n, Pool* pool, std::vector<double>* bre, std::vector<double>* bim) {
   FftPlan P;
   std::vector<double> r, i;
@@ -258,6 +315,30 @@ FftPlan make_plan(int n, Pool* pool, std::vector<double>* bre, std::vector<doubl
     roots(n, &r, &i);
     P.base.tw = pool->add(r, i);
     P.bs = 0;
+    return P;
+  }
+  if (is_prime(n) && factor_direct(n - 1, &P.sub)) {
+    // Rader: X_{g^-m} = x_0 + (a * b)_m, a_q = x_{g^q}, b_s = w^{g^-s}, cyclic of length n - 1
+    P.rd = 1;
+    plan_set_radices(&P.base, n, nullptr, 0);
+    const int m = n - 1;
+    roots(m, &r, &i);
+    P.sub.tw = pool->add(r, i);
+    const long long g = primitive_root(n);
+    const long long ginv = powmod(g, n - 2, n);
+    std::vector<double> gi(m), si(m), z(m, 0.0);
+    bre->assign(m, 0.0);
+    bim->assign(m, 0.0);
+    for (int q = 0; q < m; ++q) {
+      gi[q] = (double)powmod(g, q, n);
+      si[q] = (double)powmod(ginv, q, n);
+      const qreal ang = -2 * QPI * (qreal)((long long)si[q]) / (qreal)n;
+      (*bre)[q] = (double)qcos(ang);
+      (*bim)[q] = (double)qsin(ang);
+    }
+    P.gidx = pool->add(gi, z);
+    P.sidx = pool->add(si, z);
+    P.bhat = pool->add(std::vector<double>(m, 0.0), std::vector<double>(m, 0.0));
     return P;
   }
   P.bs = 1;

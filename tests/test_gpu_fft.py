@@ -7,7 +7,7 @@ from gpu_common import binding, torch_cuda
 
 # extended lengths (n + 25), PPE even extensions 2(n-1), smooth variants and small edge cases
 LENGTHS = [1, 2, 3, 4, 5, 7, 8, 9, 11, 16, 27, 31, 37, 64, 72, 81, 89, 90, 96, 126, 150, 153, 243, 254, 256, 280,
-           281, 510, 512, 537, 540, 567, 576, 1000, 1022, 1049, 1050, 2046]
+           281, 510, 512, 537, 540, 567, 576, 1000, 1022, 1049, 1050, 2046, 143, 221, 187, 289]
 
 
 @pytest.mark.gpu
