@@ -45,6 +45,10 @@ def parse():
     ap.add_argument("--prec", default="f64", choices=["f32", "f64"])
     ap.add_argument("--refine", type=int, default=0)
     ap.add_argument("--no-compare", action="store_true")
+    ap.add_argument("--workload", default="cavity", choices=["cavity", "uneven", "serve"],
+                    help="cavity: the 256^2 lid cavity (default); uneven: 64 solves of sizes 64^2..512^2 "
+                         "submitted together; serve: a Poisson request stream (2D part)")
+    ap.add_argument("--serve-seconds", type=float, default=1.0)
     ap.add_argument("--profile-case", action="store_true",
                     help="no timing: 2 eager RK3 steps of the workload (for ncu captures on a small batch)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
@@ -411,6 +415,55 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_serving(args):
+    """Configurations 4 and 5 through the continuous-batching server, and the same
+    requests run one at a time on the plain FP64 path (batch 1)."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2606_06247_gb300 import inputs
+    from paper_2606_06247_gb300.serve import Request, Server, summarize
+    steps = args.steps
+    if args.workload == "uneven":
+        spec = inputs.uneven_batch(64, seed=2024)
+        reqs = lambda: [Request(i, d["kind"], d["n"], d["re"], steps, 0.0) for i, d in enumerate(spec)]
+        desc = (f"64 independent solves, sizes uniform on 64^2..512^2, Re log-uniform [100, 5000], even index cavity "
+                f"(G8) / odd channel (G4 if Re < 625 else G8), {steps} RK3 steps each, submitted together")
+    else:
+        spec = inputs.poisson_requests(rate=200.0, duration=args.serve_seconds, seed=7, sizes=(64, 128, 256, 512, 1024),
+                                       steps=(50, 500))
+        reqs = lambda: [Request(i, d["kind"], d["n"], float(np.exp(np.random.default_rng(i).uniform(np.log(100), np.log(5000)))),
+                                max(1, d["steps"] * steps // 500), d["t"]) for i, d in enumerate(spec)]
+        desc = (f"Poisson arrivals 200/s for {args.serve_seconds} s, 2D cavity/channel of 64^2..1024^2, "
+                f"each 50-500 RK3 steps scaled by {steps}/500 (3D channel requests not built)")
+    torch.cuda.synchronize()
+    srv = Server(prec=args.prec, capacity=8)
+    rs = reqs()
+    wall = srv.run(rs)
+    torch.cuda.synchronize()
+    served = summarize(rs, wall)
+    # serial baseline: plain FP64, one request at a time, batch 1
+    base = reqs()
+    t0 = time.perf_counter()
+    for r in base:
+        s1 = Server(prec="f64", capacity=1)
+        r.arrival = 0.0
+        s1.submit(r)
+        while not s1.idle():
+            s1.tick(0.0)
+    torch.cuda.synchronize()
+    serial = summarize(base, time.perf_counter() - t0)
+    print(json.dumps({
+        "metric": METRIC, "value": served["particle_updates_per_s"], "unit": "particle-updates/s", "n_gpus": 1,
+        "steps": steps, "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
+        "config": {"workload": desc, "precision": args.prec, "slots_per_size_class": 8},
+        "latency_ms": {"p50": served["step_latency_ms_p50"], "p99": served["step_latency_ms_p99"]},
+        "served": served, "serial_plain_fp64": serial,
+        "speedup_vs_serial": served["particle_updates_per_s"] / serial["particle_updates_per_s"]}))
+
+
 def run_profile_case(args):
     """Two eager RK3 steps of the workload with every kernel launched on its own
     (no graph), for kernel-level captures; prints the launch count."""
@@ -432,6 +485,8 @@ if __name__ == "__main__":
     a = parse()
     if a.profile_case:
         run_profile_case(a)
+    elif a.workload in ("uneven", "serve") and a.impl == "ours":
+        run_serving(a)
     elif a.impl == "reference":
         run_reference(a)
     else:

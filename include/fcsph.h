@@ -95,6 +95,8 @@ typedef struct {
   double u_bottom, u_top;  /* tangential wall velocity at y = 0 and y = Ly    */
   int scheme;          /* FCSPH_SCHEME_FOP or FCSPH_SCHEME_RK3                 */
   int use_graph;       /* 1: capture one step in a CUDA graph and replay it   */
+  const double* nu_inst;   /* device [batch] or NULL: per-instance viscosity (overrides nu) */
+  const double* fx_inst;   /* device [batch] or NULL: per-instance body force x (overrides force_x) */
 } fcsph_step_params;
 
 /* Create a context for one grid shape: builds the FC tables (Sec. 4; FP64,

@@ -56,7 +56,8 @@ class fcsph_step_params(ctypes.Structure):
     _fields_ = [("nu", ctypes.c_double), ("rho", ctypes.c_double), ("dt", ctypes.c_double),
                 ("force_x", ctypes.c_double), ("force_y", ctypes.c_double),
                 ("u_bottom", ctypes.c_double), ("u_top", ctypes.c_double),
-                ("scheme", ctypes.c_int), ("use_graph", ctypes.c_int)]
+                ("scheme", ctypes.c_int), ("use_graph", ctypes.c_int),
+                ("nu_inst", ctypes.c_void_p), ("fx_inst", ctypes.c_void_p)]
 
 
 def _load():
@@ -213,9 +214,13 @@ class Context:
         return r.value if want_resid else None
 
     def isph_step(self, u, v, p, fu, fv, nsteps, nu, rho=1.0, dt=1e-3, force=(0.0, 0.0), u_bottom=0.0, u_top=0.0,
-                  scheme="fop", use_graph=True):
+                  scheme="fop", use_graph=True, nu_inst=None, fx_inst=None):
+        """nu_inst / fx_inst: optional CUDA float64 tensors [batch] of per-instance
+        viscosity and x body force (override nu / force[0])."""
         st = fcsph_state(u.data_ptr(), v.data_ptr(), p.data_ptr(), fu.data_ptr(), fv.data_ptr())
-        prm = fcsph_step_params(nu, rho, dt, force[0], force[1], u_bottom, u_top, SCHEME[scheme], 1 if use_graph else 0)
+        prm = fcsph_step_params(nu, rho, dt, force[0], force[1], u_bottom, u_top, SCHEME[scheme], 1 if use_graph else 0,
+                                nu_inst.data_ptr() if nu_inst is not None else None,
+                                fx_inst.data_ptr() if fx_inst is not None else None)
         self._ck(lib.isph_step(self.h, ctypes.byref(st), nsteps, ctypes.byref(prm)))
 
     def sync(self):

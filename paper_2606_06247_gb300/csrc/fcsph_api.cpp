@@ -455,6 +455,8 @@ static fcsph_status one_step(fcsph_ctx* c, const fcsph_state* s, const fcsph_ste
     sd.fy = prm->force_y;
     sd.u_bottom = prm->u_bottom;
     sd.u_top = prm->u_top;
+    sd.nu_inst = prm->nu_inst;
+    sd.fx_inst = prm->fx_inst;
     if (nsub == 3) {
       sd.a = A3[k];
       sd.g = G3[k];
@@ -488,7 +490,8 @@ fcsph_status isph_step(fcsph_ctx* c, const fcsph_state* s, int nsteps, const fcs
   }
   std::vector<double> key = {(double)(uintptr_t)s->u, (double)(uintptr_t)s->v, (double)(uintptr_t)s->p,
                              (double)(uintptr_t)s->fu, (double)(uintptr_t)s->fv, prm->nu, prm->rho, prm->dt,
-                             prm->force_x, prm->force_y, prm->u_bottom, prm->u_top, (double)prm->scheme};
+                             prm->force_x, prm->force_y, prm->u_bottom, prm->u_top, (double)prm->scheme,
+                             (double)(uintptr_t)prm->nu_inst, (double)(uintptr_t)prm->fx_inst};
   if (!c->gexec || key != c->graph_key) {
     if (c->gexec) {
       cudaGraphExecDestroy(c->gexec);

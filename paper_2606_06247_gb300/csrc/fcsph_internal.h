@@ -128,6 +128,8 @@ struct GridDev {
 struct StepDev {
   double nu, rho, dt, fx, fy, u_bottom, u_top;
   double a, g, z;        // substep coefficients
+  const double* nu_inst; // per-instance overrides (device) or null
+  const double* fx_inst;
 };
 
 struct fcsph_ctx {

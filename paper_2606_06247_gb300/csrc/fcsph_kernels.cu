@@ -386,6 +386,7 @@ struct EpiArgs {
   double* phi;        // PPE_*: out phi / residual / accumulate
   void* phi_any;      // PPE_SOLVE in the context's I/O type when not double
   int phi_double;
+  int mom_comp;       // EPI_MOM: 0 both components (6 outputs), 1 u only, 2 v only (3 outputs)
   StepDev s;
   // fused forward: nf fields, table, plan, output spectra, dct
   int fwd_nf;
@@ -447,20 +448,31 @@ __global__ void __launch_bounds__(kThreads) k_col_inv(GridDev g, const typename 
         }
       } else if (EPI == EPI_MOM) {
         const double u = ea.u[id], v = ea.v[id];
-        const double Fu = u * val[0] + v * val[1] - ea.s.nu * val[2];
-        const double Fv = u * val[3] + v * val[4] - ea.s.nu * val[5];
-        double us = u + ea.s.dt * (-ea.s.g * Fu - ea.s.z * ea.fu[id] + ea.s.a * ea.s.fx);
-        double vs = v + ea.s.dt * (-ea.s.g * Fv - ea.s.z * ea.fv[id] + ea.s.a * ea.s.fy);
-        if (j == 0) { us = ea.s.u_bottom; vs = 0.0; }
-        if (j == ny - 1) { us = ea.s.u_top; vs = 0.0; }
-        if (g.x_walls && (i == 0 || i == g.nx - 1)) { us = 0.0; vs = 0.0; }
-        ea.fu[id] = Fu;
-        ea.fv[id] = Fv;
-        ea.us[id] = us;
-        ea.vs[id] = vs;
-        if (!isfinite(us) || !isfinite(vs)) atomicOr(ea.status, 1);
-        nv[0][w] = us;
-        nv[1][w] = vs;
+        const double nu = ea.s.nu_inst ? ea.s.nu_inst[b] : ea.s.nu;
+        int slot = 0;
+        if (ea.mom_comp != 2) {
+          const double fx = ea.s.fx_inst ? ea.s.fx_inst[b] : ea.s.fx;
+          const double Fu = u * val[0] + v * val[1] - nu * val[2];
+          double us = u + ea.s.dt * (-ea.s.g * Fu - ea.s.z * ea.fu[id] + ea.s.a * fx);
+          if (j == 0) us = ea.s.u_bottom;
+          if (j == ny - 1) us = ea.s.u_top;
+          if (g.x_walls && (i == 0 || i == g.nx - 1)) us = 0.0;
+          ea.fu[id] = Fu;
+          ea.us[id] = us;
+          if (!isfinite(us)) atomicOr(ea.status, 1);
+          nv[slot++][w] = us;
+        }
+        if (ea.mom_comp != 1) {
+          const int o = ea.mom_comp == 2 ? 0 : 3;
+          const double Fv = u * val[o] + v * val[o + 1] - nu * val[o + 2];
+          double vs = v + ea.s.dt * (-ea.s.g * Fv - ea.s.z * ea.fv[id] + ea.s.a * ea.s.fy);
+          if (j == 0 || j == ny - 1) vs = 0.0;
+          if (g.x_walls && (i == 0 || i == g.nx - 1)) vs = 0.0;
+          ea.fv[id] = Fv;
+          ea.vs[id] = vs;
+          if (!isfinite(vs)) atomicOr(ea.status, 1);
+          nv[slot][w] = vs;
+        }
       } else if (EPI == EPI_DIV) {
         const double bb = ea.s.rho / (ea.s.a * ea.s.dt) * val[0];
         ea.bvec[id] = bb;
@@ -786,26 +798,34 @@ cudaError_t launch_row_sym(fcsph_ctx* c, int prec, const void* sp_in, void* sp_o
                            int bc, int kind) {
   const size_t cb = prec == FCSPH_F64 ? sizeof(double2) : sizeof(float2);
   const size_t per = (size_t)(2 * ops.nin + 2 * ops.nout) * c->plan_x.line_len() * cb;
-  bool single = ops.nin > 1;
+  bool single = true;
   for (int o = 0; o < ops.nout && single; ++o) single = ops.nterm[o] == 1 && (o == 0 || ops.field[o][0] >= ops.field[o - 1][0]);
   if (per <= kSmemBudget || !single) return row_sym_any(c, prec, sp_in, sp_out, ops, scale, bc, kind);
   const size_t fs = (size_t)c->gd.rows * c->gd.nx * cb;
+  const size_t line = (size_t)c->plan_x.line_len() * cb;
+  int gmax = (int)((kSmemMax / line - 2) / 2);  // outputs per launch with one input: (2 + 2 g) lines
+  if (gmax < 1) return cudaErrorInvalidValue;
   for (int f = 0; f < ops.nin; ++f) {
-    RowOps sub;
-    memset(&sub, 0, sizeof(sub));
-    sub.nin = 1;
-    int first = -1;
+    int first = -1, cnt = 0;
     for (int o = 0; o < ops.nout; ++o)
       if (ops.field[o][0] == f) {
         if (first < 0) first = o;
+        ++cnt;
+      }
+    for (int g0 = 0; g0 < cnt; g0 += gmax) {
+      RowOps sub;
+      memset(&sub, 0, sizeof(sub));
+      sub.nin = 1;
+      for (int o = g0; o < cnt && o < g0 + gmax; ++o) {
         sub.nterm[sub.nout] = 1;
         sub.field[sub.nout][0] = 0;
-        sub.op[sub.nout][0] = ops.op[o][0];
+        sub.op[sub.nout][0] = ops.op[first + o][0];
         sub.nout++;
       }
-    if (sub.nout == 0) continue;
-    cudaError_t e = row_sym_any(c, prec, (const char*)sp_in + f * fs, (char*)sp_out + first * fs, sub, scale, bc, kind);
-    if (e != cudaSuccess) return e;
+      cudaError_t e = row_sym_any(c, prec, (const char*)sp_in + f * fs, (char*)sp_out + (first + g0) * fs, sub, scale,
+                                  bc, kind);
+      if (e != cudaSuccess) return e;
+    }
   }
   return cudaSuccess;
 }
@@ -918,14 +938,28 @@ cudaError_t launch_step_mom(fcsph_ctx* c, const StepDev& s, const void* spec6, c
   ea.us = us;
   ea.vs = vs;
   ea.s = s;
-  ea.fwd_nf = 2;
   ea.fwd_dct = 0;
   ea.fwdE = c->dE;
   ea.fwdP = c->plan_y;
-  ea.fwd_spec = spec2;
   ea.fwd_fstride = (size_t)c->gd.rows * c->gd.nx;
   ea.fwd_bstride = 2 * ea.fwd_fstride;
-  return col_inv(c, c->prec.fft_prec, EPI_MOM, spec6, 6, ea);
+  const size_t cb = c->prec.fft_prec == FCSPH_F64 ? sizeof(double2) : sizeof(float2);
+  if (2 * 6 * (size_t)col_ls(c) * cb <= kSmemMax) {
+    ea.mom_comp = 0;
+    ea.fwd_nf = 2;
+    ea.fwd_spec = spec2;
+    return col_inv(c, c->prec.fft_prec, EPI_MOM, spec6, 6, ea);
+  }
+  // one component per launch: u from outputs 0-2, v from outputs 3-5
+  const size_t fsb = ea.fwd_fstride * cb;
+  ea.fwd_nf = 1;
+  ea.mom_comp = 1;
+  ea.fwd_spec = spec2;
+  cudaError_t e = col_inv(c, c->prec.fft_prec, EPI_MOM, spec6, 3, ea);
+  if (e != cudaSuccess) return e;
+  ea.mom_comp = 2;
+  ea.fwd_spec = (char*)spec2 + fsb;
+  return col_inv(c, c->prec.fft_prec, EPI_MOM, (const char*)spec6 + 3 * fsb, 3, ea);
 }
 
 cudaError_t launch_step_div(fcsph_ctx* c, const StepDev& s, const void* spec1, double* b, void* spec_dct) {

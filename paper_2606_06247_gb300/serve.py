@@ -1,0 +1,219 @@
+"""Continuous batching of independent wall-bounded solves on one GPU.
+
+Requests of different sizes and kinds (lid-driven cavity / channel) arrive
+over time; each asks for a number of RK3 projection steps.  A size class
+(kind, n, kernel family) owns one fcsph context with a fixed number of slots
+(its batch) and device-resident state for every slot; the class advances all
+its slots with one CUDA-graph step per tick on its own stream, so classes
+overlap on the GPU.  Between ticks, finished requests are retired (their
+state copied to the host) and queued requests take the freed slots.  New
+classes are admitted only while the estimated device footprint of all
+classes fits the memory budget.
+
+Every slot is an independent instance of the step: its result does not
+depend on which slot it occupies or on what the other slots hold, so a
+request's result is the same alone and in the mix (bitwise, same precision).
+
+The per-request Reynolds number enters through per-instance viscosity (and,
+for the channel, body force): cavity nu = 1/Re (lid speed 1, side 1);
+channel u_max = 1, nu = 1/Re, F = 8 nu.
+"""
+import collections
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+from . import binding as b
+
+DT = 1e-3
+
+
+@dataclass
+class Request:
+    rid: int
+    kind: str          # "cavity" or "channel"
+    n: int             # n x n particles
+    re: float
+    steps: int
+    arrival: float = 0.0
+    # filled by the server
+    done_steps: int = 0
+    latencies_ms: list = field(default_factory=list)
+    result: dict = None
+    t_admit: float = None
+    t_done: float = None
+
+
+def family_for(kind, re):
+    """Kernel family per the paper's guidance: G4 at low Re, G8 at high Re (cavity always G8)."""
+    if kind == "cavity":
+        return "G8"
+    return "G4" if re < 625 else "G8"
+
+
+def class_key(req):
+    return (req.kind, req.n, family_for(req.kind, req.re))
+
+
+def footprint_bytes(n, capacity, prec):
+    """Device bytes of one class: state (5 fields), workspace (6), spectra."""
+    my = n + 25
+    hy = my // 2 + 1
+    rows = max(hy, n)
+    cb = 16 if prec == "f64" else 8
+    return capacity * (11 * n * n * 8 + 8 * rows * n * cb + rows * n * 16)
+
+
+class SizeClass:
+    def __init__(self, key, capacity, prec, device):
+        kind, n, fam = key
+        self.key, self.kind, self.n, self.capacity, self.prec = key, kind, n, capacity, prec
+        x_walls = kind == "cavity"
+        dy = 1.0 / (n - 1)
+        lx = 1.0 if x_walls else n * dy
+        self.stream = torch.cuda.Stream(device=device)
+        with torch.cuda.stream(self.stream):
+            self.ctx = b.Context(n, n, lx, 1.0, x_walls=x_walls, batch=capacity, family=fam, h_over_dx=1.3,
+                                 prec=prec, stream=self.stream.cuda_stream)
+            z = torch.zeros((capacity, n, n), dtype=torch.float64, device=device)
+            self.u, self.v, self.p, self.fu, self.fv = [z.clone() for _ in range(5)]
+            self.nu = torch.full((capacity,), 1e-2, dtype=torch.float64, device=device)
+            self.fx = torch.zeros((capacity,), dtype=torch.float64, device=device)
+        self.slots = [None] * capacity
+        self.ev0 = torch.cuda.Event(enable_timing=True)
+        self.ev1 = torch.cuda.Event(enable_timing=True)
+        self.pending_event = False
+
+    def free_slots(self):
+        return [i for i, r in enumerate(self.slots) if r is None]
+
+    def active(self):
+        return [i for i, r in enumerate(self.slots) if r is not None]
+
+    def admit(self, slot, req):
+        nu = 1.0 / req.re
+        with torch.cuda.stream(self.stream):
+            for t in (self.u, self.v, self.p, self.fu, self.fv):
+                t[slot].zero_()
+            self.nu[slot] = nu
+            self.fx[slot] = 8.0 * nu if self.kind == "channel" else 0.0
+        self.slots[slot] = req
+
+    def step(self):
+        """Queue one RK3 step of every slot on this class's stream."""
+        with torch.cuda.stream(self.stream):
+            self.ev0.record(self.stream)
+            self.ctx.isph_step(self.u, self.v, self.p, self.fu, self.fv, 1, nu=1e-2, rho=1.0, dt=DT,
+                               u_top=1.0 if self.kind == "cavity" else 0.0, scheme="rk3", use_graph=True,
+                               nu_inst=self.nu, fx_inst=self.fx)
+            self.ev1.record(self.stream)
+        self.pending_event = True
+
+    def finish_tick(self, now):
+        """Wait for this tick's step, account latency, retire finished requests."""
+        retired = []
+        if not self.pending_event:
+            return retired
+        self.ev1.synchronize()
+        ms = self.ev0.elapsed_time(self.ev1)
+        self.pending_event = False
+        for i in self.active():
+            r = self.slots[i]
+            r.done_steps += 1
+            r.latencies_ms.append(ms)
+            if r.done_steps >= r.steps:
+                r.result = {"u": self.u[i].cpu().numpy(), "v": self.v[i].cpu().numpy(), "p": self.p[i].cpu().numpy()}
+                r.t_done = now
+                self.slots[i] = None
+                retired.append(r)
+        return retired
+
+
+class Server:
+    def __init__(self, prec="f64", capacity=8, mem_budget=None, device=None):
+        self.device = device if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.prec = prec
+        self.capacity = capacity
+        if mem_budget is None:
+            free, _ = torch.cuda.mem_get_info(self.device)
+            mem_budget = int(0.8 * free)
+        self.mem_budget = mem_budget
+        self.classes = collections.OrderedDict()
+        self.queue = collections.deque()
+        self.done = []
+
+    def used_bytes(self):
+        return sum(footprint_bytes(c.n, c.capacity, c.prec) for c in self.classes.values())
+
+    def submit(self, req):
+        self.queue.append(req)
+
+    def _admit(self, now):
+        waiting = collections.deque()
+        while self.queue:
+            req = self.queue.popleft()
+            key = class_key(req)
+            cls = self.classes.get(key)
+            if cls is None:
+                need = footprint_bytes(req.n, self.capacity, self.prec)
+                if self.used_bytes() + need > self.mem_budget:
+                    waiting.append(req)
+                    continue
+                cls = SizeClass(key, self.capacity, self.prec, self.device)
+                self.classes[key] = cls
+            free = cls.free_slots()
+            if not free:
+                waiting.append(req)
+                continue
+            req.t_admit = now
+            cls.admit(free[0], req)
+        self.queue = waiting
+
+    def _evict_idle(self):
+        """Drop classes with no active slot and no queued request, freeing their memory."""
+        wanted = {class_key(r) for r in self.queue}
+        for key in list(self.classes):
+            c = self.classes[key]
+            if not c.active() and key not in wanted:
+                del self.classes[key]
+
+    def tick(self, now):
+        self._admit(now)
+        busy = [c for c in self.classes.values() if c.active()]
+        for c in busy:
+            c.step()
+        for c in busy:
+            self.done.extend(c.finish_tick(now))
+        if self.queue:
+            self._evict_idle()
+        return len(busy)
+
+    def idle(self):
+        return not self.queue and not any(c.active() for c in self.classes.values())
+
+    def run(self, requests, time_scale=1.0, max_wall=None):
+        """Drive arrivals in (scaled) real time until every request finishes."""
+        pending = sorted(requests, key=lambda r: r.arrival)
+        t0 = time.perf_counter()
+        k = 0
+        while k < len(pending) or not self.idle():
+            now = (time.perf_counter() - t0) / time_scale
+            while k < len(pending) and pending[k].arrival <= now:
+                self.submit(pending[k])
+                k += 1
+            if self.tick(now) == 0 and k < len(pending) and not self.queue:
+                time.sleep(max(0.0, (pending[k].arrival - now) * time_scale))
+            if max_wall and time.perf_counter() - t0 > max_wall:
+                break
+        return time.perf_counter() - t0
+
+
+def summarize(requests, wall_s):
+    lat = np.concatenate([np.asarray(r.latencies_ms) for r in requests if r.latencies_ms]) if requests else np.zeros(0)
+    updates = sum(r.n * r.n * r.done_steps for r in requests)
+    return {"requests": len(requests), "finished": sum(1 for r in requests if r.result is not None),
+            "particle_updates": updates, "wall_s": wall_s, "particle_updates_per_s": updates / wall_s if wall_s else None,
+            "step_latency_ms_p50": float(np.percentile(lat, 50)) if lat.size else None,
+            "step_latency_ms_p99": float(np.percentile(lat, 99)) if lat.size else None}

@@ -85,3 +85,25 @@ def test_bench_workload_256_batch32_graph_sampled():
         print(f"bench workload instance {k}: parity (u, v, p) {errs} floor {fl}")
         for e, f in zip(errs, fl):
             assert e < parity_tol(f)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("n,xw", [(512, True), (1024, False)])
+def test_large_grid_step_runs_and_matches_small_batch_rows(n, xw):
+    """The large size classes (Bluestein lines of ~2048 points) split the
+    momentum epilogue and the row pass to fit shared memory; one RK3 step must
+    run and give finite fields, identical for an instance alone and in a batch."""
+    torch = torch_cuda()
+    b = binding()
+    lx = 1.0 if xw else n / (n - 1)
+    outs = []
+    for batch in (1, 2):
+        ctx = b.Context(n, n, lx, 1.0, x_walls=xw, batch=batch, family="G8", h_over_dx=1.3)
+        z = torch.zeros((batch, n, n), dtype=torch.float64, device="cuda")
+        u, v, p, fu, fv = [z.clone() for _ in range(5)]
+        ctx.isph_step(u, v, p, fu, fv, 1, nu=1e-3, rho=1.0, dt=1e-3, u_top=1.0 if xw else 0.0,
+                      force=(0.0 if xw else 8e-3, 0.0), scheme="rk3")
+        ctx.sync()
+        outs.append(u[0].cpu().numpy())
+    assert np.all(np.isfinite(outs[0])) and np.abs(outs[0]).max() > 0
+    np.testing.assert_array_equal(outs[0], outs[1])
