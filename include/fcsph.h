@@ -18,9 +18,9 @@
  * Extended grid.  my = ny + n_cont; mx = nx (periodic x) or nx + n_cont.
  * Pointers.  Every field pointer is a DEVICE pointer owned by the caller and
  *   must stay valid until the work queued on the context's stream finishes.
- *   Field element type: double when the context precision is FCSPH_F64,
- *   float when FCSPH_F32 -- except the time-stepping state of isph_step,
- *   which is always double.  Host pointers are marked "host".
+ *   Field element type: double when the context precision is FCSPH_F64 or
+ *   FCSPH_F32X2, float when FCSPH_F32 -- except the time-stepping state of
+ *   isph_step, which is always double.  Host pointers are marked "host".
  * Asynchrony.  Calls enqueue work on the stream given at fcsph_create and
  *   return; fcsph_sync waits and reports device-side errors.  No call aborts
  *   the process and no kernel traps.
@@ -47,7 +47,10 @@ typedef enum {
   FCSPH_EUNSUPPORTED = 6 /* valid request this build does not implement       */
 } fcsph_status;
 
-enum { FCSPH_F64 = 0, FCSPH_F32 = 1 };                 /* arithmetic of FFTs and symbols */
+/* arithmetic of FFTs and symbols: FP64; FP32; FP32x2 = double-float (value =
+ * hi + lo, two FP32 numbers, 48-bit significand) run on the FP32 units.
+ * F32X2 contexts use double fields like F64 ones. */
+enum { FCSPH_F64 = 0, FCSPH_F32 = 1, FCSPH_F32X2 = 2 };
 enum { FCSPH_FC_GRAM = 0, FCSPH_FC_PAPER = 1 };         /* FC table construction          */
 enum { FCSPH_DIRICHLET = 0, FCSPH_NEUMANN = 1 };        /* boundary data type (Sec. 4.4)  */
 enum { FCSPH_G2 = 1, FCSPH_G4 = 2, FCSPH_G6 = 3, FCSPH_G8 = 4, FCSPH_G10 = 5 }; /* Gaussian order 2n */
@@ -152,7 +155,8 @@ fcsph_status fcsph_sync(fcsph_ctx* ctx);
  * library's FFT engine (mixed radix Stockham / Bluestein), for testing the
  * engine.  dir = -1 forward (exp(-2 pi i k m/n)), +1 inverse (unscaled).
  * in/out: device arrays of nlines*n complex (interleaved re, im) doubles
- * (prec FCSPH_F64) or floats (FCSPH_F32); in-place allowed. */
+ * (prec FCSPH_F64, or FCSPH_F32X2: double-float arithmetic, double I/O) or
+ * floats (FCSPH_F32); in-place allowed. */
 fcsph_status fcsph_dft(int n, int nlines, int dir, int prec, const void* in, void* out, void* stream);
 
 /* fcsph_dft without any allocation.  For callers that cannot allocate device

@@ -13,7 +13,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libfcsph.so")
 
-F64, F32 = 0, 1
+F64, F32, F32X2 = 0, 1, 2
+PREC = {"f64": F64, "f32": F32, "f32x2": F32X2}
 FC_GRAM, FC_PAPER = 0, 1
 DIRICHLET, NEUMANN = 0, 1
 FAMILY = {"G2": 1, "G4": 2, "G6": 3, "G8": 4, "G10": 5}
@@ -124,11 +125,15 @@ def fc_table(variant="gram", n_match=5, n_cont=25, bc=DIRICHLET, poly_deg=0):
     return out
 
 
-def fcsph_dft(x, direction=-1, stream=None):
-    """Batched DFT over the last axis of a complex CUDA tensor (engine test entry)."""
+def fcsph_dft(x, direction=-1, stream=None, double_float=False):
+    """Batched DFT over the last axis of a complex CUDA tensor (engine test entry).
+    double_float: complex128 in and out, arithmetic in FP32 pairs (FCSPH_F32X2)."""
     import torch
     assert x.is_cuda and x.is_complex() and x.is_contiguous()
     prec = F64 if x.dtype == torch.complex128 else F32
+    if double_float:
+        assert prec == F64
+        prec = F32X2
     n = x.shape[-1]
     out = torch.empty_like(x)
     _check(lib.fcsph_dft(n, x.numel() // n if n else 0, direction, prec, _ptr(x), _ptr(out), _stream(stream)))
@@ -158,7 +163,7 @@ class Context:
         self.grid = fcsph_grid(nx, ny, lx, ly, 1 if x_walls else 0, batch)
         self.fc = fcsph_fc(FC_GRAM if variant == "gram" else FC_PAPER, n_match, n_cont, poly_deg)
         self.kernel = fcsph_kernel(FAMILY[family], h_over_dx)
-        self.prec = fcsph_precision(F64 if prec == "f64" else F32, refine)
+        self.prec = fcsph_precision(PREC[prec], refine)
         self.prec_name = prec
         self._tabs = []
         tp = []

@@ -41,7 +41,7 @@ fcsph_status cuda_fail(fcsph_ctx* c, cudaError_t e, const char* where) {
     if (e_ != cudaSuccess) return cuda_fail(c, e_, where); \
   } while (0)
 
-size_t cplx_bytes(int prec) { return prec == FCSPH_F64 ? 16 : 8; }
+size_t cplx_bytes(int prec) { return prec == FCSPH_F32 ? 8 : 16; }
 
 // Upload a host pool, fill Bluestein filters with the FP64 engine, then make
 // the FP32 copy.  `fill` lists (plan, filter) pairs.
@@ -49,6 +49,21 @@ struct Fill {
   FftPlan P;
   std::vector<double> re, im;
 };
+
+// FP32x2 copy of an FP64 pool already on the device (and synchronised): each
+// component split into hi = fl(x), lo = fl(x - hi).
+cudaError_t pool_ff_copy(const double2* d64, size_t n, void** out) {
+  std::vector<double2> h(n);
+  cudaError_t e = cudaMemcpy(h.data(), d64, n * sizeof(double2), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return e;
+  std::vector<float4> hf(n);
+  for (size_t i = 0; i < n; ++i) {
+    const float rh = (float)h[i].x, ih = (float)h[i].y;
+    hf[i] = make_float4(rh, (float)(h[i].x - (double)rh), ih, (float)(h[i].y - (double)ih));
+  }
+  if ((e = cudaMalloc(out, n * sizeof(float4))) != cudaSuccess) return e;
+  return cudaMemcpy(*out, hf.data(), n * sizeof(float4), cudaMemcpyHostToDevice);
+}
 
 fcsph_status upload_pool(fcsph_ctx* c, Pool& pool, std::vector<Fill>& fills, double2** d64, float2** d32,
                          cudaStream_t st) {
@@ -155,7 +170,7 @@ fcsph_status fcsph_create(const fcsph_grid* grid, const fcsph_fc* fc, const fcsp
     return fail(nullptr, FCSPH_EINVAL, "fcsph_create: nx, ny > 8192 not supported");
   if (kernel->family < FCSPH_G2 || kernel->family > FCSPH_G10 || !(kernel->h_over_dx >= 0))
     return fail(nullptr, FCSPH_EINVAL, "fcsph_create: bad kernel");
-  if (prec->fft_prec != FCSPH_F64 && prec->fft_prec != FCSPH_F32)
+  if (prec->fft_prec != FCSPH_F64 && prec->fft_prec != FCSPH_F32 && prec->fft_prec != FCSPH_F32X2)
     return fail(nullptr, FCSPH_EINVAL, "fcsph_create: bad precision");
   if (grid->x_walls && grid->nx < 2 * fc->n_match)
     return fail(nullptr, FCSPH_EINVAL, "fcsph_create: walled x needs nx >= 2*n_match");
@@ -204,6 +219,27 @@ fcsph_status fcsph_create(const fcsph_grid* grid, const fcsph_fc* fc, const fcsp
   c->plan_px = plan_for(g.x_walls ? 2 * (g.nx - 1) : g.nx, &pool, &fills);
   g.ex_off = pool.add(gauss_axis(g.mx, g.dx, g.h, g.mx), std::vector<double>(g.mx, 0.0));
   g.ey_off = pool.add(gauss_axis(g.my, g.dy, g.h, g.hy), std::vector<double>(g.hy, 0.0));
+  {
+    // Eq. 33 eigenvalues: DFT lam_k = 2 pi kappa / Lx (kappa signed, Nyquist positive), DCT-I lam = pi k / L
+    const double pi = 3.14159265358979323846;
+    std::vector<double> lx2(g.nx), ly2(g.ny);
+    for (int k = 0; k < g.nx; ++k) {
+      double lk;
+      if (g.x_walls) {
+        lk = pi * k / g.lx;
+      } else {
+        const int kappa = (2 * k <= g.nx) ? k : k - g.nx;
+        lk = 2.0 * pi * kappa / g.lx;
+      }
+      lx2[k] = lk * lk;
+    }
+    for (int l = 0; l < g.ny; ++l) {
+      const double ll = pi * l / g.ly;
+      ly2[l] = ll * ll;
+    }
+    g.lx2_off = pool.add(lx2, std::vector<double>(g.nx, 0.0));
+    g.ly2_off = pool.add(ly2, std::vector<double>(g.ny, 0.0));
+  }
 
   fcsph_status st = FCSPH_OK;
   cudaError_t e;
@@ -216,6 +252,7 @@ fcsph_status fcsph_create(const fcsph_grid* grid, const fcsph_fc* fc, const fcsp
     CREATE_CK(init_kernel_attributes(), "kernel attributes");
     st = upload_pool(c, pool, fills, &c->pool64, &c->pool32, c->stream);
     if (st != FCSPH_OK) goto fail_out;
+    CREATE_CK(pool_ff_copy(c->pool64, pool.re.size(), &c->poolff), "FP32x2 pool");
     const size_t ne = (size_t)g.n_cont * 2 * g.n_match;
     CREATE_CK(cudaMalloc((void**)&c->dE, 2 * ne * sizeof(double)), "cudaMalloc(E)");
     CREATE_CK(cudaMemcpy(c->dE, c->hE[0].data(), ne * sizeof(double), cudaMemcpyHostToDevice), "E upload");
@@ -250,6 +287,7 @@ fcsph_status fcsph_destroy(fcsph_ctx* c) {
   for (cudaEvent_t ev : c->ev_free) cudaEventDestroy(ev);
   cudaFree(c->pool64);
   cudaFree(c->pool32);
+  cudaFree(c->poolff);
   cudaFree(c->dE);
   cudaFree(c->spec_in);
   cudaFree(c->spec_out);
@@ -291,7 +329,7 @@ fcsph_status spectral_op(fcsph_ctx* c, const void* f, unsigned op_mask, int bc, 
     }
   const int p = c->prec.fft_prec;
   const void* fl[1] = {f};
-  FCSPH_CK(launch_col_fwd(c, p, 1, fl, p == FCSPH_F64, bc, c->spec_in, 0), "spectral_op fwd");
+  FCSPH_CK(launch_col_fwd(c, p, 1, fl, p != FCSPH_F32, bc, c->spec_in, 0), "spectral_op fwd");
   FCSPH_CK(launch_row_sym(c, p, c->spec_in, c->spec_out, ops, 1.0 / ((double)c->gd.mx * c->gd.my), bc, FCSPH_PROF_ROW_OP),
            "spectral_op row");
   FCSPH_CK(launch_col_out(c, c->spec_out, ops.nout, outs), "spectral_op inv");
@@ -311,7 +349,7 @@ fcsph_status spectral_div(fcsph_ctx* c, const void* fx, const void* fy, void* ou
   const int p = c->prec.fft_prec;
   const void* fl[2] = {fx, fy};
   void* outs[1] = {out};
-  FCSPH_CK(launch_col_fwd(c, p, 2, fl, p == FCSPH_F64, FCSPH_DIRICHLET, c->spec_in, 0), "spectral_div fwd");
+  FCSPH_CK(launch_col_fwd(c, p, 2, fl, p != FCSPH_F32, FCSPH_DIRICHLET, c->spec_in, 0), "spectral_div fwd");
   FCSPH_CK(launch_row_sym(c, p, c->spec_in, c->spec_out, ops, 1.0 / ((double)c->gd.mx * c->gd.my), FCSPH_DIRICHLET,
                           FCSPH_PROF_ROW_OP),
            "spectral_div row");
@@ -356,7 +394,7 @@ fcsph_status ppe_solve(fcsph_ctx* c, const void* rhs, void* phi, double* resid_o
   const size_t n = field_elems(c);
   double* b64 = c->work + 2 * n;
   double* phi64 = c->work + 3 * n;
-  if (p == FCSPH_F64) {
+  if (p != FCSPH_F32) {
     FCSPH_CK(cudaMemcpyAsync(b64, rhs, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream), "ppe rhs copy");
   } else {
     FCSPH_CK(cudaMemsetAsync(b64, 0, n * sizeof(double), c->stream), "ppe rhs clear");
@@ -366,7 +404,7 @@ fcsph_status ppe_solve(fcsph_ctx* c, const void* rhs, void* phi, double* resid_o
   const void* bl[1] = {b64};
   FCSPH_CK(launch_col_fwd(c, p, 1, bl, 1, FCSPH_DIRICHLET, c->spec_ppe, 1), "ppe fwd");
   FCSPH_CK(launch_row_ppe(c, p, c->spec_ppe, 0), "ppe row");
-  FCSPH_CK(launch_col_ppe_inv(c, p, c->spec_ppe, iters > 0 ? (void*)phi64 : phi, iters > 0 ? 1 : (p == FCSPH_F64),
+  FCSPH_CK(launch_col_ppe_inv(c, p, c->spec_ppe, iters > 0 ? (void*)phi64 : phi, iters > 0 ? 1 : (p != FCSPH_F32),
                               phi64, 0, nullptr, 0, nullptr),
            "ppe inv");
   if (iters > 0) {
@@ -538,7 +576,7 @@ fcsph_status fcsph_sync(fcsph_ctx* c) {
 }
 
 fcsph_status fcsph_dft(int n, int nlines, int dir, int prec, const void* in, void* out, void* stream) {
-  if (n < 1 || n > 65536 || nlines < 0 || (dir != -1 && dir != 1) || (prec != FCSPH_F64 && prec != FCSPH_F32) || !in || !out)
+  if (n < 1 || n > 65536 || nlines < 0 || (dir != -1 && dir != 1) || (prec != FCSPH_F64 && prec != FCSPH_F32 && prec != FCSPH_F32X2) || !in || !out)
     return fail(nullptr, FCSPH_EINVAL, "fcsph_dft: bad argument");
   if (nlines == 0) return FCSPH_OK;
   fcsph_ctx tmp;  // only for error reporting inside helpers
@@ -556,10 +594,16 @@ fcsph_status fcsph_dft(int n, int nlines, int dir, int prec, const void* in, voi
     cudaFree(d32);
     return fail(nullptr, s, c->err);
   }
-  cudaError_t e = launch_dft_lines(n, nlines, dir, prec, in, out, st, P, prec == FCSPH_F64 ? (const void*)d64 : (const void*)d32);
+  void* dff = nullptr;
+  cudaError_t e = cudaSuccess;
+  if (prec == FCSPH_F32X2) e = pool_ff_copy(d64, pool.re.size(), &dff);
+  if (e == cudaSuccess)
+    e = launch_dft_lines(n, nlines, dir, prec, in, out, st, P,
+                         prec == FCSPH_F64 ? (const void*)d64 : prec == FCSPH_F32 ? (const void*)d32 : dff);
   cudaError_t e2 = cudaStreamSynchronize(st);
   cudaFree(d64);
   cudaFree(d32);
+  cudaFree(dff);
   if (e != cudaSuccess) return fail(nullptr, FCSPH_ECUDA, std::string("fcsph_dft: ") + cudaGetErrorString(e));
   if (e2 != cudaSuccess) return fail(nullptr, FCSPH_ECUDA, std::string("fcsph_dft: ") + cudaGetErrorString(e2));
   return FCSPH_OK;

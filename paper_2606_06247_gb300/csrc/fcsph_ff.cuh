@@ -1,0 +1,89 @@
+// Double-float ("FP32x2") arithmetic: a value is the unevaluated sum hi + lo of
+// two FP32 numbers (|lo| <= ulp(hi)/2), a 48-bit significand carried by the
+// FP32 units.  GB300 runs FP32 at 64x its FP64 rate, so transforms in this
+// format reach FP64-class rounding (unit roundoff ~2^-48) at FP32-unit speed.
+//
+// Building blocks are the classical error-free transformations (Knuth's
+// TwoSum, Dekker's Fast2Sum, the FMA-based exact product); every operation
+// uses the _rn intrinsics, which the compiler never contracts or reorders.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace fcsph {
+
+struct ff {
+  float h, l;
+  __host__ __device__ ff() : h(0.f), l(0.f) {}
+  // plain conversions, so that constant arguments fold at compile time
+  __host__ __device__ ff(double d) : h((float)d), l((float)(d - (double)(float)d)) {}
+  __host__ __device__ explicit operator double() const { return (double)h + (double)l; }
+};
+
+__device__ __forceinline__ ff ff_make(float h, float l) {
+  ff r;
+  r.h = h;
+  r.l = l;
+  return r;
+}
+
+// s + e = a + b exactly (no assumption on |a| vs |b|)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// s + e = a + b exactly when |a| >= |b|
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  e = __fsub_rn(b, __fsub_rn(s, a));
+}
+
+__device__ __forceinline__ ff operator+(ff a, ff b) {
+  float s, e;
+  two_sum(a.h, b.h, s, e);
+  e = __fadd_rn(e, __fadd_rn(a.l, b.l));
+  float h, l;
+  fast_two_sum(s, e, h, l);
+  return ff_make(h, l);
+}
+
+__device__ __forceinline__ ff operator-(ff a) { return ff_make(-a.h, -a.l); }
+__device__ __forceinline__ ff operator-(ff a, ff b) { return a + (-b); }
+
+__device__ __forceinline__ ff operator*(ff a, ff b) {
+  const float p = __fmul_rn(a.h, b.h);
+  float e = __fmaf_rn(a.h, b.h, -p);  // exact low part of a.h * b.h
+  e = __fmaf_rn(a.h, b.l, e);
+  e = __fmaf_rn(a.l, b.h, e);
+  float h, l;
+  fast_two_sum(p, e, h, l);
+  return ff_make(h, l);
+}
+
+__device__ __forceinline__ ff& operator+=(ff& a, ff b) {
+  a = a + b;
+  return a;
+}
+
+// a / b: FP32 quotient, one correction from the double-float remainder.
+__device__ __forceinline__ ff operator/(ff a, ff b) {
+  const float q1 = __fdiv_rn(a.h, b.h);
+  const ff r = a - b * ff_make(q1, 0.f);
+  const float q2 = __fdiv_rn(r.h, b.h);
+  float h, l;
+  fast_two_sum(q1, q2, h, l);
+  return ff_make(h, l);
+}
+
+// integer stored in a pool entry (exact in the high word below 2^24)
+__device__ __forceinline__ int pool_index(float x) { return (int)x; }
+__device__ __forceinline__ int pool_index(double x) { return (int)x; }
+__device__ __forceinline__ int pool_index(ff x) { return (int)x.h; }
+
+struct ff2 {
+  ff x, y;
+};
+
+}  // namespace fcsph

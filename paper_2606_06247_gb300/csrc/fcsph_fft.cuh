@@ -17,6 +17,7 @@
 
 #include <cuda_runtime.h>
 
+#include "fcsph_ff.cuh"
 #include "fcsph_internal.h"
 
 namespace fcsph {
@@ -24,6 +25,7 @@ namespace fcsph {
 template <typename T> struct CT;
 template <> struct CT<double> { typedef double2 t; };
 template <> struct CT<float> { typedef float2 t; };
+template <> struct CT<ff> { typedef ff2 t; };
 
 template <typename V> __device__ __forceinline__ V cmul(V a, V b) {
   V r;
@@ -55,7 +57,7 @@ template <typename V, typename S> __device__ __forceinline__ V cscale(V a, S s) 
   r.y = a.y * s;
   return r;
 }
-template <typename V> __device__ __forceinline__ V mk(double x, double y) {
+template <typename V, typename A, typename B> __device__ __forceinline__ V mk(A x, B y) {
   V r;
   r.x = x;
   r.y = y;
@@ -426,7 +428,7 @@ __device__ typename CT<T>::t* fft_rader(typename CT<T>::t* a, typename CT<T>::t*
   for (int t = threadIdx.x; t < nl * m; t += blockDim.x) {
     const int line = fdiv(t, P.sub.dn);
     const int q = t - line * m;
-    V v = a[(size_t)line * ls + (int)gi[q].x];
+    V v = a[(size_t)line * ls + pool_index(gi[q].x)];
     if (INV) v.y = -v.y;
     b[(size_t)line * ls + q] = v;
   }
@@ -458,7 +460,7 @@ __device__ typename CT<T>::t* fft_rader(typename CT<T>::t* a, typename CT<T>::t*
     const V* yl = y + (size_t)line * ls;
     V v = cadd(yl[p], yl[q]);
     if (INV) v.y = -v.y;
-    out[(size_t)line * ls + (int)si[q].x] = v;
+    out[(size_t)line * ls + pool_index(si[q].x)] = v;
   }
   for (int line = threadIdx.x; line < nl; line += blockDim.x) {
     const V* yl = y + (size_t)line * ls;

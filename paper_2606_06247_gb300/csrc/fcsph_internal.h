@@ -123,6 +123,8 @@ struct GridDev {
   // pool offsets of exp(-kx^2 h^2/4), kx index < mx, and exp(-ky^2 h^2/4),
   // ky < hy (real parts): the symbol's Gaussian factor is their product
   int ex_off, ey_off;
+  // pool offsets of the PPE eigenvalues lam_k^2 (k < nx) and lam_l^2 (l < ny)
+  int lx2_off, ly2_off;
 };
 
 struct StepDev {
@@ -145,6 +147,7 @@ struct fcsph_ctx {
   std::vector<double> hE[2];    // host copies
   double2* pool64 = nullptr;
   float2* pool32 = nullptr;
+  void* poolff = nullptr;       // FP32x2 copy of the pool (hi, lo per component)
   void* spec_in = nullptr;      // [batch][2][rows][nx] complex (T)
   void* spec_out = nullptr;     // [batch][6][rows][nx] complex (T)
   void* spec_ppe = nullptr;     // [batch][rows][nx] complex (T) scratch for PPE refinement

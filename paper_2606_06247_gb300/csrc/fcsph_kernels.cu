@@ -26,6 +26,7 @@ constexpr int kThreads = 256;
 template <typename T> struct PoolOf;
 template <> struct PoolOf<double> { static const double2* get(const fcsph_ctx* c) { return c->pool64; } };
 template <> struct PoolOf<float> { static const float2* get(const fcsph_ctx* c) { return c->pool32; } };
+template <> struct PoolOf<ff> { static const ff2* get(const fcsph_ctx* c) { return static_cast<const ff2*>(c->poolff); } };
 
 __device__ __forceinline__ size_t fidx(const GridDev& g, int b, int i, int j) {
   return ((size_t)b * g.nx + i) * g.ny + j;
@@ -99,13 +100,17 @@ __device__ void col_forward_store(typename CT<T>::t* lines, typename CT<T>::t* s
     const V* L = R + (size_t)(col >> 1) * ls;
     const V z = L[k];
     const V zm = L[k == 0 ? 0 : n - k];
+    const T h = (T)0.5;
     V out;
     if (dct) {
-      out = (col & 1) ? mk<V>(0.5 * ((double)z.y + (double)zm.y), 0.0) : mk<V>(0.5 * ((double)z.x + (double)zm.x), 0.0);
+      out = (col & 1) ? mk<V>(0.0, 0.0) : mk<V>(0.0, 0.0);
+      out.x = (col & 1) ? h * (z.y + zm.y) : h * (z.x + zm.x);
     } else if ((col & 1) == 0) {
-      out = mk<V>(0.5 * ((double)z.x + (double)zm.x), 0.5 * ((double)z.y - (double)zm.y));
+      out.x = h * (z.x + zm.x);
+      out.y = h * (z.y - zm.y);
     } else {
-      out = mk<V>(0.5 * ((double)z.y + (double)zm.y), -0.5 * ((double)z.x - (double)zm.x));
+      out.x = h * (z.y + zm.y);
+      out.y = h * (zm.x - z.x);
     }
     spec[(size_t)k * g.nx + i] = out;
   }
@@ -130,11 +135,18 @@ __device__ void col_gather_hermitian(typename CT<T>::t* lines, int Pp, int ls, c
     if (ib < g.nx) B = S[ib];
     V* L = lines + ((size_t)o * Pp + p) * ls;
     const bool self = (k == 0) || (2 * k == n);
+    V z0, z1;
     if (self) {
-      L[k] = mk<V>(A.x, B.x);
+      z0.x = A.x;
+      z0.y = B.x;
+      L[k] = z0;
     } else {
-      L[k] = mk<V>((double)A.x - (double)B.y, (double)A.y + (double)B.x);
-      L[n - k] = mk<V>((double)A.x + (double)B.y, (double)B.x - (double)A.y);
+      z0.x = A.x - B.y;
+      z0.y = A.y + B.x;
+      z1.x = A.x + B.y;
+      z1.y = B.x - A.y;
+      L[k] = z0;
+      L[n - k] = z1;
     }
   }
 }
@@ -149,11 +161,12 @@ __device__ void col_gather_dct(typename CT<T>::t* lines, int Pp, int ls, const G
     const int l = e / Pp, p = e - (e / Pp) * Pp;
     const int ia = i0 + 2 * p, ib = ia + 1;
     const V* S = spec + (size_t)l * g.nx;
-    const double a = ia < g.nx ? (double)S[ia].x : 0.0;
-    const double b = ib < g.nx ? (double)S[ib].x : 0.0;
+    V z = mk<V>(0.0, 0.0);
+    if (ia < g.nx) z.x = S[ia].x;
+    if (ib < g.nx) z.y = S[ib].x;
     V* L = lines + (size_t)p * ls;
-    L[l] = mk<V>(a, b);
-    if (l >= 1 && l <= ny - 2) L[M - l] = mk<V>(a, b);
+    L[l] = z;
+    if (l >= 1 && l <= ny - 2) L[M - l] = z;
   }
 }
 
@@ -200,14 +213,17 @@ __device__ __forceinline__ typename CT<T>::t symbol(int op, T kx, T ky, bool nyq
   }
 }
 
-// sum_{m<n} s^m / m! (n = family): W_hat = e^{-s} times this.
+// sum_{m<n} s^m / m! (n = family) in Horner form with constant coefficients:
+// W_hat = e^{-s} times this.
 template <typename T> __device__ __forceinline__ T kernel_poly(int family, T s) {
-  T acc = 1, term = 1;
-  for (int m = 1; m < family; ++m) {
-    term = term * s / (T)m;
-    acc += term;
+  const T one = (T)1.0;
+  switch (family) {
+    case 1: return one;
+    case 2: return one + s;
+    case 3: return one + s * (one + s * (T)0.5);
+    case 4: return one + s * (one + s * ((T)0.5 + s * (T)(1.0 / 6.0)));
+    default: return one + s * (one + s * ((T)0.5 + s * ((T)(1.0 / 6.0) + s * (T)(1.0 / 24.0))));
   }
-  return acc;
 }
 
 // Row pass: for Rr rows ky of one instance: load nin input rows, FC-extend
@@ -321,30 +337,22 @@ __global__ void __launch_bounds__(kThreads) k_row_ppe(GridDev g, typename CT<T>:
   __syncthreads();
   V* X = fft_any<T, false>(A, B, Rr, ls, P, pool);
   V* O = (X == A) ? B : A;
-  const double pi = 3.14159265358979323846;
-  const double norm = 1.0 / ((double)n * 2.0 * (ny - 1));
+  const T norm = (T)(1.0 / ((double)n * 2.0 * (ny - 1)));
   const int nk = g.x_walls ? nx : n;
   for (int e = threadIdx.x; e < Rr * nk; e += blockDim.x) {
     const int r = e / nk, k = e - (e / nk) * nk;
     const int l = l0 + r;
-    double lk;
-    if (g.x_walls) {
-      lk = pi * k / g.lx;
-    } else {
-      const int kappa = (2 * k <= n) ? k : k - n;
-      lk = 2.0 * pi * kappa / g.lx;
-    }
-    const double ll = pi * l / g.ly;
-    const double den = lk * lk + ll * ll;
-    double f;
+    // lam_k^2 and lam_l^2 from the per-axis tables (Eq. 33 eigenvalues)
+    const T den = pool[g.lx2_off + k].x + pool[g.ly2_off + (l < ny ? l : 0)].x;
+    T f;
     if (apply == 1)
-      f = -den * norm;
+      f = -(den * norm);
     else if (apply == 2)
-      f = (k == 0 && l == 0) ? 0.0 : norm;
+      f = (k == 0 && l == 0) ? (T)0.0 : norm;
     else
-      f = (k == 0 && l == 0) ? 0.0 : -norm / den;
+      f = (k == 0 && l == 0) ? (T)0.0 : -(norm / den);
     const V x = X[(size_t)r * ls + k];
-    const V y = mk<V>((double)x.x * f, (double)x.y * f);
+    const V y = cscale(x, f);
     if (g.x_walls) {
       O[(size_t)r * ls + k] = y;
       if (k >= 1 && k <= nx - 2) O[(size_t)r * ls + n - k] = y;
@@ -565,25 +573,35 @@ __global__ void k_fc_extend_x(GridDev g, U* __restrict__ fe, const double* __res
   }
 }
 
-// Batched DFT of contiguous lines (engine test entry).
-template <typename T, bool INV>
-__global__ void __launch_bounds__(kThreads) k_dft_lines(int n, int nlines, const typename CT<T>::t* __restrict__ in,
-                                                        typename CT<T>::t* __restrict__ out, FftPlan P,
+// Batched DFT of contiguous lines (engine test entry); IO is the element type
+// in memory (double2 for the double-float engine, else the engine's own).
+template <typename T, bool INV, typename IO = typename CT<T>::t>
+__global__ void __launch_bounds__(kThreads) k_dft_lines(int n, int nlines, const IO* __restrict__ in,
+                                                        IO* __restrict__ out, FftPlan P,
                                                         const typename CT<T>::t* __restrict__ pool, int L, int ls) {
   typedef typename CT<T>::t V;
+  typedef decltype(IO().x) E;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* A = reinterpret_cast<V*>(smem_raw);
   V* B = A + (size_t)L * ls;
   const int l0 = blockIdx.x * L;
   for (int e = threadIdx.x; e < L * n; e += blockDim.x) {
     const int r = e / n, j = e - (e / n) * n;
-    A[(size_t)r * ls + j] = (l0 + r < nlines) ? in[(size_t)(l0 + r) * n + j] : mk<V>(0.0, 0.0);
+    if (l0 + r < nlines) {
+      const IO x = in[(size_t)(l0 + r) * n + j];
+      A[(size_t)r * ls + j] = mk<V>(x.x, x.y);
+    } else {
+      A[(size_t)r * ls + j] = mk<V>(0.0, 0.0);
+    }
   }
   __syncthreads();
   V* Y = fft_any<T, INV>(A, B, L, ls, P, pool);
   for (int e = threadIdx.x; e < L * n; e += blockDim.x) {
     const int r = e / n, j = e - (e / n) * n;
-    if (l0 + r < nlines) out[(size_t)(l0 + r) * n + j] = Y[(size_t)r * ls + j];
+    if (l0 + r < nlines) {
+      const V y = Y[(size_t)r * ls + j];
+      out[(size_t)(l0 + r) * n + j] = mk<IO>(static_cast<E>(y.x), static_cast<E>(y.y));
+    }
   }
 }
 
@@ -644,8 +662,6 @@ __global__ void k_sub(double* __restrict__ r, const double* __restrict__ b, cons
 // ---------------------------------------------------------------------------
 // Host-side launch helpers.
 
-size_t cbytes(int prec) { return prec == FCSPH_F64 ? sizeof(double2) : sizeof(float2); }
-
 // Largest count (>= 1, <= cap) of units fitting in `budget` bytes.
 int fit_units(size_t per_unit, size_t budget, int cap) {
   int u = (int)(budget / per_unit);
@@ -696,6 +712,10 @@ cudaError_t init_kernel_attributes() {
   FCSPH_RAISE((k_col_fwd<double, double>))
   FCSPH_RAISE((k_col_fwd<float, double>))
   FCSPH_RAISE((k_col_fwd<float, float>))
+  FCSPH_RAISE((k_col_fwd<ff, double>))
+  FCSPH_RAISE((k_row_sym<ff>))
+  FCSPH_RAISE((k_row_ppe<ff>))
+  FCSPH_RAISE((k_col_inv<ff>))
   FCSPH_RAISE((k_row_sym<double>))
   FCSPH_RAISE((k_row_sym<float>))
   FCSPH_RAISE((k_row_ppe<double>))
@@ -704,6 +724,8 @@ cudaError_t init_kernel_attributes() {
   FCSPH_RAISE((k_dft_lines<double, true>))
   FCSPH_RAISE((k_dft_lines<float, false>))
   FCSPH_RAISE((k_dft_lines<float, true>))
+  FCSPH_RAISE((k_dft_lines<ff, false, double2>))
+  FCSPH_RAISE((k_dft_lines<ff, true, double2>))
   FCSPH_RAISE((k_col_inv<double>))
   FCSPH_RAISE((k_col_inv<float>))
 #undef FCSPH_RAISE
@@ -714,7 +736,7 @@ cudaError_t launch_fc_extend(fcsph_ctx* c, const void* f, void* fext, int bc) {
   ProfScope ps(c, FCSPH_PROF_OTHER);
   const double* E = c->dE + (bc == FCSPH_NEUMANN ? 1 : 0) * c->gd.n_cont * 2 * c->gd.n_match;
   const int blocks = 152 * 8;
-  if (c->prec.fft_prec == FCSPH_F64) {
+  if (c->prec.fft_prec != FCSPH_F32) {  // double fields (F64, F32X2)
     k_fc_extend_y<double><<<blocks, kThreads, 0, c->stream>>>(c->gd, (const double*)f, (double*)fext, E);
     c->launches++;
     if (c->gd.x_walls) {
@@ -760,6 +782,10 @@ cudaError_t launch_col_fwd(fcsph_ctx* c, int prec, int nf, const void* const* fi
     if (!fields_double) return cudaErrorInvalidValue;
     return col_fwd_t<double, double>(c, nf, fields, bc, spec, dct);
   }
+  if (prec == FCSPH_F32X2) {
+    if (!fields_double) return cudaErrorInvalidValue;
+    return col_fwd_t<ff, double>(c, nf, fields, bc, spec, dct);
+  }
   if (fields_double) return col_fwd_t<float, double>(c, nf, fields, bc, spec, dct);
   return col_fwd_t<float, float>(c, nf, fields, bc, spec, dct);
 }
@@ -788,6 +814,7 @@ static cudaError_t row_sym_t(fcsph_ctx* c, const void* sp_in, void* sp_out, cons
 static cudaError_t row_sym_any(fcsph_ctx* c, int prec, const void* sp_in, void* sp_out, const RowOps& ops,
                                double scale, int bc, int kind) {
   if (prec == FCSPH_F64) return row_sym_t<double>(c, sp_in, sp_out, ops, scale, bc, kind);
+  if (prec == FCSPH_F32X2) return row_sym_t<ff>(c, sp_in, sp_out, ops, scale, bc, kind);
   return row_sym_t<float>(c, sp_in, sp_out, ops, scale, bc, kind);
 }
 
@@ -796,7 +823,7 @@ static cudaError_t row_sym_any(fcsph_ctx* c, int prec, const void* sp_in, void* 
 // must be contiguous), each with its own input row and output rows.
 cudaError_t launch_row_sym(fcsph_ctx* c, int prec, const void* sp_in, void* sp_out, const RowOps& ops, double scale,
                            int bc, int kind) {
-  const size_t cb = prec == FCSPH_F64 ? sizeof(double2) : sizeof(float2);
+  const size_t cb = prec == FCSPH_F32 ? sizeof(float2) : sizeof(double2);
   const size_t per = (size_t)(2 * ops.nin + 2 * ops.nout) * c->plan_x.line_len() * cb;
   bool single = true;
   for (int o = 0; o < ops.nout && single; ++o) single = ops.nterm[o] == 1 && (o == 0 || ops.field[o][0] >= ops.field[o - 1][0]);
@@ -860,6 +887,7 @@ static cudaError_t col_inv_common(fcsph_ctx* c, int epi, const void* spec, int n
 
 static cudaError_t col_inv(fcsph_ctx* c, int prec, int epi, const void* spec, int nout, EpiArgs& ea) {
   if (prec == FCSPH_F64) return col_inv_common<double>(c, epi, spec, nout, ea);
+  if (prec == FCSPH_F32X2) return col_inv_common<ff>(c, epi, spec, nout, ea);
   return col_inv_common<float>(c, epi, spec, nout, ea);
 }
 
@@ -872,7 +900,7 @@ static EpiArgs epi_defaults() {
 cudaError_t launch_col_out(fcsph_ctx* c, const void* spec, int nout, void* const* outs) {
   EpiArgs ea = epi_defaults();
   for (int o = 0; o < nout; ++o) ea.outs[o] = outs[o];
-  ea.out_double = c->prec.fft_prec == FCSPH_F64;
+  ea.out_double = c->prec.fft_prec != FCSPH_F32;
   return col_inv(c, c->prec.fft_prec, EPI_OUT, spec, nout, ea);
 }
 
@@ -895,6 +923,7 @@ static cudaError_t row_ppe_t(fcsph_ctx* c, void* spec, int apply) {
 
 cudaError_t launch_row_ppe(fcsph_ctx* c, int prec, void* spec, int apply) {
   if (prec == FCSPH_F64) return row_ppe_t<double>(c, spec, apply);
+  if (prec == FCSPH_F32X2) return row_ppe_t<ff>(c, spec, apply);
   return row_ppe_t<float>(c, spec, apply);
 }
 
@@ -943,7 +972,7 @@ cudaError_t launch_step_mom(fcsph_ctx* c, const StepDev& s, const void* spec6, c
   ea.fwdP = c->plan_y;
   ea.fwd_fstride = (size_t)c->gd.rows * c->gd.nx;
   ea.fwd_bstride = 2 * ea.fwd_fstride;
-  const size_t cb = c->prec.fft_prec == FCSPH_F64 ? sizeof(double2) : sizeof(float2);
+  const size_t cb = c->prec.fft_prec == FCSPH_F32 ? sizeof(float2) : sizeof(double2);
   if (2 * 6 * (size_t)col_ls(c) * cb <= kSmemMax) {
     ea.mom_comp = 0;
     ea.fwd_nf = 2;
@@ -996,40 +1025,33 @@ cudaError_t launch_step_corr(fcsph_ctx* c, const StepDev& s, const void* spec2, 
   return col_inv(c, c->prec.fft_prec, EPI_CORR, spec2, 2, ea);
 }
 
-cudaError_t launch_dft_lines(int n, int nlines, int dir, int prec, const void* in, void* out, cudaStream_t st,
-                             const FftPlan& plan, const void* pool) {
+template <typename T, typename IO>
+cudaError_t dft_lines_t(int n, int nlines, int dir, const void* in, void* out, cudaStream_t st, const FftPlan& plan,
+                        const void* pool) {
+  typedef typename CT<T>::t V;
   const int ls = plan.line_len();
+  const size_t per = 2 * (size_t)ls * sizeof(V);
+  const int L = fit_units(per, kSmemBudget, 16);
+  const size_t smem = per * L;
+  const int blocks = (nlines + L - 1) / L;
   cudaError_t e;
-  if (prec == FCSPH_F64) {
-    const size_t per = 2 * (size_t)ls * sizeof(double2);
-    const int L = fit_units(per, kSmemBudget, 16);
-    const size_t smem = per * L;
-    const int blocks = (nlines + L - 1) / L;
-    if (dir < 0) {
-      if ((e = set_smem(k_dft_lines<double, false>, smem)) != cudaSuccess) return e;
-      k_dft_lines<double, false><<<blocks, kThreads, smem, st>>>(n, nlines, (const double2*)in, (double2*)out, plan,
-                                                                 (const double2*)pool, L, ls);
-    } else {
-      if ((e = set_smem(k_dft_lines<double, true>, smem)) != cudaSuccess) return e;
-      k_dft_lines<double, true><<<blocks, kThreads, smem, st>>>(n, nlines, (const double2*)in, (double2*)out, plan,
-                                                                (const double2*)pool, L, ls);
-    }
+  if (dir < 0) {
+    if ((e = set_smem(k_dft_lines<T, false, IO>, smem)) != cudaSuccess) return e;
+    k_dft_lines<T, false, IO><<<blocks, kThreads, smem, st>>>(n, nlines, (const IO*)in, (IO*)out, plan,
+                                                              (const V*)pool, L, ls);
   } else {
-    const size_t per = 2 * (size_t)ls * sizeof(float2);
-    const int L = fit_units(per, kSmemBudget, 16);
-    const size_t smem = per * L;
-    const int blocks = (nlines + L - 1) / L;
-    if (dir < 0) {
-      if ((e = set_smem(k_dft_lines<float, false>, smem)) != cudaSuccess) return e;
-      k_dft_lines<float, false><<<blocks, kThreads, smem, st>>>(n, nlines, (const float2*)in, (float2*)out, plan,
-                                                                (const float2*)pool, L, ls);
-    } else {
-      if ((e = set_smem(k_dft_lines<float, true>, smem)) != cudaSuccess) return e;
-      k_dft_lines<float, true><<<blocks, kThreads, smem, st>>>(n, nlines, (const float2*)in, (float2*)out, plan,
-                                                               (const float2*)pool, L, ls);
-    }
+    if ((e = set_smem(k_dft_lines<T, true, IO>, smem)) != cudaSuccess) return e;
+    k_dft_lines<T, true, IO><<<blocks, kThreads, smem, st>>>(n, nlines, (const IO*)in, (IO*)out, plan,
+                                                             (const V*)pool, L, ls);
   }
   return cudaGetLastError();
+}
+
+cudaError_t launch_dft_lines(int n, int nlines, int dir, int prec, const void* in, void* out, cudaStream_t st,
+                             const FftPlan& plan, const void* pool) {
+  if (prec == FCSPH_F64) return dft_lines_t<double, double2>(n, nlines, dir, in, out, st, plan, pool);
+  if (prec == FCSPH_F32X2) return dft_lines_t<ff, double2>(n, nlines, dir, in, out, st, plan, pool);
+  return dft_lines_t<float, float2>(n, nlines, dir, in, out, st, plan, pool);
 }
 
 cudaError_t launch_resid_norm(fcsph_ctx* c, const double* r, const double* b, double* out2) {

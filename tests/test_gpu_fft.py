@@ -12,18 +12,20 @@ LENGTHS = [1, 2, 3, 4, 5, 7, 8, 9, 11, 16, 27, 31, 37, 64, 72, 81, 89, 90, 96, 1
 
 @pytest.mark.gpu
 @pytest.mark.parametrize("n", LENGTHS)
-@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("prec", ["f64", "f32", "f32x2"])
 def test_dft_matches_numpy(n, prec):
     torch = torch_cuda()
     b = binding()
     rng = np.random.default_rng(n)
     nl = 7
     x = rng.standard_normal((nl, n)) + 1j * rng.standard_normal((nl, n))
-    dt = torch.complex128 if prec == "f64" else torch.complex64
+    dt = torch.complex64 if prec == "f32" else torch.complex128
     xd = torch.tensor(x, dtype=dt).cuda()
     for direction in (-1, 1):
-        y = b.fcsph_dft(xd, direction).cpu().numpy()
+        y = b.fcsph_dft(xd, direction, double_float=prec == "f32x2").cpu().numpy()
         ref = np.fft.fft(x, axis=-1) if direction < 0 else np.fft.ifft(x, axis=-1) * n
         err = np.linalg.norm(y - ref) / np.linalg.norm(ref)
-        tol = 2e-15 * np.log2(max(n, 2)) * 4 if prec == "f64" else 3e-7 * np.log2(max(n, 2)) * 4
+        # unit roundoff: FP64 2^-53, FP32 pairs about 2^-48 (32x), FP32 2^-24
+        u = {"f64": 2e-15, "f32x2": 32 * 2e-15, "f32": 3e-7}[prec]
+        tol = u * np.log2(max(n, 2)) * 4
         assert err < tol, (n, prec, direction, err)

@@ -48,12 +48,15 @@ def test_fc_extend_matches_oracle(case):
 @pytest.mark.gpu
 @pytest.mark.parametrize("case", CASES)
 @pytest.mark.parametrize("bc", [0, 1])
-def test_spectral_op_matches_oracle_fp64(case, bc):
+@pytest.mark.parametrize("prec", ["f64", "f32x2"])
+def test_spectral_op_matches_oracle_fp64(case, bc, prec):
+    """FP64 transforms, and FP32-pair transforms (unit roundoff ~2^-48: bar x32)."""
     torch = torch_cuda()
     b = binding()
     nx, ny, xw, fam, hdx, batch = case
     lx, ly = grid_lengths(nx, ny, xw)
-    ctx = b.Context(nx, ny, lx, ly, x_walls=xw, batch=batch, family=fam, h_over_dx=hdx)
+    ctx = b.Context(nx, ny, lx, ly, x_walls=xw, batch=batch, family=fam, h_over_dx=hdx, prec=prec)
+    scale = 1.0 if prec == "f64" else 32.0
     p = oracle_problem(nx, ny, xw, fam, hdx)
     from oracle.symbols import symbol_closed
     mx, my = p.extended_shape()
@@ -70,7 +73,7 @@ def test_spectral_op_matches_oracle_fp64(case, bc):
         floors = ulp_floor(fn, f[k])
         for n, o, r, fl in zip(names, outs, refs, floors):
             err = rel_l2(o[k].cpu().numpy(), r)
-            assert err < parity_tol(fl), (n, k, err, fl)
+            assert err < parity_tol(fl, base=1e-12 * scale, factor=10.0 * scale), (n, k, err, fl)
 
 
 @pytest.mark.gpu

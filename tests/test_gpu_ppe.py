@@ -16,19 +16,22 @@ def _rhs(nx, ny, batch, seed):
 
 @pytest.mark.gpu
 @pytest.mark.parametrize("case", CASES)
-def test_ppe_matches_oracle_fp64(case):
+@pytest.mark.parametrize("prec", ["f64", "f32x2"])
+def test_ppe_matches_oracle_fp64(case, prec):
+    """FP64 transforms, and FP32-pair transforms (unit roundoff ~2^-48: bar x32)."""
     torch = torch_cuda()
     b = binding()
     nx, ny, xw, batch = case
     lx, ly = grid_lengths(nx, ny, xw)
-    ctx = b.Context(nx, ny, lx, ly, x_walls=xw, batch=batch)
+    ctx = b.Context(nx, ny, lx, ly, x_walls=xw, batch=batch, prec=prec)
+    scale = 1.0 if prec == "f64" else 32.0
     rhs = _rhs(nx, ny, batch, 5)
     phi = torch.zeros((batch, nx, ny), dtype=torch.float64, device="cuda")
     res = ctx.ppe_solve(to_dev(rhs), phi, want_resid=True)
     for k in range(batch):
         ref = oppe.ppe_solve(rhs[k], lx, ly, xw)
-        assert rel_l2(phi[k].cpu().numpy(), ref) < 1e-12
-    assert res < 1e-13
+        assert rel_l2(phi[k].cpu().numpy(), ref) < 1e-12 * scale
+    assert res < 1e-13 * scale
 
 
 @pytest.mark.gpu

@@ -108,3 +108,34 @@ def test_mixed_precision_step_error_vs_fp64_oracle():
     eu, ev = rel_l2(ug[0], uo), rel_l2(vg[0], vo)
     print(f"cavity mixed rel L2 vs FP64 oracle: u {eu:.2e} v {ev:.2e}")
     assert np.isfinite(eu) and eu < 1.0
+
+
+# FP32-pair arithmetic rounds at about 2^-48, 32 times FP64's unit roundoff:
+# the parity bar is the FP64 one scaled by 32.
+def _ff_tol(floor):
+    return parity_tol(floor, base=32e-12, factor=320.0)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("case", ["channel-fop", "channel-rk3", "cavity-rk3"])
+def test_double_float_step_matches_oracle(case):
+    b = binding()
+    if case.startswith("channel"):
+        nx, ny, xw, fam, prm = 24, 20, False, "G4", CHANNEL
+        scheme, nsteps = ("fop", 6) if case.endswith("fop") else ("rk3", 2)
+        u0, v0 = inputs.channel_initial(nx, ny, seed=1, sigma=1e-3)
+        p = oracle_problem(nx, ny, False, "G4", 1.3, scheme=scheme, nu=0.1, dt=1e-3, force=(0.8, 0.0))
+    else:
+        nx, ny, xw, fam, prm = 20, 20, True, "G8", CAVITY
+        scheme, nsteps = "rk3", 2
+        u0, v0 = inputs.cavity_initial(nx, ny, seed=3, sigma=1e-3)
+        p = oracle_problem(nx, ny, True, "G8", 1.3, scheme="rk3", nu=1e-3, dt=1e-3, u_top=1.0)
+    ug, vg, pg, _ = _run_gpu(b, nx, ny, xw, fam, 1.3, u0[None], v0[None], nsteps, prec="f32x2", scheme=scheme, **prm)
+    fn = lambda a, c: ostep.isph_steps(p, a, c, nsteps)
+    uo, vo, po = fn(u0, v0)
+    fu, fv, fp = ulp_floor(fn, u0, v0)
+    print(f"{case} FP32x2: parity u {rel_l2(ug[0], uo):.1e} v {rel_l2(vg[0], vo):.1e} p {rel_l2(pg[0], po):.1e}; "
+          f"oracle 1-ulp floor u {fu:.1e} v {fv:.1e} p {fp:.1e}")
+    assert rel_l2(ug[0], uo) < _ff_tol(fu)
+    assert rel_l2(vg[0], vo) < _ff_tol(fv)
+    assert rel_l2(pg[0], po) < _ff_tol(fp)
