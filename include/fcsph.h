@@ -182,6 +182,25 @@ fcsph_status fcsph_dft(int n, int nlines, int dir, int prec, const void* in, voi
 #define FCSPH_NOALLOC_SCRATCH_BYTES (1u << 20)
 fcsph_status fcsph_dft_noalloc(int n, int nlines, int dir, int prec, const void* in, void* out, void* stream);
 
+/* Tiling of the one-warp FFT passes: row_lines rows per CTA of the x
+ * passes, col_pairs column pairs per CTA of the wall-normal passes (each
+ * 1..8).  More lines per CTA fill more lanes of each butterfly stage but hold
+ * more shared memory, so fewer CTAs fit on an SM; the best choice depends on
+ * the precision and the transform lengths.  Takes effect at the next call
+ * (a captured isph_step graph is dropped).  FCSPH_EUNSUPPORTED if a CTA
+ * would exceed the shared memory of an SM.  Engineering choice of this
+ * library; the paper has no counterpart. */
+fcsph_status fcsph_set_tiling(fcsph_ctx* ctx, int row_lines, int col_pairs);
+fcsph_status fcsph_get_tiling(const fcsph_ctx* ctx, int* row_lines, int* col_pairs);
+
+/* Autotuner: times `steps` isph_step calls with *prm for every tiling with
+ * row_lines, col_pairs in {1, 2, 4} that fits, on a zero state the call
+ * allocates and frees (5 fields of the context's batch), then keeps the
+ * fastest.  best_ms_out (nullable, host): its milliseconds per step.
+ * Synchronises the context's stream.  Engineering choice of this library;
+ * the paper has no counterpart. */
+fcsph_status fcsph_autotune(fcsph_ctx* ctx, const fcsph_step_params* prm, int steps, double* best_ms_out);
+
 /* Kernel launches this context has queued since creation (for bookkeeping). */
 long long fcsph_launch_count(const fcsph_ctx* ctx);
 

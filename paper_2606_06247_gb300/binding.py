@@ -84,6 +84,9 @@ def _load():
         "fcsph_last_error": [P, ctypes.c_char_p, S],
         "fcsph_set_profiling": [P, I],
         "fcsph_get_profile": [P, P, P, I],
+        "fcsph_set_tiling": [P, I, I],
+        "fcsph_get_tiling": [P, ctypes.POINTER(I), ctypes.POINTER(I)],
+        "fcsph_autotune": [P, ctypes.POINTER(fcsph_step_params), I, ctypes.POINTER(D)],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -218,15 +221,36 @@ class Context:
         self._ck(lib.ppe_solve(self.h, _ptr(rhs), _ptr(phi), ctypes.byref(r) if want_resid else None))
         return r.value if want_resid else None
 
+    @staticmethod
+    def _params(nu, rho, dt, force, u_bottom, u_top, scheme, use_graph, nu_inst, fx_inst):
+        return fcsph_step_params(nu, rho, dt, force[0], force[1], u_bottom, u_top, SCHEME[scheme], 1 if use_graph else 0,
+                                 nu_inst.data_ptr() if nu_inst is not None else None,
+                                 fx_inst.data_ptr() if fx_inst is not None else None)
+
     def isph_step(self, u, v, p, fu, fv, nsteps, nu, rho=1.0, dt=1e-3, force=(0.0, 0.0), u_bottom=0.0, u_top=0.0,
                   scheme="fop", use_graph=True, nu_inst=None, fx_inst=None):
         """nu_inst / fx_inst: optional CUDA float64 tensors [batch] of per-instance
         viscosity and x body force (override nu / force[0])."""
         st = fcsph_state(u.data_ptr(), v.data_ptr(), p.data_ptr(), fu.data_ptr(), fv.data_ptr())
-        prm = fcsph_step_params(nu, rho, dt, force[0], force[1], u_bottom, u_top, SCHEME[scheme], 1 if use_graph else 0,
-                                nu_inst.data_ptr() if nu_inst is not None else None,
-                                fx_inst.data_ptr() if fx_inst is not None else None)
+        prm = self._params(nu, rho, dt, force, u_bottom, u_top, scheme, use_graph, nu_inst, fx_inst)
         self._ck(lib.isph_step(self.h, ctypes.byref(st), nsteps, ctypes.byref(prm)))
+
+    def set_tiling(self, row_lines, col_pairs):
+        self._ck(lib.fcsph_set_tiling(self.h, row_lines, col_pairs))
+
+    def get_tiling(self):
+        r, c = ctypes.c_int(), ctypes.c_int()
+        self._ck(lib.fcsph_get_tiling(self.h, ctypes.byref(r), ctypes.byref(c)))
+        return r.value, c.value
+
+    def autotune(self, steps=3, nu=1e-3, rho=1.0, dt=1e-3, force=(0.0, 0.0), u_bottom=0.0, u_top=0.0, scheme="rk3",
+                 use_graph=True, nu_inst=None, fx_inst=None):
+        """fcsph_autotune: keeps the fastest tiling; returns (row_lines, col_pairs, ms per step)."""
+        prm = self._params(nu, rho, dt, force, u_bottom, u_top, scheme, use_graph, nu_inst, fx_inst)
+        ms = ctypes.c_double()
+        self._ck(lib.fcsph_autotune(self.h, ctypes.byref(prm), steps, ctypes.byref(ms)))
+        r, c = self.get_tiling()
+        return r, c, ms.value
 
     def sync(self):
         self._ck(lib.fcsph_sync(self.h))

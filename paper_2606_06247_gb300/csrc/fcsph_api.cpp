@@ -257,6 +257,16 @@ fcsph_status fcsph_create(const fcsph_grid* grid, const fcsph_fc* fc, const fcsp
     CREATE_CK(cudaMalloc((void**)&c->dE, 2 * ne * sizeof(double)), "cudaMalloc(E)");
     CREATE_CK(cudaMemcpy(c->dE, c->hE[0].data(), ne * sizeof(double), cudaMemcpyHostToDevice), "E upload");
     CREATE_CK(cudaMemcpy(c->dE + ne, c->hE[1].data(), ne * sizeof(double), cudaMemcpyHostToDevice), "E upload");
+    if (prec->fft_prec == FCSPH_F32X2) {
+      std::vector<float2> hf(2 * ne);
+      for (size_t i = 0; i < 2 * ne; ++i) {
+        const double x = c->hE[i / ne][i % ne];
+        const float h = (float)x;
+        hf[i] = make_float2(h, (float)(x - (double)h));
+      }
+      CREATE_CK(cudaMalloc(&c->dEff, 2 * ne * sizeof(float2)), "cudaMalloc(Eff)");
+      CREATE_CK(cudaMemcpy(c->dEff, hf.data(), 2 * ne * sizeof(float2), cudaMemcpyHostToDevice), "Eff upload");
+    }
     const size_t fs = (size_t)g.rows * g.nx * g.batch;
     const size_t cb = cplx_bytes(prec->fft_prec);
     CREATE_CK(cudaMalloc(&c->spec_in, 2 * fs * cb), "cudaMalloc(spec_in)");
@@ -289,6 +299,7 @@ fcsph_status fcsph_destroy(fcsph_ctx* c) {
   cudaFree(c->pool32);
   cudaFree(c->poolff);
   cudaFree(c->dE);
+  cudaFree(c->dEff);
   cudaFree(c->spec_in);
   cudaFree(c->spec_out);
   cudaFree(c->spec_ppe);
@@ -610,6 +621,75 @@ fcsph_status fcsph_dft(int n, int nlines, int dir, int prec, const void* in, voi
 }
 
 long long fcsph_launch_count(const fcsph_ctx* c) { return c ? c->launches : -1; }
+
+static void drop_graph(fcsph_ctx* c) {
+  if (c->gexec) {
+    cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+  }
+  c->graph_key.clear();
+}
+
+fcsph_status fcsph_set_tiling(fcsph_ctx* c, int row_lines, int col_pairs) {
+  if (!c) return fail(nullptr, FCSPH_EINVAL, "fcsph_set_tiling: null context");
+  if (row_lines < 1 || row_lines > 8 || col_pairs < 1 || col_pairs > 8)
+    return fail(c, FCSPH_EINVAL, "fcsph_set_tiling: row_lines and col_pairs must be in 1..8");
+  if (tiling_smem(c, row_lines, col_pairs) > tiling_smem_limit())
+    return fail(c, FCSPH_EUNSUPPORTED, "fcsph_set_tiling: tiles exceed the shared memory of one CTA");
+  if (row_lines != c->row_lines || col_pairs != c->col_pairs) drop_graph(c);
+  c->row_lines = row_lines;
+  c->col_pairs = col_pairs;
+  return FCSPH_OK;
+}
+
+fcsph_status fcsph_get_tiling(const fcsph_ctx* c, int* row_lines, int* col_pairs) {
+  if (!c || !row_lines || !col_pairs) return fail(nullptr, FCSPH_EINVAL, "fcsph_get_tiling: bad argument");
+  *row_lines = c->row_lines;
+  *col_pairs = c->col_pairs;
+  return FCSPH_OK;
+}
+
+fcsph_status fcsph_autotune(fcsph_ctx* c, const fcsph_step_params* prm, int steps, double* best_ms_out) {
+  if (!c || !prm || steps < 1) return fail(c, FCSPH_EINVAL, "fcsph_autotune: bad argument");
+  const size_t n = field_elems(c);
+  double* buf = nullptr;
+  FCSPH_CK(cudaMalloc((void**)&buf, 5 * n * sizeof(double)), "autotune state");
+  fcsph_state s{buf, buf + n, buf + 2 * n, buf + 3 * n, buf + 4 * n};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  const int cand[3] = {1, 2, 4};
+  int best_r = c->row_lines, best_c = c->col_pairs;
+  float best = -1.f;
+  fcsph_status st = FCSPH_OK;
+  cudaError_t e = cudaMemsetAsync(buf, 0, 5 * n * sizeof(double), c->stream);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) st = cuda_fail(c, e, "autotune setup");
+  for (int ri = 0; ri < 3 && st == FCSPH_OK; ++ri)
+    for (int ci = 0; ci < 3 && st == FCSPH_OK; ++ci) {
+      if (tiling_smem(c, cand[ri], cand[ci]) > tiling_smem_limit()) continue;
+      if ((st = fcsph_set_tiling(c, cand[ri], cand[ci])) != FCSPH_OK) break;
+      if ((st = isph_step(c, &s, 1, prm)) != FCSPH_OK) break;  // warm-up (and graph capture)
+      if ((e = cudaEventRecord(e0, c->stream)) != cudaSuccess) { st = cuda_fail(c, e, "autotune event"); break; }
+      if ((st = isph_step(c, &s, steps, prm)) != FCSPH_OK) break;
+      if ((e = cudaEventRecord(e1, c->stream)) != cudaSuccess) { st = cuda_fail(c, e, "autotune event"); break; }
+      if ((e = cudaEventSynchronize(e1)) != cudaSuccess) { st = cuda_fail(c, e, "autotune sync"); break; }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (best < 0.f || ms < best) {
+        best = ms;
+        best_r = cand[ri];
+        best_c = cand[ci];
+      }
+    }
+  if (st == FCSPH_OK) st = fcsph_set_tiling(c, best_r, best_c);
+  drop_graph(c);
+  cudaStreamSynchronize(c->stream);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(buf);
+  if (st == FCSPH_OK && best_ms_out) *best_ms_out = best / steps;
+  return st;
+}
 
 fcsph_status fcsph_set_profiling(fcsph_ctx* c, int on) {
   if (!c) return fail(nullptr, FCSPH_EINVAL, "fcsph_set_profiling: null context");

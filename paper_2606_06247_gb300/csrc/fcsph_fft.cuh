@@ -380,29 +380,29 @@ __device__ void stage_big(const typename CT<T>::t* __restrict__ src, typename CT
   }
 }
 
-// Runs the stages of p on nl lines held in a (stride ls), b is scratch of the
-// same shape.  All threads of the block must call it.  Returns the buffer
-// holding the result (a or b).
-template <typename T, bool INV>
-__device__ typename CT<T>::t* fft_run(typename CT<T>::t* a, typename CT<T>::t* b, int nl, int ls, const Plan1& p,
-                                      const typename CT<T>::t* __restrict__ tw) {
+// Runs the forward stages of p on nl lines held in a (stride ls), b is
+// scratch of the same shape.  All threads of the block must call it.
+// Returns the buffer holding the result (a or b).
+template <typename T>
+__device__ __forceinline__ typename CT<T>::t* fft_run(typename CT<T>::t* a, typename CT<T>::t* b, int nl, int ls,
+                                                      const Plan1& p, const typename CT<T>::t* __restrict__ tw) {
   typedef typename CT<T>::t V;
   int Ns = 1;
   const int n = p.n;
   for (int s = 0; s < p.nst; ++s) {
     const int R = p.radix[s];
     switch (R) {
-      case 2: stage_reg<T, 2, INV>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw); break;
-      case 3: stage_reg<T, 3, INV>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw); break;
-      case 4: stage_reg<T, 4, INV>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw); break;
-      case 5: stage_reg<T, 5, INV>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw); break;
-      case 7: stage_reg<T, 7, INV>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw); break;
-      case 8: stage_reg<T, 8, INV>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw); break;
-      case 9: stage_reg<T, 9, INV>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw); break;
-      case 11: stage_reg<T, 11, INV>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw); break;
-      case 13: stage_reg<T, 13, INV>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw); break;
-      case 17: stage_reg<T, 17, INV>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw); break;
-      default: stage_big<T, INV>(a, b, nl, ls, n, Ns, R, p.dn, tw); break;
+      case 2: stage_reg<T, 2, false>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw); break;
+      case 3: stage_reg<T, 3, false>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw); break;
+      case 4: stage_reg<T, 4, false>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw); break;
+      case 5: stage_reg<T, 5, false>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw); break;
+      case 7: stage_reg<T, 7, false>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw); break;
+      case 8: stage_reg<T, 8, false>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw); break;
+      case 9: stage_reg<T, 9, false>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw); break;
+      case 11: stage_reg<T, 11, false>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw); break;
+      case 13: stage_reg<T, 13, false>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw); break;
+      case 17: stage_reg<T, 17, false>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw); break;
+      default: stage_big<T, false>(a, b, nl, ls, n, Ns, R, p.dn, tw); break;
     }
     __syncthreads();
     V* t = a;
@@ -413,110 +413,146 @@ __device__ typename CT<T>::t* fft_run(typename CT<T>::t* a, typename CT<T>::t* b
   return a;
 }
 
-// Rader transform of a prime length p = P.base.n (see FftPlan).  Slots p and
-// p + 1 of every line hold x_0 and A_0 = sum_{j>0} x_j; the Stockham stages of
-// length p - 1 never touch them.
-template <typename T, bool INV>
-__device__ typename CT<T>::t* fft_rader(typename CT<T>::t* a, typename CT<T>::t* b, int nl, int ls, const FftPlan& P,
-                                        const typename CT<T>::t* __restrict__ pool) {
+// Length-n DFT of nl lines (data in a[0..n) of each line; ls >= P.line_len()),
+// forward or (inv) unnormalised inverse; b is scratch.  Returns the buffer
+// holding the result.  Every transform runs the forward stages only, through
+// one call site, so a kernel holds a single copy of the butterflies:
+//  - inverse: IDFT(x) = conj(DFT(conj(x)));
+//  - Rader (prime n = P.base.n, P.rd): slots n and n + 1 of every line hold x_0
+//    and A_0 = sum_{j>0} x_j; x is gathered in primitive-root order g^q,
+//    transformed (length m = n - 1), multiplied by the transformed kernel and
+//    conjugated, transformed again (= conj of the inverse), and
+//    X_{g^-q} = x_0 + conj(y_q), X_0 = x_0 + A_0;
+//  - Bluestein (P.bs): X = conj(c) . IDFT_m( DFT_m(x conj(c)) . DFT_m(b) / m ),
+//    c_j = exp(i pi j^2 / n), with the IDFT again as conj(DFT(conj)).
+template <typename T>
+__device__ __noinline__ typename CT<T>::t* fft_any_rt(typename CT<T>::t* a, typename CT<T>::t* b, int nl, int ls, const FftPlan& P,
+                                         const typename CT<T>::t* __restrict__ pool, bool inv) {
   typedef typename CT<T>::t V;
-  const int p = P.base.n;
-  const int m = p - 1;
-  const V* gi = pool + P.gidx;
-  const V* si = pool + P.sidx;
+  const int n = P.base.n;
+  const bool two = P.rd || P.bs;
+  const Plan1& sp = two ? P.sub : P.base;
+  const int m = sp.n;
   const V* bh = pool + P.bhat;
-  for (int t = threadIdx.x; t < nl * m; t += blockDim.x) {
-    const int line = fdiv(t, P.sub.dn);
-    const int q = t - line * m;
-    V v = a[(size_t)line * ls + pool_index(gi[q].x)];
-    if (INV) v.y = -v.y;
-    b[(size_t)line * ls + q] = v;
-  }
-  for (int line = threadIdx.x; line < nl; line += blockDim.x) {
-    V x0 = a[(size_t)line * ls];
-    if (INV) x0.y = -x0.y;
-    a[(size_t)line * ls + p] = x0;
-    b[(size_t)line * ls + p] = x0;
-  }
-  __syncthreads();
-  V* r = fft_run<T, false>(b, a, nl, ls, P.sub, pool + P.sub.tw);
-  V* o = (r == b) ? a : b;
-  for (int t = threadIdx.x; t < nl * m; t += blockDim.x) {
-    const int line = fdiv(t, P.sub.dn);
-    const int k = t - line * m;
-    V* x = r + (size_t)line * ls + k;
-    if (k == 0) {  // A_0 = sum_{j>0} x_j, kept before the multiply overwrites it
-      r[(size_t)line * ls + p + 1] = *x;
-      o[(size_t)line * ls + p + 1] = *x;
+  V* src = a;
+  V* dst = b;
+  // ---- input stage
+  if (P.rd) {
+    const V* gi = pool + P.gidx;
+    for (int t = threadIdx.x; t < nl * m; t += blockDim.x) {
+      const int line = fdiv(t, sp.dn);
+      const int q = t - line * m;
+      V v = a[(size_t)line * ls + pool_index(gi[q].x)];
+      if (inv) v.y = -v.y;
+      b[(size_t)line * ls + q] = v;
     }
-    *x = cmul(*x, bh[k]);
+    for (int line = threadIdx.x; line < nl; line += blockDim.x) {
+      V x0 = a[(size_t)line * ls];
+      if (inv) x0.y = -x0.y;
+      a[(size_t)line * ls + n] = x0;
+      b[(size_t)line * ls + n] = x0;
+    }
+    src = b;
+    dst = a;
+  } else if (P.bs) {
+    const V* ch = pool + P.chirp;
+    for (int t = threadIdx.x; t < nl * m; t += blockDim.x) {
+      const int line = fdiv(t, sp.dn);
+      const int j = t - line * m;
+      V* x = a + (size_t)line * ls + j;
+      if (j < n) {
+        V v = *x;
+        if (inv) v.y = -v.y;
+        *x = cmulc(v, ch[j]);
+      } else {
+        *x = mk<V>(0.0, 0.0);
+      }
+    }
+  } else if (inv) {
+    for (int t = threadIdx.x; t < nl * n; t += blockDim.x) {
+      const int line = fdiv(t, P.base.dn);
+      V* x = a + (size_t)line * ls + (t - line * n);
+      x->y = -x->y;
+    }
   }
   __syncthreads();
-  V* y = fft_run<T, true>(r, o, nl, ls, P.sub, pool + P.sub.tw);
-  V* out = (y == r) ? o : r;
-  for (int t = threadIdx.x; t < nl * m; t += blockDim.x) {
-    const int line = fdiv(t, P.sub.dn);
-    const int q = t - line * m;
-    const V* yl = y + (size_t)line * ls;
-    V v = cadd(yl[p], yl[q]);
-    if (INV) v.y = -v.y;
-    out[(size_t)line * ls + pool_index(si[q].x)] = v;
+  // ---- one or two forward passes through a single call site
+  V* r = src;
+#pragma unroll 1
+  for (int pass = 0; pass < (two ? 2 : 1); ++pass) {
+    r = fft_run<T>(src, dst, nl, ls, sp, pool + sp.tw);
+    V* o = (r == src) ? dst : src;
+    if (pass == 0 && two) {
+      for (int t = threadIdx.x; t < nl * m; t += blockDim.x) {
+        const int line = fdiv(t, sp.dn);
+        const int k = t - line * m;
+        V* x = r + (size_t)line * ls + k;
+        if (P.rd && k == 0) {  // A_0 = sum_{j>0} x_j, kept before the multiply overwrites it
+          r[(size_t)line * ls + n + 1] = *x;
+          o[(size_t)line * ls + n + 1] = *x;
+        }
+        V w = cmul(*x, bh[k]);
+        w.y = -w.y;
+        *x = w;
+      }
+      __syncthreads();
+    }
+    src = r;
+    dst = o;
   }
-  for (int line = threadIdx.x; line < nl; line += blockDim.x) {
-    const V* yl = y + (size_t)line * ls;
-    V v = cadd(yl[p], yl[p + 1]);
-    if (INV) v.y = -v.y;
-    out[(size_t)line * ls] = v;
+  // ---- output stage (r holds the result of the last pass)
+  if (P.rd) {
+    const V* si = pool + P.sidx;
+    V* out = dst;
+    for (int t = threadIdx.x; t < nl * m; t += blockDim.x) {
+      const int line = fdiv(t, sp.dn);
+      const int q = t - line * m;
+      const V* yl = r + (size_t)line * ls;
+      V v;
+      v.x = yl[n].x + yl[q].x;
+      v.y = yl[n].y - yl[q].y;
+      if (inv) v.y = -v.y;
+      out[(size_t)line * ls + pool_index(si[q].x)] = v;
+    }
+    for (int line = threadIdx.x; line < nl; line += blockDim.x) {
+      const V* yl = r + (size_t)line * ls;
+      V v = cadd(yl[n], yl[n + 1]);
+      if (inv) v.y = -v.y;
+      out[(size_t)line * ls] = v;
+    }
+    __syncthreads();
+    return out;
   }
-  __syncthreads();
-  return out;
+  if (P.bs) {
+    const V* ch = pool + P.chirp;
+    for (int t = threadIdx.x; t < nl * n; t += blockDim.x) {
+      const int line = fdiv(t, P.base.dn);
+      const int j = t - line * n;
+      V* x = r + (size_t)line * ls + j;
+      V z = *x;
+      z.y = -z.y;
+      V v = cmulc(z, ch[j]);
+      if (inv) v.y = -v.y;
+      *x = v;
+    }
+    __syncthreads();
+    return r;
+  }
+  if (inv) {
+    for (int t = threadIdx.x; t < nl * n; t += blockDim.x) {
+      const int line = fdiv(t, P.base.dn);
+      V* x = r + (size_t)line * ls + (t - line * n);
+      x->y = -x->y;
+    }
+    __syncthreads();
+  }
+  return r;
 }
 
-// Length-n DFT of nl lines (data in a[0..n) of each line; ls >= P.line_len()).
 template <typename T, bool INV>
-__device__ typename CT<T>::t* fft_any(typename CT<T>::t* a, typename CT<T>::t* b, int nl, int ls, const FftPlan& P,
-                                      const typename CT<T>::t* __restrict__ pool) {
-  typedef typename CT<T>::t V;
-  if (P.rd) return fft_rader<T, INV>(a, b, nl, ls, P, pool);
-  if (!P.bs) return fft_run<T, INV>(a, b, nl, ls, P.base, pool + P.base.tw);
-  const int n = P.base.n;
-  const int m = P.sub.n;
-  const V* ch = pool + P.chirp;
-  const V* bh = pool + P.bhat;
-  // a_j = x_j conj(c_j) (x conjugated first for the inverse), zero-padded to m
-  for (int t = threadIdx.x; t < nl * m; t += blockDim.x) {
-    const int line = fdiv(t, P.sub.dn);
-    const int j = t - line * m;
-    V* x = a + (size_t)line * ls + j;
-    if (j < n) {
-      V v = *x;
-      if (INV) v.y = -v.y;
-      *x = cmulc(v, ch[j]);
-    } else {
-      *x = mk<V>(0.0, 0.0);
-    }
-  }
-  __syncthreads();
-  V* r = fft_run<T, false>(a, b, nl, ls, P.sub, pool + P.sub.tw);
-  V* o = (r == a) ? b : a;
-  for (int t = threadIdx.x; t < nl * m; t += blockDim.x) {
-    const int line = fdiv(t, P.sub.dn);
-    const int j = t - line * m;
-    V* x = r + (size_t)line * ls + j;
-    *x = cmul(*x, bh[j]);
-  }
-  __syncthreads();
-  r = fft_run<T, true>(r, o, nl, ls, P.sub, pool + P.sub.tw);
-  for (int t = threadIdx.x; t < nl * n; t += blockDim.x) {
-    const int line = fdiv(t, P.base.dn);
-    const int j = t - line * n;
-    V* x = r + (size_t)line * ls + j;
-    V v = cmulc(*x, ch[j]);
-    if (INV) v.y = -v.y;
-    *x = v;
-  }
-  __syncthreads();
-  return r;
+__device__ __forceinline__ typename CT<T>::t* fft_any(typename CT<T>::t* a, typename CT<T>::t* b, int nl, int ls,
+                                                      const FftPlan& P, const typename CT<T>::t* __restrict__ pool) {
+  return fft_any_rt<T>(a, b, nl, ls, P, pool, INV);
 }
 
 }  // namespace fcsph

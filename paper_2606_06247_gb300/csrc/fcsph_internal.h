@@ -144,6 +144,9 @@ struct fcsph_ctx {
   cudaStream_t cap_stream = nullptr;
   fcsph::FftPlan plan_y, plan_x, plan_py, plan_px;  // FC-y, FC/periodic-x, PPE-y (DCT), PPE-x
   double* dE = nullptr;         // device [2][n_cont][2 n_match] (Dirichlet, Neumann)
+  void* dEff = nullptr;         // the same in FP32 pairs (FP32x2 contexts)
+  int row_lines = 1;            // rows per CTA of the one-warp row passes
+  int col_pairs = 1;            // column pairs per CTA of the one-warp column passes
   std::vector<double> hE[2];    // host copies
   double2* pool64 = nullptr;
   float2* pool32 = nullptr;
@@ -189,6 +192,8 @@ cudaError_t init_kernel_attributes();
 cudaError_t launch_fc_extend(fcsph_ctx* c, const void* f, void* fext, int bc);
 cudaError_t launch_col_fwd(fcsph_ctx* c, int prec, int nf, const void* const* fields, int fields_double, int bc,
                            void* spec, int dct);
+size_t tiling_smem(const fcsph_ctx* c, int row_lines, int col_pairs);
+size_t tiling_smem_limit();
 cudaError_t launch_row_sym(fcsph_ctx* c, int prec, const void* spec_in, void* spec_out, const RowOps& ops,
                            double scale, int bc, int kind);
 cudaError_t launch_col_out(fcsph_ctx* c, const void* spec, int nout, void* const* outs);

@@ -22,6 +22,15 @@ using namespace fcsph;
 namespace {
 
 constexpr int kThreads = 256;
+// FFT kernels run one warp per CTA: every barrier of the shared-memory FFT is
+// then a warp barrier and no warp waits on another.
+constexpr int kFftThreads = 32;
+// Minimum resident CTAs per SM asked of the register allocator: FP32-pair
+// code would otherwise take all 255 registers (8 one-warp CTAs per SM).
+template <typename T> struct MinCtas { static constexpr int v = 1; };
+template <> struct MinCtas<ff> { static constexpr int v = 12; };
+template <> struct MinCtas<double> { static constexpr int v = 12; };
+template <> struct MinCtas<float> { static constexpr int v = 16; };
 
 template <typename T> struct PoolOf;
 template <> struct PoolOf<double> { static const double2* get(const fcsph_ctx* c) { return c->pool64; } };
@@ -50,37 +59,63 @@ struct Dot2 {
   __device__ __forceinline__ double value() const { return s + c; }
 };
 
+// FC continuation sum of one line component in the transform's precision
+// class: compensated FP64 (Dot2, table in double) for FP64 and FP32
+// transforms, FP32-pair arithmetic (table in FP32 pairs) for FP32x2.
+template <typename T> struct FcTab { typedef double t; };
+template <> struct FcTab<ff> { typedef ff t; };
+
+template <typename T> struct FcAcc {
+  Dot2 a;
+  __device__ __forceinline__ void add(double e, T x) { a.add(e, (double)x); }
+  __device__ __forceinline__ T value() const { return (T)a.value(); }
+};
+template <> struct FcAcc<ff> {
+  ff a;
+  __device__ __forceinline__ void add(ff e, ff x) { a += e * x; }
+  __device__ __forceinline__ ff value() const { return a; }
+};
+
+// Appends the C continuation values of nl lines (stride ls, data in [0, n)):
+// line[n + c] = sum_m E[c][m] line[n - d + m] + E[c][d + m] line[m].
+template <typename T>
+__device__ __forceinline__ void fc_append(typename CT<T>::t* lines, int nl, int ls, int n, int C, int d,
+                                          const typename FcTab<T>::t* __restrict__ E) {
+  typedef typename CT<T>::t V;
+  for (int e = threadIdx.x; e < nl * C; e += blockDim.x) {
+    const int p = e / C, c = e - (e / C) * C;
+    V* L = lines + (size_t)p * ls;
+    const typename FcTab<T>::t* Er = E + c * 2 * d;
+    FcAcc<T> ax, ay;
+    for (int m = 0; m < d; ++m) {
+      const V vr = L[n - d + m];
+      const V vl = L[m];
+      ax.add(Er[m], vr.x);
+      ax.add(Er[d + m], vl.x);
+      ay.add(Er[m], vr.y);
+      ay.add(Er[d + m], vl.y);
+    }
+    L[n + c] = mk<V>(ax.value(), ay.value());
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Forward transform of packed column pairs held in shared memory.
 // lines: Pp lines of stride ls, line p has column i0+2p in .x and i0+2p+1 in
 // .y for j < ny.  dct = 0: FC-extend to my with table E ([C][2d], FP64
-// accumulation) and FFT (length my); dct = 1: even extension to 2(ny-1) and
+// accumulation, FP32 pairs for FP32x2) and FFT (length my); dct = 1: even extension to 2(ny-1) and
 // FFT (DCT-I, Eq. 31).  Stores the half spectrum (or the ny real DCT
 // coefficients as (c, 0)) into spec[ky][i] for this instance/field.
 template <typename T>
 __device__ void col_forward_store(typename CT<T>::t* lines, typename CT<T>::t* scratch, int Pp, int ls,
-                                  const GridDev& g, int i0, const double* __restrict__ E, const FftPlan& P,
+                                  const GridDev& g, int i0, const typename FcTab<T>::t* __restrict__ E,
+                                  const FftPlan& P,
                                   const typename CT<T>::t* __restrict__ pool, int dct,
                                   typename CT<T>::t* __restrict__ spec) {
   typedef typename CT<T>::t V;
   const int ny = g.ny;
   if (!dct) {
-    const int C = g.n_cont, d = g.n_match;
-    for (int e = threadIdx.x; e < Pp * C; e += blockDim.x) {
-      const int p = e / C, c = e - (e / C) * C;
-      const V* L = lines + (size_t)p * ls;
-      Dot2 ax, ay;
-      const double* Er = E + c * 2 * d;
-      for (int m = 0; m < d; ++m) {
-        const V vr = L[ny - d + m];
-        const V vl = L[m];
-        ax.add(Er[m], (double)vr.x);
-        ax.add(Er[d + m], (double)vl.x);
-        ay.add(Er[m], (double)vr.y);
-        ay.add(Er[d + m], (double)vl.y);
-      }
-      lines[(size_t)p * ls + ny + c] = mk<V>(ax.value(), ay.value());
-    }
+    fc_append<T>(lines, Pp, ls, ny, g.n_cont, g.n_match, E);
   } else {
     const int M = 2 * (ny - 1);
     for (int e = threadIdx.x; e < Pp * (ny - 2); e += blockDim.x) {
@@ -173,8 +208,8 @@ __device__ void col_gather_dct(typename CT<T>::t* lines, int Pp, int ls, const G
 // ---------------------------------------------------------------------------
 // Column forward: load nf real fields, FC (or DCT) + FFT, store spectra.
 template <typename T, typename U>
-__global__ void __launch_bounds__(kThreads) k_col_fwd(GridDev g, const U* __restrict__ f0, const U* __restrict__ f1,
-                                                      const double* __restrict__ E, FftPlan P,
+__global__ void __launch_bounds__(kFftThreads, MinCtas<T>::v) k_col_fwd(GridDev g, const U* __restrict__ f0, const U* __restrict__ f1,
+                                                         const typename FcTab<T>::t* __restrict__ E, const __grid_constant__ FftPlan P,
                                                       const typename CT<T>::t* __restrict__ pool, int dct,
                                                       typename CT<T>::t* __restrict__ spec, size_t fstride,
                                                       size_t bstride, int Pp, int ls) {
@@ -227,22 +262,24 @@ template <typename T> __device__ __forceinline__ T kernel_poly(int family, T s) 
 }
 
 // Row pass: for Rr rows ky of one instance: load nin input rows, FC-extend
-// in x (walled x), FFT (length mx), form each output sum_t S_t * F_t times
-// `scale`, inverse FFT, truncate to nx, store.
+// in x (walled x), FFT (length mx); then for each output in turn form
+// sum_t S_t * F_t times `scale`, inverse FFT, truncate to nx and store.
+// Shared memory: the nin input rows and their scratch (2 nin Rr lines; one
+// half holds the spectra, the other serves the outputs), plus Rr lines when
+// nin = 1.
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_row_sym(GridDev g, const typename CT<T>::t* __restrict__ sp_in,
-                                                      typename CT<T>::t* __restrict__ sp_out, size_t fstride_in,
-                                                      size_t bstride_in, size_t fstride_out, size_t bstride_out,
-                                                      RowOps ops, const double* __restrict__ E, FftPlan P,
-                                                      const typename CT<T>::t* __restrict__ pool, double scale,
-                                                      int Rr, int ls) {
+__global__ void __launch_bounds__(kFftThreads, MinCtas<T>::v) k_row_sym(GridDev g, const typename CT<T>::t* __restrict__ sp_in,
+                                                         typename CT<T>::t* __restrict__ sp_out, size_t fstride_in,
+                                                         size_t bstride_in, size_t fstride_out, size_t bstride_out,
+                                                         const __grid_constant__ RowOps ops,
+                                                         const typename FcTab<T>::t* __restrict__ E,
+                                                         const __grid_constant__ FftPlan P, const typename CT<T>::t* __restrict__ pool,
+                                                         double scale, int Rr, int ls) {
   typedef typename CT<T>::t V;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nin = ops.nin, nout = ops.nout;
   V* A = reinterpret_cast<V*>(smem_raw);
   V* B = A + (size_t)nin * Rr * ls;
-  V* Cq = B + (size_t)nin * Rr * ls;
-  V* D = Cq + (size_t)nout * Rr * ls;
   const int b = blockIdx.y;
   const int ky0 = blockIdx.x * Rr;
   const int nx = g.nx, mx = g.mx;
@@ -256,53 +293,42 @@ __global__ void __launch_bounds__(kThreads) k_row_sym(GridDev g, const typename 
   }
   __syncthreads();
   if (g.x_walls) {
-    const int C = g.n_cont, d = g.n_match;
-    for (int e = threadIdx.x; e < nin * Rr * C; e += blockDim.x) {
-      const int line = e / C, c = e - (e / C) * C;
-      const V* L = A + (size_t)line * ls;
-      const double* Er = E + c * 2 * d;
-      Dot2 ax, ay;
-      for (int m = 0; m < d; ++m) {
-        const V vr = L[nx - d + m];
-        const V vl = L[m];
-        ax.add(Er[m], (double)vr.x);
-        ax.add(Er[d + m], (double)vl.x);
-        ay.add(Er[m], (double)vr.y);
-        ay.add(Er[d + m], (double)vl.y);
-      }
-      A[(size_t)line * ls + nx + c] = mk<V>(ax.value(), ay.value());
-    }
+    fc_append<T>(A, nin * Rr, ls, nx, g.n_cont, g.n_match, E);
     __syncthreads();
   }
   V* X = fft_any<T, false>(A, B, nin * Rr, ls, P, pool);
+  V* Cq = (X == A) ? B : A;
+  V* D = nin >= 2 ? Cq + (size_t)Rr * ls : B + (size_t)Rr * ls;
   const T hh = (T)(g.h * g.h * 0.25);
   const T ckx = (T)(2.0 * 3.14159265358979323846 / (mx * g.dx));
   const T cky = (T)(2.0 * 3.14159265358979323846 / (g.my * g.dy));
-  for (int e = threadIdx.x; e < Rr * mx; e += blockDim.x) {
-    const int r = e / mx, kxi = e - (e / mx) * mx;
-    const int ky = ky0 + r;
-    const int kappa = (2 * kxi <= mx) ? kxi : kxi - mx;
-    const T kx = ckx * (T)kappa, kyw = cky * (T)ky;
-    const bool nyq_x = (mx % 2 == 0) && (2 * kxi == mx);
-    const bool nyq_y = (g.my % 2 == 0) && (2 * ky == g.my);
-    // e^{-s} = e^{-kx^2 h^2/4} e^{-ky^2 h^2/4} from the per-axis tables
-    const T What = pool[g.ex_off + kxi].x * pool[g.ey_off + ky].x * kernel_poly<T>(g.family, (kx * kx + kyw * kyw) * hh);
-    for (int o = 0; o < nout; ++o) {
+  const T tscale = (T)scale;
+  for (int o = 0; o < nout; ++o) {
+    for (int e = threadIdx.x; e < Rr * mx; e += blockDim.x) {
+      const int r = e / mx, kxi = e - (e / mx) * mx;
+      const int ky = ky0 + r;
+      const int kappa = (2 * kxi <= mx) ? kxi : kxi - mx;
+      const T kx = ckx * (T)kappa, kyw = cky * (T)ky;
+      const bool nyq_x = (mx % 2 == 0) && (2 * kxi == mx);
+      const bool nyq_y = (g.my % 2 == 0) && (2 * ky == g.my);
+      // e^{-s} = e^{-kx^2 h^2/4} e^{-ky^2 h^2/4} from the per-axis tables
+      const T What = pool[g.ex_off + kxi].x * pool[g.ey_off + (ky < g.hy ? ky : 0)].x *
+                     kernel_poly<T>(g.family, (kx * kx + kyw * kyw) * hh);
       V acc = mk<V>(0.0, 0.0);
       for (int t = 0; t < ops.nterm[o]; ++t) {
         const V s = symbol<T>(ops.op[o][t], kx, kyw, nyq_x, nyq_y, What);
         acc = cadd(acc, cmul(s, X[((size_t)ops.field[o][t] * Rr + r) * ls + kxi]));
       }
-      Cq[((size_t)o * Rr + r) * ls + kxi] = cscale(acc, (T)scale);
+      Cq[(size_t)r * ls + kxi] = cscale(acc, tscale);
     }
-  }
-  __syncthreads();
-  V* Y = fft_any<T, true>(Cq, D, nout * Rr, ls, P, pool);
-  for (int e = threadIdx.x; e < nout * Rr * nx; e += blockDim.x) {
-    const int line = e / nx, i = e - (e / nx) * nx;
-    const int o = line / Rr, r = line - (line / Rr) * Rr;
-    const int ky = ky0 + r;
-    if (ky < g.hy) sp_out[b * bstride_out + o * fstride_out + (size_t)ky * nx + i] = Y[(size_t)line * ls + i];
+    __syncthreads();
+    V* Y = fft_any<T, true>(Cq, D, Rr, ls, P, pool);
+    for (int e = threadIdx.x; e < Rr * nx; e += blockDim.x) {
+      const int r = e / nx, i = e - (e / nx) * nx;
+      const int ky = ky0 + r;
+      if (ky < g.hy) sp_out[b * bstride_out + o * fstride_out + (size_t)ky * nx + i] = Y[(size_t)r * ls + i];
+    }
+    __syncthreads();
   }
 }
 
@@ -314,8 +340,8 @@ __global__ void __launch_bounds__(kThreads) k_row_sym(GridDev g, const typename 
 // (apply = 2, removes the constant mode), times the inverse-transform scales,
 // transform back, store.
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_row_ppe(GridDev g, typename CT<T>::t* __restrict__ spec,
-                                                      size_t bstride, FftPlan P,
+__global__ void __launch_bounds__(kFftThreads, MinCtas<T>::v) k_row_ppe(GridDev g, typename CT<T>::t* __restrict__ spec,
+                                                      size_t bstride, const __grid_constant__ FftPlan P,
                                                       const typename CT<T>::t* __restrict__ pool, int apply, int Rr,
                                                       int ls) {
   typedef typename CT<T>::t V;
@@ -394,12 +420,11 @@ struct EpiArgs {
   double* phi;        // PPE_*: out phi / residual / accumulate
   void* phi_any;      // PPE_SOLVE in the context's I/O type when not double
   int phi_double;
-  int mom_comp;       // EPI_MOM: 0 both components (6 outputs), 1 u only, 2 v only (3 outputs)
   StepDev s;
   // fused forward: nf fields, table, plan, output spectra, dct
   int fwd_nf;
   int fwd_dct;
-  const double* fwdE;
+  const void* fwdE;   // FC table in the transform's FcTab type
   FftPlan fwdP;
   void* fwd_spec;
   size_t fwd_fstride, fwd_bstride;
@@ -408,120 +433,152 @@ struct EpiArgs {
 
 // The epilogue kind is a runtime argument (uniform across the grid): one
 // instantiation per precision keeps the build small.
+//
+// Column pairs i0 + 2p, i0 + 2p + 1 (p < Pp) of one instance.  The nout
+// inverse transforms run one at a time: gather the half spectrum of output o
+// into packed lines Z, inverse FFT (scratch S), then the epilogue consumes
+// output o.  Per-point FP64 values that later outputs or the fused forward
+// need live in `acc` (nacc double2 lines of ny per pair: the two columns in
+// .x / .y): the momentum terms accumulate there (u.grad + nu lap per
+// component), the other epilogues leave the new field there.  The fused
+// forward then transforms acc[f] (f < fwd_nf) with Z and S as its lines.
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_col_inv(GridDev g, const typename CT<T>::t* __restrict__ spec,
-                                                      size_t fstride, size_t bstride, int nout, int nlines,
-                                                      FftPlan P, const typename CT<T>::t* __restrict__ pool,
-                                                      EpiArgs ea, int Pp, int ls, const int EPI) {
+__global__ void __launch_bounds__(kFftThreads, MinCtas<T>::v) k_col_inv(GridDev g, const typename CT<T>::t* __restrict__ spec,
+                                                         size_t fstride, size_t bstride, int nout, int nacc,
+                                                         const __grid_constant__ FftPlan P,
+                                                         const typename CT<T>::t* __restrict__ pool,
+                                                         const __grid_constant__ EpiArgs ea, int Pp, int ls,
+                                                         const int EPI) {
   typedef typename CT<T>::t V;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* Z = reinterpret_cast<V*>(smem_raw);
-  V* S = Z + (size_t)nlines * Pp * ls;
+  V* S = Z + (size_t)Pp * ls;
+  double2* acc = reinterpret_cast<double2*>(S + (size_t)Pp * ls);
   const int b = blockIdx.y;
   const int i0 = blockIdx.x * 2 * Pp;
   const int ny = g.ny;
   const bool ppe = (EPI == EPI_PPE_SOLVE || EPI == EPI_PPE_RESID || EPI == EPI_PPE_ADD);
-  V* R;
-  if (ppe) {
-    col_gather_dct<T>(Z, Pp, ls, g, i0, spec + b * bstride);
-    __syncthreads();
-    R = fft_any<T, false>(Z, S, Pp, ls, P, pool);
-  } else {
-    col_gather_hermitian<T>(Z, Pp, ls, g, i0, spec + b * bstride, fstride, nout, P.base.n);
-    __syncthreads();
-    R = fft_any<T, true>(Z, S, nout * Pp, ls, P, pool);
-  }
-  V* F = (R == Z) ? S : Z;  // free region for the fused forward
-  const int W = 2 * Pp;
-  for (int e = threadIdx.x; e < Pp * ny; e += blockDim.x) {
-    const int p = e / ny, j = e - (e / ny) * ny;
-    double nv[2][2];  // [field][column]
+  for (int o = 0; o < nout; ++o) {
+    V* R;
+    if (ppe) {
+      col_gather_dct<T>(Z, Pp, ls, g, i0, spec + b * bstride);
+      __syncthreads();
+      R = fft_any<T, false>(Z, S, Pp, ls, P, pool);
+    } else {
+      col_gather_hermitian<T>(Z, Pp, ls, g, i0, spec + b * bstride + o * fstride, fstride, 1, P.base.n);
+      __syncthreads();
+      R = fft_any<T, true>(Z, S, Pp, ls, P, pool);
+    }
+    for (int e = threadIdx.x; e < Pp * ny; e += blockDim.x) {
+      const int p = e / ny, j = e - (e / ny) * ny;
+      const V z = R[(size_t)p * ls + j];
+      double2* A = acc + (size_t)p * ny + j;  // + f * Pp * ny for field f
 #pragma unroll
-    for (int w = 0; w < 2; ++w) {
-      const int i = i0 + 2 * p + w;
-      nv[0][w] = nv[1][w] = 0.0;
-      if (i >= g.nx) continue;
-      const size_t id = fidx(g, b, i, j);
-      double val[6];
-      for (int o = 0; o < (ppe ? 1 : nout); ++o) {
-        const V z = R[((size_t)o * Pp + p) * ls + j];
-        val[o] = (double)(w ? z.y : z.x);
-      }
-      if (EPI == EPI_OUT) {
-        for (int o = 0; o < nout; ++o) {
+      for (int w = 0; w < 2; ++w) {
+        const int i = i0 + 2 * p + w;
+        if (i >= g.nx) continue;
+        const size_t id = fidx(g, b, i, j);
+        const double val = (double)(w ? z.y : z.x);
+        double nv = 0.0;
+        int slot = -1;
+        if (EPI == EPI_OUT) {
           if (ea.out_double)
-            reinterpret_cast<double*>(ea.outs[o])[id] = val[o];
+            reinterpret_cast<double*>(ea.outs[o])[id] = val;
           else
-            reinterpret_cast<float*>(ea.outs[o])[id] = (float)val[o];
+            reinterpret_cast<float*>(ea.outs[o])[id] = (float)val;
+        } else if (EPI == EPI_MOM) {
+          // outputs 0-2: u_x, u_y, lap u of u; 3-5 the same of v
+          const int comp = o / 3, term = o - comp * 3;
+          double* a = w ? &A[(size_t)comp * Pp * ny].y : &A[(size_t)comp * Pp * ny].x;
+          if (term == 0) {
+            *a = ea.u[id] * val;
+          } else if (term == 1) {
+            *a += ea.v[id] * val;
+          } else {
+            const double nu = ea.s.nu_inst ? ea.s.nu_inst[b] : ea.s.nu;
+            const double F = *a - nu * val;
+            if (comp == 0) {
+              const double u = ea.u[id];
+              const double fx = ea.s.fx_inst ? ea.s.fx_inst[b] : ea.s.fx;
+              double us = u + ea.s.dt * (-ea.s.g * F - ea.s.z * ea.fu[id] + ea.s.a * fx);
+              if (j == 0) us = ea.s.u_bottom;
+              if (j == ny - 1) us = ea.s.u_top;
+              if (g.x_walls && (i == 0 || i == g.nx - 1)) us = 0.0;
+              ea.fu[id] = F;
+              ea.us[id] = us;
+              if (!isfinite(us)) atomicOr(ea.status, 1);
+              *a = us;
+            } else {
+              const double v = ea.v[id];
+              double vs = v + ea.s.dt * (-ea.s.g * F - ea.s.z * ea.fv[id] + ea.s.a * ea.s.fy);
+              if (j == 0 || j == ny - 1) vs = 0.0;
+              if (g.x_walls && (i == 0 || i == g.nx - 1)) vs = 0.0;
+              ea.fv[id] = F;
+              ea.vs[id] = vs;
+              if (!isfinite(vs)) atomicOr(ea.status, 1);
+              *a = vs;
+            }
+          }
+        } else if (EPI == EPI_DIV) {
+          nv = ea.s.rho / (ea.s.a * ea.s.dt) * val;
+          ea.bvec[id] = nv;
+          slot = 0;
+        } else if (EPI == EPI_CORR) {
+          const double c = ea.s.a * ea.s.dt / ea.s.rho;
+          if (o == 0) {
+            double u = ea.us[id] - c * val;
+            if (j == 0) u = ea.s.u_bottom;
+            if (j == ny - 1) u = ea.s.u_top;
+            if (g.x_walls && (i == 0 || i == g.nx - 1)) u = 0.0;
+            ea.uo[id] = u;
+            if (!isfinite(u)) atomicOr(ea.status, 1);
+            nv = u;
+          } else {
+            double v = ea.vs[id] - c * val;
+            if (j == 0 || j == ny - 1) v = 0.0;
+            if (g.x_walls && (i == 0 || i == g.nx - 1)) v = 0.0;
+            ea.vo[id] = v;
+            if (!isfinite(v)) atomicOr(ea.status, 1);
+            nv = v;
+          }
+          slot = o;
+        } else if (EPI == EPI_PPE_SOLVE) {
+          if (ea.phi_double)
+            reinterpret_cast<double*>(ea.phi_any)[id] = val;
+          else
+            reinterpret_cast<float*>(ea.phi_any)[id] = (float)val;
+          if (ea.phi) ea.phi[id] = val;
+          nv = val;
+          slot = 0;
+        } else if (EPI == EPI_PPE_RESID) {
+          ea.phi[id] = ea.bvec[id] - val;  // r = b - L phi
+        } else if (EPI == EPI_PPE_ADD) {
+          nv = ea.phi[id] + val;
+          ea.phi[id] = nv;
+          slot = 0;
         }
-      } else if (EPI == EPI_MOM) {
-        const double u = ea.u[id], v = ea.v[id];
-        const double nu = ea.s.nu_inst ? ea.s.nu_inst[b] : ea.s.nu;
-        int slot = 0;
-        if (ea.mom_comp != 2) {
-          const double fx = ea.s.fx_inst ? ea.s.fx_inst[b] : ea.s.fx;
-          const double Fu = u * val[0] + v * val[1] - nu * val[2];
-          double us = u + ea.s.dt * (-ea.s.g * Fu - ea.s.z * ea.fu[id] + ea.s.a * fx);
-          if (j == 0) us = ea.s.u_bottom;
-          if (j == ny - 1) us = ea.s.u_top;
-          if (g.x_walls && (i == 0 || i == g.nx - 1)) us = 0.0;
-          ea.fu[id] = Fu;
-          ea.us[id] = us;
-          if (!isfinite(us)) atomicOr(ea.status, 1);
-          nv[slot++][w] = us;
+        if (slot >= 0 && slot < nacc) {
+          double2* a = A + (size_t)slot * Pp * ny;
+          if (w)
+            a->y = nv;
+          else
+            a->x = nv;
         }
-        if (ea.mom_comp != 1) {
-          const int o = ea.mom_comp == 2 ? 0 : 3;
-          const double Fv = u * val[o] + v * val[o + 1] - nu * val[o + 2];
-          double vs = v + ea.s.dt * (-ea.s.g * Fv - ea.s.z * ea.fv[id] + ea.s.a * ea.s.fy);
-          if (j == 0 || j == ny - 1) vs = 0.0;
-          if (g.x_walls && (i == 0 || i == g.nx - 1)) vs = 0.0;
-          ea.fv[id] = Fv;
-          ea.vs[id] = vs;
-          if (!isfinite(vs)) atomicOr(ea.status, 1);
-          nv[slot][w] = vs;
-        }
-      } else if (EPI == EPI_DIV) {
-        const double bb = ea.s.rho / (ea.s.a * ea.s.dt) * val[0];
-        ea.bvec[id] = bb;
-        nv[0][w] = bb;
-      } else if (EPI == EPI_CORR) {
-        const double c = ea.s.a * ea.s.dt / ea.s.rho;
-        double u = ea.us[id] - c * val[0];
-        double v = ea.vs[id] - c * val[1];
-        if (j == 0) { u = ea.s.u_bottom; v = 0.0; }
-        if (j == ny - 1) { u = ea.s.u_top; v = 0.0; }
-        if (g.x_walls && (i == 0 || i == g.nx - 1)) { u = 0.0; v = 0.0; }
-        ea.uo[id] = u;
-        ea.vo[id] = v;
-        if (!isfinite(u) || !isfinite(v)) atomicOr(ea.status, 1);
-        nv[0][w] = u;
-        nv[1][w] = v;
-      } else if (EPI == EPI_PPE_SOLVE) {
-        if (ea.phi_double)
-          reinterpret_cast<double*>(ea.phi_any)[id] = val[0];
-        else
-          reinterpret_cast<float*>(ea.phi_any)[id] = (float)val[0];
-        if (ea.phi) ea.phi[id] = val[0];
-        nv[0][w] = val[0];
-      } else if (EPI == EPI_PPE_RESID) {
-        ea.phi[id] = ea.bvec[id] - val[0];  // r = b - L phi
-      } else if (EPI == EPI_PPE_ADD) {
-        const double ph = ea.phi[id] + val[0];
-        ea.phi[id] = ph;
-        nv[0][w] = ph;
       }
     }
-    if (ea.fwd_nf > 0) {
-      for (int f = 0; f < ea.fwd_nf; ++f) F[(size_t)f * Pp * ls + (size_t)p * ls + j] = mk<V>(nv[f][0], nv[f][1]);
-    }
+    __syncthreads();
   }
-  if (ea.fwd_nf <= 0) return;
-  __syncthreads();
   for (int f = 0; f < ea.fwd_nf; ++f) {
-    // forward of field f uses the lines of F (f-th block) with R as scratch
-    col_forward_store<T>(F + (size_t)f * Pp * ls, R, Pp, ls, g, i0, ea.fwdE, ea.fwdP, pool, ea.fwd_dct,
-                         reinterpret_cast<V*>(ea.fwd_spec) + b * ea.fwd_bstride + f * ea.fwd_fstride);
+    // fields beyond nx (ragged last pair) are zero
+    for (int e = threadIdx.x; e < Pp * ny; e += blockDim.x) {
+      const int p = e / ny, j = e - (e / ny) * ny;
+      const double2 a = acc[((size_t)f * Pp + p) * ny + j];
+      const int i = i0 + 2 * p;
+      Z[(size_t)p * ls + j] = mk<V>(i < g.nx ? a.x : 0.0, i + 1 < g.nx ? a.y : 0.0);
+    }
+    __syncthreads();
+    col_forward_store<T>(Z, S, Pp, ls, g, i0, reinterpret_cast<const typename FcTab<T>::t*>(ea.fwdE), ea.fwdP, pool,
+                         ea.fwd_dct, reinterpret_cast<V*>(ea.fwd_spec) + b * ea.fwd_bstride + f * ea.fwd_fstride);
     __syncthreads();
   }
 }
@@ -577,7 +634,7 @@ __global__ void k_fc_extend_x(GridDev g, U* __restrict__ fe, const double* __res
 // in memory (double2 for the double-float engine, else the engine's own).
 template <typename T, bool INV, typename IO = typename CT<T>::t>
 __global__ void __launch_bounds__(kThreads) k_dft_lines(int n, int nlines, const IO* __restrict__ in,
-                                                        IO* __restrict__ out, FftPlan P,
+                                                        IO* __restrict__ out, const __grid_constant__ FftPlan P,
                                                         const typename CT<T>::t* __restrict__ pool, int L, int ls) {
   typedef typename CT<T>::t V;
   typedef decltype(IO().x) E;
@@ -670,17 +727,7 @@ int fit_units(size_t per_unit, size_t budget, int cap) {
   return u;
 }
 
-// Units per CTA so that `total` units spread over at least ~4 CTAs per SM
-// (152 SMs), within the shared-memory fit.
-int spread_units(int fit, long long total) {
-  const long long target = 4LL * 152;
-  long long u = (total + target - 1) / target;
-  if (u < 1) u = 1;
-  if (u > fit) u = fit;
-  return (int)u;
-}
-
-constexpr size_t kSmemBudget = 96 * 1024;  // per CTA, leaves room for 2 CTAs/SM
+constexpr size_t kSmemBudget = 96 * 1024;  // per CTA of the multi-line engine test kernel
 constexpr size_t kSmemMax = 227 * 1024;
 
 // Every kernel's dynamic shared-memory limit is raised once, at the first
@@ -692,6 +739,13 @@ template <typename K> cudaError_t set_smem(K, size_t bytes) {
 
 template <typename K> cudaError_t raise_smem(K kernel) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax);
+}
+
+// FC table (bc) in the FcTab type of precision prec.
+const void* fc_table(const fcsph_ctx* c, int prec, int bc) {
+  const size_t off = (bc == FCSPH_NEUMANN ? 1 : 0) * (size_t)c->gd.n_cont * 2 * c->gd.n_match;
+  if (prec == FCSPH_F32X2) return static_cast<const ff*>(c->dEff) + off;
+  return c->dE + off;
 }
 
 int col_ls(const fcsph_ctx* c) {
@@ -732,6 +786,19 @@ cudaError_t init_kernel_attributes() {
   return cudaSuccess;
 }
 
+// Largest dynamic shared memory any FFT kernel of context c needs with
+// row_lines rows per row-pass CTA and col_pairs column pairs per column CTA.
+size_t tiling_smem(const fcsph_ctx* c, int row_lines, int col_pairs) {
+  const size_t cb = c->prec.fft_prec == FCSPH_F32 ? sizeof(float2) : sizeof(double2);
+  const size_t row = 4 * (size_t)row_lines * c->plan_x.line_len() * cb;
+  const size_t ppe = 2 * (size_t)row_lines * c->plan_px.line_len() * cb;
+  const size_t col = (size_t)col_pairs * (2 * (size_t)col_ls(c) * cb + 2 * (size_t)c->gd.ny * sizeof(double2));
+  size_t m = row > ppe ? row : ppe;
+  return m > col ? m : col;
+}
+
+size_t tiling_smem_limit() { return kSmemMax; }
+
 cudaError_t launch_fc_extend(fcsph_ctx* c, const void* f, void* fext, int bc) {
   ProfScope ps(c, FCSPH_PROF_OTHER);
   const double* E = c->dE + (bc == FCSPH_NEUMANN ? 1 : 0) * c->gd.n_cont * 2 * c->gd.n_match;
@@ -754,24 +821,25 @@ cudaError_t launch_fc_extend(fcsph_ctx* c, const void* f, void* fext, int bc) {
   return cudaGetLastError();
 }
 
+
 template <typename T, typename U>
-static cudaError_t col_fwd_t(fcsph_ctx* c, int nf, const void* const* fields, int bc, void* spec, int dct) {
+static cudaError_t col_fwd_t(fcsph_ctx* c, int prec, int nf, const void* const* fields, int bc, void* spec, int dct) {
   const GridDev& g = c->gd;
   const FftPlan& P = dct ? c->plan_py : c->plan_y;
-  const int ls = col_ls(c);
-  const size_t per = 2 * (size_t)ls * sizeof(typename CT<T>::t);
-  const int Pp = spread_units(fit_units(per, kSmemBudget, (g.nx + 1) / 2), (long long)nf * g.batch * ((g.nx + 1) / 2));
-  const size_t smem = per * Pp;
+  const int ls = P.line_len();
+  const int Pp = c->col_pairs;
+  const size_t smem = 2 * (size_t)ls * sizeof(typename CT<T>::t) * Pp;
   cudaError_t e = set_smem(k_col_fwd<T, U>, smem);
   if (e != cudaSuccess) return e;
-  const double* E = c->dE + (bc == FCSPH_NEUMANN ? 1 : 0) * g.n_cont * 2 * g.n_match;
+  const auto* E = static_cast<const typename FcTab<T>::t*>(fc_table(c, prec, bc));
   dim3 grid((g.nx + 2 * Pp - 1) / (2 * Pp), nf, g.batch);
   const size_t fstride = (size_t)g.rows * g.nx;
   const size_t bstride = (dct ? 1 : 2) * fstride;
   ProfScope ps(c, FCSPH_PROF_COL_FWD);
-  k_col_fwd<T, U><<<grid, kThreads, smem, c->stream>>>(g, (const U*)fields[0], (const U*)(nf > 1 ? fields[1] : fields[0]),
-                                                       E, P, PoolOf<T>::get(c), dct, (typename CT<T>::t*)spec, fstride,
-                                                       bstride, Pp, ls);
+  k_col_fwd<T, U><<<grid, kFftThreads, smem, c->stream>>>(g, (const U*)fields[0],
+                                                          (const U*)(nf > 1 ? fields[1] : fields[0]), E, P,
+                                                          PoolOf<T>::get(c), dct, (typename CT<T>::t*)spec, fstride,
+                                                          bstride, Pp, ls);
   c->launches++;
   return cudaGetLastError();
 }
@@ -780,107 +848,72 @@ cudaError_t launch_col_fwd(fcsph_ctx* c, int prec, int nf, const void* const* fi
                            void* spec, int dct) {
   if (prec == FCSPH_F64) {
     if (!fields_double) return cudaErrorInvalidValue;
-    return col_fwd_t<double, double>(c, nf, fields, bc, spec, dct);
+    return col_fwd_t<double, double>(c, prec, nf, fields, bc, spec, dct);
   }
   if (prec == FCSPH_F32X2) {
     if (!fields_double) return cudaErrorInvalidValue;
-    return col_fwd_t<ff, double>(c, nf, fields, bc, spec, dct);
+    return col_fwd_t<ff, double>(c, prec, nf, fields, bc, spec, dct);
   }
-  if (fields_double) return col_fwd_t<float, double>(c, nf, fields, bc, spec, dct);
-  return col_fwd_t<float, float>(c, nf, fields, bc, spec, dct);
+  if (fields_double) return col_fwd_t<float, double>(c, prec, nf, fields, bc, spec, dct);
+  return col_fwd_t<float, float>(c, prec, nf, fields, bc, spec, dct);
 }
 
 template <typename T>
-static cudaError_t row_sym_t(fcsph_ctx* c, const void* sp_in, void* sp_out, const RowOps& ops, double scale, int bc,
-                             int kind) {
+static cudaError_t row_sym_t(fcsph_ctx* c, int prec, const void* sp_in, void* sp_out, const RowOps& ops, double scale,
+                             int bc, int kind) {
   const GridDev& g = c->gd;
   const int ls = c->plan_x.line_len();
-  const size_t per = (size_t)(2 * ops.nin + 2 * ops.nout) * ls * sizeof(typename CT<T>::t);
-  const int Rr = spread_units(fit_units(per, kSmemBudget, 8), (long long)g.batch * g.hy);
-  const size_t smem = per * Rr;
+  const int Rr = c->row_lines;
+  const int nlines = 2 * ops.nin + (ops.nin == 1 ? 1 : 0);
+  const size_t smem = (size_t)nlines * Rr * ls * sizeof(typename CT<T>::t);
   cudaError_t e = set_smem(k_row_sym<T>, smem);
   if (e != cudaSuccess) return e;
-  const double* E = c->dE + (bc == FCSPH_NEUMANN ? 1 : 0) * g.n_cont * 2 * g.n_match;
+  const auto* E = static_cast<const typename FcTab<T>::t*>(fc_table(c, prec, bc));
   const size_t fs = (size_t)g.rows * g.nx;
   dim3 grid((g.hy + Rr - 1) / Rr, g.batch);
   ProfScope ps(c, kind);
-  k_row_sym<T><<<grid, kThreads, smem, c->stream>>>(g, (const typename CT<T>::t*)sp_in, (typename CT<T>::t*)sp_out, fs,
-                                                    2 * fs, fs, 6 * fs, ops, E, c->plan_x, PoolOf<T>::get(c), scale, Rr,
-                                                    ls);
+  k_row_sym<T><<<grid, kFftThreads, smem, c->stream>>>(g, (const typename CT<T>::t*)sp_in, (typename CT<T>::t*)sp_out,
+                                                       fs, 2 * fs, fs, 6 * fs, ops, E, c->plan_x, PoolOf<T>::get(c),
+                                                       scale, Rr, ls);
   c->launches++;
   return cudaGetLastError();
 }
 
-static cudaError_t row_sym_any(fcsph_ctx* c, int prec, const void* sp_in, void* sp_out, const RowOps& ops,
-                               double scale, int bc, int kind) {
-  if (prec == FCSPH_F64) return row_sym_t<double>(c, sp_in, sp_out, ops, scale, bc, kind);
-  if (prec == FCSPH_F32X2) return row_sym_t<ff>(c, sp_in, sp_out, ops, scale, bc, kind);
-  return row_sym_t<float>(c, sp_in, sp_out, ops, scale, bc, kind);
-}
-
-// When one row would need more shared memory than the budget and every output
-// is a single term, the pass runs once per input field (outputs of a field
-// must be contiguous), each with its own input row and output rows.
+// One launch for any number of outputs: the outputs are formed and inverted
+// one at a time, so shared memory does not grow with them.
 cudaError_t launch_row_sym(fcsph_ctx* c, int prec, const void* sp_in, void* sp_out, const RowOps& ops, double scale,
                            int bc, int kind) {
-  const size_t cb = prec == FCSPH_F32 ? sizeof(float2) : sizeof(double2);
-  const size_t per = (size_t)(2 * ops.nin + 2 * ops.nout) * c->plan_x.line_len() * cb;
-  bool single = true;
-  for (int o = 0; o < ops.nout && single; ++o) single = ops.nterm[o] == 1 && (o == 0 || ops.field[o][0] >= ops.field[o - 1][0]);
-  if (per <= kSmemBudget || !single) return row_sym_any(c, prec, sp_in, sp_out, ops, scale, bc, kind);
-  const size_t fs = (size_t)c->gd.rows * c->gd.nx * cb;
-  const size_t line = (size_t)c->plan_x.line_len() * cb;
-  int gmax = (int)((kSmemMax / line - 2) / 2);  // outputs per launch with one input: (2 + 2 g) lines
-  if (gmax < 1) return cudaErrorInvalidValue;
-  for (int f = 0; f < ops.nin; ++f) {
-    int first = -1, cnt = 0;
-    for (int o = 0; o < ops.nout; ++o)
-      if (ops.field[o][0] == f) {
-        if (first < 0) first = o;
-        ++cnt;
-      }
-    for (int g0 = 0; g0 < cnt; g0 += gmax) {
-      RowOps sub;
-      memset(&sub, 0, sizeof(sub));
-      sub.nin = 1;
-      for (int o = g0; o < cnt && o < g0 + gmax; ++o) {
-        sub.nterm[sub.nout] = 1;
-        sub.field[sub.nout][0] = 0;
-        sub.op[sub.nout][0] = ops.op[first + o][0];
-        sub.nout++;
-      }
-      cudaError_t e = row_sym_any(c, prec, (const char*)sp_in + f * fs, (char*)sp_out + (first + g0) * fs, sub, scale,
-                                  bc, kind);
-      if (e != cudaSuccess) return e;
-    }
-  }
-  return cudaSuccess;
+  if (prec == FCSPH_F64) return row_sym_t<double>(c, prec, sp_in, sp_out, ops, scale, bc, kind);
+  if (prec == FCSPH_F32X2) return row_sym_t<ff>(c, prec, sp_in, sp_out, ops, scale, bc, kind);
+  return row_sym_t<float>(c, prec, sp_in, sp_out, ops, scale, bc, kind);
 }
 
 template <typename T>
 static cudaError_t col_inv_common(fcsph_ctx* c, int epi, const void* spec, int nout, EpiArgs& ea) {
-  // nout inverse lines per column pair; the fused forward reuses that space
   const GridDev& g = c->gd;
-  const int ls = col_ls(c);
-  const int lines = nout > ea.fwd_nf ? nout : (ea.fwd_nf > 0 ? ea.fwd_nf : 1);
-  const size_t per = 2 * (size_t)lines * ls * sizeof(typename CT<T>::t);
-  const int Pp = spread_units(fit_units(per, kSmemBudget, (g.nx + 1) / 2), (long long)g.batch * ((g.nx + 1) / 2));
-  const size_t smem = per * Pp;
+  const FftPlan& P = epi >= EPI_PPE_SOLVE ? c->plan_py : c->plan_y;
+  // lines sized for the inverse plan and the fused forward's plan
+  int ls = P.line_len();
+  if (ea.fwd_nf > 0 && ea.fwdP.line_len() > ls) ls = ea.fwdP.line_len();
+  const int Pp = c->col_pairs;
+  // FP64 per-point values kept across outputs: the two momentum components,
+  // else the fields of the fused forward
+  const int nacc = epi == EPI_MOM ? 2 : ea.fwd_nf;
+  const size_t smem = ((size_t)2 * ls * sizeof(typename CT<T>::t) + (size_t)nacc * g.ny * sizeof(double2)) * Pp;
   const size_t fs = (size_t)g.rows * g.nx;
   const size_t bs = (epi >= EPI_PPE_SOLVE ? 1 : 6) * fs;  // spec_ppe or spec_out
   dim3 grid((g.nx + 2 * Pp - 1) / (2 * Pp), g.batch);
-  const FftPlan& P = epi >= EPI_PPE_SOLVE ? c->plan_py : c->plan_y;
   const typename CT<T>::t* pool = PoolOf<T>::get(c);
   if (epi < EPI_OUT || epi > EPI_PPE_ADD) return cudaErrorInvalidValue;
+  if (ea.fwd_nf > 2 || (epi == EPI_MOM && nout != 6)) return cudaErrorInvalidValue;
   ea.status = c->dstatus;
   static const int kinds[7] = {FCSPH_PROF_COL_OUT, FCSPH_PROF_COL_MOM, FCSPH_PROF_COL_DIV, FCSPH_PROF_COL_CORR,
                                FCSPH_PROF_COL_PPE, FCSPH_PROF_COL_PPE, FCSPH_PROF_COL_PPE};
   ProfScope ps(c, kinds[epi]);
   cudaError_t e = set_smem(k_col_inv<T>, smem);
   if (e != cudaSuccess) return e;
-  k_col_inv<T><<<grid, kThreads, smem, c->stream>>>(g, (const typename CT<T>::t*)spec, fs, bs, nout, lines, P, pool, ea,
-                                                    Pp, ls, epi);
-
+  k_col_inv<T><<<grid, kFftThreads, smem, c->stream>>>(g, (const typename CT<T>::t*)spec, fs, bs, nout, nacc, P, pool,
+                                                       ea, Pp, ls, epi);
   c->launches++;
   return cudaGetLastError();
 }
@@ -908,15 +941,14 @@ template <typename T>
 static cudaError_t row_ppe_t(fcsph_ctx* c, void* spec, int apply) {
   const GridDev& g = c->gd;
   const int ls = c->plan_px.line_len();
-  const size_t per = 2 * (size_t)ls * sizeof(typename CT<T>::t);
-  const int Rr = spread_units(fit_units(per, kSmemBudget, 16), (long long)g.batch * g.ny);
-  const size_t smem = per * Rr;
+  const int Rr = c->row_lines;
+  const size_t smem = 2 * (size_t)ls * sizeof(typename CT<T>::t) * Rr;
   cudaError_t e = set_smem(k_row_ppe<T>, smem);
   if (e != cudaSuccess) return e;
   dim3 grid((g.ny + Rr - 1) / Rr, g.batch);
   ProfScope ps(c, FCSPH_PROF_ROW_PPE);
-  k_row_ppe<T><<<grid, kThreads, smem, c->stream>>>(g, (typename CT<T>::t*)spec, (size_t)g.rows * g.nx, c->plan_px,
-                                                    PoolOf<T>::get(c), apply, Rr, ls);
+  k_row_ppe<T><<<grid, kFftThreads, smem, c->stream>>>(g, (typename CT<T>::t*)spec, (size_t)g.rows * g.nx, c->plan_px,
+                                                       PoolOf<T>::get(c), apply, Rr, ls);
   c->launches++;
   return cudaGetLastError();
 }
@@ -948,7 +980,7 @@ cudaError_t launch_col_ppe_inv(fcsph_ctx* c, int prec, const void* spec, void* p
   if (neumann_fwd) {
     ea.fwd_nf = 1;
     ea.fwd_dct = 0;
-    ea.fwdE = c->dE + c->gd.n_cont * 2 * c->gd.n_match;
+    ea.fwdE = fc_table(c, prec, FCSPH_NEUMANN);
     ea.fwdP = c->plan_y;
     ea.fwd_spec = spec_fwd;
     ea.fwd_fstride = (size_t)c->gd.rows * c->gd.nx;
@@ -967,28 +999,14 @@ cudaError_t launch_step_mom(fcsph_ctx* c, const StepDev& s, const void* spec6, c
   ea.us = us;
   ea.vs = vs;
   ea.s = s;
+  ea.fwd_nf = 2;
   ea.fwd_dct = 0;
-  ea.fwdE = c->dE;
+  ea.fwdE = fc_table(c, c->prec.fft_prec, FCSPH_DIRICHLET);
   ea.fwdP = c->plan_y;
+  ea.fwd_spec = spec2;
   ea.fwd_fstride = (size_t)c->gd.rows * c->gd.nx;
   ea.fwd_bstride = 2 * ea.fwd_fstride;
-  const size_t cb = c->prec.fft_prec == FCSPH_F32 ? sizeof(float2) : sizeof(double2);
-  if (2 * 6 * (size_t)col_ls(c) * cb <= kSmemMax) {
-    ea.mom_comp = 0;
-    ea.fwd_nf = 2;
-    ea.fwd_spec = spec2;
-    return col_inv(c, c->prec.fft_prec, EPI_MOM, spec6, 6, ea);
-  }
-  // one component per launch: u from outputs 0-2, v from outputs 3-5
-  const size_t fsb = ea.fwd_fstride * cb;
-  ea.fwd_nf = 1;
-  ea.mom_comp = 1;
-  ea.fwd_spec = spec2;
-  cudaError_t e = col_inv(c, c->prec.fft_prec, EPI_MOM, spec6, 3, ea);
-  if (e != cudaSuccess) return e;
-  ea.mom_comp = 2;
-  ea.fwd_spec = (char*)spec2 + fsb;
-  return col_inv(c, c->prec.fft_prec, EPI_MOM, (const char*)spec6 + 3 * fsb, 3, ea);
+  return col_inv(c, c->prec.fft_prec, EPI_MOM, spec6, 6, ea);
 }
 
 cudaError_t launch_step_div(fcsph_ctx* c, const StepDev& s, const void* spec1, double* b, void* spec_dct) {
@@ -997,7 +1015,7 @@ cudaError_t launch_step_div(fcsph_ctx* c, const StepDev& s, const void* spec1, d
   ea.s = s;
   ea.fwd_nf = 1;
   ea.fwd_dct = 1;
-  ea.fwdE = c->dE;
+  ea.fwdE = fc_table(c, c->prec.fft_prec, FCSPH_DIRICHLET);
   ea.fwdP = c->plan_py;
   ea.fwd_spec = spec_dct;
   ea.fwd_fstride = (size_t)c->gd.rows * c->gd.nx;
@@ -1016,7 +1034,7 @@ cudaError_t launch_step_corr(fcsph_ctx* c, const StepDev& s, const void* spec2, 
   if (spec_next) {
     ea.fwd_nf = 2;
     ea.fwd_dct = 0;
-    ea.fwdE = c->dE;
+    ea.fwdE = fc_table(c, c->prec.fft_prec, FCSPH_DIRICHLET);
     ea.fwdP = c->plan_y;
     ea.fwd_spec = spec_next;
     ea.fwd_fstride = (size_t)c->gd.rows * c->gd.nx;

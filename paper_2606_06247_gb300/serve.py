@@ -62,7 +62,7 @@ def footprint_bytes(n, capacity, prec):
     my = n + 25
     hy = my // 2 + 1
     rows = max(hy, n)
-    cb = 16 if prec == "f64" else 8
+    cb = 8 if prec == "f32" else 16
     return capacity * (11 * n * n * 8 + 8 * rows * n * cb + rows * n * 16)
 
 
