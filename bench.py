@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--batch", type=int, default=32)
     ap.add_argument("--prec", default="f32x2", choices=["f32", "f64", "f32x2"])
     ap.add_argument("--refine", type=int, default=0)
+    ap.add_argument("--tiling", default=None,
+                    help="rows,pairs per CTA for the headline context instead of the autotuner (profiling runs)")
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--workload", default="cavity", choices=["cavity", "uneven", "serve", "planes"],
                     help="cavity: the 256^2 lid cavity (default); uneven: 64 solves of sizes 64^2..512^2 "
@@ -314,7 +316,10 @@ def run_ours(args):
 
     # ---- headline: the chosen precision, batched, device resident
     ctx = make(args.prec, args.refine if args.prec == "f32" else 0)
-    ctx.autotune(steps=2, **prm)
+    if args.tiling:
+        ctx.set_tiling(*[int(x) for x in args.tiling.split(",")])
+    else:
+        ctx.autotune(steps=2, **prm)
     dtype_name = {"f64": "f64", "f32x2": "f32x2", "f32": "f32"}[args.prec]
     st = state()
     total_ms, per_ms, launches, clocks = timed(ctx, st, args.steps, args.warmup)

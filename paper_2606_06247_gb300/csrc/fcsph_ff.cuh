@@ -17,6 +17,8 @@ struct ff {
   __host__ __device__ ff() : h(0.f), l(0.f) {}
   // plain conversions, so that constant arguments fold at compile time
   __host__ __device__ ff(double d) : h((float)d), l((float)(d - (double)(float)d)) {}
+  // exact for |i| < 2^24 (wavenumber indices), without a trip through FP64
+  __host__ __device__ ff(int i) : h((float)i), l(0.f) {}
   __host__ __device__ explicit operator double() const { return (double)h + (double)l; }
 };
 
