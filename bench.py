@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--tiling", default=None,
                     help="rows,pairs per CTA for the headline context instead of the autotuner (profiling runs)")
     ap.add_argument("--no-compare", action="store_true")
-    ap.add_argument("--workload", default="cavity", choices=["cavity", "uneven", "serve", "planes"],
+    ap.add_argument("--workload", default="cavity", choices=["cavity", "uneven", "serve", "planes", "lines"],
                     help="cavity: the 256^2 lid cavity (default); uneven: 64 solves of sizes 64^2..512^2 "
                          "submitted together; serve: a Poisson request stream (2D part)")
     ap.add_argument("--serve-seconds", type=float, default=1.0)
@@ -608,6 +608,58 @@ def run_planes(args):
                       "variants": lines}))
 
 
+def run_lines(args):
+    """Configuration 3a: 4096 independent wall-normal lines of 512 nodes (walls
+    at both ends), band-limited trig sums plus degree-4 polynomials, d/dy and
+    d^2/dy^2 per call through line_op (one fused kernel).  Algorithmic bytes:
+    4 B in + 2 x 4 B out per node (FP32 fields).  One call moves 25 MB, which
+    fits in L2, so the timed calls rotate through 8 input/output sets (200 MB)."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2606_06247_gb300 import binding as b
+    from paper_2606_06247_gb300 import inputs
+    L, n, sets = 4096, 512, 8
+    base = inputs.band_limited_lines(L, n, seed=12345)
+    peaks, src = load_peaks()
+    variants = {}
+    for prec, n_cont in (("f32", 25), ("f32", 28), ("f32x2", 25), ("f64", 25)):
+        dt = torch.float32 if prec == "f32" else torch.float64
+        dy = 1.0 / (n - 1)
+        ctx = b.Context(L, n, L * dy, 1.0, batch=1, n_cont=n_cont, family="G4", h_over_dx=1.3, prec=prec)
+        fs = [torch.tensor(base, dtype=dt, device="cuda").reshape(1, L, n) for _ in range(sets)]
+        outs = [[torch.empty_like(fs[0]) for _ in range(2)] for _ in range(sets)]
+        for k in range(max(3, args.warmup)):
+            ctx.line_op(fs[k % sets], ["DY", "LAP"], outs[k % sets])
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        calls = max(args.steps, sets)
+        e0.record()
+        for k in range(calls):
+            ctx.line_op(fs[k % sets], ["DY", "LAP"], outs[k % sets])
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / calls
+        es = 4 if prec == "f32" else 8
+        gbs = L * n * 3 * es / (ms * 1e-3) / 1e9
+        variants[f"{prec} n_cont={n_cont} (n_e={n + n_cont})"] = {
+            "ms_per_call": ms, "alg_GBps": gbs, "frac_of_hbm": gbs / peaks["hbm_gbs"], "launches_per_call": 1,
+            "lines_per_s": L / (ms * 1e-3)}
+        del ctx, fs, outs
+        torch.cuda.empty_cache()
+    head = variants["f32 n_cont=25 (n_e=537)"]
+    print(json.dumps({"metric": "FC-extended line operator throughput (algorithmic HBM GB/s)", "value": head["alg_GBps"],
+                      "unit": "GB/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+                      "dtype": "f32", "data": "synthetic",
+                      "config": {"workload": "4096 lines of 512 nodes, walls at both ends, FC(Gram) d=5 C=25, G4 "
+                                             "h=1.3dy, line_op DY+LAP, FP32 fields, 8 rotating buffer sets",
+                                 "peak_source": src},
+                      "roofline": {"bound": "hbm", "achieved": head["alg_GBps"], "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                                   "frac": head["frac_of_hbm"], "traffic": None},
+                      "variants": variants}))
+
+
 def run_profile_case(args):
     """Two eager RK3 steps of the workload with every kernel launched on its own
     (no graph), for kernel-level captures; prints the launch count."""
@@ -633,6 +685,8 @@ if __name__ == "__main__":
         run_serving(a)
     elif a.workload == "planes" and a.impl == "ours":
         run_planes(a)
+    elif a.workload == "lines" and a.impl == "ours":
+        run_lines(a)
     elif a.impl == "reference":
         run_reference(a)
     else:

@@ -133,6 +133,16 @@ fcsph_status fc_extend(fcsph_ctx* ctx, const void* f, void* f_ext, int bc);
  * device pointer per set bit.  FC with the Dirichlet (bc=0) or Neumann table. */
 fcsph_status spectral_op(fcsph_ctx* ctx, const void* f, unsigned op_mask, int bc, void* const* outs);
 
+/* The wall-normal operators of Eqs. 11/13/16 on independent lines: every
+ * column f[b][i][0..ny) of the context's grid is one line with walls at both
+ * ends, FC-extended on its own (table bc) and transformed in y only; each bit
+ * of op_mask (order W, DX, DY, LAP) gives the symbol at kx = 0, i.e.
+ * smoothing, 0 (DX), d/dy and d^2/dy^2 of the line.  outs as in spectral_op
+ * (one device pointer per set bit, the context's I/O type).  Lines need not
+ * have x neighbours: nx is only the count of lines per instance.  One kernel
+ * per call; every line's FC, transforms and outputs stay on chip. */
+fcsph_status line_op(fcsph_ctx* ctx, const void* f, unsigned op_mask, int bc, void* const* outs);
+
 /* div(fx, fy) = IFFT( S_x FFT(Fx) + S_y FFT(Fy) ) on the physical nodes. */
 fcsph_status spectral_div(fcsph_ctx* ctx, const void* fx, const void* fy, void* out);
 

@@ -75,6 +75,7 @@ def _load():
         "fc_extend": [P, P, P, I],
         "spectral_op": [P, P, U, I, P],
         "spectral_div": [P, P, P, P],
+        "line_op": [P, P, U, I, P],
         "ppe_solve": [P, P, P, ctypes.POINTER(D)],
         "isph_step": [P, ctypes.POINTER(fcsph_state), I, ctypes.POINTER(fcsph_step_params)],
         "fcsph_sync": [P],
@@ -212,6 +213,16 @@ class Context:
         by_name = dict(zip(ops, outs))
         arr = (ctypes.c_void_p * len(order))(*[by_name[o].data_ptr() for o in order])
         self._ck(lib.spectral_op(self.h, _ptr(f), mask, bc, arr))
+
+    def line_op(self, f, ops, outs, bc=DIRICHLET):
+        """Wall-normal operators of every column as an independent line (line_op)."""
+        mask = 0
+        for o in ops:
+            mask |= OPS[o]
+        order = [o for o in ("W", "DX", "DY", "LAP") if mask & OPS[o]]
+        by_name = dict(zip(ops, outs))
+        arr = (ctypes.c_void_p * len(order))(*[by_name[o].data_ptr() for o in order])
+        self._ck(lib.line_op(self.h, _ptr(f), mask, bc, arr))
 
     def spectral_div(self, fx, fy, out):
         self._ck(lib.spectral_div(self.h, _ptr(fx), _ptr(fy), _ptr(out)))

@@ -347,6 +347,20 @@ fcsph_status spectral_op(fcsph_ctx* c, const void* f, unsigned op_mask, int bc, 
   return FCSPH_OK;
 }
 
+fcsph_status line_op(fcsph_ctx* c, const void* f, unsigned op_mask, int bc, void* const* outs) {
+  if (!c || !f || !outs || (bc != 0 && bc != 1)) return fail(c, FCSPH_EINVAL, "line_op: bad argument");
+  if (op_mask == 0 || op_mask > 15u) return fail(c, FCSPH_EINVAL, "line_op: op_mask must be a nonempty subset of W|DX|DY|LAP");
+  const int sym[4] = {SYM_W, SYM_DX, SYM_DY, SYM_LAP};
+  int ops[4], n = 0;
+  for (int b = 0; b < 4; ++b)
+    if (op_mask & (1u << b)) {
+      if (!outs[n]) return fail(c, FCSPH_EINVAL, "line_op: null output pointer");
+      ops[n++] = sym[b];
+    }
+  FCSPH_CK(launch_line_op(c, f, ops, n, bc, outs), "line_op");
+  return FCSPH_OK;
+}
+
 fcsph_status spectral_div(fcsph_ctx* c, const void* fx, const void* fy, void* out) {
   if (!c || !fx || !fy || !out) return fail(c, FCSPH_EINVAL, "spectral_div: bad argument");
   RowOps ops = ops_none();

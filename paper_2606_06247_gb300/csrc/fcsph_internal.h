@@ -194,6 +194,7 @@ cudaError_t launch_col_fwd(fcsph_ctx* c, int prec, int nf, const void* const* fi
                            void* spec, int dct);
 size_t tiling_smem(const fcsph_ctx* c, int row_lines, int col_pairs);
 size_t tiling_smem_limit();
+cudaError_t launch_line_op(fcsph_ctx* c, const void* f, const int* ops, int nout, int bc, void* const* outs);
 cudaError_t launch_row_sym(fcsph_ctx* c, int prec, const void* spec_in, void* spec_out, const RowOps& ops,
                            double scale, int bc, int kind);
 cudaError_t launch_col_out(fcsph_ctx* c, const void* spec, int nout, void* const* outs);

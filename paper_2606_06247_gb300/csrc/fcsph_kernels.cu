@@ -333,6 +333,84 @@ __global__ void __launch_bounds__(kFftThreads, MinCtas<T>::v) k_row_sym(GridDev 
 }
 
 // ---------------------------------------------------------------------------
+// Line operator: every column of [batch][nx][ny] is an independent
+// wall-normal line.  Per column pair (packed as one complex line): FC-extend
+// (table E), FFT (length my); then for each output the symbol at kx = 0 --
+// W_hat(ky), i ky W_hat (zero on the Nyquist mode), -ky^2 W_hat, and 0 for
+// d/dx -- times the spectrum, inverse FFT, truncation to ny, scale 1/my.  The
+// symbols are Hermitian in ky, so the real and imaginary parts of the packed
+// result are the two columns' outputs.  One kernel per call.
+struct LineOuts {
+  int nout;
+  int op[4];
+  void* out[4];
+};
+
+template <typename T, typename U>
+__global__ void __launch_bounds__(kFftThreads, MinCtas<T>::v) k_line_op(GridDev g, const U* __restrict__ f,
+                                                                      long long ncols,
+                                                                      const typename FcTab<T>::t* __restrict__ E,
+                                                                      const __grid_constant__ FftPlan P,
+                                                                      const typename CT<T>::t* __restrict__ pool,
+                                                                      const __grid_constant__ LineOuts lo, int Pp,
+                                                                      int ls) {
+  typedef typename CT<T>::t V;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* X = reinterpret_cast<V*>(smem_raw);
+  V* Cq = X + (size_t)Pp * ls;
+  V* D = Cq + (size_t)Pp * ls;
+  const long long c0 = (long long)blockIdx.x * 2 * Pp;
+  const int ny = g.ny, my = g.my;
+  for (int e = threadIdx.x; e < 2 * Pp * ny; e += blockDim.x) {
+    const int col = e / ny, j = e - (e / ny) * ny;
+    const long long cc = c0 + col;
+    const double v = cc < ncols ? (double)f[cc * ny + j] : 0.0;
+    T* L = reinterpret_cast<T*>(X + (size_t)(col >> 1) * ls + j);
+    L[col & 1] = (T)v;
+  }
+  __syncthreads();
+  fc_append<T>(X, Pp, ls, ny, g.n_cont, g.n_match, E);
+  __syncthreads();
+  V* R = fft_any<T, false>(X, Cq, Pp, ls, P, pool);
+  V* W1 = (R == X) ? Cq : X;
+  const T hh = (T)(g.h * g.h * 0.25);
+  const T cky = (T)(2.0 * 3.14159265358979323846 / (my * g.dy));
+  const T tscale = (T)(1.0 / my);
+  for (int o = 0; o < lo.nout; ++o) {
+    const int op = lo.op[o];
+    for (int e = threadIdx.x; e < Pp * my; e += blockDim.x) {
+      const int p = e / my, k = e - (e / my) * my;
+      const int kappa = (2 * k <= my) ? k : k - my;
+      const T ky = cky * (T)kappa;
+      const T What = pool[g.ey_off + (kappa < 0 ? -kappa : kappa)].x * kernel_poly<T>(g.family, ky * ky * hh);
+      const bool nyq = (my % 2 == 0) && (2 * k == my);
+      V s;
+      if (op == SYM_W)
+        s = mk<V>(What, 0);
+      else if (op == SYM_DY)
+        s = mk<V>(0, nyq ? (T)0 : ky * What);
+      else if (op == SYM_LAP)
+        s = mk<V>(-(ky * ky) * What, 0);
+      else
+        s = mk<V>(0, 0);
+      W1[(size_t)p * ls + k] = cscale(cmul(s, R[(size_t)p * ls + k]), tscale);
+    }
+    __syncthreads();
+    V* Y = fft_any<T, true>(W1, D, Pp, ls, P, pool);
+    U* out = reinterpret_cast<U*>(lo.out[o]);
+    for (int e = threadIdx.x; e < 2 * Pp * ny; e += blockDim.x) {
+      const int col = e / ny, j = e - (e / ny) * ny;
+      const long long cc = c0 + col;
+      if (cc < ncols) {
+        const V z = Y[(size_t)(col >> 1) * ls + j];
+        out[cc * ny + j] = (U)(double)((col & 1) ? z.y : z.x);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
 // PPE row pass (Eqs. 31-33): rows l < ny hold DCT-I-in-y coefficients.  x
 // periodic: FFT (length nx); walled x: DCT-I via FFT of the even extension
 // (length 2(nx-1)).  Multiply by -1/(lam_k^2 + lam_l^2) (apply = 0, (0,0) -> 0),
@@ -781,6 +859,9 @@ cudaError_t init_kernel_attributes() {
   FCSPH_RAISE((k_dft_lines<ff, false, double2>))
   FCSPH_RAISE((k_dft_lines<ff, true, double2>))
   FCSPH_RAISE((k_col_inv<double>))
+  FCSPH_RAISE((k_line_op<double, double>))
+  FCSPH_RAISE((k_line_op<ff, double>))
+  FCSPH_RAISE((k_line_op<float, float>))
   FCSPH_RAISE((k_col_inv<float>))
 #undef FCSPH_RAISE
   return cudaSuccess;
@@ -886,6 +967,39 @@ cudaError_t launch_row_sym(fcsph_ctx* c, int prec, const void* sp_in, void* sp_o
   if (prec == FCSPH_F64) return row_sym_t<double>(c, prec, sp_in, sp_out, ops, scale, bc, kind);
   if (prec == FCSPH_F32X2) return row_sym_t<ff>(c, prec, sp_in, sp_out, ops, scale, bc, kind);
   return row_sym_t<float>(c, prec, sp_in, sp_out, ops, scale, bc, kind);
+}
+
+template <typename T, typename U>
+static cudaError_t line_op_t(fcsph_ctx* c, int prec, const void* f, const int* ops, int nout, int bc, void* const* outs) {
+  const GridDev& g = c->gd;
+  const FftPlan& P = c->plan_y;
+  const int ls = P.line_len();
+  const int Pp = c->col_pairs;
+  const size_t smem = 3 * (size_t)Pp * ls * sizeof(typename CT<T>::t);
+  cudaError_t e = set_smem(k_line_op<T, U>, smem);
+  if (e != cudaSuccess) return e;
+  LineOuts lo;
+  memset(&lo, 0, sizeof(lo));
+  lo.nout = nout;
+  for (int o = 0; o < nout; ++o) {
+    lo.op[o] = ops[o];
+    lo.out[o] = outs[o];
+  }
+  const long long ncols = (long long)g.batch * g.nx;
+  const long long blocks = (ncols + 2 * Pp - 1) / (2 * Pp);
+  const auto* E = static_cast<const typename FcTab<T>::t*>(fc_table(c, prec, bc));
+  ProfScope ps(c, FCSPH_PROF_COL_OUT);
+  k_line_op<T, U><<<(unsigned)blocks, kFftThreads, smem, c->stream>>>(g, (const U*)f, ncols, E, P, PoolOf<T>::get(c),
+                                                                      lo, Pp, ls);
+  c->launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_line_op(fcsph_ctx* c, const void* f, const int* ops, int nout, int bc, void* const* outs) {
+  const int prec = c->prec.fft_prec;
+  if (prec == FCSPH_F64) return line_op_t<double, double>(c, prec, f, ops, nout, bc, outs);
+  if (prec == FCSPH_F32X2) return line_op_t<ff, double>(c, prec, f, ops, nout, bc, outs);
+  return line_op_t<float, float>(c, prec, f, ops, nout, bc, outs);
 }
 
 template <typename T>

@@ -4,10 +4,12 @@ Requests of different sizes and kinds (lid-driven cavity / channel) arrive
 over time; each asks for a number of RK3 projection steps.  A size class
 (kind, n, kernel family) owns one fcsph context with a fixed number of slots
 (its batch) and device-resident state for every slot; the class advances all
-its slots with one CUDA-graph step per tick on its own stream, so classes
-overlap on the GPU.  Between ticks, finished requests are retired (their
-state copied to the host) and queued requests take the freed slots.  New
-classes are admitted only while the estimated device footprint of all
+its slots with one CUDA-graph step at a time on its own stream, so classes
+overlap on the GPU.  Classes run independently: the host polls each class's
+end-of-step event and, when a class's step is done, retires its finished
+requests (state copied to the host), admits queued requests into the freed
+slots and launches its next step, without waiting for the other classes.
+New classes are admitted only while the estimated device footprint of all
 classes fits the memory budget.
 
 Every slot is an independent instance of the step: its result does not
@@ -164,7 +166,8 @@ class Server:
                 cls = SizeClass(key, self.capacity, self.prec, self.device)
                 self.classes[key] = cls
             free = cls.free_slots()
-            if not free:
+            if not free or cls.pending_event:
+                # a class in flight takes new requests when its step is done
                 waiting.append(req)
                 continue
             req.t_admit = now
@@ -176,22 +179,28 @@ class Server:
         wanted = {class_key(r) for r in self.queue}
         for key in list(self.classes):
             c = self.classes[key]
-            if not c.active() and key not in wanted:
+            if not c.active() and not c.pending_event and key not in wanted:
                 del self.classes[key]
 
-    def tick(self, now):
+    def tick(self, now, block=False):
+        """Retire the classes whose step is done, admit queued requests, and
+        launch the next step of every idle class with active slots.  With
+        block=True it first waits for every class in flight.  Returns the
+        number of classes in flight after the call."""
+        for c in self.classes.values():
+            if c.pending_event and (block or c.ev1.query()):
+                self.done.extend(c.finish_tick(now))
         self._admit(now)
-        busy = [c for c in self.classes.values() if c.active()]
-        for c in busy:
-            c.step()
-        for c in busy:
-            self.done.extend(c.finish_tick(now))
+        for c in self.classes.values():
+            if not c.pending_event and c.active():
+                c.step()
         if self.queue:
             self._evict_idle()
-        return len(busy)
+            self._admit(now)
+        return sum(1 for c in self.classes.values() if c.pending_event)
 
     def idle(self):
-        return not self.queue and not any(c.active() for c in self.classes.values())
+        return not self.queue and not any(c.active() or c.pending_event for c in self.classes.values())
 
     def run(self, requests, time_scale=1.0, max_wall=None):
         """Drive arrivals in (scaled) real time until every request finishes."""
@@ -203,8 +212,11 @@ class Server:
             while k < len(pending) and pending[k].arrival <= now:
                 self.submit(pending[k])
                 k += 1
-            if self.tick(now) == 0 and k < len(pending) and not self.queue:
+            inflight = self.tick(now)
+            if inflight == 0 and k < len(pending) and not self.queue:
                 time.sleep(max(0.0, (pending[k].arrival - now) * time_scale))
+            elif inflight:
+                time.sleep(5e-5)  # poll the classes' events again shortly
             if max_wall and time.perf_counter() - t0 > max_wall:
                 break
         return time.perf_counter() - t0

@@ -15,19 +15,20 @@ def _reqs():
 
 
 @pytest.mark.gpu
-def test_result_is_the_same_alone_and_in_the_mix():
+@pytest.mark.parametrize("prec", ["f64", "f32x2"])
+def test_result_is_the_same_alone_and_in_the_mix(prec):
     torch_cuda()
     binding()
     from paper_2606_06247_gb300.serve import Server
     mix = _reqs()
-    srv = Server(capacity=4)
+    srv = Server(prec=prec, capacity=4)
     for r in mix:
         srv.submit(r)
     while not srv.idle():
         srv.tick(0.0)
     assert all(r.result is not None and r.done_steps == r.steps for r in mix)
     for r in _reqs():
-        alone = Server(capacity=4)
+        alone = Server(prec=prec, capacity=4)
         alone.submit(r)
         while not alone.idle():
             alone.tick(0.0)
