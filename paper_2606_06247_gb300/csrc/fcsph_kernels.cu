@@ -82,20 +82,21 @@ template <typename T>
 __device__ __forceinline__ void fc_append(typename CT<T>::t* lines, int nl, int ls, int n, int C, int d,
                                           const typename FcTab<T>::t* __restrict__ E) {
   typedef typename CT<T>::t V;
-  for (int e = threadIdx.x; e < nl * C; e += blockDim.x) {
-    const int p = e / C, c = e - (e / C) * C;
+  for (int p = 0; p < nl; ++p) {
     V* L = lines + (size_t)p * ls;
-    const typename FcTab<T>::t* Er = E + c * 2 * d;
-    FcAcc<T> ax, ay;
-    for (int m = 0; m < d; ++m) {
-      const V vr = L[n - d + m];
-      const V vl = L[m];
-      ax.add(Er[m], vr.x);
-      ax.add(Er[d + m], vl.x);
-      ay.add(Er[m], vr.y);
-      ay.add(Er[d + m], vl.y);
+    for (int c = threadIdx.x; c < C; c += blockDim.x) {
+      const typename FcTab<T>::t* Er = E + c * 2 * d;
+      FcAcc<T> ax, ay;
+      for (int m = 0; m < d; ++m) {
+        const V vr = L[n - d + m];
+        const V vl = L[m];
+        ax.add(Er[m], vr.x);
+        ax.add(Er[d + m], vl.x);
+        ay.add(Er[m], vr.y);
+        ay.add(Er[d + m], vl.y);
+      }
+      L[n + c] = mk<V>(ax.value(), ay.value());
     }
-    L[n + c] = mk<V>(ax.value(), ay.value());
   }
 }
 
@@ -118,36 +119,33 @@ __device__ void col_forward_store(typename CT<T>::t* lines, typename CT<T>::t* s
     fc_append<T>(lines, Pp, ls, ny, g.n_cont, g.n_match, E);
   } else {
     const int M = 2 * (ny - 1);
-    for (int e = threadIdx.x; e < Pp * (ny - 2); e += blockDim.x) {
-      const int p = e / (ny - 2), jj = 1 + e - (e / (ny - 2)) * (ny - 2);
-      lines[(size_t)p * ls + M - jj] = lines[(size_t)p * ls + jj];
-    }
+    for (int p = 0; p < Pp; ++p)
+      for (int jj = 1 + threadIdx.x; jj <= ny - 2; jj += blockDim.x)
+        lines[(size_t)p * ls + M - jj] = lines[(size_t)p * ls + jj];
   }
   __syncthreads();
   V* R = fft_any<T, false>(lines, scratch, Pp, ls, P, pool);
   const int n = P.base.n;
-  const int W = 2 * Pp;
   const int nk = dct ? ny : g.hy;
-  for (int e = threadIdx.x; e < nk * W; e += blockDim.x) {
-    const int k = e / W, col = e - (e / W) * W;
-    const int i = i0 + col;
-    if (i >= g.nx) continue;
-    const V* L = R + (size_t)(col >> 1) * ls;
-    const V z = L[k];
-    const V zm = L[k == 0 ? 0 : n - k];
-    const T h = (T)0.5;
-    V out;
-    if (dct) {
-      out = (col & 1) ? mk<V>(0.0, 0.0) : mk<V>(0.0, 0.0);
-      out.x = (col & 1) ? h * (z.y + zm.y) : h * (z.x + zm.x);
-    } else if ((col & 1) == 0) {
-      out.x = h * (z.x + zm.x);
-      out.y = h * (z.y - zm.y);
-    } else {
-      out.x = h * (z.y + zm.y);
-      out.y = h * (zm.x - z.x);
+  const T h = (T)0.5;
+  for (int p = 0; p < Pp; ++p) {
+    const int i = i0 + 2 * p;
+    const V* L = R + (size_t)p * ls;
+    for (int k = threadIdx.x; k < nk; k += blockDim.x) {
+      const V z = L[k];
+      const V zm = L[k == 0 ? 0 : n - k];
+      V a, b;  // columns i and i + 1
+      if (dct) {
+        a = mk<V>(h * (z.x + zm.x), 0);
+        b = mk<V>(h * (z.y + zm.y), 0);
+      } else {
+        a = mk<V>(h * (z.x + zm.x), h * (z.y - zm.y));
+        b = mk<V>(h * (z.y + zm.y), h * (zm.x - z.x));
+      }
+      V* S = spec + (size_t)k * g.nx + i;
+      if (i < g.nx) S[0] = a;
+      if (i + 1 < g.nx) S[1] = b;
     }
-    spec[(size_t)k * g.nx + i] = out;
   }
 }
 
@@ -159,31 +157,31 @@ __device__ void col_gather_hermitian(typename CT<T>::t* lines, int Pp, int ls, c
                                      const typename CT<T>::t* __restrict__ spec, size_t fstride, int nout, int n) {
   typedef typename CT<T>::t V;
   const int hy = g.hy;
-  for (int e = threadIdx.x; e < nout * hy * Pp; e += blockDim.x) {
-    const int o = e / (hy * Pp);
-    const int r = e - o * hy * Pp;
-    const int k = r / Pp, p = r - (r / Pp) * Pp;
-    const int ia = i0 + 2 * p, ib = ia + 1;
-    const V* S = spec + o * fstride + (size_t)k * g.nx;
-    V A = mk<V>(0.0, 0.0), B = mk<V>(0.0, 0.0);
-    if (ia < g.nx) A = S[ia];
-    if (ib < g.nx) B = S[ib];
-    V* L = lines + ((size_t)o * Pp + p) * ls;
-    const bool self = (k == 0) || (2 * k == n);
-    V z0, z1;
-    if (self) {
-      z0.x = A.x;
-      z0.y = B.x;
-      L[k] = z0;
-    } else {
-      z0.x = A.x - B.y;
-      z0.y = A.y + B.x;
-      z1.x = A.x + B.y;
-      z1.y = B.x - A.y;
-      L[k] = z0;
-      L[n - k] = z1;
+  for (int o = 0; o < nout; ++o)
+    for (int p = 0; p < Pp; ++p) {
+      const int ia = i0 + 2 * p, ib = ia + 1;
+      V* L = lines + ((size_t)o * Pp + p) * ls;
+      for (int k = threadIdx.x; k < hy; k += blockDim.x) {
+        const V* S = spec + o * fstride + (size_t)k * g.nx;
+        V A = mk<V>(0.0, 0.0), B = mk<V>(0.0, 0.0);
+        if (ia < g.nx) A = S[ia];
+        if (ib < g.nx) B = S[ib];
+        const bool self = (k == 0) || (2 * k == n);
+        V z0, z1;
+        if (self) {
+          z0.x = A.x;
+          z0.y = B.x;
+          L[k] = z0;
+        } else {
+          z0.x = A.x - B.y;
+          z0.y = A.y + B.x;
+          z1.x = A.x + B.y;
+          z1.y = B.x - A.y;
+          L[k] = z0;
+          L[n - k] = z1;
+        }
+      }
     }
-  }
 }
 
 // Packed DCT-I coefficient pairs (real parts of spec rows l < ny) into lines.
@@ -192,16 +190,17 @@ __device__ void col_gather_dct(typename CT<T>::t* lines, int Pp, int ls, const G
                                const typename CT<T>::t* __restrict__ spec) {
   typedef typename CT<T>::t V;
   const int ny = g.ny, M = 2 * (ny - 1);
-  for (int e = threadIdx.x; e < ny * Pp; e += blockDim.x) {
-    const int l = e / Pp, p = e - (e / Pp) * Pp;
+  for (int p = 0; p < Pp; ++p) {
     const int ia = i0 + 2 * p, ib = ia + 1;
-    const V* S = spec + (size_t)l * g.nx;
-    V z = mk<V>(0.0, 0.0);
-    if (ia < g.nx) z.x = S[ia].x;
-    if (ib < g.nx) z.y = S[ib].x;
     V* L = lines + (size_t)p * ls;
-    L[l] = z;
-    if (l >= 1 && l <= ny - 2) L[M - l] = z;
+    for (int l = threadIdx.x; l < ny; l += blockDim.x) {
+      const V* S = spec + (size_t)l * g.nx;
+      V z = mk<V>(0.0, 0.0);
+      if (ia < g.nx) z.x = S[ia].x;
+      if (ib < g.nx) z.y = S[ib].x;
+      L[l] = z;
+      if (l >= 1 && l <= ny - 2) L[M - l] = z;
+    }
   }
 }
 
@@ -223,11 +222,11 @@ __global__ void __launch_bounds__(kFftThreads, MinCtas<T>::v) k_col_fwd(GridDev 
   const int W = 2 * Pp;
   const int ny = g.ny;
   const size_t base = ((size_t)b * g.nx + i0) * ny;
-  for (int e = threadIdx.x; e < W * ny; e += blockDim.x) {
-    const int col = e / ny, j = e - (e / ny) * ny;
-    const double v = (i0 + col < g.nx) ? (double)src[base + e] : 0.0;
-    T* L = reinterpret_cast<T*>(lines + (size_t)(col >> 1) * ls + j);
-    L[col & 1] = (T)v;
+  for (int col = 0; col < W; ++col) {
+    T* L = reinterpret_cast<T*>(lines + (size_t)(col >> 1) * ls) + (col & 1);
+    const bool in = i0 + col < g.nx;
+    for (int j = threadIdx.x; j < ny; j += blockDim.x)
+      L[2 * j] = (T)(in ? (double)src[base + (size_t)col * ny + j] : 0.0);
   }
   __syncthreads();
   col_forward_store<T>(lines, scratch, Pp, ls, g, i0, E, P, pool, dct, spec + b * bstride + f * fstride);
@@ -283,14 +282,13 @@ __global__ void __launch_bounds__(kFftThreads, MinCtas<T>::v) k_row_sym(GridDev 
   const int b = blockIdx.y;
   const int ky0 = blockIdx.x * Rr;
   const int nx = g.nx, mx = g.mx;
-  for (int e = threadIdx.x; e < nin * Rr * nx; e += blockDim.x) {
-    const int line = e / nx, i = e - (e / nx) * nx;
-    const int f = line / Rr, r = line - (line / Rr) * Rr;
-    const int ky = ky0 + r;
-    V v = mk<V>(0.0, 0.0);
-    if (ky < g.hy) v = sp_in[b * bstride_in + f * fstride_in + (size_t)ky * nx + i];
-    A[(size_t)line * ls + i] = v;
-  }
+  for (int f = 0; f < nin; ++f)
+    for (int r = 0; r < Rr; ++r) {
+      const int ky = ky0 + r;
+      V* L = A + ((size_t)f * Rr + r) * ls;
+      const V* S = sp_in + b * bstride_in + f * fstride_in + (size_t)ky * nx;
+      for (int i = threadIdx.x; i < nx; i += blockDim.x) L[i] = ky < g.hy ? S[i] : mk<V>(0.0, 0.0);
+    }
   __syncthreads();
   if (g.x_walls) {
     fc_append<T>(A, nin * Rr, ls, nx, g.n_cont, g.n_match, E);
@@ -304,8 +302,8 @@ __global__ void __launch_bounds__(kFftThreads, MinCtas<T>::v) k_row_sym(GridDev 
   const T cky = (T)(2.0 * 3.14159265358979323846 / (g.my * g.dy));
   const T tscale = (T)scale;
   for (int o = 0; o < nout; ++o) {
-    for (int e = threadIdx.x; e < Rr * mx; e += blockDim.x) {
-      const int r = e / mx, kxi = e - (e / mx) * mx;
+    for (int r = 0; r < Rr; ++r)
+    for (int kxi = threadIdx.x; kxi < mx; kxi += blockDim.x) {
       const int ky = ky0 + r;
       const int kappa = (2 * kxi <= mx) ? kxi : kxi - mx;
       const T kx = ckx * (T)kappa, kyw = cky * (T)ky;
@@ -323,10 +321,12 @@ __global__ void __launch_bounds__(kFftThreads, MinCtas<T>::v) k_row_sym(GridDev 
     }
     __syncthreads();
     V* Y = fft_any<T, true>(Cq, D, Rr, ls, P, pool);
-    for (int e = threadIdx.x; e < Rr * nx; e += blockDim.x) {
-      const int r = e / nx, i = e - (e / nx) * nx;
+    for (int r = 0; r < Rr; ++r) {
       const int ky = ky0 + r;
-      if (ky < g.hy) sp_out[b * bstride_out + o * fstride_out + (size_t)ky * nx + i] = Y[(size_t)r * ls + i];
+      if (ky >= g.hy) break;
+      V* S = sp_out + b * bstride_out + o * fstride_out + (size_t)ky * nx;
+      const V* Yl = Y + (size_t)r * ls;
+      for (int i = threadIdx.x; i < nx; i += blockDim.x) S[i] = Yl[i];
     }
     __syncthreads();
   }
@@ -361,12 +361,10 @@ __global__ void __launch_bounds__(kFftThreads, MinCtas<T>::v) k_line_op(GridDev 
   V* D = Cq + (size_t)Pp * ls;
   const long long c0 = (long long)blockIdx.x * 2 * Pp;
   const int ny = g.ny, my = g.my;
-  for (int e = threadIdx.x; e < 2 * Pp * ny; e += blockDim.x) {
-    const int col = e / ny, j = e - (e / ny) * ny;
+  for (int col = 0; col < 2 * Pp; ++col) {
     const long long cc = c0 + col;
-    const double v = cc < ncols ? (double)f[cc * ny + j] : 0.0;
-    T* L = reinterpret_cast<T*>(X + (size_t)(col >> 1) * ls + j);
-    L[col & 1] = (T)v;
+    T* L = reinterpret_cast<T*>(X + (size_t)(col >> 1) * ls) + (col & 1);
+    for (int j = threadIdx.x; j < ny; j += blockDim.x) L[2 * j] = (T)(cc < ncols ? (double)f[cc * ny + j] : 0.0);
   }
   __syncthreads();
   fc_append<T>(X, Pp, ls, ny, g.n_cont, g.n_match, E);
@@ -378,8 +376,8 @@ __global__ void __launch_bounds__(kFftThreads, MinCtas<T>::v) k_line_op(GridDev 
   const T tscale = (T)(1.0 / my);
   for (int o = 0; o < lo.nout; ++o) {
     const int op = lo.op[o];
-    for (int e = threadIdx.x; e < Pp * my; e += blockDim.x) {
-      const int p = e / my, k = e - (e / my) * my;
+    for (int p = 0; p < Pp; ++p)
+    for (int k = threadIdx.x; k < my; k += blockDim.x) {
       const int kappa = (2 * k <= my) ? k : k - my;
       const T ky = cky * (T)kappa;
       const T What = pool[g.ey_off + (kappa < 0 ? -kappa : kappa)].x * kernel_poly<T>(g.family, ky * ky * hh);
@@ -398,13 +396,11 @@ __global__ void __launch_bounds__(kFftThreads, MinCtas<T>::v) k_line_op(GridDev 
     __syncthreads();
     V* Y = fft_any<T, true>(W1, D, Pp, ls, P, pool);
     U* out = reinterpret_cast<U*>(lo.out[o]);
-    for (int e = threadIdx.x; e < 2 * Pp * ny; e += blockDim.x) {
-      const int col = e / ny, j = e - (e / ny) * ny;
+    for (int col = 0; col < 2 * Pp; ++col) {
       const long long cc = c0 + col;
-      if (cc < ncols) {
-        const V z = Y[(size_t)(col >> 1) * ls + j];
-        out[cc * ny + j] = (U)(double)((col & 1) ? z.y : z.x);
-      }
+      if (cc >= ncols) break;
+      const V* Yl = Y + (size_t)(col >> 1) * ls;
+      for (int j = threadIdx.x; j < ny; j += blockDim.x) out[cc * ny + j] = (U)(double)((col & 1) ? Yl[j].y : Yl[j].x);
     }
     __syncthreads();
   }
@@ -430,21 +426,23 @@ __global__ void __launch_bounds__(kFftThreads, MinCtas<T>::v) k_row_ppe(GridDev 
   const int l0 = blockIdx.x * Rr;
   const int nx = g.nx, ny = g.ny;
   const int n = P.base.n;  // nx or 2(nx-1)
-  for (int e = threadIdx.x; e < Rr * nx; e += blockDim.x) {
-    const int r = e / nx, i = e - (e / nx) * nx;
+  for (int r = 0; r < Rr; ++r) {
     const int l = l0 + r;
-    V v = mk<V>(0.0, 0.0);
-    if (l < ny) v = spec[b * bstride + (size_t)l * nx + i];
-    A[(size_t)r * ls + i] = v;
-    if (g.x_walls && i >= 1 && i <= nx - 2) A[(size_t)r * ls + n - i] = v;
+    V* L = A + (size_t)r * ls;
+    const V* S = spec + b * bstride + (size_t)l * nx;
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+      const V v = l < ny ? S[i] : mk<V>(0.0, 0.0);
+      L[i] = v;
+      if (g.x_walls && i >= 1 && i <= nx - 2) L[n - i] = v;
+    }
   }
   __syncthreads();
   V* X = fft_any<T, false>(A, B, Rr, ls, P, pool);
   V* O = (X == A) ? B : A;
   const T norm = (T)(1.0 / ((double)n * 2.0 * (ny - 1)));
   const int nk = g.x_walls ? nx : n;
-  for (int e = threadIdx.x; e < Rr * nk; e += blockDim.x) {
-    const int r = e / nk, k = e - (e / nk) * nk;
+  for (int r = 0; r < Rr; ++r)
+  for (int k = threadIdx.x; k < nk; k += blockDim.x) {
     const int l = l0 + r;
     // lam_k^2 and lam_l^2 from the per-axis tables (Eq. 33 eigenvalues)
     const T den = pool[g.lx2_off + k].x + pool[g.ly2_off + (l < ny ? l : 0)].x;
@@ -470,10 +468,12 @@ __global__ void __launch_bounds__(kFftThreads, MinCtas<T>::v) k_row_ppe(GridDev 
     Y = fft_any<T, false>(O, X, Rr, ls, P, pool);  // DCT-I is its own inverse up to the folded scale
   else
     Y = fft_any<T, true>(X, O, Rr, ls, P, pool);
-  for (int e = threadIdx.x; e < Rr * nx; e += blockDim.x) {
-    const int r = e / nx, i = e - (e / nx) * nx;
+  for (int r = 0; r < Rr; ++r) {
     const int l = l0 + r;
-    if (l < ny) spec[b * bstride + (size_t)l * nx + i] = Y[(size_t)r * ls + i];
+    if (l >= ny) break;
+    V* S = spec + b * bstride + (size_t)l * nx;
+    const V* Yl = Y + (size_t)r * ls;
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) S[i] = Yl[i];
   }
 }
 
@@ -547,8 +547,8 @@ __global__ void __launch_bounds__(kFftThreads, MinCtas<T>::v) k_col_inv(GridDev 
       __syncthreads();
       R = fft_any<T, true>(Z, S, Pp, ls, P, pool);
     }
-    for (int e = threadIdx.x; e < Pp * ny; e += blockDim.x) {
-      const int p = e / ny, j = e - (e / ny) * ny;
+    for (int p = 0; p < Pp; ++p)
+    for (int j = threadIdx.x; j < ny; j += blockDim.x) {
       const V z = R[(size_t)p * ls + j];
       double2* A = acc + (size_t)p * ny + j;  // + f * Pp * ny for field f
 #pragma unroll
@@ -648,11 +648,12 @@ __global__ void __launch_bounds__(kFftThreads, MinCtas<T>::v) k_col_inv(GridDev 
   }
   for (int f = 0; f < ea.fwd_nf; ++f) {
     // fields beyond nx (ragged last pair) are zero
-    for (int e = threadIdx.x; e < Pp * ny; e += blockDim.x) {
-      const int p = e / ny, j = e - (e / ny) * ny;
-      const double2 a = acc[((size_t)f * Pp + p) * ny + j];
+    for (int p = 0; p < Pp; ++p) {
       const int i = i0 + 2 * p;
-      Z[(size_t)p * ls + j] = mk<V>(i < g.nx ? a.x : 0.0, i + 1 < g.nx ? a.y : 0.0);
+      const double2* a = acc + ((size_t)f * Pp + p) * ny;
+      V* L = Z + (size_t)p * ls;
+      for (int j = threadIdx.x; j < ny; j += blockDim.x)
+        L[j] = mk<V>(i < g.nx ? a[j].x : 0.0, i + 1 < g.nx ? a[j].y : 0.0);
     }
     __syncthreads();
     col_forward_store<T>(Z, S, Pp, ls, g, i0, reinterpret_cast<const typename FcTab<T>::t*>(ea.fwdE), ea.fwdP, pool,

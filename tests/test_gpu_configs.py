@@ -43,6 +43,41 @@ def test_channel_64_fop_100_steps_full_field():
     assert rel_l2(u[0].cpu().numpy(), ua) < 2e-3  # FOP start-up vs the analytic series
 
 
+def _couette(y, t, U, nu, nterms=400):
+    u = U * y
+    for n in range(1, nterms):
+        u = u + 2 * U / np.pi * (-1) ** n / n * np.sin(n * np.pi * y) * np.exp(-nu * n * n * np.pi ** 2 * t)
+    return u
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", ["f64", "f32x2"])
+def test_couette_64_rk3_parity_and_analytic(prec):
+    """Plane Couette start-up (Sec. 6.4): u = 0 at y = 0, u = 1 at y = 1, from rest."""
+    torch = torch_cuda()
+    b = binding()
+    N = 64
+    lx, ly = grid_lengths(N, N, False)
+    ctx = b.Context(N, N, lx, ly, family="G4", h_over_dx=1.3, prec=prec)
+    z = np.zeros((1, N, N))
+    u, v = to_dev(z), to_dev(z)
+    p, fu, fv = torch.zeros_like(u), torch.zeros_like(u), torch.zeros_like(u)
+    ctx.isph_step(u, v, p, fu, fv, 100, nu=0.1, rho=1.0, dt=1e-3, u_top=1.0, scheme="rk3")
+    ctx.sync()
+    prob = oracle_problem(N, N, False, "G4", 1.3, scheme="rk3", nu=0.1, dt=1e-3, u_top=1.0)
+    fn = lambda a, c: ostep.isph_steps(prob, a, c, 100)
+    uo, vo, po = fn(z[0], z[0])
+    fl = ulp_floor(fn, z[0], z[0], scale=1.0)
+    scale = 1.0 if prec == "f64" else 32.0
+    ug = u[0].cpu().numpy()
+    err = rel_l2(ug, uo)
+    print(f"couette 64^2 RK3 x100 {prec}: parity u {err:.1e} (floor {fl[0]:.1e}), |v| max {np.abs(v.cpu().numpy()).max():.1e}")
+    assert err < parity_tol(fl[0], base=1e-12 * scale, factor=10.0 * scale)
+    y = np.linspace(0, 1, N)
+    assert rel_l2(ug, np.tile(_couette(y, 0.1, 1.0, 0.1), (N, 1))) < 2e-3
+    assert np.abs(v.cpu().numpy()).max() < 1e-11
+
+
 @pytest.mark.gpu
 def test_cavity_64_rk3_parity_size():
     torch = torch_cuda()

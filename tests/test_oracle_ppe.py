@@ -39,3 +39,4 @@ def test_solve_inverts_laplacian_up_to_the_mean_mode():
         r = ppe.laplacian(phi, 1.0, 1.0, xw) - b
         # the residual is the (0,0) transform mode of b alone: a constant field
         assert np.abs(r - r.mean()).max() < 1e-12 * np.abs(b).max()
+

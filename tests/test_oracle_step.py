@@ -65,3 +65,29 @@ def test_cavity_walls_and_lid_are_imposed():
     u, v, phi = step.isph_steps(p, u, v, 3)
     assert np.all(u[1:-1, -1] == 1.0) and u[0, -1] == 0 and u[-1, -1] == 0
     assert np.all(u[0, :] == 0) and np.all(v[:, 0] == 0) and np.all(np.isfinite(u))
+
+
+def _couette_series(y, t, U, nu, nterms=400):
+    # Sec. 6.4: u(y,t) = U y + (2U/pi) sum_{n>=1} (-1)^n / n sin(n pi y) e^{-nu n^2 pi^2 t}
+    u = U * y
+    for n in range(1, nterms):
+        u = u + 2 * U / np.pi * (-1) ** n / n * np.sin(n * np.pi * y) * np.exp(-nu * n * n * np.pi ** 2 * t)
+    return u
+
+
+def test_couette_startup_matches_analytic_series():
+    # moving top wall (u = 1 at y = 1), stationary bottom wall, fluid at rest: the
+    # asymmetric Dirichlet data go through the same FC extension unchanged
+    N = 32
+    E = gram_golden(5, 25)
+    p = step.Problem(nx=N, ny=N, Lx=N / (N - 1), Ly=1.0, x_walls=False, family="G4", h_over_dx=1.3,
+                     E_dir=E, E_neu=E, nu=0.1, rho=1.0, dt=1e-3, force=(0.0, 0.0), u_top=1.0,
+                     scheme="rk3").build_symbols()
+    z = np.zeros((N, N))
+    u, v, phi = step.isph_steps(p, z, z, 100)
+    y = np.linspace(0, 1, N)
+    ua = np.tile(_couette_series(y, 0.1, 1.0, 0.1), (N, 1))
+    assert norms.l2_rel(u, ua) < 2e-3
+    assert np.abs(v).max() < 1e-12                       # the flow stays one-dimensional
+    assert np.abs(u - u.mean(axis=0, keepdims=True)).max() < 1e-12
+    assert np.all(u[:, 0] == 0) and np.all(u[:, -1] == 1)
