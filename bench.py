@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--tiling", default=None,
                     help="rows,pairs per CTA for the headline context instead of the autotuner (profiling runs)")
     ap.add_argument("--no-compare", action="store_true")
-    ap.add_argument("--workload", default="cavity", choices=["cavity", "uneven", "serve", "planes", "lines"],
+    ap.add_argument("--workload", default="cavity", choices=["cavity", "uneven", "serve", "planes", "lines", "dipole"],
                     help="cavity: the 256^2 lid cavity (default); uneven: 64 solves of sizes 64^2..512^2 "
                          "submitted together; serve: a Poisson request stream (2D part)")
     ap.add_argument("--serve-seconds", type=float, default=1.0)
@@ -660,6 +660,78 @@ def run_lines(args):
                       "variants": variants}))
 
 
+def run_dipole(args):
+    """Sec. 6.5 vortex dipole rebound, Re = 100: 161^2 particles on [-1, 1]^2,
+    walls all round (FC in x and y), G4 h = 1.3 dx, RK3 dt = 1.25e-3.  Reports
+    the batched throughput (B independent dipoles, one graph per step) and one
+    dipole run to t = 10 with E(t) = 1/2 int |u|^2 and Z(t) = 1/2 int omega^2
+    (trapezoidal rule; omega from the library's spectral d/dx, d/dy)."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2606_06247_gb300 import binding as b
+    from paper_2606_06247_gb300 import inputs
+    n, dt, nu = 161, 1.25e-3, 0.01
+    prm = dict(nu=nu, rho=1.0, dt=dt, scheme="rk3")
+    u0, v0 = inputs.dipole_initial(n)
+    h = 2.0 / (n - 1)
+    wq = torch.ones(n, dtype=torch.float64, device="cuda")
+    wq[0] = wq[-1] = 0.5
+    W2 = (wq[:, None] * wq[None, :]) * (0.5 * h * h)
+    B = args.batch
+    out = {}
+    for prec in (args.prec, "f64"):
+        ctx = b.Context(n, n, 2.0, 2.0, x_walls=True, batch=B, family="G4", h_over_dx=1.3, prec=prec)
+        ctx.autotune(steps=2, **prm)
+        st = [torch.tensor(np.broadcast_to(a, (B, n, n)).copy(), dtype=torch.float64, device="cuda") for a in (u0, v0)]
+        st += [torch.zeros_like(st[0]) for _ in range(3)]
+        ctx.isph_step(*st, max(3, args.warmup), use_graph=True, **prm)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ctx.isph_step(*st, args.steps, use_graph=True, **prm)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        out[prec] = {"ms_per_step": ms, "particle_updates_per_s": B * n * n / (ms * 1e-3), "tiling": list(ctx.get_tiling())}
+        del ctx, st
+    # one dipole to t = 10 with the energy and enstrophy history
+    ctx = b.Context(n, n, 2.0, 2.0, x_walls=True, batch=1, family="G4", h_over_dx=1.3, prec=args.prec)
+    u = torch.tensor(u0[None], dtype=torch.float64, device="cuda")
+    v = torch.tensor(v0[None], dtype=torch.float64, device="cuda")
+    p, fu, fv = torch.zeros_like(u), torch.zeros_like(u), torch.zeros_like(u)
+    vx, uy = torch.empty_like(u), torch.empty_like(u)
+    hist = []
+    marks = [0.0, 0.25, 0.5, 1.0, 2.0, 3.0, 5.0, 7.5, 10.0]
+    t, k = 0.0, 0
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for tm in marks:
+        nst = int(round((tm - t) / dt))
+        if nst > 0:
+            ctx.isph_step(u, v, p, fu, fv, nst, use_graph=True, **prm)
+            t += nst * dt
+        ctx.spectral_op(v, ["DX"], [vx])
+        ctx.spectral_op(u, ["DY"], [uy])
+        E = float((W2 * (u[0] ** 2 + v[0] ** 2)).sum())
+        Z = float((W2 * (vx[0] - uy[0]) ** 2).sum())
+        hist.append({"t": round(t, 6), "E": E, "Z": Z})
+    e1.record()
+    torch.cuda.synchronize()
+    run_s = e0.elapsed_time(e1) / 1e3
+    head = out[args.prec]
+    print(json.dumps({
+        "metric": METRIC, "value": head["particle_updates_per_s"], "unit": "particle-updates/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
+        "dtype": args.prec, "data": "synthetic",
+        "config": {"workload": f"vortex dipole rebound Re=100, 161x161 on [-1,1]^2 walls all round, G4 h=1.3dx, "
+                               f"RK3 dt=1.25e-3, batch of {B} dipoles", "batch": B},
+        "variants": out,
+        "history": {"precision": args.prec, "run_seconds": run_s, "steps": int(round(10.0 / dt)), "E_Z": hist}}))
+
+
 def run_profile_case(args):
     """Two eager RK3 steps of the workload with every kernel launched on its own
     (no graph), for kernel-level captures; prints the launch count."""
@@ -687,6 +759,8 @@ if __name__ == "__main__":
         run_planes(a)
     elif a.workload == "lines" and a.impl == "ours":
         run_lines(a)
+    elif a.workload == "dipole" and a.impl == "ours":
+        run_dipole(a)
     elif a.impl == "reference":
         run_reference(a)
     else:

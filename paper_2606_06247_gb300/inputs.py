@@ -30,6 +30,24 @@ def cavity_initial(nx, ny, seed=None, sigma=0.0):
     return u, v
 
 
+def dipole_initial(n, omega_e=299.528, r0=0.1, x1=-0.1, x2=0.1):
+    """Sec. 6.5 vortex dipole on [-1, 1]^2 (walls all round, nodes on the walls):
+    two monopoles of vorticity omega_e (1 - (r/r0)^2) e^{-(r/r0)^2} at (x1, 0)
+    and (x2, 0) with opposite signs; the printed velocity field of each is
+    (-(1/2)|omega_e| (y - y_c), (1/2)|omega_e| (x - x_c)) e^{-(r/r0)^2}, with
+    the sign of the second monopole reversed.  |omega_e| = 299.528 gives a
+    total kinetic energy E(0) = 2.  Returns (u, v) of shape (n, n), [i][j] =
+    (x_i, y_j)."""
+    x = np.linspace(-1.0, 1.0, n)
+    X, Y = np.meshgrid(x, x, indexing="ij")
+    e1 = np.exp(-((X - x1) ** 2 + Y ** 2) / r0 ** 2)
+    e2 = np.exp(-((X - x2) ** 2 + Y ** 2) / r0 ** 2)
+    w = 0.5 * abs(omega_e)
+    u = -w * Y * e1 + w * Y * e2
+    v = w * (X - x1) * e1 - w * (X - x2) * e2
+    return u, v
+
+
 def smooth_field(nx, ny, seed=0, modes=4, poly_deg=4):
     """A smooth non-periodic field on x in [0,1), y in [0,1]: a few random
     low Fourier modes times random polynomials in y (band-limited in x)."""

@@ -9,6 +9,7 @@ import pytest
 from gpu_common import binding, grid_lengths, oracle_problem, parity_tol, rel_l2, to_dev, torch_cuda, ulp_floor
 from oracle import step as ostep
 from paper_2606_06247_gb300 import inputs
+from tables import gram_golden
 
 
 def _series(y, t, F, nu, nterms=4001):
@@ -142,3 +143,30 @@ def test_large_grid_step_runs_and_matches_small_batch_rows(n, xw):
         outs.append(u[0].cpu().numpy())
     assert np.all(np.isfinite(outs[0])) and np.abs(outs[0]).max() > 0
     np.testing.assert_array_equal(outs[0], outs[1])
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", ["f64", "f32x2"])
+def test_dipole_161_rk3_parity(prec):
+    """Sec. 6.5 vortex dipole, Re = 100, 161^2 on [-1, 1]^2 with walls all round,
+    G4, dt = 1.25e-3: 4 RK3 steps against the oracle."""
+    torch = torch_cuda()
+    b = binding()
+    n = 161
+    ctx = b.Context(n, n, 2.0, 2.0, x_walls=True, family="G4", h_over_dx=1.3, prec=prec)
+    u0, v0 = inputs.dipole_initial(n)
+    u, v = to_dev(u0[None]), to_dev(v0[None])
+    p, fu, fv = torch.zeros_like(u), torch.zeros_like(u), torch.zeros_like(u)
+    ctx.isph_step(u, v, p, fu, fv, 4, nu=0.01, rho=1.0, dt=1.25e-3, scheme="rk3")
+    ctx.sync()
+    prob = ostep.Problem(nx=n, ny=n, Lx=2.0, Ly=2.0, x_walls=True, family="G4", h_over_dx=1.3,
+                         E_dir=gram_golden(5, 25), E_neu=gram_golden(5, 25), nu=0.01, rho=1.0, dt=1.25e-3,
+                         scheme="rk3").build_symbols()
+    fn = lambda a, c: ostep.isph_steps(prob, a, c, 4)
+    uo, vo, po = fn(u0, v0)
+    fl = ulp_floor(fn, u0, v0)
+    scale = 1.0 if prec == "f64" else 32.0
+    errs = [rel_l2(u[0].cpu().numpy(), uo), rel_l2(v[0].cpu().numpy(), vo), rel_l2(p[0].cpu().numpy(), po)]
+    print(f"dipole 161^2 {prec}: parity (u, v, p) {errs}, floor {fl}")
+    for e, f in zip(errs, fl):
+        assert e < parity_tol(f, base=1e-12 * scale, factor=10.0 * scale)

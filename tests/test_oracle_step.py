@@ -91,3 +91,35 @@ def test_couette_startup_matches_analytic_series():
     assert np.abs(v).max() < 1e-12                       # the flow stays one-dimensional
     assert np.abs(u - u.mean(axis=0, keepdims=True)).max() < 1e-12
     assert np.all(u[:, 0] == 0) and np.all(u[:, -1] == 1)
+
+
+def _energy(u, v, h):
+    # trapezoidal rule for E = 1/2 int |u|^2 over the nodes of a walled square
+    w = np.ones(u.shape[0])
+    w[0] = w[-1] = 0.5
+    return 0.5 * h * h * float((w[:, None] * w[None, :] * (u ** 2 + v ** 2)).sum())
+
+
+def test_dipole_initial_energy_is_two():
+    # Sec. 6.5: omega_e = 299.528 is chosen so that E(0) = 2 (printed to 6 digits)
+    for n in (161, 401):
+        u, v = inputs.dipole_initial(n)
+        assert abs(_energy(u, v, 2.0 / (n - 1)) - 2.0) < 1e-5
+
+
+def test_dipole_energy_decays_at_twice_nu_times_enstrophy():
+    # Navier-Stokes with no-slip walls: dE/dt = -nu int |grad u|^2 = -2 nu Z,
+    # Z = 1/2 int omega^2.  One RK3 step of the oracle at 161^2, Re = 100.
+    n = 161
+    E = gram_golden(5, 25)
+    p = step.Problem(nx=n, ny=n, Lx=2.0, Ly=2.0, x_walls=True, family="G4", h_over_dx=1.3, E_dir=E, E_neu=E,
+                     nu=0.01, rho=1.0, dt=1.25e-4, scheme="rk3").build_symbols()
+    u0, v0 = inputs.dipole_initial(n)
+    h = 2.0 / (n - 1)
+    from oracle import ops
+    vx, = ops.apply_symbols(v0, [p.sym["DX"]], E, E)
+    uy, = ops.apply_symbols(u0, [p.sym["DY"]], E, E)
+    Z0 = _energy(vx - uy, np.zeros_like(u0), h)
+    u1, v1, _ = step.isph_steps(p, u0, v0, 1)
+    rate = (_energy(u1, v1, h) - _energy(u0, v0, h)) / p.dt
+    assert abs(rate + 2 * p.nu * Z0) < 3e-3 * 2 * p.nu * Z0
