@@ -54,7 +54,8 @@ enum { FCSPH_F64 = 0, FCSPH_F32 = 1, FCSPH_F32X2 = 2 };
 enum { FCSPH_FC_GRAM = 0, FCSPH_FC_PAPER = 1 };         /* FC table construction          */
 enum { FCSPH_DIRICHLET = 0, FCSPH_NEUMANN = 1 };        /* boundary data type (Sec. 4.4)  */
 enum { FCSPH_G2 = 1, FCSPH_G4 = 2, FCSPH_G6 = 3, FCSPH_G8 = 4, FCSPH_G10 = 5 }; /* Gaussian order 2n */
-enum { FCSPH_OP_W = 1u, FCSPH_OP_DX = 2u, FCSPH_OP_DY = 4u, FCSPH_OP_LAP = 8u }; /* spectral_op mask */
+enum { FCSPH_OP_W = 1u, FCSPH_OP_DX = 2u, FCSPH_OP_DY = 4u, FCSPH_OP_LAP = 8u,
+       FCSPH_OP_DZ = 16u };                             /* spectral_op mask (DZ: 3D grids) */
 enum { FCSPH_SCHEME_FOP = 0, FCSPH_SCHEME_RK3 = 1 };    /* Sec. 2.2                       */
 
 typedef struct {
@@ -62,6 +63,8 @@ typedef struct {
   double lx, ly;   /* domain lengths (see Grid above)                          */
   int x_walls;     /* 0: x periodic; 1: walls at both x ends                   */
   int batch;       /* independent instances per call (>= 1)                    */
+  int nz;          /* 3D channel: nodes in z (periodic, like x); <= 1 = 2D     */
+  double lz;       /* 3D channel: z period (dz = lz / nz)                      */
 } fcsph_grid;
 
 typedef struct {
@@ -84,12 +87,14 @@ typedef struct {
 typedef struct fcsph_ctx fcsph_ctx;
 
 /* Time-stepping state of isph_step.  All device pointers to double arrays
- * [batch][nx][ny], owned by the caller.  fu, fv hold F^{k-1} between RK3
- * substeps (Eq. 5); their content on entry is ignored at the first substep. */
+ * [batch][nx][ny] (2D) or [batch][nx][nz][ny] (3D), owned by the caller.
+ * fu, fv (fw) hold F^{k-1} between RK3 substeps (Eq. 5); their content on
+ * entry is ignored at the first substep.  w, fw: 3D grids only (else NULL). */
 typedef struct {
   double *u, *v;   /* velocity, updated in place                              */
   double *p;       /* out: pressure phi of the last substep (Eq. 8)           */
   double *fu, *fv; /* scratch: F^{k-1} of Eq. 5                               */
+  double *w, *fw;  /* 3D: z velocity and its F^{k-1}                          */
 } fcsph_state;
 
 typedef struct {
@@ -100,6 +105,7 @@ typedef struct {
   int use_graph;       /* 1: capture one step in a CUDA graph and replay it   */
   const double* nu_inst;   /* device [batch] or NULL: per-instance viscosity (overrides nu) */
   const double* fx_inst;   /* device [batch] or NULL: per-instance body force x (overrides force_x) */
+  double force_z;      /* 3D: body force in z                                  */
 } fcsph_step_params;
 
 /* Create a context for one grid shape: builds the FC tables (Sec. 4; FP64,
@@ -128,9 +134,11 @@ fcsph_status fcsph_fc_table(const fcsph_fc* fc, int bc, double* out_host, size_t
  * (walled x) along x for every extended y row.  bc: FCSPH_DIRICHLET/NEUMANN. */
 fcsph_status fc_extend(fcsph_ctx* ctx, const void* f, void* f_ext, int bc);
 
-/* Eqs. 11/13/16: for each bit set in op_mask (in the order W, DX, DY, LAP),
- * outs[k] receives that operator of f on the physical nodes.  outs has one
- * device pointer per set bit.  FC with the Dirichlet (bc=0) or Neumann table. */
+/* Eqs. 11/13/16: for each bit set in op_mask (in the order W, DX, DY, LAP,
+ * DZ), outs[k] receives that operator of f on the physical nodes.  outs has
+ * one device pointer per set bit.  FC with the Dirichlet (bc=0) or Neumann
+ * table.  3D grids (nz > 1): f and outs are [batch][nx][nz][ny], the
+ * transforms run in y (FC), z and x, and DZ is allowed; 2D grids reject DZ. */
 fcsph_status spectral_op(fcsph_ctx* ctx, const void* f, unsigned op_mask, int bc, void* const* outs);
 
 /* The wall-normal operators of Eqs. 11/13/16 on independent lines: every
@@ -143,7 +151,8 @@ fcsph_status spectral_op(fcsph_ctx* ctx, const void* f, unsigned op_mask, int bc
  * per call; every line's FC, transforms and outputs stay on chip. */
 fcsph_status line_op(fcsph_ctx* ctx, const void* f, unsigned op_mask, int bc, void* const* outs);
 
-/* div(fx, fy) = IFFT( S_x FFT(Fx) + S_y FFT(Fy) ) on the physical nodes. */
+/* div(fx, fy) = IFFT( S_x FFT(Fx) + S_y FFT(Fy) ) on the physical nodes.
+ * 2D grids only (FCSPH_EUNSUPPORTED on a 3D grid). */
 fcsph_status spectral_div(fcsph_ctx* ctx, const void* fx, const void* fy, void* out);
 
 /* Eqs. 31-33: phi with lap(phi) = rhs under the DFT(x) x DCT-I(y) (periodic x)
@@ -151,11 +160,14 @@ fcsph_status spectral_div(fcsph_ctx* ctx, const void* fx, const void* fy, void* 
  * With ppe_refine_iters > 0 (F32 contexts) each sweep forms the residual in
  * FP64 and adds an FP32 correction.  resid_out (host, nullable): relative
  * residual ||L phi - rhs + mean mode|| / ||rhs||, computed on the device in
- * FP64 (synchronises the stream when non-NULL). */
+ * FP64 (synchronises the stream when non-NULL).  3D grids: DFT(x) x DFT(z) x
+ * DCT-I(y), the (0,0,0) mode is 0 (no refinement). */
 fcsph_status ppe_solve(fcsph_ctx* ctx, const void* rhs, void* phi, double* resid_out);
 
 /* Advance `nsteps` projection steps (Eqs. 5-9; FOP = 1 substep, RK3 = 3)
- * of every instance.  Velocity uses the Dirichlet table, phi the Neumann one. */
+ * of every instance.  Velocity uses the Dirichlet table, phi the Neumann one.
+ * 3D grids advance (u, v, w): the y walls take u = u_bottom / u_top and
+ * v = w = 0; state->w and state->fw are required. */
 fcsph_status isph_step(fcsph_ctx* ctx, const fcsph_state* state, int nsteps, const fcsph_step_params* params);
 
 /* Wait for the context's stream; report device-side errors (non-finite state). */
@@ -206,7 +218,8 @@ fcsph_status fcsph_get_tiling(const fcsph_ctx* ctx, int* row_lines, int* col_pai
 /* Autotuner: times `steps` isph_step calls with *prm for every tiling with
  * row_lines, col_pairs in {1, 2, 4} that fits, on a zero state the call
  * allocates and frees (5 fields of the context's batch), then keeps the
- * fastest.  best_ms_out (nullable, host): its milliseconds per step.
+ * fastest (2D: 5 fields, 3D: 7).  best_ms_out (nullable, host): its
+ * milliseconds per step.
  * Synchronises the context's stream.  Engineering choice of this library;
  * the paper has no counterpart. */
 fcsph_status fcsph_autotune(fcsph_ctx* ctx, const fcsph_step_params* prm, int steps, double* best_ms_out);

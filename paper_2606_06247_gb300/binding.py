@@ -18,8 +18,8 @@ PREC = {"f64": F64, "f32": F32, "f32x2": F32X2}
 FC_GRAM, FC_PAPER = 0, 1
 DIRICHLET, NEUMANN = 0, 1
 FAMILY = {"G2": 1, "G4": 2, "G6": 3, "G8": 4, "G10": 5}
-OP_W, OP_DX, OP_DY, OP_LAP = 1, 2, 4, 8
-OPS = {"W": OP_W, "DX": OP_DX, "DY": OP_DY, "LAP": OP_LAP}
+OP_W, OP_DX, OP_DY, OP_LAP, OP_DZ = 1, 2, 4, 8, 16
+OPS = {"W": OP_W, "DX": OP_DX, "DY": OP_DY, "LAP": OP_LAP, "DZ": OP_DZ}
 SCHEME = {"fop": 0, "rk3": 1}
 PROF_KINDS = ["col_fwd", "row_mom", "row_div", "row_grad", "row_op", "col_mom", "col_div", "col_corr", "col_out",
               "row_ppe", "col_ppe", "other"]
@@ -34,7 +34,7 @@ class FcsphError(RuntimeError):
 
 class fcsph_grid(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("lx", ctypes.c_double), ("ly", ctypes.c_double),
-                ("x_walls", ctypes.c_int), ("batch", ctypes.c_int)]
+                ("x_walls", ctypes.c_int), ("batch", ctypes.c_int), ("nz", ctypes.c_int), ("lz", ctypes.c_double)]
 
 
 class fcsph_fc(ctypes.Structure):
@@ -50,7 +50,7 @@ class fcsph_precision(ctypes.Structure):
 
 
 class fcsph_state(ctypes.Structure):
-    _fields_ = [(n, ctypes.c_void_p) for n in ("u", "v", "p", "fu", "fv")]
+    _fields_ = [(n, ctypes.c_void_p) for n in ("u", "v", "p", "fu", "fv", "w", "fw")]
 
 
 class fcsph_step_params(ctypes.Structure):
@@ -58,7 +58,7 @@ class fcsph_step_params(ctypes.Structure):
                 ("force_x", ctypes.c_double), ("force_y", ctypes.c_double),
                 ("u_bottom", ctypes.c_double), ("u_top", ctypes.c_double),
                 ("scheme", ctypes.c_int), ("use_graph", ctypes.c_int),
-                ("nu_inst", ctypes.c_void_p), ("fx_inst", ctypes.c_void_p)]
+                ("nu_inst", ctypes.c_void_p), ("fx_inst", ctypes.c_void_p), ("force_z", ctypes.c_double)]
 
 
 def _load():
@@ -163,8 +163,10 @@ class Context:
     """fcsph_create/destroy plus the per-call entry points."""
 
     def __init__(self, nx, ny, lx, ly, x_walls=False, batch=1, n_match=5, n_cont=25, variant="gram", poly_deg=0,
-                 family="G4", h_over_dx=1.3, prec="f64", refine=0, table_dir=None, table_neu=None, stream=None):
-        self.grid = fcsph_grid(nx, ny, lx, ly, 1 if x_walls else 0, batch)
+                 family="G4", h_over_dx=1.3, prec="f64", refine=0, table_dir=None, table_neu=None, stream=None,
+                 nz=1, lz=0.0):
+        """nz > 1: a 3D channel (x and z periodic, walls in y), fields [batch][nx][nz][ny]."""
+        self.grid = fcsph_grid(nx, ny, lx, ly, 1 if x_walls else 0, batch, nz, lz)
         self.fc = fcsph_fc(FC_GRAM if variant == "gram" else FC_PAPER, n_match, n_cont, poly_deg)
         self.kernel = fcsph_kernel(FAMILY[family], h_over_dx)
         self.prec = fcsph_precision(PREC[prec], refine)
@@ -206,10 +208,13 @@ class Context:
         self._ck(lib.fc_extend(self.h, _ptr(f), _ptr(f_ext), bc))
 
     def spectral_op(self, f, ops, outs, bc=DIRICHLET):
+        """outs[k] for ops[k]; the C call takes them in its bit order W, DX, DY, LAP, DZ."""
+        assert len(ops) == len(outs) and len(set(ops)) == len(ops)
         mask = 0
         for o in ops:
             mask |= OPS[o]
-        order = [o for o in ("W", "DX", "DY", "LAP") if mask & OPS[o]]
+        order = [o for o in ("W", "DX", "DY", "LAP", "DZ") if mask & OPS[o]]
+        assert len(order) == len(ops)
         by_name = dict(zip(ops, outs))
         arr = (ctypes.c_void_p * len(order))(*[by_name[o].data_ptr() for o in order])
         self._ck(lib.spectral_op(self.h, _ptr(f), mask, bc, arr))
@@ -219,7 +224,8 @@ class Context:
         mask = 0
         for o in ops:
             mask |= OPS[o]
-        order = [o for o in ("W", "DX", "DY", "LAP") if mask & OPS[o]]
+        order = [o for o in ("W", "DX", "DY", "LAP", "DZ") if mask & OPS[o]]
+        assert len(order) == len(ops) and len(outs) == len(ops)
         by_name = dict(zip(ops, outs))
         arr = (ctypes.c_void_p * len(order))(*[by_name[o].data_ptr() for o in order])
         self._ck(lib.line_op(self.h, _ptr(f), mask, bc, arr))
@@ -234,15 +240,18 @@ class Context:
 
     @staticmethod
     def _params(nu, rho, dt, force, u_bottom, u_top, scheme, use_graph, nu_inst, fx_inst):
+        fz = force[2] if len(force) > 2 else 0.0
         return fcsph_step_params(nu, rho, dt, force[0], force[1], u_bottom, u_top, SCHEME[scheme], 1 if use_graph else 0,
                                  nu_inst.data_ptr() if nu_inst is not None else None,
-                                 fx_inst.data_ptr() if fx_inst is not None else None)
+                                 fx_inst.data_ptr() if fx_inst is not None else None, fz)
 
     def isph_step(self, u, v, p, fu, fv, nsteps, nu, rho=1.0, dt=1e-3, force=(0.0, 0.0), u_bottom=0.0, u_top=0.0,
-                  scheme="fop", use_graph=True, nu_inst=None, fx_inst=None):
+                  scheme="fop", use_graph=True, nu_inst=None, fx_inst=None, w=None, fw=None):
         """nu_inst / fx_inst: optional CUDA float64 tensors [batch] of per-instance
-        viscosity and x body force (override nu / force[0])."""
-        st = fcsph_state(u.data_ptr(), v.data_ptr(), p.data_ptr(), fu.data_ptr(), fv.data_ptr())
+        viscosity and x body force (override nu / force[0]).  3D grids: w, fw (z
+        velocity and its F^{k-1}) and force = (fx, fy, fz)."""
+        st = fcsph_state(u.data_ptr(), v.data_ptr(), p.data_ptr(), fu.data_ptr(), fv.data_ptr(),
+                         w.data_ptr() if w is not None else None, fw.data_ptr() if fw is not None else None)
         prm = self._params(nu, rho, dt, force, u_bottom, u_top, scheme, use_graph, nu_inst, fx_inst)
         self._ck(lib.isph_step(self.h, ctypes.byref(st), nsteps, ctypes.byref(prm)))
 

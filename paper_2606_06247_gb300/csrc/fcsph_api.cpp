@@ -117,7 +117,12 @@ RowOps ops_none() {
   return o;
 }
 
-size_t field_elems(const fcsph_ctx* c) { return (size_t)c->gd.batch * c->gd.nx * c->gd.ny; }
+size_t field_elems(const fcsph_ctx* c) { return (size_t)c->gd.batch * c->gd.ncol * c->gd.ny; }
+
+// Spectrum buffer geometry (fields per instance) and z passes of the 3D grid.
+static size_t spec_fs(const fcsph_ctx* c) { return (size_t)c->gd.rows * c->gd.ncol; }
+static size_t in_bstride(const fcsph_ctx* c) { return (c->gd.nz > 1 ? 3 : 2) * spec_fs(c); }
+static size_t out_bstride(const fcsph_ctx* c) { return (c->gd.nz > 1 ? 12 : 6) * spec_fs(c); }
 
 }  // namespace
 
@@ -174,6 +179,11 @@ fcsph_status fcsph_create(const fcsph_grid* grid, const fcsph_fc* fc, const fcsp
     return fail(nullptr, FCSPH_EINVAL, "fcsph_create: bad precision");
   if (grid->x_walls && grid->nx < 2 * fc->n_match)
     return fail(nullptr, FCSPH_EINVAL, "fcsph_create: walled x needs nx >= 2*n_match");
+  const int nz = grid->nz > 1 ? grid->nz : 1;
+  if (nz > 1 && (grid->x_walls || !(grid->lz > 0) || nz > 8192))
+    return fail(nullptr, FCSPH_EINVAL, "fcsph_create: a 3D grid (nz > 1) needs periodic x, lz > 0, nz <= 8192");
+  if (nz > 1 && prec->ppe_refine_iters > 0)
+    return fail(nullptr, FCSPH_EUNSUPPORTED, "fcsph_create: PPE refinement is 2D only");
   fcsph_ctx* c = new fcsph_ctx();
   c->grid = *grid;
   c->fc = *fc;
@@ -196,6 +206,9 @@ fcsph_status fcsph_create(const fcsph_grid* grid, const fcsph_fc* fc, const fcsp
   GridDev& g = c->gd;
   g.nx = grid->nx;
   g.ny = grid->ny;
+  g.nz = nz;
+  g.ncol = g.nx * nz;
+  g.dz = nz > 1 ? grid->lz / nz : 1.0;
   g.batch = grid->batch;
   g.x_walls = grid->x_walls ? 1 : 0;
   g.n_match = fc->n_match;
@@ -219,6 +232,8 @@ fcsph_status fcsph_create(const fcsph_grid* grid, const fcsph_fc* fc, const fcsp
   c->plan_px = plan_for(g.x_walls ? 2 * (g.nx - 1) : g.nx, &pool, &fills);
   g.ex_off = pool.add(gauss_axis(g.mx, g.dx, g.h, g.mx), std::vector<double>(g.mx, 0.0));
   g.ey_off = pool.add(gauss_axis(g.my, g.dy, g.h, g.hy), std::vector<double>(g.hy, 0.0));
+  g.ez_off = pool.add(gauss_axis(nz, g.dz, g.h, nz), std::vector<double>(nz, 0.0));
+  if (nz > 1) c->plan_z = plan_for(nz, &pool, &fills);
   {
     // Eq. 33 eigenvalues: DFT lam_k = 2 pi kappa / Lx (kappa signed, Nyquist positive), DCT-I lam = pi k / L
     const double pi = 3.14159265358979323846;
@@ -239,6 +254,13 @@ fcsph_status fcsph_create(const fcsph_grid* grid, const fcsph_fc* fc, const fcsp
     }
     g.lx2_off = pool.add(lx2, std::vector<double>(g.nx, 0.0));
     g.ly2_off = pool.add(ly2, std::vector<double>(g.ny, 0.0));
+    std::vector<double> lz2(nz, 0.0);
+    for (int k = 0; k < nz && nz > 1; ++k) {
+      const int kappa = (2 * k <= nz) ? k : k - nz;
+      const double lk = 2.0 * pi * kappa / grid->lz;
+      lz2[k] = lk * lk;
+    }
+    g.lz2_off = pool.add(lz2, std::vector<double>(nz, 0.0));
   }
 
   fcsph_status st = FCSPH_OK;
@@ -267,12 +289,13 @@ fcsph_status fcsph_create(const fcsph_grid* grid, const fcsph_fc* fc, const fcsp
       CREATE_CK(cudaMalloc(&c->dEff, 2 * ne * sizeof(float2)), "cudaMalloc(Eff)");
       CREATE_CK(cudaMemcpy(c->dEff, hf.data(), 2 * ne * sizeof(float2), cudaMemcpyHostToDevice), "Eff upload");
     }
-    const size_t fs = (size_t)g.rows * g.nx * g.batch;
+    const size_t fs = (size_t)g.rows * g.ncol * g.batch;
     const size_t cb = cplx_bytes(prec->fft_prec);
-    CREATE_CK(cudaMalloc(&c->spec_in, 2 * fs * cb), "cudaMalloc(spec_in)");
-    CREATE_CK(cudaMalloc(&c->spec_out, 6 * fs * cb), "cudaMalloc(spec_out)");
+    const bool d3 = g.nz > 1;
+    CREATE_CK(cudaMalloc(&c->spec_in, (d3 ? 3 : 2) * fs * cb), "cudaMalloc(spec_in)");
+    CREATE_CK(cudaMalloc(&c->spec_out, (d3 ? 12 : 6) * fs * cb), "cudaMalloc(spec_out)");
     CREATE_CK(cudaMalloc(&c->spec_ppe, fs * 16), "cudaMalloc(spec_ppe)");  // FP64-sized: refinement
-    CREATE_CK(cudaMalloc((void**)&c->work, 6 * field_elems(c) * sizeof(double)), "cudaMalloc(work)");
+    CREATE_CK(cudaMalloc((void**)&c->work, (d3 ? 7 : 6) * field_elems(c) * sizeof(double)), "cudaMalloc(work)");
     CREATE_CK(cudaMalloc((void**)&c->dred, 8 * sizeof(double)), "cudaMalloc(red)");
     CREATE_CK(cudaMalloc((void**)&c->dstatus, sizeof(int)), "cudaMalloc(status)");
     CREATE_CK(cudaMemset(c->dstatus, 0, sizeof(int)), "status clear");
@@ -326,11 +349,13 @@ fcsph_status fc_extend(fcsph_ctx* c, const void* f, void* f_ext, int bc) {
 
 fcsph_status spectral_op(fcsph_ctx* c, const void* f, unsigned op_mask, int bc, void* const* outs) {
   if (!c || !f || !outs || (bc != 0 && bc != 1)) return fail(c, FCSPH_EINVAL, "spectral_op: bad argument");
-  if (op_mask == 0 || op_mask > 15u) return fail(c, FCSPH_EINVAL, "spectral_op: op_mask must be a nonempty subset of W|DX|DY|LAP");
+  const unsigned all = c->gd.nz > 1 ? 31u : 15u;
+  if (op_mask == 0 || (op_mask & ~all))
+    return fail(c, FCSPH_EINVAL, "spectral_op: op_mask must be a nonempty subset of W|DX|DY|LAP (|DZ on 3D grids)");
   RowOps ops = ops_none();
   ops.nin = 1;
-  const int sym[4] = {SYM_W, SYM_DX, SYM_DY, SYM_LAP};
-  for (int b = 0; b < 4; ++b)
+  const int sym[5] = {SYM_W, SYM_DX, SYM_DY, SYM_LAP, SYM_DZ};
+  for (int b = 0; b < 5; ++b)
     if (op_mask & (1u << b)) {
       if (!outs[ops.nout]) return fail(c, FCSPH_EINVAL, "spectral_op: null output pointer");
       ops.nterm[ops.nout] = 1;
@@ -341,8 +366,11 @@ fcsph_status spectral_op(fcsph_ctx* c, const void* f, unsigned op_mask, int bc, 
   const int p = c->prec.fft_prec;
   const void* fl[1] = {f};
   FCSPH_CK(launch_col_fwd(c, p, 1, fl, p != FCSPH_F32, bc, c->spec_in, 0), "spectral_op fwd");
-  FCSPH_CK(launch_row_sym(c, p, c->spec_in, c->spec_out, ops, 1.0 / ((double)c->gd.mx * c->gd.my), bc, FCSPH_PROF_ROW_OP),
+  FCSPH_CK(launch_zpass(c, p, c->spec_in, 1, in_bstride(c), c->gd.hy, 0), "spectral_op z fwd");
+  FCSPH_CK(launch_row_sym(c, p, c->spec_in, c->spec_out, ops, 1.0 / ((double)c->gd.mx * c->gd.my * c->gd.nz), bc,
+                          FCSPH_PROF_ROW_OP),
            "spectral_op row");
+  FCSPH_CK(launch_zpass(c, p, c->spec_out, ops.nout, out_bstride(c), c->gd.hy, 1), "spectral_op z inv");
   FCSPH_CK(launch_col_out(c, c->spec_out, ops.nout, outs), "spectral_op inv");
   return FCSPH_OK;
 }
@@ -363,6 +391,7 @@ fcsph_status line_op(fcsph_ctx* c, const void* f, unsigned op_mask, int bc, void
 
 fcsph_status spectral_div(fcsph_ctx* c, const void* fx, const void* fy, void* out) {
   if (!c || !fx || !fy || !out) return fail(c, FCSPH_EINVAL, "spectral_div: bad argument");
+  if (c->gd.nz > 1) return fail(c, FCSPH_EUNSUPPORTED, "spectral_div: 2D grids only");
   RowOps ops = ops_none();
   ops.nin = 2;
   ops.nout = 1;
@@ -428,7 +457,9 @@ fcsph_status ppe_solve(fcsph_ctx* c, const void* rhs, void* phi, double* resid_o
   const int iters = p == FCSPH_F32 ? c->prec.ppe_refine_iters : 0;
   const void* bl[1] = {b64};
   FCSPH_CK(launch_col_fwd(c, p, 1, bl, 1, FCSPH_DIRICHLET, c->spec_ppe, 1), "ppe fwd");
+  FCSPH_CK(launch_zpass(c, p, c->spec_ppe, 1, spec_fs(c), c->gd.ny, 0), "ppe z fwd");
   FCSPH_CK(launch_row_ppe(c, p, c->spec_ppe, 0), "ppe row");
+  FCSPH_CK(launch_zpass(c, p, c->spec_ppe, 1, spec_fs(c), c->gd.ny, 1), "ppe z inv");
   FCSPH_CK(launch_col_ppe_inv(c, p, c->spec_ppe, iters > 0 ? (void*)phi64 : phi, iters > 0 ? 1 : (p != FCSPH_F32),
                               phi64, 0, nullptr, 0, nullptr),
            "ppe inv");
@@ -442,7 +473,9 @@ fcsph_status ppe_solve(fcsph_ctx* c, const void* rhs, void* phi, double* resid_o
     double* r = c->work + 4 * n;
     const void* pl[1] = {phi64};
     FCSPH_CK(launch_col_fwd(c, FCSPH_F64, 1, pl, 1, FCSPH_DIRICHLET, c->spec_ppe, 1), "resid fwd");
+    FCSPH_CK(launch_zpass(c, FCSPH_F64, c->spec_ppe, 1, spec_fs(c), c->gd.ny, 0), "resid z fwd");
     FCSPH_CK(launch_row_ppe(c, FCSPH_F64, c->spec_ppe, 1), "resid row");
+    FCSPH_CK(launch_zpass(c, FCSPH_F64, c->spec_ppe, 1, spec_fs(c), c->gd.ny, 1), "resid z inv");
     FCSPH_CK(launch_col_ppe_inv(c, FCSPH_F64, c->spec_ppe, r, 1, nullptr, 1, b64, 0, nullptr), "resid inv");
     FCSPH_CK(launch_resid_norm(c, r, b64, c->dred), "resid norm");
     double h2[2];
@@ -454,53 +487,73 @@ fcsph_status ppe_solve(fcsph_ctx* c, const void* rhs, void* phi, double* resid_o
 }
 
 // One substep (Eqs. 5-9).  Precondition: spec_in holds the Dirichlet-FC
-// forward transforms of (u, v).  Postcondition (fwd_next): the same for the
-// new (u, v).
+// y transforms of the velocity components.  Postcondition (fwd_next): the
+// same for the new velocity.  3D grids transform every x pass's inputs in z
+// first and its outputs back in z after.
 static fcsph_status substep(fcsph_ctx* c, const fcsph_state* s, const StepDev& sd, int fwd_next) {
   const int p = c->prec.fft_prec;
   const size_t n = field_elems(c);
-  double* us = c->work;
-  double* vs = c->work + n;
+  const bool d3 = c->gd.nz > 1;
+  const int nc = d3 ? 3 : 2;
+  const int hy = c->gd.hy, ny = c->gd.ny;
+  double* vs[3] = {c->work, c->work + n, c->work + 3 * n};  // u*, v*, w*
   double* b = c->work + 2 * n;
-  const double scale = 1.0 / ((double)c->gd.mx * c->gd.my);
+  const double scale = 1.0 / ((double)c->gd.mx * c->gd.my * c->gd.nz);
+  const double* vel[3] = {s->u, s->v, s->w};
+  double* Fp[3] = {s->fu, s->fv, s->fw};
+  double* vo[3] = {s->u, s->v, s->w};
+  // momentum: d/dx, d/dy, (d/dz,) lap of every component
   RowOps mom = ops_none();
-  mom.nin = 2;
-  mom.nout = 6;
-  const int opl[3] = {SYM_DX, SYM_DY, SYM_LAP};
-  for (int o = 0; o < 6; ++o) {
+  mom.nin = nc;
+  mom.nout = nc * (nc + 1);
+  const int opl2[3] = {SYM_DX, SYM_DY, SYM_LAP};
+  const int opl3[4] = {SYM_DX, SYM_DY, SYM_DZ, SYM_LAP};
+  for (int o = 0; o < mom.nout; ++o) {
     mom.nterm[o] = 1;
-    mom.field[o][0] = o / 3;
-    mom.op[o][0] = opl[o % 3];
+    mom.field[o][0] = o / (nc + 1);
+    mom.op[o][0] = d3 ? opl3[o % 4] : opl2[o % 3];
   }
+  FCSPH_CK(launch_zpass(c, p, c->spec_in, nc, in_bstride(c), hy, 0), "step mom z fwd");
   FCSPH_CK(launch_row_sym(c, p, c->spec_in, c->spec_out, mom, scale, FCSPH_DIRICHLET, FCSPH_PROF_ROW_MOM), "step mom row");
-  FCSPH_CK(launch_step_mom(c, sd, c->spec_out, s->u, s->v, s->fu, s->fv, us, vs, c->spec_in), "step mom col");
+  FCSPH_CK(launch_zpass(c, p, c->spec_out, mom.nout, out_bstride(c), hy, 1), "step mom z inv");
+  FCSPH_CK(launch_step_mom(c, sd, c->spec_out, vel, Fp, vs, c->spec_in), "step mom col");
+  // divergence of u*
   RowOps dv = ops_none();
-  dv.nin = 2;
+  dv.nin = nc;
   dv.nout = 1;
-  dv.nterm[0] = 2;
-  dv.field[0][0] = 0;
-  dv.op[0][0] = SYM_DX;
-  dv.field[0][1] = 1;
-  dv.op[0][1] = SYM_DY;
+  dv.nterm[0] = nc;
+  const int dops[3] = {SYM_DX, SYM_DY, SYM_DZ};
+  for (int t = 0; t < nc; ++t) {
+    dv.field[0][t] = t;
+    dv.op[0][t] = dops[t];
+  }
+  FCSPH_CK(launch_zpass(c, p, c->spec_in, nc, in_bstride(c), hy, 0), "step div z fwd");
   FCSPH_CK(launch_row_sym(c, p, c->spec_in, c->spec_out, dv, scale, FCSPH_DIRICHLET, FCSPH_PROF_ROW_DIV), "step div row");
+  FCSPH_CK(launch_zpass(c, p, c->spec_out, 1, out_bstride(c), hy, 1), "step div z inv");
   FCSPH_CK(launch_step_div(c, sd, c->spec_out, b, c->spec_ppe), "step div col");
   // PPE: the DCT-y forward of b is already in spec_ppe (fused above)
   const int iters = p == FCSPH_F32 ? c->prec.ppe_refine_iters : 0;
+  FCSPH_CK(launch_zpass(c, p, c->spec_ppe, 1, spec_fs(c), ny, 0), "step ppe z fwd");
   FCSPH_CK(launch_row_ppe(c, p, c->spec_ppe, 0), "step ppe row");
+  FCSPH_CK(launch_zpass(c, p, c->spec_ppe, 1, spec_fs(c), ny, 1), "step ppe z inv");
   FCSPH_CK(launch_col_ppe_inv(c, p, c->spec_ppe, s->p, 1, s->p, 0, nullptr, iters == 0 ? 1 : 0, c->spec_in),
            "step ppe col");
   if (iters > 0) {
     fcsph_status st = ppe_refine(c, b, s->p, iters, 1);
     if (st != FCSPH_OK) return st;
   }
+  // gradient of phi and the correction
   RowOps gr = ops_none();
   gr.nin = 1;
-  gr.nout = 2;
-  gr.nterm[0] = gr.nterm[1] = 1;
-  gr.op[0][0] = SYM_DX;
-  gr.op[1][0] = SYM_DY;
+  gr.nout = nc;
+  for (int o = 0; o < nc; ++o) {
+    gr.nterm[o] = 1;
+    gr.op[o][0] = dops[o];
+  }
+  FCSPH_CK(launch_zpass(c, p, c->spec_in, 1, in_bstride(c), hy, 0), "step grad z fwd");
   FCSPH_CK(launch_row_sym(c, p, c->spec_in, c->spec_out, gr, scale, FCSPH_NEUMANN, FCSPH_PROF_ROW_GRAD), "step grad row");
-  FCSPH_CK(launch_step_corr(c, sd, c->spec_out, us, vs, s->u, s->v, fwd_next ? c->spec_in : nullptr), "step corr col");
+  FCSPH_CK(launch_zpass(c, p, c->spec_out, nc, out_bstride(c), hy, 1), "step grad z inv");
+  FCSPH_CK(launch_step_corr(c, sd, c->spec_out, vs, vo, fwd_next ? c->spec_in : nullptr), "step corr col");
   return FCSPH_OK;
 }
 
@@ -516,6 +569,7 @@ static fcsph_status one_step(fcsph_ctx* c, const fcsph_state* s, const fcsph_ste
     sd.dt = prm->dt;
     sd.fx = prm->force_x;
     sd.fy = prm->force_y;
+    sd.fz = prm->force_z;
     sd.u_bottom = prm->u_bottom;
     sd.u_top = prm->u_top;
     sd.nu_inst = prm->nu_inst;
@@ -538,12 +592,14 @@ static fcsph_status one_step(fcsph_ctx* c, const fcsph_state* s, const fcsph_ste
 fcsph_status isph_step(fcsph_ctx* c, const fcsph_state* s, int nsteps, const fcsph_step_params* prm) {
   if (!c || !s || !prm || nsteps < 0) return fail(c, FCSPH_EINVAL, "isph_step: bad argument");
   if (!s->u || !s->v || !s->p || !s->fu || !s->fv) return fail(c, FCSPH_EINVAL, "isph_step: null state pointer");
+  if (c->gd.nz > 1 && (!s->w || !s->fw)) return fail(c, FCSPH_EINVAL, "isph_step: a 3D grid needs w and fw");
   if (prm->scheme != FCSPH_SCHEME_FOP && prm->scheme != FCSPH_SCHEME_RK3)
     return fail(c, FCSPH_EINVAL, "isph_step: bad scheme");
   if (!(prm->dt > 0) || !(prm->rho > 0) || !(prm->nu >= 0)) return fail(c, FCSPH_EINVAL, "isph_step: need dt, rho > 0, nu >= 0");
   if (nsteps == 0) return FCSPH_OK;
-  const void* uv[2] = {s->u, s->v};
-  FCSPH_CK(launch_col_fwd(c, c->prec.fft_prec, 2, uv, 1, FCSPH_DIRICHLET, c->spec_in, 0), "step initial fwd");
+  const void* uvw[3] = {s->u, s->v, s->w};
+  FCSPH_CK(launch_col_fwd(c, c->prec.fft_prec, c->gd.nz > 1 ? 3 : 2, uvw, 1, FCSPH_DIRICHLET, c->spec_in, 0),
+           "step initial fwd");
   if (!prm->use_graph) {
     for (int it = 0; it < nsteps; ++it) {
       fcsph_status st = one_step(c, s, prm);
@@ -554,7 +610,8 @@ fcsph_status isph_step(fcsph_ctx* c, const fcsph_state* s, int nsteps, const fcs
   std::vector<double> key = {(double)(uintptr_t)s->u, (double)(uintptr_t)s->v, (double)(uintptr_t)s->p,
                              (double)(uintptr_t)s->fu, (double)(uintptr_t)s->fv, prm->nu, prm->rho, prm->dt,
                              prm->force_x, prm->force_y, prm->u_bottom, prm->u_top, (double)prm->scheme,
-                             (double)(uintptr_t)prm->nu_inst, (double)(uintptr_t)prm->fx_inst};
+                             (double)(uintptr_t)prm->nu_inst, (double)(uintptr_t)prm->fx_inst,
+                             (double)(uintptr_t)s->w, (double)(uintptr_t)s->fw, prm->force_z};
   if (!c->gexec || key != c->graph_key) {
     if (c->gexec) {
       cudaGraphExecDestroy(c->gexec);
@@ -666,15 +723,20 @@ fcsph_status fcsph_get_tiling(const fcsph_ctx* c, int* row_lines, int* col_pairs
 fcsph_status fcsph_autotune(fcsph_ctx* c, const fcsph_step_params* prm, int steps, double* best_ms_out) {
   if (!c || !prm || steps < 1) return fail(c, FCSPH_EINVAL, "fcsph_autotune: bad argument");
   const size_t n = field_elems(c);
+  const int nf = c->gd.nz > 1 ? 7 : 5;
   double* buf = nullptr;
-  FCSPH_CK(cudaMalloc((void**)&buf, 5 * n * sizeof(double)), "autotune state");
-  fcsph_state s{buf, buf + n, buf + 2 * n, buf + 3 * n, buf + 4 * n};
+  FCSPH_CK(cudaMalloc((void**)&buf, nf * n * sizeof(double)), "autotune state");
+  fcsph_state s{buf, buf + n, buf + 2 * n, buf + 3 * n, buf + 4 * n, nullptr, nullptr};
+  if (nf == 7) {
+    s.w = buf + 5 * n;
+    s.fw = buf + 6 * n;
+  }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   const int cand[3] = {1, 2, 4};
   int best_r = c->row_lines, best_c = c->col_pairs;
   float best = -1.f;
   fcsph_status st = FCSPH_OK;
-  cudaError_t e = cudaMemsetAsync(buf, 0, 5 * n * sizeof(double), c->stream);
+  cudaError_t e = cudaMemsetAsync(buf, 0, nf * n * sizeof(double), c->stream);
   if (e == cudaSuccess) e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
   if (e != cudaSuccess) st = cuda_fail(c, e, "autotune setup");

@@ -103,18 +103,25 @@ std::vector<double> gauss_axis(int m, double d, double h, int count);
 
 // Operator descriptors for the spectral row pass: output o is
 // sum_{t < nterm[o]} symbol(op[o][t]) * spectrum(field[o][t]).
-enum { SYM_W = 0, SYM_DX = 1, SYM_DY = 2, SYM_LAP = 3 };
+enum { SYM_W = 0, SYM_DX = 1, SYM_DY = 2, SYM_LAP = 3, SYM_DZ = 4 };
+constexpr int kMaxRowOut = 12;   // 3D momentum: 3 components x (3 gradients + Laplacian)
+constexpr int kMaxRowTerms = 3;  // 3D divergence
 struct RowOps {
   int nin;               // input spectra per instance
   int nout;              // output spectra per instance
-  int nterm[6];
-  int field[6][2];
-  int op[6][2];
+  int nterm[kMaxRowOut];
+  int field[kMaxRowOut][kMaxRowTerms];
+  int op[kMaxRowOut][kMaxRowTerms];
 };
 
 // Everything a kernel needs about the grid and the method's constants.
 struct GridDev {
   int nx, ny, batch, x_walls;
+  // 3D channel: nz > 1 z nodes (periodic); every (x, z) pair is a wall-normal
+  // column, ncol = nx * nz per instance (ncol = nx, nz = 1 in 2D)
+  int nz, ncol;
+  double dz;
+  int ez_off, lz2_off;   // pool offsets: exp(-kz^2 h^2/4) and lam_z^2, index < nz
   int mx, my, hy;        // extended lengths, y half-spectrum rows
   int n_match, n_cont;
   int rows;              // spectrum rows allocated per field (max(hy, ny))
@@ -128,7 +135,7 @@ struct GridDev {
 };
 
 struct StepDev {
-  double nu, rho, dt, fx, fy, u_bottom, u_top;
+  double nu, rho, dt, fx, fy, fz, u_bottom, u_top;
   double a, g, z;        // substep coefficients
   const double* nu_inst; // per-instance overrides (device) or null
   const double* fx_inst;
@@ -143,6 +150,7 @@ struct fcsph_ctx {
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;
   fcsph::FftPlan plan_y, plan_x, plan_py, plan_px;  // FC-y, FC/periodic-x, PPE-y (DCT), PPE-x
+  fcsph::FftPlan plan_z;                            // 3D: periodic z (operators and PPE)
   double* dE = nullptr;         // device [2][n_cont][2 n_match] (Dirichlet, Neumann)
   void* dEff = nullptr;         // the same in FP32 pairs (FP32x2 contexts)
   int row_lines = 1;            // rows per CTA of the one-warp row passes
@@ -201,11 +209,12 @@ cudaError_t launch_col_out(fcsph_ctx* c, const void* spec, int nout, void* const
 cudaError_t launch_row_ppe(fcsph_ctx* c, int prec, void* spec, int apply);
 cudaError_t launch_col_ppe_inv(fcsph_ctx* c, int prec, const void* spec, void* phi, int phi_double, double* phi64,
                                int mode, const double* rhs, int neumann_fwd, void* spec_fwd);
-cudaError_t launch_step_mom(fcsph_ctx* c, const StepDev& s, const void* spec6, const double* u, const double* v,
-                            double* fu, double* fv, double* us, double* vs, void* spec2);
+cudaError_t launch_step_mom(fcsph_ctx* c, const StepDev& s, const void* spec_mom, const double* const* vel,
+                            double* const* Fp, double* const* vs, void* spec_next);
 cudaError_t launch_step_div(fcsph_ctx* c, const StepDev& s, const void* spec1, double* b, void* spec_dct);
-cudaError_t launch_step_corr(fcsph_ctx* c, const StepDev& s, const void* spec2, const double* us, const double* vs,
-                             double* u, double* v, void* spec_next);
+cudaError_t launch_step_corr(fcsph_ctx* c, const StepDev& s, const void* spec_grad, double* const* vs,
+                             double* const* vo, void* spec_next);
+cudaError_t launch_zpass(fcsph_ctx* c, int prec, void* spec, int nf, size_t bstride, int rows_used, int inv);
 cudaError_t launch_dft_lines(int n, int nlines, int dir, int prec, const void* in, void* out, cudaStream_t st,
                              const fcsph::FftPlan& plan, const void* pool);
 // out2[0] = sum over instances of sum (r - instance mean)^2, out2[1] = sum b^2

@@ -38,7 +38,7 @@ template <> struct PoolOf<float> { static const float2* get(const fcsph_ctx* c) 
 template <> struct PoolOf<ff> { static const ff2* get(const fcsph_ctx* c) { return static_cast<const ff2*>(c->poolff); } };
 
 __device__ __forceinline__ size_t fidx(const GridDev& g, int b, int i, int j) {
-  return ((size_t)b * g.nx + i) * g.ny + j;
+  return ((size_t)b * g.ncol + i) * g.ny + j;
 }
 
 // ---------------------------------------------------------------------------
@@ -142,9 +142,9 @@ __device__ void col_forward_store(typename CT<T>::t* lines, typename CT<T>::t* s
         a = mk<V>(h * (z.x + zm.x), h * (z.y - zm.y));
         b = mk<V>(h * (z.y + zm.y), h * (zm.x - z.x));
       }
-      V* S = spec + (size_t)k * g.nx + i;
-      if (i < g.nx) S[0] = a;
-      if (i + 1 < g.nx) S[1] = b;
+      V* S = spec + (size_t)k * g.ncol + i;
+      if (i < g.ncol) S[0] = a;
+      if (i + 1 < g.ncol) S[1] = b;
     }
   }
 }
@@ -162,10 +162,10 @@ __device__ void col_gather_hermitian(typename CT<T>::t* lines, int Pp, int ls, c
       const int ia = i0 + 2 * p, ib = ia + 1;
       V* L = lines + ((size_t)o * Pp + p) * ls;
       for (int k = threadIdx.x; k < hy; k += blockDim.x) {
-        const V* S = spec + o * fstride + (size_t)k * g.nx;
+        const V* S = spec + o * fstride + (size_t)k * g.ncol;
         V A = mk<V>(0.0, 0.0), B = mk<V>(0.0, 0.0);
-        if (ia < g.nx) A = S[ia];
-        if (ib < g.nx) B = S[ib];
+        if (ia < g.ncol) A = S[ia];
+        if (ib < g.ncol) B = S[ib];
         const bool self = (k == 0) || (2 * k == n);
         V z0, z1;
         if (self) {
@@ -194,10 +194,10 @@ __device__ void col_gather_dct(typename CT<T>::t* lines, int Pp, int ls, const G
     const int ia = i0 + 2 * p, ib = ia + 1;
     V* L = lines + (size_t)p * ls;
     for (int l = threadIdx.x; l < ny; l += blockDim.x) {
-      const V* S = spec + (size_t)l * g.nx;
+      const V* S = spec + (size_t)l * g.ncol;
       V z = mk<V>(0.0, 0.0);
-      if (ia < g.nx) z.x = S[ia].x;
-      if (ib < g.nx) z.y = S[ib].x;
+      if (ia < g.ncol) z.x = S[ia].x;
+      if (ib < g.ncol) z.y = S[ib].x;
       L[l] = z;
       if (l >= 1 && l <= ny - 2) L[M - l] = z;
     }
@@ -207,7 +207,7 @@ __device__ void col_gather_dct(typename CT<T>::t* lines, int Pp, int ls, const G
 // ---------------------------------------------------------------------------
 // Column forward: load nf real fields, FC (or DCT) + FFT, store spectra.
 template <typename T, typename U>
-__global__ void __launch_bounds__(kFftThreads, MinCtas<T>::v) k_col_fwd(GridDev g, const U* __restrict__ f0, const U* __restrict__ f1,
+__global__ void __launch_bounds__(kFftThreads, MinCtas<T>::v) k_col_fwd(GridDev g, const U* __restrict__ f0, const U* __restrict__ f1, const U* __restrict__ f2,
                                                          const typename FcTab<T>::t* __restrict__ E, const __grid_constant__ FftPlan P,
                                                       const typename CT<T>::t* __restrict__ pool, int dct,
                                                       typename CT<T>::t* __restrict__ spec, size_t fstride,
@@ -218,13 +218,13 @@ __global__ void __launch_bounds__(kFftThreads, MinCtas<T>::v) k_col_fwd(GridDev 
   V* scratch = lines + (size_t)Pp * ls;
   const int b = blockIdx.z, f = blockIdx.y;
   const int i0 = blockIdx.x * 2 * Pp;
-  const U* src = f == 0 ? f0 : f1;
+  const U* src = f == 0 ? f0 : (f == 1 ? f1 : f2);
   const int W = 2 * Pp;
   const int ny = g.ny;
-  const size_t base = ((size_t)b * g.nx + i0) * ny;
+  const size_t base = ((size_t)b * g.ncol + i0) * ny;
   for (int col = 0; col < W; ++col) {
     T* L = reinterpret_cast<T*>(lines + (size_t)(col >> 1) * ls) + (col & 1);
-    const bool in = i0 + col < g.nx;
+    const bool in = i0 + col < g.ncol;
     for (int j = threadIdx.x; j < ny; j += blockDim.x)
       L[2 * j] = (T)(in ? (double)src[base + (size_t)col * ny + j] : 0.0);
   }
@@ -234,16 +234,19 @@ __global__ void __launch_bounds__(kFftThreads, MinCtas<T>::v) k_col_fwd(GridDev 
 
 // ---------------------------------------------------------------------------
 // Symbols (Eq. 16 reading): W_hat(s) = e^{-s} sum_{m<n} s^m/m!, s = |k|^2 h^2/4;
-// DX = i kx W_hat, DY = i ky W_hat (zero on the own-axis Nyquist line),
-// LAP = -|k|^2 W_hat, W = W_hat.  Returned as (re, im) in the compute type.
+// DX = i kx W_hat, DY = i ky W_hat, DZ = i kz W_hat (each zero on its own
+// axis' Nyquist plane), LAP = -|k|^2 W_hat, W = W_hat (kz = 0 in 2D).
+// Returned as (re, im) in the compute type.
 template <typename T>
-__device__ __forceinline__ typename CT<T>::t symbol(int op, T kx, T ky, bool nyq_x, bool nyq_y, T What) {
+__device__ __forceinline__ typename CT<T>::t symbol(int op, T kx, T ky, T kz, bool nyq_x, bool nyq_y, bool nyq_z,
+                                                    T What) {
   typedef typename CT<T>::t V;
   switch (op) {
     case SYM_W: return mk<V>(What, 0.0);
     case SYM_DX: return mk<V>(0.0, nyq_x ? (T)0 : kx * What);
     case SYM_DY: return mk<V>(0.0, nyq_y ? (T)0 : ky * What);
-    default: return mk<V>(-(kx * kx + ky * ky) * What, 0.0);
+    case SYM_DZ: return mk<V>(0.0, nyq_z ? (T)0 : kz * What);
+    default: return mk<V>(-(kx * kx + ky * ky + kz * kz) * What, 0.0);
   }
 }
 
@@ -260,10 +263,13 @@ template <typename T> __device__ __forceinline__ T kernel_poly(int family, T s) 
   }
 }
 
-// Row pass: for Rr rows ky of one instance: load nin input rows, FC-extend
-// in x (walled x), FFT (length mx); then for each output in turn form
+// Row (x) pass over the x lines of the y half-spectra: line q of an instance
+// is the ky = q / nz row at z index kq = q % nz (3D: the spectra are already
+// transformed in z; 2D: nz = 1, line q = row ky), its nx elements at stride
+// nz.  For Rr lines of one instance: load nin input lines, FC-extend in x
+// (walled x), FFT (length mx); then for each output in turn form
 // sum_t S_t * F_t times `scale`, inverse FFT, truncate to nx and store.
-// Shared memory: the nin input rows and their scratch (2 nin Rr lines; one
+// Shared memory: the nin input lines and their scratch (2 nin Rr lines; one
 // half holds the spectra, the other serves the outputs), plus Rr lines when
 // nin = 1.
 template <typename T>
@@ -280,14 +286,15 @@ __global__ void __launch_bounds__(kFftThreads, MinCtas<T>::v) k_row_sym(GridDev 
   V* A = reinterpret_cast<V*>(smem_raw);
   V* B = A + (size_t)nin * Rr * ls;
   const int b = blockIdx.y;
-  const int ky0 = blockIdx.x * Rr;
-  const int nx = g.nx, mx = g.mx;
+  const int q0 = blockIdx.x * Rr;
+  const int nx = g.nx, mx = g.mx, nz = g.nz;
+  const int nq = g.hy * nz;
   for (int f = 0; f < nin; ++f)
     for (int r = 0; r < Rr; ++r) {
-      const int ky = ky0 + r;
+      const int q = q0 + r;
       V* L = A + ((size_t)f * Rr + r) * ls;
-      const V* S = sp_in + b * bstride_in + f * fstride_in + (size_t)ky * nx;
-      for (int i = threadIdx.x; i < nx; i += blockDim.x) L[i] = ky < g.hy ? S[i] : mk<V>(0.0, 0.0);
+      const V* S = sp_in + b * bstride_in + f * fstride_in + (size_t)(q / nz) * g.ncol + (q % nz);
+      for (int i = threadIdx.x; i < nx; i += blockDim.x) L[i] = q < nq ? S[(size_t)i * nz] : mk<V>(0.0, 0.0);
     }
   __syncthreads();
   if (g.x_walls) {
@@ -300,33 +307,40 @@ __global__ void __launch_bounds__(kFftThreads, MinCtas<T>::v) k_row_sym(GridDev 
   const T hh = (T)(g.h * g.h * 0.25);
   const T ckx = (T)(2.0 * 3.14159265358979323846 / (mx * g.dx));
   const T cky = (T)(2.0 * 3.14159265358979323846 / (g.my * g.dy));
+  const T ckz = (T)(2.0 * 3.14159265358979323846 / (nz * g.dz));
   const T tscale = (T)scale;
   for (int o = 0; o < nout; ++o) {
-    for (int r = 0; r < Rr; ++r)
-    for (int kxi = threadIdx.x; kxi < mx; kxi += blockDim.x) {
-      const int ky = ky0 + r;
-      const int kappa = (2 * kxi <= mx) ? kxi : kxi - mx;
-      const T kx = ckx * (T)kappa, kyw = cky * (T)ky;
-      const bool nyq_x = (mx % 2 == 0) && (2 * kxi == mx);
+    for (int r = 0; r < Rr; ++r) {
+      const int q = q0 + r < nq ? q0 + r : 0;
+      const int ky = q / nz, kq = q - (q / nz) * nz;
+      const int kzeta = (2 * kq <= nz) ? kq : kq - nz;
+      const T kyw = cky * (T)ky, kz = ckz * (T)kzeta;
       const bool nyq_y = (g.my % 2 == 0) && (2 * ky == g.my);
-      // e^{-s} = e^{-kx^2 h^2/4} e^{-ky^2 h^2/4} from the per-axis tables
-      const T What = pool[g.ex_off + kxi].x * pool[g.ey_off + (ky < g.hy ? ky : 0)].x *
-                     kernel_poly<T>(g.family, (kx * kx + kyw * kyw) * hh);
-      V acc = mk<V>(0.0, 0.0);
-      for (int t = 0; t < ops.nterm[o]; ++t) {
-        const V s = symbol<T>(ops.op[o][t], kx, kyw, nyq_x, nyq_y, What);
-        acc = cadd(acc, cmul(s, X[((size_t)ops.field[o][t] * Rr + r) * ls + kxi]));
+      const bool nyq_z = (nz % 2 == 0) && (2 * kq == nz);
+      // e^{-s} = e^{-kx^2 h^2/4} e^{-ky^2 h^2/4} e^{-kz^2 h^2/4} from the per-axis tables
+      const T Wyz = pool[g.ey_off + ky].x * pool[g.ez_off + kq].x;
+      const T kyz2 = kyw * kyw + kz * kz;
+      for (int kxi = threadIdx.x; kxi < mx; kxi += blockDim.x) {
+        const int kappa = (2 * kxi <= mx) ? kxi : kxi - mx;
+        const T kx = ckx * (T)kappa;
+        const bool nyq_x = (mx % 2 == 0) && (2 * kxi == mx);
+        const T What = pool[g.ex_off + kxi].x * Wyz * kernel_poly<T>(g.family, (kx * kx + kyz2) * hh);
+        V acc = mk<V>(0.0, 0.0);
+        for (int t = 0; t < ops.nterm[o]; ++t) {
+          const V s = symbol<T>(ops.op[o][t], kx, kyw, kz, nyq_x, nyq_y, nyq_z, What);
+          acc = cadd(acc, cmul(s, X[((size_t)ops.field[o][t] * Rr + r) * ls + kxi]));
+        }
+        Cq[(size_t)r * ls + kxi] = cscale(acc, tscale);
       }
-      Cq[(size_t)r * ls + kxi] = cscale(acc, tscale);
     }
     __syncthreads();
     V* Y = fft_any<T, true>(Cq, D, Rr, ls, P, pool);
     for (int r = 0; r < Rr; ++r) {
-      const int ky = ky0 + r;
-      if (ky >= g.hy) break;
-      V* S = sp_out + b * bstride_out + o * fstride_out + (size_t)ky * nx;
+      const int q = q0 + r;
+      if (q >= nq) break;
+      V* S = sp_out + b * bstride_out + o * fstride_out + (size_t)(q / nz) * g.ncol + (q % nz);
       const V* Yl = Y + (size_t)r * ls;
-      for (int i = threadIdx.x; i < nx; i += blockDim.x) S[i] = Yl[i];
+      for (int i = threadIdx.x; i < nx; i += blockDim.x) S[(size_t)i * nz] = Yl[i];
     }
     __syncthreads();
   }
@@ -407,12 +421,45 @@ __global__ void __launch_bounds__(kFftThreads, MinCtas<T>::v) k_line_op(GridDev 
 }
 
 // ---------------------------------------------------------------------------
+// z pass of the 3D channel: in the spectra [b][field][row][x][z] every run of
+// nz values (fixed b, field, row, x) is one periodic z line; L lines per CTA
+// are transformed in place, forward or (inv) unnormalised inverse.
+template <typename T>
+__global__ void __launch_bounds__(kFftThreads, MinCtas<T>::v) k_zlines(typename CT<T>::t* __restrict__ spec,
+                                                                      int lines_per_field, size_t fstride,
+                                                                      size_t bstride, const __grid_constant__ FftPlan P,
+                                                                      const typename CT<T>::t* __restrict__ pool, int L,
+                                                                      int ls, int inv) {
+  typedef typename CT<T>::t V;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* A = reinterpret_cast<V*>(smem_raw);
+  V* B = A + (size_t)L * ls;
+  const int n = P.base.n;
+  V* base = spec + blockIdx.z * bstride + blockIdx.y * fstride;
+  const int l0 = blockIdx.x * L;
+  for (int r = 0; r < L; ++r) {
+    const bool in = l0 + r < lines_per_field;
+    const V* S = base + (size_t)(l0 + r) * n;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) A[(size_t)r * ls + j] = in ? S[j] : mk<V>(0.0, 0.0);
+  }
+  __syncthreads();
+  V* Y = fft_any_rt<T>(A, B, L, ls, P, pool, inv != 0);
+  for (int r = 0; r < L; ++r) {
+    if (l0 + r >= lines_per_field) break;
+    V* S = base + (size_t)(l0 + r) * n;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) S[j] = Y[(size_t)r * ls + j];
+  }
+}
+
+// ---------------------------------------------------------------------------
 // PPE row pass (Eqs. 31-33): rows l < ny hold DCT-I-in-y coefficients.  x
 // periodic: FFT (length nx); walled x: DCT-I via FFT of the even extension
 // (length 2(nx-1)).  Multiply by -1/(lam_k^2 + lam_l^2) (apply = 0, (0,0) -> 0),
 // by -(lam_k^2 + lam_l^2) (apply = 1), or by 1 except 0 on the (0,0) mode
 // (apply = 2, removes the constant mode), times the inverse-transform scales,
-// transform back, store.
+// transform back, store.  3D: line q is the l = q / nz row at z index
+// kq = q % nz of the DFT-z-transformed coefficients, elements at stride nz,
+// and lam_z^2 joins the denominator.
 template <typename T>
 __global__ void __launch_bounds__(kFftThreads, MinCtas<T>::v) k_row_ppe(GridDev g, typename CT<T>::t* __restrict__ spec,
                                                       size_t bstride, const __grid_constant__ FftPlan P,
@@ -423,15 +470,16 @@ __global__ void __launch_bounds__(kFftThreads, MinCtas<T>::v) k_row_ppe(GridDev 
   V* A = reinterpret_cast<V*>(smem_raw);
   V* B = A + (size_t)Rr * ls;
   const int b = blockIdx.y;
-  const int l0 = blockIdx.x * Rr;
-  const int nx = g.nx, ny = g.ny;
+  const int q0 = blockIdx.x * Rr;
+  const int nx = g.nx, ny = g.ny, nz = g.nz;
+  const int nq = ny * nz;
   const int n = P.base.n;  // nx or 2(nx-1)
   for (int r = 0; r < Rr; ++r) {
-    const int l = l0 + r;
+    const int q = q0 + r;
     V* L = A + (size_t)r * ls;
-    const V* S = spec + b * bstride + (size_t)l * nx;
+    const V* S = spec + b * bstride + (size_t)(q / nz) * g.ncol + (q % nz);
     for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-      const V v = l < ny ? S[i] : mk<V>(0.0, 0.0);
+      const V v = q < nq ? S[(size_t)i * nz] : mk<V>(0.0, 0.0);
       L[i] = v;
       if (g.x_walls && i >= 1 && i <= nx - 2) L[n - i] = v;
     }
@@ -439,20 +487,23 @@ __global__ void __launch_bounds__(kFftThreads, MinCtas<T>::v) k_row_ppe(GridDev 
   __syncthreads();
   V* X = fft_any<T, false>(A, B, Rr, ls, P, pool);
   V* O = (X == A) ? B : A;
-  const T norm = (T)(1.0 / ((double)n * 2.0 * (ny - 1)));
+  const T norm = (T)(1.0 / ((double)n * 2.0 * (ny - 1) * nz));
   const int nk = g.x_walls ? nx : n;
-  for (int r = 0; r < Rr; ++r)
+  for (int r = 0; r < Rr; ++r) {
+    const int q = q0 + r < nq ? q0 + r : 0;
+    const int l = q / nz, kq = q - (q / nz) * nz;
+    // lam_l^2 (+ lam_z^2) from the per-axis tables (Eq. 33 eigenvalues)
+    const T dyz = pool[g.ly2_off + l].x + pool[g.lz2_off + kq].x;
+    const bool zero_yz = l == 0 && kq == 0;
   for (int k = threadIdx.x; k < nk; k += blockDim.x) {
-    const int l = l0 + r;
-    // lam_k^2 and lam_l^2 from the per-axis tables (Eq. 33 eigenvalues)
-    const T den = pool[g.lx2_off + k].x + pool[g.ly2_off + (l < ny ? l : 0)].x;
+    const T den = pool[g.lx2_off + k].x + dyz;
     T f;
     if (apply == 1)
       f = -(den * norm);
     else if (apply == 2)
-      f = (k == 0 && l == 0) ? (T)0.0 : norm;
+      f = (k == 0 && zero_yz) ? (T)0.0 : norm;
     else
-      f = (k == 0 && l == 0) ? (T)0.0 : -(norm / den);
+      f = (k == 0 && zero_yz) ? (T)0.0 : -(norm / den);
     const V x = X[(size_t)r * ls + k];
     const V y = cscale(x, f);
     if (g.x_walls) {
@@ -462,6 +513,7 @@ __global__ void __launch_bounds__(kFftThreads, MinCtas<T>::v) k_row_ppe(GridDev 
       X[(size_t)r * ls + k] = y;
     }
   }
+  }
   __syncthreads();
   V* Y;
   if (g.x_walls)
@@ -469,11 +521,11 @@ __global__ void __launch_bounds__(kFftThreads, MinCtas<T>::v) k_row_ppe(GridDev 
   else
     Y = fft_any<T, true>(X, O, Rr, ls, P, pool);
   for (int r = 0; r < Rr; ++r) {
-    const int l = l0 + r;
-    if (l >= ny) break;
-    V* S = spec + b * bstride + (size_t)l * nx;
+    const int q = q0 + r;
+    if (q >= nq) break;
+    V* S = spec + b * bstride + (size_t)(q / nz) * g.ncol + (q % nz);
     const V* Yl = Y + (size_t)r * ls;
-    for (int i = threadIdx.x; i < nx; i += blockDim.x) S[i] = Yl[i];
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) S[(size_t)i * nz] = Yl[i];
   }
 }
 
@@ -485,15 +537,12 @@ struct EpiArgs {
   // EPI_OUT
   void* outs[6];
   int out_double;
-  // step state (double)
-  const double* u;
-  const double* v;
-  double* fu;
-  double* fv;
-  double* us;
-  double* vs;
-  double* uo;
-  double* vo;
+  // step state (double), per velocity component (2D: u, v; 3D: u, v, w)
+  const double* vel[3];   // MOM: velocity at the start of the substep
+  double* Fp[3];          // MOM: F^{k-1} in, F^k out
+  double* vs[3];          // MOM: u* out; CORR: u* in
+  double* vo[3];          // CORR: corrected velocity out
+  int mom_terms;          // MOM: outputs per component (d/dx, d/dy, [d/dz], lap)
   double* bvec;       // DIV: out b; PPE_RESID: in b
   double* phi;        // PPE_*: out phi / residual / accumulate
   void* phi_any;      // PPE_SOLVE in the context's I/O type when not double
@@ -554,7 +603,7 @@ __global__ void __launch_bounds__(kFftThreads, MinCtas<T>::v) k_col_inv(GridDev 
 #pragma unroll
       for (int w = 0; w < 2; ++w) {
         const int i = i0 + 2 * p + w;
-        if (i >= g.nx) continue;
+        if (i >= g.ncol) continue;
         const size_t id = fidx(g, b, i, j);
         const double val = (double)(w ? z.y : z.x);
         double nv = 0.0;
@@ -565,60 +614,43 @@ __global__ void __launch_bounds__(kFftThreads, MinCtas<T>::v) k_col_inv(GridDev 
           else
             reinterpret_cast<float*>(ea.outs[o])[id] = (float)val;
         } else if (EPI == EPI_MOM) {
-          // outputs 0-2: u_x, u_y, lap u of u; 3-5 the same of v
-          const int comp = o / 3, term = o - comp * 3;
+          // output comp * nt + term: d/dx, d/dy, (d/dz,) lap of component comp;
+          // F_comp = u . grad(comp) - nu lap(comp) accumulates in acc[comp]
+          const int nt = ea.mom_terms;
+          const int comp = o / nt, term = o - comp * nt;
           double* a = w ? &A[(size_t)comp * Pp * ny].y : &A[(size_t)comp * Pp * ny].x;
           if (term == 0) {
-            *a = ea.u[id] * val;
-          } else if (term == 1) {
-            *a += ea.v[id] * val;
+            *a = ea.vel[0][id] * val;
+          } else if (term < nt - 1) {
+            *a += ea.vel[term][id] * val;
           } else {
             const double nu = ea.s.nu_inst ? ea.s.nu_inst[b] : ea.s.nu;
             const double F = *a - nu * val;
-            if (comp == 0) {
-              const double u = ea.u[id];
-              const double fx = ea.s.fx_inst ? ea.s.fx_inst[b] : ea.s.fx;
-              double us = u + ea.s.dt * (-ea.s.g * F - ea.s.z * ea.fu[id] + ea.s.a * fx);
-              if (j == 0) us = ea.s.u_bottom;
-              if (j == ny - 1) us = ea.s.u_top;
-              if (g.x_walls && (i == 0 || i == g.nx - 1)) us = 0.0;
-              ea.fu[id] = F;
-              ea.us[id] = us;
-              if (!isfinite(us)) atomicOr(ea.status, 1);
-              *a = us;
-            } else {
-              const double v = ea.v[id];
-              double vs = v + ea.s.dt * (-ea.s.g * F - ea.s.z * ea.fv[id] + ea.s.a * ea.s.fy);
-              if (j == 0 || j == ny - 1) vs = 0.0;
-              if (g.x_walls && (i == 0 || i == g.nx - 1)) vs = 0.0;
-              ea.fv[id] = F;
-              ea.vs[id] = vs;
-              if (!isfinite(vs)) atomicOr(ea.status, 1);
-              *a = vs;
-            }
+            const double f = comp == 0 ? (ea.s.fx_inst ? ea.s.fx_inst[b] : ea.s.fx) : (comp == 1 ? ea.s.fy : ea.s.fz);
+            double cs = ea.vel[comp][id] + ea.s.dt * (-ea.s.g * F - ea.s.z * ea.Fp[comp][id] + ea.s.a * f);
+            // y walls: the tangential x velocity takes the wall speeds, the others 0
+            if (j == 0) cs = comp == 0 ? ea.s.u_bottom : 0.0;
+            if (j == ny - 1) cs = comp == 0 ? ea.s.u_top : 0.0;
+            if (g.x_walls && (i == 0 || i == g.nx - 1)) cs = 0.0;
+            ea.Fp[comp][id] = F;
+            ea.vs[comp][id] = cs;
+            if (!isfinite(cs)) atomicOr(ea.status, 1);
+            *a = cs;
           }
         } else if (EPI == EPI_DIV) {
           nv = ea.s.rho / (ea.s.a * ea.s.dt) * val;
           ea.bvec[id] = nv;
           slot = 0;
         } else if (EPI == EPI_CORR) {
+          // output o: d phi / d(axis o) -> component o
           const double c = ea.s.a * ea.s.dt / ea.s.rho;
-          if (o == 0) {
-            double u = ea.us[id] - c * val;
-            if (j == 0) u = ea.s.u_bottom;
-            if (j == ny - 1) u = ea.s.u_top;
-            if (g.x_walls && (i == 0 || i == g.nx - 1)) u = 0.0;
-            ea.uo[id] = u;
-            if (!isfinite(u)) atomicOr(ea.status, 1);
-            nv = u;
-          } else {
-            double v = ea.vs[id] - c * val;
-            if (j == 0 || j == ny - 1) v = 0.0;
-            if (g.x_walls && (i == 0 || i == g.nx - 1)) v = 0.0;
-            ea.vo[id] = v;
-            if (!isfinite(v)) atomicOr(ea.status, 1);
-            nv = v;
-          }
+          double cn = ea.vs[o][id] - c * val;
+          if (j == 0) cn = o == 0 ? ea.s.u_bottom : 0.0;
+          if (j == ny - 1) cn = o == 0 ? ea.s.u_top : 0.0;
+          if (g.x_walls && (i == 0 || i == g.nx - 1)) cn = 0.0;
+          ea.vo[o][id] = cn;
+          if (!isfinite(cn)) atomicOr(ea.status, 1);
+          nv = cn;
           slot = o;
         } else if (EPI == EPI_PPE_SOLVE) {
           if (ea.phi_double)
@@ -653,7 +685,7 @@ __global__ void __launch_bounds__(kFftThreads, MinCtas<T>::v) k_col_inv(GridDev 
       const double2* a = acc + ((size_t)f * Pp + p) * ny;
       V* L = Z + (size_t)p * ls;
       for (int j = threadIdx.x; j < ny; j += blockDim.x)
-        L[j] = mk<V>(i < g.nx ? a[j].x : 0.0, i + 1 < g.nx ? a[j].y : 0.0);
+        L[j] = mk<V>(i < g.ncol ? a[j].x : 0.0, i + 1 < g.ncol ? a[j].y : 0.0);
     }
     __syncthreads();
     col_forward_store<T>(Z, S, Pp, ls, g, i0, reinterpret_cast<const typename FcTab<T>::t*>(ea.fwdE), ea.fwdP, pool,
@@ -667,13 +699,13 @@ __global__ void __launch_bounds__(kFftThreads, MinCtas<T>::v) k_col_inv(GridDev 
 // then x continuation of every extended row (walled x).
 template <typename U>
 __global__ void k_fc_extend_y(GridDev g, const U* __restrict__ f, U* __restrict__ fe, const double* __restrict__ E) {
-  const size_t total = (size_t)g.batch * g.nx * g.my;
+  const size_t total = (size_t)g.batch * g.ncol * g.my;
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
     const int j = (int)(t % g.my);
     const size_t bi = t / g.my;
-    const int i = (int)(bi % g.nx);
-    const int b = (int)(bi / g.nx);
-    const U* col = f + ((size_t)b * g.nx + i) * g.ny;
+    const int i = (int)(bi % g.ncol);
+    const int b = (int)(bi / g.ncol);
+    const U* col = f + ((size_t)b * g.ncol + i) * g.ny;
     double v;
     if (j < g.ny) {
       v = (double)col[j];
@@ -686,7 +718,7 @@ __global__ void k_fc_extend_y(GridDev g, const U* __restrict__ f, U* __restrict_
       }
       v = acc.value();
     }
-    fe[((size_t)b * g.mx + i) * g.my + j] = (U)v;
+    fe[((size_t)b * (g.x_walls ? g.mx : g.ncol) + i) * g.my + j] = (U)v;
   }
 }
 
@@ -827,6 +859,12 @@ const void* fc_table(const fcsph_ctx* c, int prec, int bc) {
   return c->dE + off;
 }
 
+// Fields per instance of the spectrum buffers: spec_in holds the forward
+// transforms of the velocity components (2D: 2, 3D: 3), spec_out the row
+// pass outputs (2D: 6, 3D: 12).
+size_t spec_in_fields(const fcsph_ctx* c) { return c->gd.nz > 1 ? 3 : 2; }
+size_t spec_out_fields(const fcsph_ctx* c) { return c->gd.nz > 1 ? 12 : 6; }
+
 int col_ls(const fcsph_ctx* c) {
   int ls = c->plan_y.line_len();
   if (c->plan_py.line_len() > ls) ls = c->plan_py.line_len();
@@ -861,6 +899,9 @@ cudaError_t init_kernel_attributes() {
   FCSPH_RAISE((k_dft_lines<ff, true, double2>))
   FCSPH_RAISE((k_col_inv<double>))
   FCSPH_RAISE((k_line_op<double, double>))
+  FCSPH_RAISE((k_zlines<double>))
+  FCSPH_RAISE((k_zlines<ff>))
+  FCSPH_RAISE((k_zlines<float>))
   FCSPH_RAISE((k_line_op<ff, double>))
   FCSPH_RAISE((k_line_op<float, float>))
   FCSPH_RAISE((k_col_inv<float>))
@@ -872,9 +913,9 @@ cudaError_t init_kernel_attributes() {
 // row_lines rows per row-pass CTA and col_pairs column pairs per column CTA.
 size_t tiling_smem(const fcsph_ctx* c, int row_lines, int col_pairs) {
   const size_t cb = c->prec.fft_prec == FCSPH_F32 ? sizeof(float2) : sizeof(double2);
-  const size_t row = 4 * (size_t)row_lines * c->plan_x.line_len() * cb;
+  const size_t row = (c->gd.nz > 1 ? 6 : 4) * (size_t)row_lines * c->plan_x.line_len() * cb;
   const size_t ppe = 2 * (size_t)row_lines * c->plan_px.line_len() * cb;
-  const size_t col = (size_t)col_pairs * (2 * (size_t)col_ls(c) * cb + 2 * (size_t)c->gd.ny * sizeof(double2));
+  const size_t col = (size_t)col_pairs * (2 * (size_t)col_ls(c) * cb + (c->gd.nz > 1 ? 3 : 2) * (size_t)c->gd.ny * sizeof(double2));
   size_t m = row > ppe ? row : ppe;
   return m > col ? m : col;
 }
@@ -914,12 +955,13 @@ static cudaError_t col_fwd_t(fcsph_ctx* c, int prec, int nf, const void* const* 
   cudaError_t e = set_smem(k_col_fwd<T, U>, smem);
   if (e != cudaSuccess) return e;
   const auto* E = static_cast<const typename FcTab<T>::t*>(fc_table(c, prec, bc));
-  dim3 grid((g.nx + 2 * Pp - 1) / (2 * Pp), nf, g.batch);
-  const size_t fstride = (size_t)g.rows * g.nx;
-  const size_t bstride = (dct ? 1 : 2) * fstride;
+  dim3 grid((g.ncol + 2 * Pp - 1) / (2 * Pp), nf, g.batch);
+  const size_t fstride = (size_t)g.rows * g.ncol;
+  const size_t bstride = (dct ? 1 : spec_in_fields(c)) * fstride;
   ProfScope ps(c, FCSPH_PROF_COL_FWD);
   k_col_fwd<T, U><<<grid, kFftThreads, smem, c->stream>>>(g, (const U*)fields[0],
-                                                          (const U*)(nf > 1 ? fields[1] : fields[0]), E, P,
+                                                          (const U*)(nf > 1 ? fields[1] : fields[0]),
+                                                          (const U*)(nf > 2 ? fields[2] : fields[0]), E, P,
                                                           PoolOf<T>::get(c), dct, (typename CT<T>::t*)spec, fstride,
                                                           bstride, Pp, ls);
   c->launches++;
@@ -951,11 +993,12 @@ static cudaError_t row_sym_t(fcsph_ctx* c, int prec, const void* sp_in, void* sp
   cudaError_t e = set_smem(k_row_sym<T>, smem);
   if (e != cudaSuccess) return e;
   const auto* E = static_cast<const typename FcTab<T>::t*>(fc_table(c, prec, bc));
-  const size_t fs = (size_t)g.rows * g.nx;
-  dim3 grid((g.hy + Rr - 1) / Rr, g.batch);
+  const size_t fs = (size_t)g.rows * g.ncol;
+  dim3 grid((g.hy * g.nz + Rr - 1) / Rr, g.batch);
   ProfScope ps(c, kind);
   k_row_sym<T><<<grid, kFftThreads, smem, c->stream>>>(g, (const typename CT<T>::t*)sp_in, (typename CT<T>::t*)sp_out,
-                                                       fs, 2 * fs, fs, 6 * fs, ops, E, c->plan_x, PoolOf<T>::get(c),
+                                                       fs, spec_in_fields(c) * fs, fs, spec_out_fields(c) * fs, ops, E,
+                                                       c->plan_x, PoolOf<T>::get(c),
                                                        scale, Rr, ls);
   c->launches++;
   return cudaGetLastError();
@@ -986,7 +1029,7 @@ static cudaError_t line_op_t(fcsph_ctx* c, int prec, const void* f, const int* o
     lo.op[o] = ops[o];
     lo.out[o] = outs[o];
   }
-  const long long ncols = (long long)g.batch * g.nx;
+  const long long ncols = (long long)g.batch * g.ncol;
   const long long blocks = (ncols + 2 * Pp - 1) / (2 * Pp);
   const auto* E = static_cast<const typename FcTab<T>::t*>(fc_table(c, prec, bc));
   ProfScope ps(c, FCSPH_PROF_COL_OUT);
@@ -1004,6 +1047,35 @@ cudaError_t launch_line_op(fcsph_ctx* c, const void* f, const int* ops, int nout
 }
 
 template <typename T>
+static cudaError_t zpass_t(fcsph_ctx* c, void* spec, int nf, size_t bstride, int rows_used, int inv) {
+  const GridDev& g = c->gd;
+  const FftPlan& P = c->plan_z;
+  const int ls = P.line_len();
+  int L = 256 / g.nz;
+  if (L < 1) L = 1;
+  if (L > 8) L = 8;
+  const size_t smem = 2 * (size_t)L * ls * sizeof(typename CT<T>::t);
+  cudaError_t e = set_smem(k_zlines<T>, smem);
+  if (e != cudaSuccess) return e;
+  const int lines = rows_used * g.nx;
+  dim3 grid((lines + L - 1) / L, nf, g.batch);
+  ProfScope ps(c, FCSPH_PROF_OTHER);
+  k_zlines<T><<<grid, kFftThreads, smem, c->stream>>>((typename CT<T>::t*)spec, lines, (size_t)g.rows * g.ncol, bstride,
+                                                      P, PoolOf<T>::get(c), L, ls, inv);
+  c->launches++;
+  return cudaGetLastError();
+}
+
+// 3D: z transforms of nf fields of every instance (fields 0..nf-1 of the
+// buffer, instance stride bstride, rows_used spectrum rows each); no-op in 2D.
+cudaError_t launch_zpass(fcsph_ctx* c, int prec, void* spec, int nf, size_t bstride, int rows_used, int inv) {
+  if (c->gd.nz <= 1 || nf <= 0) return cudaSuccess;
+  if (prec == FCSPH_F64) return zpass_t<double>(c, spec, nf, bstride, rows_used, inv);
+  if (prec == FCSPH_F32X2) return zpass_t<ff>(c, spec, nf, bstride, rows_used, inv);
+  return zpass_t<float>(c, spec, nf, bstride, rows_used, inv);
+}
+
+template <typename T>
 static cudaError_t col_inv_common(fcsph_ctx* c, int epi, const void* spec, int nout, EpiArgs& ea) {
   const GridDev& g = c->gd;
   const FftPlan& P = epi >= EPI_PPE_SOLVE ? c->plan_py : c->plan_y;
@@ -1013,14 +1085,14 @@ static cudaError_t col_inv_common(fcsph_ctx* c, int epi, const void* spec, int n
   const int Pp = c->col_pairs;
   // FP64 per-point values kept across outputs: the two momentum components,
   // else the fields of the fused forward
-  const int nacc = epi == EPI_MOM ? 2 : ea.fwd_nf;
+  const int nacc = ea.fwd_nf;
   const size_t smem = ((size_t)2 * ls * sizeof(typename CT<T>::t) + (size_t)nacc * g.ny * sizeof(double2)) * Pp;
-  const size_t fs = (size_t)g.rows * g.nx;
-  const size_t bs = (epi >= EPI_PPE_SOLVE ? 1 : 6) * fs;  // spec_ppe or spec_out
-  dim3 grid((g.nx + 2 * Pp - 1) / (2 * Pp), g.batch);
+  const size_t fs = (size_t)g.rows * g.ncol;
+  const size_t bs = (epi >= EPI_PPE_SOLVE ? 1 : spec_out_fields(c)) * fs;  // spec_ppe or spec_out
+  dim3 grid((g.ncol + 2 * Pp - 1) / (2 * Pp), g.batch);
   const typename CT<T>::t* pool = PoolOf<T>::get(c);
   if (epi < EPI_OUT || epi > EPI_PPE_ADD) return cudaErrorInvalidValue;
-  if (ea.fwd_nf > 2 || (epi == EPI_MOM && nout != 6)) return cudaErrorInvalidValue;
+  if (ea.fwd_nf > 3 || (epi == EPI_MOM && nout != ea.fwd_nf * ea.mom_terms)) return cudaErrorInvalidValue;
   ea.status = c->dstatus;
   static const int kinds[7] = {FCSPH_PROF_COL_OUT, FCSPH_PROF_COL_MOM, FCSPH_PROF_COL_DIV, FCSPH_PROF_COL_CORR,
                                FCSPH_PROF_COL_PPE, FCSPH_PROF_COL_PPE, FCSPH_PROF_COL_PPE};
@@ -1060,9 +1132,9 @@ static cudaError_t row_ppe_t(fcsph_ctx* c, void* spec, int apply) {
   const size_t smem = 2 * (size_t)ls * sizeof(typename CT<T>::t) * Rr;
   cudaError_t e = set_smem(k_row_ppe<T>, smem);
   if (e != cudaSuccess) return e;
-  dim3 grid((g.ny + Rr - 1) / Rr, g.batch);
+  dim3 grid((g.ny * g.nz + Rr - 1) / Rr, g.batch);
   ProfScope ps(c, FCSPH_PROF_ROW_PPE);
-  k_row_ppe<T><<<grid, kFftThreads, smem, c->stream>>>(g, (typename CT<T>::t*)spec, (size_t)g.rows * g.nx, c->plan_px,
+  k_row_ppe<T><<<grid, kFftThreads, smem, c->stream>>>(g, (typename CT<T>::t*)spec, (size_t)g.rows * g.ncol, c->plan_px,
                                                        PoolOf<T>::get(c), apply, Rr, ls);
   c->launches++;
   return cudaGetLastError();
@@ -1098,30 +1170,31 @@ cudaError_t launch_col_ppe_inv(fcsph_ctx* c, int prec, const void* spec, void* p
     ea.fwdE = fc_table(c, prec, FCSPH_NEUMANN);
     ea.fwdP = c->plan_y;
     ea.fwd_spec = spec_fwd;
-    ea.fwd_fstride = (size_t)c->gd.rows * c->gd.nx;
-    ea.fwd_bstride = 2 * ea.fwd_fstride;
+    ea.fwd_fstride = (size_t)c->gd.rows * c->gd.ncol;
+    ea.fwd_bstride = spec_in_fields(c) * ea.fwd_fstride;
   }
   return col_inv(c, prec, epi, spec, 1, ea);
 }
 
-cudaError_t launch_step_mom(fcsph_ctx* c, const StepDev& s, const void* spec6, const double* u, const double* v,
-                            double* fu, double* fv, double* us, double* vs, void* spec2) {
+cudaError_t launch_step_mom(fcsph_ctx* c, const StepDev& s, const void* spec_mom, const double* const* vel,
+                            double* const* Fp, double* const* vs, void* spec_next) {
+  const int nc = c->gd.nz > 1 ? 3 : 2;
   EpiArgs ea = epi_defaults();
-  ea.u = u;
-  ea.v = v;
-  ea.fu = fu;
-  ea.fv = fv;
-  ea.us = us;
-  ea.vs = vs;
+  for (int q = 0; q < nc; ++q) {
+    ea.vel[q] = vel[q];
+    ea.Fp[q] = Fp[q];
+    ea.vs[q] = vs[q];
+  }
+  ea.mom_terms = nc + 1;
   ea.s = s;
-  ea.fwd_nf = 2;
+  ea.fwd_nf = nc;
   ea.fwd_dct = 0;
   ea.fwdE = fc_table(c, c->prec.fft_prec, FCSPH_DIRICHLET);
   ea.fwdP = c->plan_y;
-  ea.fwd_spec = spec2;
-  ea.fwd_fstride = (size_t)c->gd.rows * c->gd.nx;
-  ea.fwd_bstride = 2 * ea.fwd_fstride;
-  return col_inv(c, c->prec.fft_prec, EPI_MOM, spec6, 6, ea);
+  ea.fwd_spec = spec_next;
+  ea.fwd_fstride = (size_t)c->gd.rows * c->gd.ncol;
+  ea.fwd_bstride = nc * ea.fwd_fstride;
+  return col_inv(c, c->prec.fft_prec, EPI_MOM, spec_mom, nc * (nc + 1), ea);
 }
 
 cudaError_t launch_step_div(fcsph_ctx* c, const StepDev& s, const void* spec1, double* b, void* spec_dct) {
@@ -1133,29 +1206,30 @@ cudaError_t launch_step_div(fcsph_ctx* c, const StepDev& s, const void* spec1, d
   ea.fwdE = fc_table(c, c->prec.fft_prec, FCSPH_DIRICHLET);
   ea.fwdP = c->plan_py;
   ea.fwd_spec = spec_dct;
-  ea.fwd_fstride = (size_t)c->gd.rows * c->gd.nx;
+  ea.fwd_fstride = (size_t)c->gd.rows * c->gd.ncol;
   ea.fwd_bstride = ea.fwd_fstride;
   return col_inv(c, c->prec.fft_prec, EPI_DIV, spec1, 1, ea);
 }
 
-cudaError_t launch_step_corr(fcsph_ctx* c, const StepDev& s, const void* spec2, const double* us, const double* vs,
-                             double* u, double* v, void* spec_next) {
+cudaError_t launch_step_corr(fcsph_ctx* c, const StepDev& s, const void* spec_grad, double* const* vs,
+                             double* const* vo, void* spec_next) {
+  const int nc = c->gd.nz > 1 ? 3 : 2;
   EpiArgs ea = epi_defaults();
-  ea.us = (double*)us;
-  ea.vs = (double*)vs;
-  ea.uo = u;
-  ea.vo = v;
+  for (int q = 0; q < nc; ++q) {
+    ea.vs[q] = vs[q];
+    ea.vo[q] = vo[q];
+  }
   ea.s = s;
   if (spec_next) {
-    ea.fwd_nf = 2;
+    ea.fwd_nf = nc;
     ea.fwd_dct = 0;
     ea.fwdE = fc_table(c, c->prec.fft_prec, FCSPH_DIRICHLET);
     ea.fwdP = c->plan_y;
     ea.fwd_spec = spec_next;
-    ea.fwd_fstride = (size_t)c->gd.rows * c->gd.nx;
-    ea.fwd_bstride = 2 * ea.fwd_fstride;
+    ea.fwd_fstride = (size_t)c->gd.rows * c->gd.ncol;
+    ea.fwd_bstride = nc * ea.fwd_fstride;
   }
-  return col_inv(c, c->prec.fft_prec, EPI_CORR, spec2, 2, ea);
+  return col_inv(c, c->prec.fft_prec, EPI_CORR, spec_grad, nc, ea);
 }
 
 template <typename T, typename IO>
@@ -1190,7 +1264,7 @@ cudaError_t launch_dft_lines(int n, int nlines, int dir, int prec, const void* i
 cudaError_t launch_resid_norm(fcsph_ctx* c, const double* r, const double* b, double* out2) {
   cudaMemsetAsync(out2, 0, 2 * sizeof(double), c->stream);
   ProfScope ps(c, FCSPH_PROF_OTHER);
-  k_resid_inst<<<c->gd.batch, kThreads, 0, c->stream>>>(r, b, (size_t)c->gd.nx * c->gd.ny, out2);
+  k_resid_inst<<<c->gd.batch, kThreads, 0, c->stream>>>(r, b, (size_t)c->gd.ncol * c->gd.ny, out2);
   c->launches++;
   return cudaGetLastError();
 }
