@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--tiling", default=None,
                     help="rows,pairs per CTA for the headline context instead of the autotuner (profiling runs)")
     ap.add_argument("--no-compare", action="store_true")
-    ap.add_argument("--workload", default="cavity", choices=["cavity", "uneven", "serve", "planes", "lines", "dipole"],
+    ap.add_argument("--workload", default="cavity", choices=["cavity", "uneven", "serve", "planes", "lines", "dipole", "channel3d"],
                     help="cavity: the 256^2 lid cavity (default); uneven: 64 solves of sizes 64^2..512^2 "
                          "submitted together; serve: a Poisson request stream (2D part)")
     ap.add_argument("--serve-seconds", type=float, default=1.0)
@@ -537,8 +537,8 @@ def run_serving(args):
                                        steps=(50, 500))
         reqs = lambda: [Request(i, d["kind"], d["n"], float(np.exp(np.random.default_rng(i).uniform(np.log(100), np.log(5000)))),
                                 max(1, d["steps"] * steps // 500), d["t"]) for i, d in enumerate(spec)]
-        desc = (f"Poisson arrivals 200/s for {args.serve_seconds} s, 2D cavity/channel of 64^2..1024^2, "
-                f"each 50-500 RK3 steps scaled by {steps}/500 (3D channel requests not built)")
+        desc = (f"Poisson arrivals 200/s for {args.serve_seconds} s, 80% 2D cavity/channel of 64^2..1024^2, "
+                f"20% 3D channel of 64^3..128^3, each 50-500 RK3 steps scaled by {steps}/500")
     torch.cuda.synchronize()
     srv = Server(prec=args.prec, capacity=8)
     rs = reqs()
@@ -732,6 +732,59 @@ def run_dipole(args):
         "history": {"precision": args.prec, "run_seconds": run_s, "steps": int(round(10.0 / dt)), "E_Z": hist}}))
 
 
+def run_channel3d(args):
+    """3D channel (config 5's 3D requests): n^3 particles, x and z periodic
+    (lx = lz = n dy), walls at y = 0, 1, G4 h = 1.3 dx, Re = 100 (u_max = 1:
+    nu = 0.01, body force 0.08 in x), RK3 dt = 1e-3, a batch of B channels at
+    rest.  Reports the throughput per precision and, after 100 steps, each
+    precision's L2 error of u against the analytic start-up series (the flow
+    stays one-dimensional).  (At nu = 0.1 the explicit step is past its
+    viscous stability limit on a 128^3 lattice.)"""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2606_06247_gb300 import binding as b
+    n = int(os.environ.get("FCSPH_BENCH_N3", "128"))
+    B = max(1, min(args.batch, 4))
+    dy = 1.0 / (n - 1)
+    prm = dict(nu=0.01, rho=1.0, dt=1e-3, force=(0.08, 0.0, 0.0), scheme="rk3")
+    ua = torch.tensor(_startup_series(np.linspace(0, 1, n), 0.1, 0.08, 0.01), dtype=torch.float64, device="cuda")
+    out = {}
+    for prec in ("f32x2", "f64"):
+        ctx = b.Context(n, n, n * dy, 1.0, batch=B, family="G4", h_over_dx=1.3, prec=prec, nz=n, lz=n * dy)
+        z = torch.zeros((B, n, n, n), dtype=torch.float64, device="cuda")
+        u, v, w, p, fu, fv, fw = [z.clone() for _ in range(7)]
+        st = dict(w=w, fw=fw)
+        ctx.isph_step(u, v, p, fu, fv, max(3, args.warmup), **st, **prm)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ctx.isph_step(u, v, p, fu, fv, args.steps, **st, **prm)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        for q in (u, v, w, p, fu, fv, fw):
+            q.zero_()
+        ctx.isph_step(u, v, p, fu, fv, 100, **st, **prm)
+        torch.cuda.synchronize()
+        err = float(torch.linalg.vector_norm(u[0] - ua) / torch.linalg.vector_norm(ua.expand_as(u[0])))
+        out[prec] = {"ms_per_step": ms, "particle_updates_per_s": B * n ** 3 / (ms * 1e-3),
+                     "l2_u_vs_analytic_after_100_steps": err, "max_abs_w": float(w.abs().max())}
+        del ctx, z, u, v, w, p, fu, fv, fw
+        torch.cuda.empty_cache()
+    head = out["f32x2"]
+    print(json.dumps({
+        "metric": METRIC, "value": head["particle_updates_per_s"], "unit": "particle-updates/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
+        "dtype": "f32x2", "data": "synthetic",
+        "config": {"workload": f"3D channel {n}^3 (x, z periodic, walls in y), FC(Gram) d=5 C=25 in y, G4 h=1.3dx, "
+                               f"Re=100, RK3 dt=1e-3, batch of {B}", "batch": B, "n": n},
+        "variants": out,
+        "equal_l2": abs(out["f32x2"]["l2_u_vs_analytic_after_100_steps"] - out["f64"]["l2_u_vs_analytic_after_100_steps"])
+                    <= 1e-6 * out["f64"]["l2_u_vs_analytic_after_100_steps"]}))
+
+
 def run_profile_case(args):
     """Two eager RK3 steps of the workload with every kernel launched on its own
     (no graph), for kernel-level captures; prints the launch count."""
@@ -761,6 +814,8 @@ if __name__ == "__main__":
         run_lines(a)
     elif a.workload == "dipole" and a.impl == "ours":
         run_dipole(a)
+    elif a.workload == "channel3d" and a.impl == "ours":
+        run_channel3d(a)
     elif a.impl == "reference":
         run_reference(a)
     else:

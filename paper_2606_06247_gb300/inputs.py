@@ -110,8 +110,11 @@ def uneven_batch(n_instances=64, seed=2024, sizes=(64, 128, 256, 512), re_range=
     return [dict(n=int(n[i]), re=float(re[i]), kind=kind[i]) for i in range(n_instances)]
 
 
-def poisson_requests(rate=200.0, duration=10.0, seed=7, sizes=(64, 128, 256, 512, 1024), steps=(50, 500)):
-    """Arrival times of a Poisson stream and the size/steps of each request (2D part)."""
+def poisson_requests(rate=200.0, duration=10.0, seed=7, sizes=(64, 128, 256, 512, 1024), steps=(50, 500),
+                     frac_3d=0.2, sizes_3d=(64, 96, 128)):
+    """Arrival times of a Poisson stream and the size/steps of each request:
+    a fraction frac_3d are 3D channels of n^3 (n from sizes_3d), the others
+    2D cavities or channels of n^2 (n from sizes)."""
     rng = np.random.default_rng(seed)
     t = 0.0
     out = []
@@ -119,6 +122,10 @@ def poisson_requests(rate=200.0, duration=10.0, seed=7, sizes=(64, 128, 256, 512
         t += rng.exponential(1.0 / rate)
         if t > duration:
             break
-        out.append(dict(t=t, n=int(rng.choice(np.asarray(sizes))), steps=int(rng.integers(steps[0], steps[1] + 1)),
-                        kind="cavity" if rng.uniform() < 0.5 else "channel"))
+        st = int(rng.integers(steps[0], steps[1] + 1))
+        if rng.uniform() < frac_3d:
+            out.append(dict(t=t, n=int(rng.choice(np.asarray(sizes_3d))), steps=st, kind="channel3d"))
+        else:
+            out.append(dict(t=t, n=int(rng.choice(np.asarray(sizes))), steps=st,
+                            kind="cavity" if rng.uniform() < 0.5 else "channel"))
     return out

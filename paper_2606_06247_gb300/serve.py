@@ -1,8 +1,9 @@
 """Continuous batching of independent wall-bounded solves on one GPU.
 
-Requests of different sizes and kinds (lid-driven cavity / channel) arrive
-over time; each asks for a number of RK3 projection steps.  A size class
-(kind, n, kernel family) owns one fcsph context with a fixed number of slots
+Requests of different sizes and kinds (lid-driven cavity / channel / 3D
+channel of n^3) arrive over time; each asks for a number of RK3 projection
+steps.  A size class (kind, n, kernel family) owns one fcsph context with a
+fixed number of slots
 (its batch) and device-resident state for every slot; the class advances all
 its slots with one CUDA-graph step at a time on its own stream, so classes
 overlap on the GPU.  Classes run independently: the host polls each class's
@@ -17,8 +18,8 @@ depend on which slot it occupies or on what the other slots hold, so a
 request's result is the same alone and in the mix (bitwise, same precision).
 
 The per-request Reynolds number enters through per-instance viscosity (and,
-for the channel, body force): cavity nu = 1/Re (lid speed 1, side 1);
-channel u_max = 1, nu = 1/Re, F = 8 nu.
+for the channels, body force): cavity nu = 1/Re (lid speed 1, side 1);
+channel (2D and 3D) u_max = 1, nu = 1/Re, F = 8 nu.
 """
 import collections
 import time
@@ -35,8 +36,8 @@ DT = 1e-3
 @dataclass
 class Request:
     rid: int
-    kind: str          # "cavity" or "channel"
-    n: int             # n x n particles
+    kind: str          # "cavity", "channel" or "channel3d"
+    n: int             # n x n (3D: n x n x n) particles
     re: float
     steps: int
     arrival: float = 0.0
@@ -59,28 +60,39 @@ def class_key(req):
     return (req.kind, req.n, family_for(req.kind, req.re))
 
 
-def footprint_bytes(n, capacity, prec):
-    """Device bytes of one class: state (5 fields), workspace (6), spectra."""
+def particles(req):
+    return req.n ** 3 if req.kind == "channel3d" else req.n ** 2
+
+
+def footprint_bytes(n, capacity, prec, d3=False):
+    """Device bytes of one class: state, workspace and spectra per slot
+    (2D: 5 + 6 fields, 8 spectra; 3D: 7 + 7 fields, 15 spectra)."""
     my = n + 25
     hy = my // 2 + 1
     rows = max(hy, n)
     cb = 8 if prec == "f32" else 16
-    return capacity * (11 * n * n * 8 + 8 * rows * n * cb + rows * n * 16)
+    ncol = n * n if d3 else n
+    fields, specs = (14, 15) if d3 else (11, 8)
+    return capacity * (fields * ncol * n * 8 + specs * rows * ncol * cb + rows * ncol * 16)
 
 
 class SizeClass:
     def __init__(self, key, capacity, prec, device):
         kind, n, fam = key
         self.key, self.kind, self.n, self.capacity, self.prec = key, kind, n, capacity, prec
+        self.d3 = kind == "channel3d"
         x_walls = kind == "cavity"
         dy = 1.0 / (n - 1)
         lx = 1.0 if x_walls else n * dy
         self.stream = torch.cuda.Stream(device=device)
         with torch.cuda.stream(self.stream):
             self.ctx = b.Context(n, n, lx, 1.0, x_walls=x_walls, batch=capacity, family=fam, h_over_dx=1.3,
-                                 prec=prec, stream=self.stream.cuda_stream)
-            z = torch.zeros((capacity, n, n), dtype=torch.float64, device=device)
+                                 prec=prec, stream=self.stream.cuda_stream, nz=n if self.d3 else 1,
+                                 lz=n * dy if self.d3 else 0.0)
+            shape = (capacity, n, n, n) if self.d3 else (capacity, n, n)
+            z = torch.zeros(shape, dtype=torch.float64, device=device)
             self.u, self.v, self.p, self.fu, self.fv = [z.clone() for _ in range(5)]
+            self.w, self.fw = (z.clone(), z.clone()) if self.d3 else (None, None)
             self.nu = torch.full((capacity,), 1e-2, dtype=torch.float64, device=device)
             self.fx = torch.zeros((capacity,), dtype=torch.float64, device=device)
         self.slots = [None] * capacity
@@ -97,10 +109,11 @@ class SizeClass:
     def admit(self, slot, req):
         nu = 1.0 / req.re
         with torch.cuda.stream(self.stream):
-            for t in (self.u, self.v, self.p, self.fu, self.fv):
-                t[slot].zero_()
+            for t in (self.u, self.v, self.p, self.fu, self.fv, self.w, self.fw):
+                if t is not None:
+                    t[slot].zero_()
             self.nu[slot] = nu
-            self.fx[slot] = 8.0 * nu if self.kind == "channel" else 0.0
+            self.fx[slot] = 8.0 * nu if self.kind in ("channel", "channel3d") else 0.0
         self.slots[slot] = req
 
     def step(self):
@@ -109,7 +122,7 @@ class SizeClass:
             self.ev0.record(self.stream)
             self.ctx.isph_step(self.u, self.v, self.p, self.fu, self.fv, 1, nu=1e-2, rho=1.0, dt=DT,
                                u_top=1.0 if self.kind == "cavity" else 0.0, scheme="rk3", use_graph=True,
-                               nu_inst=self.nu, fx_inst=self.fx)
+                               nu_inst=self.nu, fx_inst=self.fx, w=self.w, fw=self.fw)
             self.ev1.record(self.stream)
         self.pending_event = True
 
@@ -127,6 +140,8 @@ class SizeClass:
             r.latencies_ms.append(ms)
             if r.done_steps >= r.steps:
                 r.result = {"u": self.u[i].cpu().numpy(), "v": self.v[i].cpu().numpy(), "p": self.p[i].cpu().numpy()}
+                if self.d3:
+                    r.result["w"] = self.w[i].cpu().numpy()
                 r.t_done = now
                 self.slots[i] = None
                 retired.append(r)
@@ -147,7 +162,7 @@ class Server:
         self.done = []
 
     def used_bytes(self):
-        return sum(footprint_bytes(c.n, c.capacity, c.prec) for c in self.classes.values())
+        return sum(footprint_bytes(c.n, c.capacity, c.prec, c.d3) for c in self.classes.values())
 
     def submit(self, req):
         self.queue.append(req)
@@ -159,7 +174,7 @@ class Server:
             key = class_key(req)
             cls = self.classes.get(key)
             if cls is None:
-                need = footprint_bytes(req.n, self.capacity, self.prec)
+                need = footprint_bytes(req.n, self.capacity, self.prec, req.kind == "channel3d")
                 if self.used_bytes() + need > self.mem_budget:
                     waiting.append(req)
                     continue
@@ -224,7 +239,7 @@ class Server:
 
 def summarize(requests, wall_s):
     lat = np.concatenate([np.asarray(r.latencies_ms) for r in requests if r.latencies_ms]) if requests else np.zeros(0)
-    updates = sum(r.n * r.n * r.done_steps for r in requests)
+    updates = sum(particles(r) * r.done_steps for r in requests)
     return {"requests": len(requests), "finished": sum(1 for r in requests if r.result is not None),
             "particle_updates": updates, "wall_s": wall_s, "particle_updates_per_s": updates / wall_s if wall_s else None,
             "step_latency_ms_p50": float(np.percentile(lat, 50)) if lat.size else None,

@@ -11,7 +11,8 @@ from oracle import step as ostep
 def _reqs():
     from paper_2606_06247_gb300.serve import Request
     return [Request(0, "cavity", 32, 400.0, 4), Request(1, "channel", 32, 50.0, 6), Request(2, "cavity", 48, 1000.0, 3),
-            Request(3, "cavity", 32, 2500.0, 5), Request(4, "channel", 40, 800.0, 2)]
+            Request(3, "cavity", 32, 2500.0, 5), Request(4, "channel", 40, 800.0, 2),
+            Request(5, "channel3d", 16, 300.0, 3), Request(6, "channel3d", 16, 900.0, 2)]
 
 
 @pytest.mark.gpu
@@ -33,7 +34,7 @@ def test_result_is_the_same_alone_and_in_the_mix(prec):
         while not alone.idle():
             alone.tick(0.0)
         m = [x for x in mix if x.rid == r.rid][0]
-        for f in ("u", "v", "p"):
+        for f in r.result:
             np.testing.assert_array_equal(r.result[f], m.result[f])
 
 
