@@ -79,6 +79,41 @@ __device__ __forceinline__ ff operator/(ff a, ff b) {
   return ff_make(h, l);
 }
 
+// acc + a * c with one renormalisation: the exact product's high word and
+// its error (3 FMAs) join acc through TwoSum; 15 FP32 instructions instead of
+// the 18 of a separate multiply and add.
+__device__ __forceinline__ ff ff_fma(ff acc, ff a, ff c) {
+  const float p = __fmul_rn(a.h, c.h);
+  float e = __fmaf_rn(a.h, c.h, -p);
+  e = __fmaf_rn(a.h, c.l, e);
+  e = __fmaf_rn(a.l, c.h, e);
+  float s, t;
+  two_sum(acc.h, p, s, t);
+  t = __fadd_rn(t, __fadd_rn(acc.l, e));
+  float h, l;
+  fast_two_sum(s, t, h, l);
+  return ff_make(h, l);
+}
+
+// a * b + c * d: both exact products' high words through one TwoSum, their
+// error terms added once; 19 FP32 instructions instead of 25.
+__device__ __forceinline__ ff ff_dot2(ff a, ff b, ff c, ff d) {
+  const float p1 = __fmul_rn(a.h, b.h);
+  float e1 = __fmaf_rn(a.h, b.h, -p1);
+  e1 = __fmaf_rn(a.h, b.l, e1);
+  e1 = __fmaf_rn(a.l, b.h, e1);
+  const float p2 = __fmul_rn(c.h, d.h);
+  float e2 = __fmaf_rn(c.h, d.h, -p2);
+  e2 = __fmaf_rn(c.h, d.l, e2);
+  e2 = __fmaf_rn(c.l, d.h, e2);
+  float s, t;
+  two_sum(p1, p2, s, t);
+  t = __fadd_rn(t, __fadd_rn(e1, e2));
+  float h, l;
+  fast_two_sum(s, t, h, l);
+  return ff_make(h, l);
+}
+
 // integer stored in a pool entry (exact in the high word below 2^24)
 __device__ __forceinline__ int pool_index(float x) { return (int)x; }
 __device__ __forceinline__ int pool_index(double x) { return (int)x; }
@@ -87,5 +122,24 @@ __device__ __forceinline__ int pool_index(ff x) { return (int)x.h; }
 struct ff2 {
   ff x, y;
 };
+
+// Complex products of FP32-pair values (overloads of the generic ones).
+__device__ __forceinline__ ff2 cmul(ff2 a, ff2 b) {
+  ff2 r;
+  r.x = ff_dot2(a.x, b.x, -a.y, b.y);
+  r.y = ff_dot2(a.x, b.y, a.y, b.x);
+  return r;
+}
+__device__ __forceinline__ ff2 cmulc(ff2 a, ff2 b) {  // a * conj(b)
+  ff2 r;
+  r.x = ff_dot2(a.x, b.x, a.y, b.y);
+  r.y = ff_dot2(a.y, b.x, -a.x, b.y);
+  return r;
+}
+
+// acc + a * c in every compute type (a contracted FMA for float and double).
+__device__ __forceinline__ ff madd(ff acc, ff a, ff c) { return ff_fma(acc, a, c); }
+__device__ __forceinline__ float madd(float acc, float a, float c) { return acc + a * c; }
+__device__ __forceinline__ double madd(double acc, double a, double c) { return acc + a * c; }
 
 }  // namespace fcsph

@@ -228,10 +228,10 @@ __device__ __forceinline__ void dft_odd(typename CT<T>::t* v) {
     for (int r = 1; r <= h; ++r) {
       const T c = (T)cosk<R>((r * q) % R);
       const T s = (T)sink<R>((r * q) % R);
-      re.x += A[r - 1].x * c;
-      re.y += A[r - 1].y * c;
-      im.x += B[r - 1].x * s;
-      im.y += B[r - 1].y * s;
+      re.x = madd(re.x, A[r - 1].x, c);
+      re.y = madd(re.y, A[r - 1].y, c);
+      im.x = madd(im.x, B[r - 1].x, s);
+      im.y = madd(im.y, B[r - 1].y, s);
     }
     const V ri = rot<V, INV>(im);  // -i * im (forward)
     o[q] = cadd(re, ri);
