@@ -170,3 +170,34 @@ def test_dipole_161_rk3_parity(prec):
     print(f"dipole 161^2 {prec}: parity (u, v, p) {errs}, floor {fl}")
     for e, f in zip(errs, fl):
         assert e < parity_tol(f, base=1e-12 * scale, factor=10.0 * scale)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("scheme,nsteps", [("fop", 100), ("rk3", 40)])
+def test_channel_64_paper_fc_variant(scheme, nsteps):
+    """The paper's own FC (Sec. 4, Eqs. 14-29) at its parameters: fitted
+    degree p = 5 on 10 matching points, n_cont = N/4, the Neumann row for phi
+    (Sec. 4.4).  The library builds both tables; the oracle builds its own."""
+    from oracle import fc as ofc
+    torch = torch_cuda()
+    b = binding()
+    N, C = 64, 16
+    lx, ly = grid_lengths(N, N, False)
+    u0, v0 = inputs.channel_initial(N, N, seed=1, sigma=1e-6)
+    ctx = b.Context(N, N, lx, ly, family="G4", h_over_dx=1.3, variant="paper", n_match=10, n_cont=C, poly_deg=5)
+    u, v = to_dev(u0[None]), to_dev(v0[None])
+    p, fu, fv = torch.zeros_like(u), torch.zeros_like(u), torch.zeros_like(u)
+    ctx.isph_step(u, v, p, fu, fv, nsteps, nu=0.1, rho=1.0, dt=1e-3, force=(0.8, 0.0), scheme=scheme)
+    ctx.sync()
+    prob = ostep.Problem(nx=N, ny=N, Lx=lx, Ly=ly, x_walls=False, family="G4", h_over_dx=1.3,
+                         E_dir=ofc.paper_table(10, C, 5, ofc.DIRICHLET), E_neu=ofc.paper_table(10, C, 5, ofc.NEUMANN),
+                         nu=0.1, rho=1.0, dt=1e-3, force=(0.8, 0.0), scheme=scheme).build_symbols()
+    fn = lambda a, c: ostep.isph_steps(prob, a, c, nsteps)
+    uo, vo, po = fn(u0, v0)
+    fl = ulp_floor(fn, u0, v0)
+    errs = [rel_l2(u[0].cpu().numpy(), uo), rel_l2(v[0].cpu().numpy(), vo), rel_l2(p[0].cpu().numpy(), po)]
+    print(f"paper FC variant {scheme}: parity (u, v, p) {errs}, floor {fl}")
+    for e, f in zip(errs, fl):
+        assert e < parity_tol(f)
+    y = np.linspace(0, 1, N)
+    assert rel_l2(u[0].cpu().numpy(), np.tile(_series(y, nsteps * 1e-3, 0.8, 0.1), (N, 1))) < 3e-3
