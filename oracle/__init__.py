@@ -19,6 +19,7 @@ Continuation (FC)-based spectral ISPH scheme ..."):
   ops      -- spectral SPH operators on the FC-extended grid (Eqs. 11, 13)
   ppe      -- spectral PPE on the physical nodes (Eqs. 31-33)
   step     -- FOP / low-storage RK3 projection step (Eqs. 5-9, Sec. 2.2)
+  advection -- Gaussian vortex convection with inflow/outflow (Sec. 6.2)
   channel3d -- the same operators, PPE and step in three dimensions (x, z
               periodic, walls in y)
   norms    -- L2 norm of Eq. 34 and companions
