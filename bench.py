@@ -472,15 +472,12 @@ def run_ours(args):
             "vs_baseline": None, "dtype": dtype_name, "data": "synthetic",
             "path": {"f64": "plain FP64", "f32x2": "FP32-pair transforms (48-bit significand), FP64 state",
                      "f32": "mixed (FP32 transforms)"}[args.prec],
-            "config": {"workload": f"lid-driven cavity {N}x{N} Re=1000, FC(Gram) d=5 C=25 on x and y, "
-                                   f"G8 h=1.3dx, RK3 dt=1e-3, batch of {B} instances", "batch": B, "nx": N, "ny": N,
-                       "precision": {"f32": ("FP32 FFT/symbols, FP64 FC sums, state and PPE residual, "
-                                             f"{args.refine} refinement sweeps"),
-                                     "f32x2": "FP32-pair (double-float) FFT/symbols/FC sums, FP64 state",
-                                     "f64": "FP64"}[args.prec],
-                       "tiling": list(ctx.get_tiling()),
-                       "l2": f"inputs larger than L2 (state + workspace {B * N * N * 8 * 11 / 2**20:.0f} MiB)",
-                       "parallelism": f"replicas x{ws}"},
+            "config": dict(cavity_config(B, ws),
+                           precision={"f32": ("FP32 FFT/symbols, FP64 FC sums, state and PPE residual, "
+                                              f"{args.refine} refinement sweeps"),
+                                      "f32x2": "FP32-pair (double-float) FFT/symbols/FC sums, FP64 state",
+                                      "f64": "FP64"}[args.prec],
+                           tiling=list(ctx.get_tiling())),
             "latency_ms": {"p50": per_sorted[len(per_sorted) // 2], "p99": per_sorted[min(len(per_sorted) - 1, int(0.99 * len(per_sorted)))]},
             "roofline": roof,
             "kernels": kinds,
@@ -496,6 +493,14 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def cavity_config(B, ws):
+    """The headline workload's config, shared by both arms."""
+    return {"workload": f"lid-driven cavity {N}x{N} Re=1000, FC(Gram) d=5 C=25 on x and y, "
+                        f"G8 h=1.3dx, RK3 dt=1e-3, batch of {B} instances", "batch": B, "nx": N, "ny": N,
+            "l2": f"inputs larger than L2 (state + workspace {B * N * N * 8 * 11 / 2**20:.0f} MiB)",
+            "parallelism": f"replicas x{ws}"}
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -509,10 +514,11 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "particle-updates/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"lid-driven cavity {N}x{N} Re=1000, FC(Gram) d=5 C=25 on x and y, G8 h=1.3dx, "
-                                   "RK3 dt=1e-3; one instance per step (bounded sample)", "batch": 1, "nx": N, "ny": N},
+            "config": dict(cavity_config(args.batch, ws), precision="FP64 numpy oracle on the host cores"),
             "cpu_baseline": {"value": value, "unit": "particle-updates/s", "cores": cpu_cores(), "kind": "oracle",
-                             "sample": f"{args.steps} single-instance RK3 steps of the 256^2 cavity after {args.warmup} warm-up"},
+                             "sample": (f"bounded sample: each step advances 1 of the {args.batch} instances by one RK3 "
+                                        f"step ({args.steps} steps after {args.warmup} warm-up); rate per "
+                                        "particle-update")},
             "e2e": {"value": value, "unit": "particle-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 

@@ -67,3 +67,26 @@ def test_bad_arguments_are_rejected(lib):
     prm = lib.fcsph_step_params(1e-3, 1.0, 1e-3, 0.0, 0.0, 0.0, 1.0, 1, 1, None, None)
     assert L.fcsph_autotune(None, ctypes.byref(prm), 3, None) == 1
     assert L.fcsph_sync(None) == 1
+
+
+def test_create_rejects_bad_grids_before_touching_the_gpu(lib):
+    """fcsph_create validates its arguments first, so these run without a GPU."""
+    import ctypes as C
+
+    def create(nx=32, ny=32, batch=1, x_walls=0, nz=1, lz=0.0, family=2, prec=0, refine=0, n_match=5, n_cont=25):
+        g = lib.fcsph_grid(nx, ny, 1.0, 1.0, x_walls, batch, nz, lz)
+        fc = lib.fcsph_fc(0, n_match, n_cont, 0)
+        k = lib.fcsph_kernel(family, 1.3)
+        p = lib.fcsph_precision(prec, refine)
+        h = C.c_void_p()
+        return lib.lib.fcsph_create(C.byref(g), C.byref(fc), C.byref(k), C.byref(p), None, None, None, C.byref(h))
+
+    assert create(batch=0) == 1                    # no instances
+    assert create(nx=3) == 1                       # too few x nodes
+    assert create(ny=8) == 1                       # fewer than 2 * n_match wall-normal nodes
+    assert create(x_walls=1, nz=4, lz=1.0) == 1    # 3D needs periodic x
+    assert create(nz=4, lz=0.0) == 1               # 3D needs a z period
+    assert create(prec=7) == 1                     # unknown precision
+    assert create(family=0) == 1                   # unknown kernel family
+    assert create(nx=9000) == 1                    # beyond the supported size
+    assert create(nz=4, lz=1.0, prec=1, refine=2) == 6  # PPE refinement is 2D only
