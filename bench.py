@@ -65,6 +65,22 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(x, ws, device="cpu"):
+    """The largest per-rank value (the slowest rank's time) on every rank."""
+    if ws <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, ws, t_max_ms):
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return units_per_rank * ws / (t_max_ms / 1e3)
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -323,13 +339,8 @@ def run_ours(args):
     dtype_name = {"f64": "f64", "f32x2": "f32x2", "f32": "f32"}[args.prec]
     st = state()
     total_ms, per_ms, launches, clocks = timed(ctx, st, args.steps, args.warmup)
-    t_max = total_ms
-    if ws > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    updates = ws * B * N * N * args.steps
-    value = updates / (t_max / 1e3)
+    t_max = max_over_ranks(total_ms, ws, dev)
+    value = job_rate(B * N * N * args.steps, ws, t_max)
 
     # ---- per-kernel durations (eager launches, events on the launching stream)
     ctx.set_profiling(True)
