@@ -279,7 +279,7 @@ fcsph_status fcsph_create(const fcsph_grid* grid, const fcsph_fc* fc, const fcsp
     CREATE_CK(cudaMalloc((void**)&c->dE, 2 * ne * sizeof(double)), "cudaMalloc(E)");
     CREATE_CK(cudaMemcpy(c->dE, c->hE[0].data(), ne * sizeof(double), cudaMemcpyHostToDevice), "E upload");
     CREATE_CK(cudaMemcpy(c->dE + ne, c->hE[1].data(), ne * sizeof(double), cudaMemcpyHostToDevice), "E upload");
-    if (prec->fft_prec == FCSPH_F32X2) {
+    if (prec->fft_prec != FCSPH_F64) {  // FP32-pair tables for the FP32 and FP32x2 FC sums
       std::vector<float2> hf(2 * ne);
       for (size_t i = 0; i < 2 * ne; ++i) {
         const double x = c->hE[i / ne][i % ne];

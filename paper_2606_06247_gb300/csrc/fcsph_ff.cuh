@@ -20,6 +20,7 @@ struct ff {
   // exact for |i| < 2^24 (wavenumber indices), without a trip through FP64
   __host__ __device__ ff(int i) : h((float)i), l(0.f) {}
   __host__ __device__ explicit operator double() const { return (double)h + (double)l; }
+  __host__ __device__ explicit operator float() const { return h + l; }
 };
 
 __device__ __forceinline__ ff ff_make(float h, float l) {

@@ -59,11 +59,14 @@ struct Dot2 {
   __device__ __forceinline__ double value() const { return s + c; }
 };
 
-// FC continuation sum of one line component in the transform's precision
-// class: compensated FP64 (Dot2, table in double) for FP64 and FP32
-// transforms, FP32-pair arithmetic (table in FP32 pairs) for FP32x2.
+// FC continuation sum of one line component: compensated FP64 (Dot2, table
+// in double) for FP64 transforms; FP32-pair arithmetic (table in FP32 pairs)
+// for FP32x2 and FP32 transforms.  For FP32 the pair sum (error ~2^-48 of
+// sum |E b|) rounds to the same FP32 value an FP64 sum would, on the FP32
+// units: the sum needs more than FP32 because the terms reach ~1e3-1e4 |b|.
 template <typename T> struct FcTab { typedef double t; };
 template <> struct FcTab<ff> { typedef ff t; };
+template <> struct FcTab<float> { typedef ff t; };
 
 template <typename T> struct FcAcc {
   Dot2 a;
@@ -74,6 +77,11 @@ template <> struct FcAcc<ff> {
   ff a;
   __device__ __forceinline__ void add(ff e, ff x) { a += e * x; }
   __device__ __forceinline__ ff value() const { return a; }
+};
+template <> struct FcAcc<float> {
+  ff a;
+  __device__ __forceinline__ void add(ff e, float x) { a = ff_fma(a, e, ff_make(x, 0.f)); }
+  __device__ __forceinline__ float value() const { return __fadd_rn(a.h, a.l); }
 };
 
 // Appends the C continuation values of nl lines (stride ls, data in [0, n)):
@@ -226,7 +234,7 @@ __global__ void __launch_bounds__(kFftThreads, MinCtas<T>::v) k_col_fwd(GridDev 
     T* L = reinterpret_cast<T*>(lines + (size_t)(col >> 1) * ls) + (col & 1);
     const bool in = i0 + col < g.ncol;
     for (int j = threadIdx.x; j < ny; j += blockDim.x)
-      L[2 * j] = (T)(in ? (double)src[base + (size_t)col * ny + j] : 0.0);
+      L[2 * j] = in ? (T)src[base + (size_t)col * ny + j] : (T)0;
   }
   __syncthreads();
   col_forward_store<T>(lines, scratch, Pp, ls, g, i0, E, P, pool, dct, spec + b * bstride + f * fstride);
@@ -378,7 +386,7 @@ __global__ void __launch_bounds__(kFftThreads, MinCtas<T>::v) k_line_op(GridDev 
   for (int col = 0; col < 2 * Pp; ++col) {
     const long long cc = c0 + col;
     T* L = reinterpret_cast<T*>(X + (size_t)(col >> 1) * ls) + (col & 1);
-    for (int j = threadIdx.x; j < ny; j += blockDim.x) L[2 * j] = (T)(cc < ncols ? (double)f[cc * ny + j] : 0.0);
+    for (int j = threadIdx.x; j < ny; j += blockDim.x) L[2 * j] = cc < ncols ? (T)f[cc * ny + j] : (T)0;
   }
   __syncthreads();
   fc_append<T>(X, Pp, ls, ny, g.n_cont, g.n_match, E);
@@ -414,7 +422,7 @@ __global__ void __launch_bounds__(kFftThreads, MinCtas<T>::v) k_line_op(GridDev 
       const long long cc = c0 + col;
       if (cc >= ncols) break;
       const V* Yl = Y + (size_t)(col >> 1) * ls;
-      for (int j = threadIdx.x; j < ny; j += blockDim.x) out[cc * ny + j] = (U)(double)((col & 1) ? Yl[j].y : Yl[j].x);
+      for (int j = threadIdx.x; j < ny; j += blockDim.x) out[cc * ny + j] = (U)((col & 1) ? Yl[j].y : Yl[j].x);
     }
     __syncthreads();
   }
@@ -605,15 +613,19 @@ __global__ void __launch_bounds__(kFftThreads, MinCtas<T>::v) k_col_inv(GridDev 
         const int i = i0 + 2 * p + w;
         if (i >= g.ncol) continue;
         const size_t id = fidx(g, b, i, j);
-        const double val = (double)(w ? z.y : z.x);
+        const T zv = w ? z.y : z.x;
+        if (EPI == EPI_OUT) {
+          // straight from the compute type to the output type
+          if (ea.out_double)
+            reinterpret_cast<double*>(ea.outs[o])[id] = (double)zv;
+          else
+            reinterpret_cast<float*>(ea.outs[o])[id] = (float)zv;
+          continue;
+        }
+        const double val = (double)zv;
         double nv = 0.0;
         int slot = -1;
-        if (EPI == EPI_OUT) {
-          if (ea.out_double)
-            reinterpret_cast<double*>(ea.outs[o])[id] = val;
-          else
-            reinterpret_cast<float*>(ea.outs[o])[id] = (float)val;
-        } else if (EPI == EPI_MOM) {
+        if (EPI == EPI_MOM) {
           // output comp * nt + term: d/dx, d/dy, (d/dz,) lap of component comp;
           // F_comp = u . grad(comp) - nu lap(comp) accumulates in acc[comp]
           const int nt = ea.mom_terms;
@@ -855,7 +867,7 @@ template <typename K> cudaError_t raise_smem(K kernel) {
 // FC table (bc) in the FcTab type of precision prec.
 const void* fc_table(const fcsph_ctx* c, int prec, int bc) {
   const size_t off = (bc == FCSPH_NEUMANN ? 1 : 0) * (size_t)c->gd.n_cont * 2 * c->gd.n_match;
-  if (prec == FCSPH_F32X2) return static_cast<const ff*>(c->dEff) + off;
+  if (prec == FCSPH_F32X2 || prec == FCSPH_F32) return static_cast<const ff*>(c->dEff) + off;
   return c->dE + off;
 }
 
