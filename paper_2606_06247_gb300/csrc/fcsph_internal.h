@@ -14,8 +14,9 @@
 namespace fcsph {
 
 constexpr int kMaxStages = 12;
-// Largest prime factor handled by a direct Stockham stage; lengths with a
-// larger prime factor go through Bluestein's chirp-z convolution.
+// Largest prime factor handled by a direct Stockham stage.  A prime length p
+// whose p - 1 factors into such stages uses Rader's algorithm; other lengths
+// with a larger prime factor go through Bluestein's chirp-z convolution.
 constexpr int kMaxDirectPrime = 31;
 
 // Division by a fixed d (< 2^31 dividends) as (umulhi(x, m) + x) >> l.

@@ -1,16 +1,20 @@
 // CUDA kernels of the FC spectral ISPH hot path (sm_103a).
 //
-// Data layout (HBM).  Real fields f[b][i][j] (j = y, contiguous).  Spectra
-// after the y transform are stored transposed, S[b][field][ky][i] (i
-// contiguous), so that the x pass reads whole rows.  The FC-extended grid is
-// never materialised in HBM on the hot path: the continuation is computed in
-// shared memory inside the transform kernels.
+// Data layout (HBM).  Real fields f[b][c][j] (j = y, contiguous; c = x index,
+// or x * nz + z on a 3D grid).  Spectra after the y transform are stored
+// transposed, S[b][field][ky][c] (c contiguous), so that the x pass reads
+// whole rows (3D: x lines at stride nz, after a z pass over contiguous runs).
+// The FC-extended grid is never materialised in HBM on the hot path: the
+// continuation is computed in shared memory inside the transform kernels.
 //
-// Column kernels (y direction) handle 2*Pp adjacent columns of one instance:
-// two real columns are packed into one complex line (a + i b), transformed
-// together, and separated with the Hermitian split
+// Every transform kernel runs one warp per CTA, so each barrier of the
+// shared-memory FFT is a warp barrier.  Column kernels (y direction) handle
+// 2*Pp adjacent columns of one instance: two real columns are packed into
+// one complex line (a + i b), transformed together, and separated with the
+// Hermitian split
 //   A_k = (Z_k + conj Z_{-k}) / 2,  B_k = (Z_k - conj Z_{-k}) / (2i).
-// Row kernels (x direction) handle Rr spectrum rows of one instance.
+// Row kernels (x direction) handle Rr x lines of one instance; outputs are
+// formed and inverted one at a time.
 #include <cstdio>
 #include <cstring>
 
