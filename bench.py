@@ -234,6 +234,39 @@ def ff_peak_tflops(sm_mhz=2070.0):
     return 152 * 128 * sm_mhz * 1e6 / FF_INST_PER_FLOP / 1e12
 
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of a kernel kind, from one ncu
+# capture of `bench.py --profile-case --batch B --prec P` (first RK3 substep; command and table in
+# profiles/), keyed by (precision, kind, batch).  Valid only for the kernel sources they were taken on:
+# KERNEL_SOURCES_SHA256 is the hash of csrc/ at capture time, and a different hash reports null.
+MEASURED_TRAFFIC = {
+    ("f32x2", "row_mom", 32): 91668224, ("f32x2", "col_mom", 32): 237278464,
+    ("f64", "row_mom", 32): 83464704, ("f64", "col_mom", 32): 242213888,
+    ("f32", "row_mom", 32): 21289216, ("f32", "col_mom", 32): 162235904,
+}
+KERNEL_SOURCES_SHA256 = "233ea5a043d056a90f0ef14cd3f1d17232de5579b89e9712f1c04df08934942e"
+
+
+def kernel_sources_sha256():
+    import hashlib
+    d = os.path.join(ROOT, "paper_2606_06247_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(d)):
+        if name.endswith((".cu", ".cuh", ".h", ".cpp")):
+            with open(os.path.join(d, name), "rb") as f:
+                h.update(name.encode() + b"\0" + f.read())
+    return h.hexdigest()
+
+
+def measured_traffic(prec, kind, batch):
+    """(bytes per launch or None, note)."""
+    v = MEASURED_TRAFFIC.get((prec, kind, batch))
+    if v is None:
+        return None, "no ncu capture for this precision, kernel and batch"
+    if kernel_sources_sha256() != KERNEL_SOURCES_SHA256:
+        return None, "kernel sources changed since the ncu capture"
+    return v, "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch"
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -365,6 +398,7 @@ def run_ours(args):
         fl = kernel_flops(k, N, N, my, mx, hy, px, B, split)
         d["alg_gflop"] = fl / 1e9
         d["gflops"] = fl / (d["avg_ms"] * 1e-3) / 1e9 if fl else None
+    traffic, traffic_note = measured_traffic(args.prec, dom, B)
     if args.prec in ("f64", "f32x2"):
         if args.prec == "f64":
             pk = fp64_peak_tflops(peaks.get("sm_max_mhz", 2070.0)) * 1e3
@@ -374,13 +408,13 @@ def run_ours(args):
             src = (f"derived: 152 SMs x 128 FP32 lanes x max SM clock / {FF_INST_PER_FLOP} FP32 instructions "
                    "per FP32-pair flop")
         roof = {"kernel": dom, "bound": "alu", "achieved": kinds[dom]["gflops"], "peak": pk, "unit": "GFLOP/s",
-                "frac": (kinds[dom]["gflops"] or 0) / pk, "traffic": None,
+                "frac": (kinds[dom]["gflops"] or 0) / pk, "traffic": traffic, "traffic_source": traffic_note,
                 "peak_source": src,
                 "alg_gflop_per_launch": kinds[dom]["alg_gflop"], "avg_launch_ms": kinds[dom]["avg_ms"],
                 "hbm_gbs_alg": kinds[dom]["gbs"], "hbm_frac_of_measured": (kinds[dom]["gbs"] or 0) / peaks["hbm_gbs"]}
     else:
         roof = {"kernel": dom, "bound": "hbm", "achieved": kinds[dom]["gbs"], "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": (kinds[dom]["gbs"] or 0) / peaks["hbm_gbs"], "traffic": None,
+                "frac": (kinds[dom]["gbs"] or 0) / peaks["hbm_gbs"], "traffic": traffic, "traffic_source": traffic_note,
                 "peak_source": peak_src + " hbm_gbs", "alg_bytes_per_launch": kinds[dom]["alg_bytes"],
                 "avg_launch_ms": kinds[dom]["avg_ms"]}
     prof_total = sum(d["ms"] for d in kinds.values())
@@ -429,6 +463,7 @@ def run_ours(args):
                 compare[f"{pr}_value"] = B * N * N * n2 / (t2 / 1e3)
                 compare[f"{pr}_ms_per_step"] = t2 / n2
                 compare[f"{pr}_tiling"] = list(c2.get_tiling())
+                compare[f"{pr}_cta_threads"] = list(c2.get_cta_threads())
             sa = state()
             c2.isph_step(*sa, nsteps_cmp, use_graph=True, **prm)
             torch.cuda.synchronize()
@@ -484,11 +519,11 @@ def run_ours(args):
             "path": {"f64": "plain FP64", "f32x2": "FP32-pair transforms (48-bit significand), FP64 state",
                      "f32": "mixed (FP32 transforms)"}[args.prec],
             "config": dict(cavity_config(B, ws),
-                           precision={"f32": ("FP32 FFT/symbols, FP64 FC sums, state and PPE residual, "
+                           precision={"f32": ("FP32 FFT/symbols, FP32-pair FC sums, FP64 state and PPE residual, "
                                               f"{args.refine} refinement sweeps"),
                                       "f32x2": "FP32-pair (double-float) FFT/symbols/FC sums, FP64 state",
                                       "f64": "FP64"}[args.prec],
-                           tiling=list(ctx.get_tiling())),
+                           tiling=list(ctx.get_tiling()), cta_threads=list(ctx.get_cta_threads())),
             "latency_ms": {"p50": per_sorted[len(per_sorted) // 2], "p99": per_sorted[min(len(per_sorted) - 1, int(0.99 * len(per_sorted)))]},
             "roofline": roof,
             "kernels": kinds,
@@ -583,8 +618,11 @@ def run_serving(args):
         "speedup_vs_serial": served["particle_updates_per_s"] / serial["particle_updates_per_s"]}))
 
 
+WIDTH_SWEEP = [(r, c) for r in (32, 64, 128) for c in (32, 64, 128)]
+
+
 def run_planes(args):
-    """Configuration 3b: FC-extended operator microbench on 256 planes of
+    """FC-extended operator microbench on 256 planes of
     1024 x 1024 (x periodic, walls in y), FP32 fields, d/dx, d/dy and the
     Laplacian per call.  Algorithmic bytes: 4 B in + 3 x 4 B out per node."""
     import numpy as np
@@ -599,21 +637,31 @@ def run_planes(args):
     outs = [torch.empty_like(f) for _ in range(3)]
     peaks, src = load_peaks()
     lines = {}
-    for n_cont in (25, 26):
-        ctx = b.Context(n, n, n / (n - 1), 1.0, batch=P, n_cont=n_cont, family="G4", h_over_dx=1.3, prec="f32")
-        for _ in range(max(3, args.warmup)):
-            ctx.spectral_op(f, ["DX", "DY", "LAP"], outs)
-        torch.cuda.synchronize()
+    def call_ms(ctx, calls):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        for _ in range(args.steps):
+        for _ in range(calls):
             ctx.spectral_op(f, ["DX", "DY", "LAP"], outs)
         e1.record()
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / args.steps
+        return e0.elapsed_time(e1) / calls
+
+    for n_cont in (25, 26):
+        ctx = b.Context(n, n, n / (n - 1), 1.0, batch=P, n_cont=n_cont, family="G4", h_over_dx=1.3, prec="f32")
+        # CTA widths: a short sweep (row, column threads), then the timed calls at the fastest
+        sweep = {}
+        for w in WIDTH_SWEEP:
+            ctx.set_cta_threads(*w)
+            call_ms(ctx, 1)
+            sweep[f"{w[0]},{w[1]}"] = call_ms(ctx, 2)
+        best_w = min(sweep, key=sweep.get)
+        ctx.set_cta_threads(*[int(x) for x in best_w.split(",")])
+        call_ms(ctx, max(3, args.warmup))
+        ms = call_ms(ctx, args.steps)
         gbs = P * n * n * 16 / (ms * 1e-3) / 1e9
         lines[f"n_cont={n_cont} (n_e={n + n_cont})"] = {"ms_per_call": ms, "alg_GBps": gbs, "frac_of_hbm": gbs / peaks["hbm_gbs"],
-                                                        "launches_per_call": 3}
+                                                        "launches_per_call": 3, "cta_threads": best_w,
+                                                        "width_sweep_ms": sweep}
         del ctx
         torch.cuda.empty_cache()
     best = max(v["alg_GBps"] for v in lines.values())
@@ -626,7 +674,7 @@ def run_planes(args):
 
 
 def run_lines(args):
-    """Configuration 3a: 4096 independent wall-normal lines of 512 nodes (walls
+    """Line-operator microbench: 4096 independent wall-normal lines of 512 nodes (walls
     at both ends), band-limited trig sums plus degree-4 polynomials, d/dy and
     d^2/dy^2 per call through line_op (one fused kernel).  Algorithmic bytes:
     4 B in + 2 x 4 B out per node (FP32 fields).  One call moves 25 MB, which
@@ -647,22 +695,31 @@ def run_lines(args):
         ctx = b.Context(L, n, L * dy, 1.0, batch=1, n_cont=n_cont, family="G4", h_over_dx=1.3, prec=prec)
         fs = [torch.tensor(base, dtype=dt, device="cuda").reshape(1, L, n) for _ in range(sets)]
         outs = [[torch.empty_like(fs[0]) for _ in range(2)] for _ in range(sets)]
-        for k in range(max(3, args.warmup)):
-            ctx.line_op(fs[k % sets], ["DY", "LAP"], outs[k % sets])
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+        def call_ms(calls):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for k in range(calls):
+                ctx.line_op(fs[k % sets], ["DY", "LAP"], outs[k % sets])
+            e1.record()
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / calls
+
+        sweep = {}
+        if prec == "f32":  # CTA width of the line kernel: a short sweep, then the timed calls at the fastest
+            for w in (32, 64, 128):
+                ctx.set_cta_threads(32, w)
+                call_ms(sets)
+                sweep[w] = call_ms(2 * sets)
+            ctx.set_cta_threads(32, min(sweep, key=sweep.get))
+        call_ms(max(3, args.warmup, sets))
         calls = max(args.steps, sets)
-        e0.record()
-        for k in range(calls):
-            ctx.line_op(fs[k % sets], ["DY", "LAP"], outs[k % sets])
-        e1.record()
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / calls
+        ms = call_ms(calls)
         es = 4 if prec == "f32" else 8
         gbs = L * n * 3 * es / (ms * 1e-3) / 1e9
         variants[f"{prec} n_cont={n_cont} (n_e={n + n_cont})"] = {
             "ms_per_call": ms, "alg_GBps": gbs, "frac_of_hbm": gbs / peaks["hbm_gbs"], "launches_per_call": 1,
-            "lines_per_s": L / (ms * 1e-3)}
+            "lines_per_s": L / (ms * 1e-3), "cta_threads": ctx.get_cta_threads()[1], "width_sweep_ms": sweep}
         del ctx, fs, outs
         torch.cuda.empty_cache()
     head = variants["f32 n_cont=25 (n_e=537)"]
@@ -750,7 +807,7 @@ def run_dipole(args):
 
 
 def run_channel3d(args):
-    """3D channel (config 5's 3D requests): n^3 particles, x and z periodic
+    """3D channel (the 3D requests of the serving mix): n^3 particles, x and z periodic
     (lx = lz = n dy), walls at y = 0, 1, G4 h = 1.3 dx, Re = 100 (u_max = 1:
     nu = 0.01, body force 0.08 in x), RK3 dt = 1e-3, a batch of B channels at
     rest.  Reports the throughput per precision and, after 100 steps, each

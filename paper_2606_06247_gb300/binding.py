@@ -87,6 +87,8 @@ def _load():
         "fcsph_get_profile": [P, P, P, I],
         "fcsph_set_tiling": [P, I, I],
         "fcsph_get_tiling": [P, ctypes.POINTER(I), ctypes.POINTER(I)],
+        "fcsph_set_cta_threads": [P, I, I],
+        "fcsph_get_cta_threads": [P, ctypes.POINTER(I), ctypes.POINTER(I)],
         "fcsph_autotune": [P, ctypes.POINTER(fcsph_step_params), I, ctypes.POINTER(D)],
     }
     for name, args in sig.items():
@@ -263,9 +265,19 @@ class Context:
         self._ck(lib.fcsph_get_tiling(self.h, ctypes.byref(r), ctypes.byref(c)))
         return r.value, c.value
 
+    def set_cta_threads(self, row_threads, col_threads):
+        """fcsph_set_cta_threads: threads per CTA of the row and column passes (32, 64, 128; FP32 only > 32)."""
+        self._ck(lib.fcsph_set_cta_threads(self.h, row_threads, col_threads))
+
+    def get_cta_threads(self):
+        r, c = ctypes.c_int(), ctypes.c_int()
+        self._ck(lib.fcsph_get_cta_threads(self.h, ctypes.byref(r), ctypes.byref(c)))
+        return r.value, c.value
+
     def autotune(self, steps=3, nu=1e-3, rho=1.0, dt=1e-3, force=(0.0, 0.0), u_bottom=0.0, u_top=0.0, scheme="rk3",
                  use_graph=True, nu_inst=None, fx_inst=None):
-        """fcsph_autotune: keeps the fastest tiling; returns (row_lines, col_pairs, ms per step)."""
+        """fcsph_autotune: keeps the fastest tiling (and, FP32, CTA widths); returns (row_lines, col_pairs,
+        ms per step)."""
         prm = self._params(nu, rho, dt, force, u_bottom, u_top, scheme, use_graph, nu_inst, fx_inst)
         ms = ctypes.c_double()
         self._ck(lib.fcsph_autotune(self.h, ctypes.byref(prm), steps, ctypes.byref(ms)))

@@ -234,6 +234,13 @@ fcsph_status fcsph_create(const fcsph_grid* grid, const fcsph_fc* fc, const fcsp
   g.ey_off = pool.add(gauss_axis(g.my, g.dy, g.h, g.hy), std::vector<double>(g.hy, 0.0));
   g.ez_off = pool.add(gauss_axis(nz, g.dz, g.h, nz), std::vector<double>(nz, 0.0));
   if (nz > 1) c->plan_z = plan_for(nz, &pool, &fills);
+  if (prec->fft_prec == FCSPH_F32) {
+    // FP32 lines of ~1000 points and more: one warp per CTA leaves too few
+    // warps per SM (shared memory bound); share each CTA's lines among 2
+    // (row passes) or 4 (column passes) warps.
+    c->row_threads = c->plan_x.line_len() >= kWideLine ? 64 : 32;
+    c->col_threads = c->plan_y.line_len() >= kWideLine ? 128 : 32;
+  }
   {
     // Eq. 33 eigenvalues: DFT lam_k = 2 pi kappa / Lx (kappa signed, Nyquist positive), DCT-I lam = pi k / L
     const double pi = 3.14159265358979323846;
@@ -713,6 +720,26 @@ fcsph_status fcsph_set_tiling(fcsph_ctx* c, int row_lines, int col_pairs) {
   return FCSPH_OK;
 }
 
+fcsph_status fcsph_set_cta_threads(fcsph_ctx* c, int row_threads, int col_threads) {
+  if (!c) return fail(nullptr, FCSPH_EINVAL, "fcsph_set_cta_threads: null context");
+  auto ok = [](int t) { return t == 32 || t == 64 || t == 128; };
+  if (!ok(row_threads) || !ok(col_threads))
+    return fail(c, FCSPH_EINVAL, "fcsph_set_cta_threads: widths must be 32, 64 or 128");
+  if (c->prec.fft_prec != FCSPH_F32 && (row_threads != 32 || col_threads != 32))
+    return fail(c, FCSPH_EUNSUPPORTED, "fcsph_set_cta_threads: only FP32 contexts have wide CTAs");
+  if (row_threads != c->row_threads || col_threads != c->col_threads) drop_graph(c);
+  c->row_threads = row_threads;
+  c->col_threads = col_threads;
+  return FCSPH_OK;
+}
+
+fcsph_status fcsph_get_cta_threads(const fcsph_ctx* c, int* row_threads, int* col_threads) {
+  if (!c || !row_threads || !col_threads) return fail(nullptr, FCSPH_EINVAL, "fcsph_get_cta_threads: bad argument");
+  *row_threads = c->row_threads;
+  *col_threads = c->col_threads;
+  return FCSPH_OK;
+}
+
 fcsph_status fcsph_get_tiling(const fcsph_ctx* c, int* row_lines, int* col_pairs) {
   if (!c || !row_lines || !col_pairs) return fail(nullptr, FCSPH_EINVAL, "fcsph_get_tiling: bad argument");
   *row_lines = c->row_lines;
@@ -758,6 +785,26 @@ fcsph_status fcsph_autotune(fcsph_ctx* c, const fcsph_step_params* prm, int step
       }
     }
   if (st == FCSPH_OK) st = fcsph_set_tiling(c, best_r, best_c);
+  // FP32: then the CTA widths at the chosen tiling
+  int best_rt = c->row_threads, best_ct = c->col_threads;
+  const int widths[3] = {32, 64, 128};
+  for (int ri = 0; ri < 3 && st == FCSPH_OK && c->prec.fft_prec == FCSPH_F32; ++ri)
+    for (int ci = 0; ci < 3 && st == FCSPH_OK; ++ci) {
+      if ((st = fcsph_set_cta_threads(c, widths[ri], widths[ci])) != FCSPH_OK) break;
+      if ((st = isph_step(c, &s, 1, prm)) != FCSPH_OK) break;
+      if ((e = cudaEventRecord(e0, c->stream)) != cudaSuccess) { st = cuda_fail(c, e, "autotune event"); break; }
+      if ((st = isph_step(c, &s, steps, prm)) != FCSPH_OK) break;
+      if ((e = cudaEventRecord(e1, c->stream)) != cudaSuccess) { st = cuda_fail(c, e, "autotune event"); break; }
+      if ((e = cudaEventSynchronize(e1)) != cudaSuccess) { st = cuda_fail(c, e, "autotune sync"); break; }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) {
+        best = ms;
+        best_rt = widths[ri];
+        best_ct = widths[ci];
+      }
+    }
+  if (st == FCSPH_OK) st = fcsph_set_cta_threads(c, best_rt, best_ct);
   drop_graph(c);
   cudaStreamSynchronize(c->stream);
   if (e0) cudaEventDestroy(e0);

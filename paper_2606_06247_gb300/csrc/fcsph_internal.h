@@ -18,6 +18,9 @@ constexpr int kMaxStages = 12;
 // whose p - 1 factors into such stages uses Rader's algorithm; other lengths
 // with a larger prime factor go through Bluestein's chirp-z convolution.
 constexpr int kMaxDirectPrime = 31;
+// FP32 transform lines at least this long (shared-memory line length) get
+// multi-warp CTAs by default (fcsph_set_cta_threads).
+constexpr int kWideLine = 768;
 
 // Division by a fixed d (< 2^31 dividends) as (umulhi(x, m) + x) >> l.
 struct FastDiv {
@@ -154,8 +157,10 @@ struct fcsph_ctx {
   fcsph::FftPlan plan_z;                            // 3D: periodic z (operators and PPE)
   double* dE = nullptr;         // device [2][n_cont][2 n_match] (Dirichlet, Neumann)
   void* dEff = nullptr;         // the same in FP32 pairs (FP32x2 contexts)
-  int row_lines = 1;            // rows per CTA of the one-warp row passes
-  int col_pairs = 1;            // column pairs per CTA of the one-warp column passes
+  int row_lines = 1;            // rows per CTA of the row passes
+  int col_pairs = 1;            // column pairs per CTA of the column passes
+  int row_threads = 32;         // CTA width of the row (and z) passes: 32, 64, 128 (FP32 only > 32)
+  int col_threads = 32;         // CTA width of the column passes
   std::vector<double> hE[2];    // host copies
   double2* pool64 = nullptr;
   float2* pool32 = nullptr;

@@ -17,6 +17,7 @@
 // formed and inverted one at a time.
 #include <cstdio>
 #include <cstring>
+#include <type_traits>
 
 #include "fcsph_fft.cuh"
 #include "fcsph_internal.h"
@@ -26,15 +27,38 @@ using namespace fcsph;
 namespace {
 
 constexpr int kThreads = 256;
-// FFT kernels run one warp per CTA: every barrier of the shared-memory FFT is
-// then a warp barrier and no warp waits on another.
-constexpr int kFftThreads = 32;
+// FFT kernels are templated on their CTA width NT.  One warp per CTA is the
+// default: every barrier of the shared-memory FFT is then a warp barrier and
+// no warp waits on another.  FP32 kernels also come with 2- and 4-warp CTAs
+// (NT = 64, 128) that share one set of lines: long lines (~1000 points) then
+// hold less shared memory per warp, so more warps fit on an SM.
 // Minimum resident CTAs per SM asked of the register allocator: FP32-pair
 // code would otherwise take all 255 registers (8 one-warp CTAs per SM).
-template <typename T> struct MinCtas { static constexpr int v = 1; };
-template <> struct MinCtas<ff> { static constexpr int v = 12; };
-template <> struct MinCtas<double> { static constexpr int v = 12; };
-template <> struct MinCtas<float> { static constexpr int v = 16; };
+// One-warp CTAs: FP64 and FP32x2 <= 168 registers, FP32 <= 128; FP32 with
+// 64 threads <= 128, with 128 threads <= 64 (more resident warps beat the
+// few spills this costs in the column and row passes).
+template <typename T, int NT> struct MinCtas { static constexpr int v = 1; };
+template <> struct MinCtas<ff, 32> { static constexpr int v = 12; };
+template <> struct MinCtas<double, 32> { static constexpr int v = 12; };
+template <> struct MinCtas<float, 32> { static constexpr int v = 16; };
+template <> struct MinCtas<float, 64> { static constexpr int v = 8; };
+template <> struct MinCtas<float, 128> { static constexpr int v = 8; };
+// The line operator keeps three lines and its outputs live across the
+// transforms: at 128 threads it gets <= 128 registers (4 CTAs per SM) rather
+// than spilling at 64.
+template <typename T, int NT> struct LineMinCtas { static constexpr int v = MinCtas<T, NT>::v; };
+template <> struct LineMinCtas<float, 128> { static constexpr int v = 4; };
+
+// Calls f(std::integral_constant<int, NT>) for the CTA width nt: 32, 64 or
+// 128 threads for FP32 kernels, 32 for the others.
+template <typename T, typename F> cudaError_t with_width(int nt, F&& f) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (nt == 64) return f(std::integral_constant<int, 64>{});
+    if (nt == 128) return f(std::integral_constant<int, 128>{});
+  }
+  if (nt != 32) return cudaErrorInvalidValue;
+  return f(std::integral_constant<int, 32>{});
+}
 
 template <typename T> struct PoolOf;
 template <> struct PoolOf<double> { static const double2* get(const fcsph_ctx* c) { return c->pool64; } };
@@ -218,8 +242,8 @@ __device__ void col_gather_dct(typename CT<T>::t* lines, int Pp, int ls, const G
 
 // ---------------------------------------------------------------------------
 // Column forward: load nf real fields, FC (or DCT) + FFT, store spectra.
-template <typename T, typename U>
-__global__ void __launch_bounds__(kFftThreads, MinCtas<T>::v) k_col_fwd(GridDev g, const U* __restrict__ f0, const U* __restrict__ f1, const U* __restrict__ f2,
+template <typename T, typename U, int NT>
+__global__ void __launch_bounds__(NT, MinCtas<T, NT>::v) k_col_fwd(GridDev g, const U* __restrict__ f0, const U* __restrict__ f1, const U* __restrict__ f2,
                                                          const typename FcTab<T>::t* __restrict__ E, const __grid_constant__ FftPlan P,
                                                       const typename CT<T>::t* __restrict__ pool, int dct,
                                                       typename CT<T>::t* __restrict__ spec, size_t fstride,
@@ -284,8 +308,8 @@ template <typename T> __device__ __forceinline__ T kernel_poly(int family, T s) 
 // Shared memory: the nin input lines and their scratch (2 nin Rr lines; one
 // half holds the spectra, the other serves the outputs), plus Rr lines when
 // nin = 1.
-template <typename T>
-__global__ void __launch_bounds__(kFftThreads, MinCtas<T>::v) k_row_sym(GridDev g, const typename CT<T>::t* __restrict__ sp_in,
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT, MinCtas<T, NT>::v) k_row_sym(GridDev g, const typename CT<T>::t* __restrict__ sp_in,
                                                          typename CT<T>::t* __restrict__ sp_out, size_t fstride_in,
                                                          size_t bstride_in, size_t fstride_out, size_t bstride_out,
                                                          const __grid_constant__ RowOps ops,
@@ -372,8 +396,8 @@ struct LineOuts {
   void* out[4];
 };
 
-template <typename T, typename U>
-__global__ void __launch_bounds__(kFftThreads, MinCtas<T>::v) k_line_op(GridDev g, const U* __restrict__ f,
+template <typename T, typename U, int NT>
+__global__ void __launch_bounds__(NT, LineMinCtas<T, NT>::v) k_line_op(GridDev g, const U* __restrict__ f,
                                                                       long long ncols,
                                                                       const typename FcTab<T>::t* __restrict__ E,
                                                                       const __grid_constant__ FftPlan P,
@@ -436,8 +460,8 @@ __global__ void __launch_bounds__(kFftThreads, MinCtas<T>::v) k_line_op(GridDev 
 // z pass of the 3D channel: in the spectra [b][field][row][x][z] every run of
 // nz values (fixed b, field, row, x) is one periodic z line; L lines per CTA
 // are transformed in place, forward or (inv) unnormalised inverse.
-template <typename T>
-__global__ void __launch_bounds__(kFftThreads, MinCtas<T>::v) k_zlines(typename CT<T>::t* __restrict__ spec,
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT, MinCtas<T, NT>::v) k_zlines(typename CT<T>::t* __restrict__ spec,
                                                                       int lines_per_field, size_t fstride,
                                                                       size_t bstride, const __grid_constant__ FftPlan P,
                                                                       const typename CT<T>::t* __restrict__ pool, int L,
@@ -472,8 +496,8 @@ __global__ void __launch_bounds__(kFftThreads, MinCtas<T>::v) k_zlines(typename 
 // transform back, store.  3D: line q is the l = q / nz row at z index
 // kq = q % nz of the DFT-z-transformed coefficients, elements at stride nz,
 // and lam_z^2 joins the denominator.
-template <typename T>
-__global__ void __launch_bounds__(kFftThreads, MinCtas<T>::v) k_row_ppe(GridDev g, typename CT<T>::t* __restrict__ spec,
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT, MinCtas<T, NT>::v) k_row_ppe(GridDev g, typename CT<T>::t* __restrict__ spec,
                                                       size_t bstride, const __grid_constant__ FftPlan P,
                                                       const typename CT<T>::t* __restrict__ pool, int apply, int Rr,
                                                       int ls) {
@@ -581,8 +605,8 @@ struct EpiArgs {
 // .x / .y): the momentum terms accumulate there (u.grad + nu lap per
 // component), the other epilogues leave the new field there.  The fused
 // forward then transforms acc[f] (f < fwd_nf) with Z and S as its lines.
-template <typename T>
-__global__ void __launch_bounds__(kFftThreads, MinCtas<T>::v) k_col_inv(GridDev g, const typename CT<T>::t* __restrict__ spec,
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT, MinCtas<T, NT>::v) k_col_inv(GridDev g, const typename CT<T>::t* __restrict__ spec,
                                                          size_t fstride, size_t bstride, int nout, int nacc,
                                                          const __grid_constant__ FftPlan P,
                                                          const typename CT<T>::t* __restrict__ pool,
@@ -860,7 +884,7 @@ constexpr size_t kSmemMax = 227 * 1024;
 // Every kernel's dynamic shared-memory limit is raised once, at the first
 // context creation (init_kernel_attributes), so that no attribute call ever
 // happens while a stream is being captured; launches only check the size.
-template <typename K> cudaError_t set_smem(K, size_t bytes) {
+cudaError_t check_smem(size_t bytes) {
   return bytes > kSmemMax ? cudaErrorInvalidValue : cudaSuccess;
 }
 
@@ -896,31 +920,38 @@ cudaError_t init_kernel_attributes() {
   cudaError_t e = cudaSuccess;
 #define FCSPH_RAISE(K)                           \
   if ((e = raise_smem(K)) != cudaSuccess) return e;
-  FCSPH_RAISE((k_col_fwd<double, double>))
-  FCSPH_RAISE((k_col_fwd<float, double>))
-  FCSPH_RAISE((k_col_fwd<float, float>))
-  FCSPH_RAISE((k_col_fwd<ff, double>))
-  FCSPH_RAISE((k_row_sym<ff>))
-  FCSPH_RAISE((k_row_ppe<ff>))
-  FCSPH_RAISE((k_col_inv<ff>))
-  FCSPH_RAISE((k_row_sym<double>))
-  FCSPH_RAISE((k_row_sym<float>))
-  FCSPH_RAISE((k_row_ppe<double>))
-  FCSPH_RAISE((k_row_ppe<float>))
+  FCSPH_RAISE((k_col_fwd<double, double, 32>))
+  FCSPH_RAISE((k_col_fwd<ff, double, 32>))
+  FCSPH_RAISE((k_row_sym<ff, 32>))
+  FCSPH_RAISE((k_row_ppe<ff, 32>))
+  FCSPH_RAISE((k_col_inv<ff, 32>))
+  FCSPH_RAISE((k_zlines<ff, 32>))
+  FCSPH_RAISE((k_line_op<ff, double, 32>))
+  FCSPH_RAISE((k_row_sym<double, 32>))
+  FCSPH_RAISE((k_row_ppe<double, 32>))
+  FCSPH_RAISE((k_col_inv<double, 32>))
+  FCSPH_RAISE((k_zlines<double, 32>))
+  FCSPH_RAISE((k_line_op<double, double, 32>))
   FCSPH_RAISE((k_dft_lines<double, false>))
   FCSPH_RAISE((k_dft_lines<double, true>))
   FCSPH_RAISE((k_dft_lines<float, false>))
   FCSPH_RAISE((k_dft_lines<float, true>))
   FCSPH_RAISE((k_dft_lines<ff, false, double2>))
   FCSPH_RAISE((k_dft_lines<ff, true, double2>))
-  FCSPH_RAISE((k_col_inv<double>))
-  FCSPH_RAISE((k_line_op<double, double>))
-  FCSPH_RAISE((k_zlines<double>))
-  FCSPH_RAISE((k_zlines<ff>))
-  FCSPH_RAISE((k_zlines<float>))
-  FCSPH_RAISE((k_line_op<ff, double>))
-  FCSPH_RAISE((k_line_op<float, float>))
-  FCSPH_RAISE((k_col_inv<float>))
+  for (int nt : {32, 64, 128}) {
+    e = with_width<float>(nt, [](auto w) {
+      constexpr int NT = decltype(w)::value;
+      cudaError_t r = cudaSuccess;
+      if ((r = raise_smem(k_col_fwd<float, double, NT>)) != cudaSuccess) return r;
+      if ((r = raise_smem(k_col_fwd<float, float, NT>)) != cudaSuccess) return r;
+      if ((r = raise_smem(k_row_sym<float, NT>)) != cudaSuccess) return r;
+      if ((r = raise_smem(k_row_ppe<float, NT>)) != cudaSuccess) return r;
+      if ((r = raise_smem(k_col_inv<float, NT>)) != cudaSuccess) return r;
+      if ((r = raise_smem(k_zlines<float, NT>)) != cudaSuccess) return r;
+      return raise_smem(k_line_op<float, float, NT>);
+    });
+    if (e != cudaSuccess) return e;
+  }
 #undef FCSPH_RAISE
   return cudaSuccess;
 }
@@ -968,20 +999,23 @@ static cudaError_t col_fwd_t(fcsph_ctx* c, int prec, int nf, const void* const* 
   const int ls = P.line_len();
   const int Pp = c->col_pairs;
   const size_t smem = 2 * (size_t)ls * sizeof(typename CT<T>::t) * Pp;
-  cudaError_t e = set_smem(k_col_fwd<T, U>, smem);
+  cudaError_t e = check_smem(smem);
   if (e != cudaSuccess) return e;
   const auto* E = static_cast<const typename FcTab<T>::t*>(fc_table(c, prec, bc));
   dim3 grid((g.ncol + 2 * Pp - 1) / (2 * Pp), nf, g.batch);
   const size_t fstride = (size_t)g.rows * g.ncol;
   const size_t bstride = (dct ? 1 : spec_in_fields(c)) * fstride;
   ProfScope ps(c, FCSPH_PROF_COL_FWD);
-  k_col_fwd<T, U><<<grid, kFftThreads, smem, c->stream>>>(g, (const U*)fields[0],
-                                                          (const U*)(nf > 1 ? fields[1] : fields[0]),
-                                                          (const U*)(nf > 2 ? fields[2] : fields[0]), E, P,
-                                                          PoolOf<T>::get(c), dct, (typename CT<T>::t*)spec, fstride,
-                                                          bstride, Pp, ls);
-  c->launches++;
-  return cudaGetLastError();
+  return with_width<T>(c->col_threads, [&](auto w) {
+    constexpr int NT = decltype(w)::value;
+    k_col_fwd<T, U, NT><<<grid, NT, smem, c->stream>>>(g, (const U*)fields[0],
+                                                       (const U*)(nf > 1 ? fields[1] : fields[0]),
+                                                       (const U*)(nf > 2 ? fields[2] : fields[0]), E, P,
+                                                       PoolOf<T>::get(c), dct, (typename CT<T>::t*)spec, fstride,
+                                                       bstride, Pp, ls);
+    c->launches++;
+    return cudaGetLastError();
+  });
 }
 
 cudaError_t launch_col_fwd(fcsph_ctx* c, int prec, int nf, const void* const* fields, int fields_double, int bc,
@@ -1006,18 +1040,20 @@ static cudaError_t row_sym_t(fcsph_ctx* c, int prec, const void* sp_in, void* sp
   const int Rr = c->row_lines;
   const int nlines = 2 * ops.nin + (ops.nin == 1 ? 1 : 0);
   const size_t smem = (size_t)nlines * Rr * ls * sizeof(typename CT<T>::t);
-  cudaError_t e = set_smem(k_row_sym<T>, smem);
+  cudaError_t e = check_smem(smem);
   if (e != cudaSuccess) return e;
   const auto* E = static_cast<const typename FcTab<T>::t*>(fc_table(c, prec, bc));
   const size_t fs = (size_t)g.rows * g.ncol;
   dim3 grid((g.hy * g.nz + Rr - 1) / Rr, g.batch);
   ProfScope ps(c, kind);
-  k_row_sym<T><<<grid, kFftThreads, smem, c->stream>>>(g, (const typename CT<T>::t*)sp_in, (typename CT<T>::t*)sp_out,
-                                                       fs, spec_in_fields(c) * fs, fs, spec_out_fields(c) * fs, ops, E,
-                                                       c->plan_x, PoolOf<T>::get(c),
-                                                       scale, Rr, ls);
-  c->launches++;
-  return cudaGetLastError();
+  return with_width<T>(c->row_threads, [&](auto w) {
+    constexpr int NT = decltype(w)::value;
+    k_row_sym<T, NT><<<grid, NT, smem, c->stream>>>(g, (const typename CT<T>::t*)sp_in, (typename CT<T>::t*)sp_out,
+                                                    fs, spec_in_fields(c) * fs, fs, spec_out_fields(c) * fs, ops, E,
+                                                    c->plan_x, PoolOf<T>::get(c), scale, Rr, ls);
+    c->launches++;
+    return cudaGetLastError();
+  });
 }
 
 // One launch for any number of outputs: the outputs are formed and inverted
@@ -1036,7 +1072,7 @@ static cudaError_t line_op_t(fcsph_ctx* c, int prec, const void* f, const int* o
   const int ls = P.line_len();
   const int Pp = c->col_pairs;
   const size_t smem = 3 * (size_t)Pp * ls * sizeof(typename CT<T>::t);
-  cudaError_t e = set_smem(k_line_op<T, U>, smem);
+  cudaError_t e = check_smem(smem);
   if (e != cudaSuccess) return e;
   LineOuts lo;
   memset(&lo, 0, sizeof(lo));
@@ -1049,10 +1085,13 @@ static cudaError_t line_op_t(fcsph_ctx* c, int prec, const void* f, const int* o
   const long long blocks = (ncols + 2 * Pp - 1) / (2 * Pp);
   const auto* E = static_cast<const typename FcTab<T>::t*>(fc_table(c, prec, bc));
   ProfScope ps(c, FCSPH_PROF_COL_OUT);
-  k_line_op<T, U><<<(unsigned)blocks, kFftThreads, smem, c->stream>>>(g, (const U*)f, ncols, E, P, PoolOf<T>::get(c),
-                                                                      lo, Pp, ls);
-  c->launches++;
-  return cudaGetLastError();
+  return with_width<T>(c->col_threads, [&](auto w) {
+    constexpr int NT = decltype(w)::value;
+    k_line_op<T, U, NT><<<(unsigned)blocks, NT, smem, c->stream>>>(g, (const U*)f, ncols, E, P, PoolOf<T>::get(c),
+                                                                   lo, Pp, ls);
+    c->launches++;
+    return cudaGetLastError();
+  });
 }
 
 cudaError_t launch_line_op(fcsph_ctx* c, const void* f, const int* ops, int nout, int bc, void* const* outs) {
@@ -1071,15 +1110,18 @@ static cudaError_t zpass_t(fcsph_ctx* c, void* spec, int nf, size_t bstride, int
   if (L < 1) L = 1;
   if (L > 8) L = 8;
   const size_t smem = 2 * (size_t)L * ls * sizeof(typename CT<T>::t);
-  cudaError_t e = set_smem(k_zlines<T>, smem);
+  cudaError_t e = check_smem(smem);
   if (e != cudaSuccess) return e;
   const int lines = rows_used * g.nx;
   dim3 grid((lines + L - 1) / L, nf, g.batch);
   ProfScope ps(c, FCSPH_PROF_OTHER);
-  k_zlines<T><<<grid, kFftThreads, smem, c->stream>>>((typename CT<T>::t*)spec, lines, (size_t)g.rows * g.ncol, bstride,
-                                                      P, PoolOf<T>::get(c), L, ls, inv);
-  c->launches++;
-  return cudaGetLastError();
+  return with_width<T>(c->row_threads, [&](auto w) {
+    constexpr int NT = decltype(w)::value;
+    k_zlines<T, NT><<<grid, NT, smem, c->stream>>>((typename CT<T>::t*)spec, lines, (size_t)g.rows * g.ncol, bstride,
+                                                   P, PoolOf<T>::get(c), L, ls, inv);
+    c->launches++;
+    return cudaGetLastError();
+  });
 }
 
 // 3D: z transforms of nf fields of every instance (fields 0..nf-1 of the
@@ -1113,12 +1155,15 @@ static cudaError_t col_inv_common(fcsph_ctx* c, int epi, const void* spec, int n
   static const int kinds[7] = {FCSPH_PROF_COL_OUT, FCSPH_PROF_COL_MOM, FCSPH_PROF_COL_DIV, FCSPH_PROF_COL_CORR,
                                FCSPH_PROF_COL_PPE, FCSPH_PROF_COL_PPE, FCSPH_PROF_COL_PPE};
   ProfScope ps(c, kinds[epi]);
-  cudaError_t e = set_smem(k_col_inv<T>, smem);
+  cudaError_t e = check_smem(smem);
   if (e != cudaSuccess) return e;
-  k_col_inv<T><<<grid, kFftThreads, smem, c->stream>>>(g, (const typename CT<T>::t*)spec, fs, bs, nout, nacc, P, pool,
-                                                       ea, Pp, ls, epi);
-  c->launches++;
-  return cudaGetLastError();
+  return with_width<T>(c->col_threads, [&](auto w) {
+    constexpr int NT = decltype(w)::value;
+    k_col_inv<T, NT><<<grid, NT, smem, c->stream>>>(g, (const typename CT<T>::t*)spec, fs, bs, nout, nacc, P, pool,
+                                                    ea, Pp, ls, epi);
+    c->launches++;
+    return cudaGetLastError();
+  });
 }
 
 static cudaError_t col_inv(fcsph_ctx* c, int prec, int epi, const void* spec, int nout, EpiArgs& ea) {
@@ -1146,14 +1191,17 @@ static cudaError_t row_ppe_t(fcsph_ctx* c, void* spec, int apply) {
   const int ls = c->plan_px.line_len();
   const int Rr = c->row_lines;
   const size_t smem = 2 * (size_t)ls * sizeof(typename CT<T>::t) * Rr;
-  cudaError_t e = set_smem(k_row_ppe<T>, smem);
+  cudaError_t e = check_smem(smem);
   if (e != cudaSuccess) return e;
   dim3 grid((g.ny * g.nz + Rr - 1) / Rr, g.batch);
   ProfScope ps(c, FCSPH_PROF_ROW_PPE);
-  k_row_ppe<T><<<grid, kFftThreads, smem, c->stream>>>(g, (typename CT<T>::t*)spec, (size_t)g.rows * g.ncol, c->plan_px,
-                                                       PoolOf<T>::get(c), apply, Rr, ls);
-  c->launches++;
-  return cudaGetLastError();
+  return with_width<T>(c->row_threads, [&](auto w) {
+    constexpr int NT = decltype(w)::value;
+    k_row_ppe<T, NT><<<grid, NT, smem, c->stream>>>(g, (typename CT<T>::t*)spec, (size_t)g.rows * g.ncol, c->plan_px,
+                                                    PoolOf<T>::get(c), apply, Rr, ls);
+    c->launches++;
+    return cudaGetLastError();
+  });
 }
 
 cudaError_t launch_row_ppe(fcsph_ctx* c, int prec, void* spec, int apply) {
@@ -1259,11 +1307,11 @@ cudaError_t dft_lines_t(int n, int nlines, int dir, const void* in, void* out, c
   const int blocks = (nlines + L - 1) / L;
   cudaError_t e;
   if (dir < 0) {
-    if ((e = set_smem(k_dft_lines<T, false, IO>, smem)) != cudaSuccess) return e;
+    if ((e = check_smem(smem)) != cudaSuccess) return e;
     k_dft_lines<T, false, IO><<<blocks, kThreads, smem, st>>>(n, nlines, (const IO*)in, (IO*)out, plan,
                                                               (const V*)pool, L, ls);
   } else {
-    if ((e = set_smem(k_dft_lines<T, true, IO>, smem)) != cudaSuccess) return e;
+    if ((e = check_smem(smem)) != cudaSuccess) return e;
     k_dft_lines<T, true, IO><<<blocks, kThreads, smem, st>>>(n, nlines, (const IO*)in, (IO*)out, plan,
                                                              (const V*)pool, L, ls);
   }

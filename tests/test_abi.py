@@ -64,6 +64,8 @@ def test_bad_arguments_are_rejected(lib):
     assert L.fcsph_set_tiling(None, 1, 1) == 1
     r, c = ctypes.c_int(), ctypes.c_int()
     assert L.fcsph_get_tiling(None, ctypes.byref(r), ctypes.byref(c)) == 1
+    assert L.fcsph_set_cta_threads(None, 32, 32) == 1
+    assert L.fcsph_get_cta_threads(None, ctypes.byref(r), ctypes.byref(c)) == 1
     prm = lib.fcsph_step_params(1e-3, 1.0, 1e-3, 0.0, 0.0, 0.0, 1.0, 1, 1, None, None)
     assert L.fcsph_autotune(None, ctypes.byref(prm), 3, None) == 1
     assert L.fcsph_sync(None) == 1

@@ -1,7 +1,8 @@
-"""Launch-shape selection (fcsph_set_tiling, fcsph_autotune): the tiling only
-changes which CTA carries which line, never the arithmetic of a line, so every
-tiling gives bitwise the same step; the autotuner keeps a valid tiling and
-leaves the caller's state alone."""
+"""Launch-shape selection (fcsph_set_tiling, fcsph_set_cta_threads,
+fcsph_autotune): the tiling and the CTA width only change which CTA and which
+thread carry which line and butterfly, never the arithmetic of a line, so
+every launch shape gives bitwise the same results; the autotuner keeps a
+valid shape and leaves the caller's state alone."""
 import numpy as np
 import pytest
 
@@ -77,3 +78,97 @@ def test_set_tiling_rejects_bad_shapes():
     with pytest.raises(b.FcsphError) as e:
         big.set_tiling(1, 8)
     assert e.value.status == 6
+
+
+WIDTHS = [(32, 32), (64, 128), (128, 64), (64, 64), (128, 128)]
+
+
+def _same_across_widths(ctx, run):
+    ref = None
+    for w in WIDTHS:
+        ctx.set_cta_threads(*w)
+        assert ctx.get_cta_threads() == w
+        out = run()
+        if ref is None:
+            ref = out
+        else:
+            for a, r in zip(out, ref):
+                np.testing.assert_array_equal(a, r, err_msg=f"widths {w}")
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("nx,ny,x_walls", [(37, 30, True), (64, 256, False), (40, 512, False)])
+def test_every_cta_width_gives_the_same_fp32_results(nx, ny, x_walls):
+    """FP32 operators, line operator, pressure solve and RK3 steps: bitwise
+    equal for every pair of CTA widths.  The lengths cover a direct plan
+    (55 = 5 * 11), Rader (281) and Bluestein (537) columns."""
+    torch = torch_cuda()
+    b = binding()
+    batch = 2
+    lx, ly = grid_lengths(nx, ny, x_walls)
+    fam = "G8" if x_walls else "G4"
+    ctx = b.Context(nx, ny, lx, ly, x_walls=x_walls, batch=batch, family=fam, h_over_dx=1.3, prec="f32")
+    rng = np.random.default_rng(5)
+    f = torch.tensor(rng.standard_normal((batch, nx, ny)), dtype=torch.float32, device="cuda")
+    rhs = f - f.mean(dim=(1, 2), keepdim=True)
+
+    def ops():
+        outs = [torch.empty_like(f) for _ in range(4)]
+        ctx.spectral_op(f, ["W", "DX", "DY", "LAP"], outs)
+        lo = [torch.empty_like(f) for _ in range(2)]
+        ctx.line_op(f, ["DY", "LAP"], lo)
+        phi = torch.empty_like(f)
+        ctx.ppe_solve(rhs, phi)
+        ctx.sync()
+        return [x.cpu().numpy() for x in outs + lo + [phi]]
+
+    _same_across_widths(ctx, ops)
+    prm = dict(CAVITY) if x_walls else dict(nu=0.1, rho=1.0, dt=1e-3, force=(0.8, 0.0), scheme="rk3")
+
+    def steps():
+        st = _state(torch, nx, ny, batch, 7)
+        ctx.isph_step(*st, 2, use_graph=True, **prm)
+        ctx.sync()
+        return [x.cpu().numpy() for x in st]
+
+    _same_across_widths(ctx, steps)
+
+
+@pytest.mark.gpu
+def test_every_cta_width_gives_the_same_fp32_3d_step():
+    torch = torch_cuda()
+    b = binding()
+    nx, nz, ny = 8, 6, 20
+    dy = 1.0 / (ny - 1)
+    ctx = b.Context(nx, ny, nx * dy, 1.0, family="G4", h_over_dx=1.3, prec="f32", nz=nz, lz=nz * dy)
+    rng = np.random.default_rng(9)
+    init = [1e-3 * rng.standard_normal((1, nx, nz, ny)) for _ in range(3)]
+
+    def steps():
+        u, v, w = (to_dev(a) for a in init)
+        p, fu, fv, fw = (torch.zeros_like(u) for _ in range(4))
+        ctx.isph_step(u, v, p, fu, fv, 2, w=w, fw=fw, nu=0.1, rho=1.0, dt=1e-3, force=(0.8, 0.0, 0.1), scheme="rk3")
+        ctx.sync()
+        return [x.cpu().numpy() for x in (u, v, w, p)]
+
+    _same_across_widths(ctx, steps)
+
+
+@pytest.mark.gpu
+def test_cta_widths_are_checked():
+    torch_cuda()
+    b = binding()
+    big = b.Context(1024, 1024, 1024 / 1023, 1.0, batch=1, prec="f32")
+    assert big.get_cta_threads() == (64, 128)      # FP32, lines of >= 768 points
+    small = b.Context(64, 64, 64 / 63, 1.0, batch=1, prec="f32")
+    assert small.get_cta_threads() == (32, 32)
+    for bad in [(0, 32), (32, 96), (256, 32)]:
+        with pytest.raises(b.FcsphError) as e:
+            small.set_cta_threads(*bad)
+        assert e.value.status == 1
+    for prec in ("f64", "f32x2"):
+        ctx = b.Context(64, 64, 64 / 63, 1.0, batch=1, prec=prec)
+        assert ctx.get_cta_threads() == (32, 32)
+        with pytest.raises(b.FcsphError) as e:
+            ctx.set_cta_threads(64, 32)
+        assert e.value.status == 6
