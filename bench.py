@@ -58,7 +58,8 @@ def parse():
                          "submitted together; serve: a Poisson request stream (2D part)")
     ap.add_argument("--serve-seconds", type=float, default=1.0)
     ap.add_argument("--profile-case", action="store_true",
-                    help="no timing: 2 eager RK3 steps of the workload (for ncu captures on a small batch)")
+                    help="no timing: 2 eager RK3 steps of the cavity, or (--workload planes) 3 spectral_op calls "
+                         "on --batch planes of 1024^2, for ncu captures on a small batch")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -861,12 +862,28 @@ def run_channel3d(args):
 
 def run_profile_case(args):
     """Two eager RK3 steps of the workload with every kernel launched on its own
-    (no graph), for kernel-level captures; prints the launch count."""
+    (no graph), for kernel-level captures; prints the launch count.  With
+    --workload planes: three spectral_op calls (DX, DY, LAP) on `batch` planes
+    of 1024^2 (n_cont 26, FP32, default CTA widths)."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
     from paper_2606_06247_gb300 import binding as b
     B = args.batch
+    if args.workload == "planes":
+        import numpy as np
+        from paper_2606_06247_gb300 import inputs
+        n = 1024
+        base = inputs.band_limited_planes(4, n, n, seed=12346, n_modes=64, max_mode=64)
+        f = torch.tensor(np.tile(base, ((B + 3) // 4, 1, 1))[:B], dtype=torch.float32, device="cuda")
+        outs = [torch.empty_like(f) for _ in range(3)]
+        ctx = b.Context(n, n, n / (n - 1), 1.0, batch=B, n_cont=26, family="G4", h_over_dx=1.3, prec="f32")
+        for _ in range(3):
+            ctx.spectral_op(f, ["DX", "DY", "LAP"], outs)
+        ctx.sync()
+        print(json.dumps({"profile_case": "planes", "batch": B, "cta_threads": ctx.get_cta_threads(),
+                          "launches": ctx.launch_count}))
+        return
     ctx = b.Context(N, N, 1.0, 1.0, x_walls=True, batch=B, n_match=N_MATCH, n_cont=N_CONT, family=FAMILY,
                     h_over_dx=HDX, prec=args.prec, refine=args.refine if args.prec == "f32" else 0)
     z = torch.zeros((B, N, N), dtype=torch.float64, device="cuda")
