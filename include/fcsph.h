@@ -216,22 +216,25 @@ fcsph_status fcsph_set_tiling(fcsph_ctx* ctx, int row_lines, int col_pairs);
 fcsph_status fcsph_get_tiling(const fcsph_ctx* ctx, int* row_lines, int* col_pairs);
 
 /* CTA width of the FFT passes: row_threads threads per CTA of the x (and z)
- * passes, col_threads per CTA of the wall-normal passes, each 32, 64 or 128;
- * the threads of a CTA share its lines.  Wider CTAs hold less shared memory
- * per warp, which pays for long FP32 lines; FP64 and FP32x2 contexts run one
- * warp per CTA only (anything but 32, 32: FCSPH_EUNSUPPORTED).  The result
- * does not depend on the widths.  FP32 contexts start at 64 (row) and 128
- * (column) threads where that pass's transform lines hold >= 768 points, else
- * 32.  Takes effect at the next call (a captured isph_step graph is dropped).
- * Engineering choice of this library; the paper has no counterpart. */
+ * passes, col_threads per CTA of the wall-normal passes, each 32, 64 or 128
+ * (else FCSPH_EINVAL); the threads of a CTA share its lines.  Wider CTAs
+ * carry each line with more threads, which pays when a pass has too few
+ * lines to fill the GPU, and hold less shared memory per warp, which pays for
+ * long FP32 lines.  The result does not depend on the widths.  A context
+ * starts, per pass, at 128 threads if its one-warp CTAs (rows or column pairs
+ * of all instances) would fill at most a quarter of the GPU's 152 x 12, at 64
+ * if at most half, else at 32; FP32 passes whose transform lines hold >= 768
+ * points take at least 64 (row) and 128 (column) threads.  Takes effect at
+ * the next call (a captured isph_step graph is dropped).  Engineering choice
+ * of this library; the paper has no counterpart. */
 fcsph_status fcsph_set_cta_threads(fcsph_ctx* ctx, int row_threads, int col_threads);
 fcsph_status fcsph_get_cta_threads(const fcsph_ctx* ctx, int* row_threads, int* col_threads);
 
 /* Autotuner: times `steps` isph_step calls with *prm for every tiling with
  * row_lines, col_pairs in {1, 2, 4} that fits, on a zero state the call
  * allocates and frees (5 fields of the context's batch), then keeps the
- * fastest (2D: 5 fields, 3D: 7); FP32 contexts then time every pair of CTA
- * widths in {32, 64, 128} at that tiling and keep the fastest.  best_ms_out
+ * fastest (2D: 5 fields, 3D: 7); then it times every pair of CTA widths in
+ * {32, 64, 128} at that tiling and keeps the fastest.  best_ms_out
  * (nullable, host): its milliseconds per step.
  * Synchronises the context's stream.  Engineering choice of this library;
  * the paper has no counterpart. */

@@ -2,6 +2,7 @@
 // and the call sequences of fc_extend / spectral_op / spectral_div /
 // ppe_solve / isph_step (Sec. 5.2).  All arithmetic runs in the kernels of
 // fcsph_kernels.cu; this file only validates, allocates and sequences.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -109,6 +110,16 @@ FftPlan plan_for(int n, Pool* pool, std::vector<Fill>* fills) {
     fills->push_back(f);
   }
   return P;
+}
+
+// Default CTA width of a pass of `ctas` one-warp CTAs: 12 such CTAs fit on
+// each of the 152 SMs; a pass that fills a quarter of that or less gets
+// 4-warp CTAs, half or less 2-warp CTAs.
+int default_width(long long ctas) {
+  const long long full = 152LL * 12;
+  if (4 * ctas <= full) return 128;
+  if (2 * ctas <= full) return 64;
+  return 32;
 }
 
 RowOps ops_none() {
@@ -234,12 +245,19 @@ fcsph_status fcsph_create(const fcsph_grid* grid, const fcsph_fc* fc, const fcsp
   g.ey_off = pool.add(gauss_axis(g.my, g.dy, g.h, g.hy), std::vector<double>(g.hy, 0.0));
   g.ez_off = pool.add(gauss_axis(nz, g.dz, g.h, nz), std::vector<double>(nz, 0.0));
   if (nz > 1) c->plan_z = plan_for(nz, &pool, &fills);
-  if (prec->fft_prec == FCSPH_F32) {
-    // FP32 lines of ~1000 points and more: one warp per CTA leaves too few
-    // warps per SM (shared memory bound); share each CTA's lines among 2
-    // (row passes) or 4 (column passes) warps.
-    c->row_threads = c->plan_x.line_len() >= kWideLine ? 64 : 32;
-    c->col_threads = c->plan_y.line_len() >= kWideLine ? 128 : 32;
+  {
+    // Passes with fewer one-warp CTAs than the GPU holds leave SMs idle: give
+    // each CTA 2 or 4 warps instead.  FP32 lines of ~1000 points and more:
+    // one warp per CTA leaves too few warps per SM (shared memory bound), so
+    // those passes share each CTA's lines among 2 (row) or 4 (column) warps.
+    const long long col_ctas = (long long)((g.ncol + 1) / 2) * g.batch;
+    const long long row_ctas = (long long)g.hy * g.nz * g.batch;
+    c->row_threads = default_width(row_ctas);
+    c->col_threads = default_width(col_ctas);
+    if (prec->fft_prec == FCSPH_F32) {
+      if (c->plan_x.line_len() >= kWideLine) c->row_threads = std::max(c->row_threads, 64);
+      if (c->plan_y.line_len() >= kWideLine) c->col_threads = 128;
+    }
   }
   {
     // Eq. 33 eigenvalues: DFT lam_k = 2 pi kappa / Lx (kappa signed, Nyquist positive), DCT-I lam = pi k / L
@@ -725,8 +743,6 @@ fcsph_status fcsph_set_cta_threads(fcsph_ctx* c, int row_threads, int col_thread
   auto ok = [](int t) { return t == 32 || t == 64 || t == 128; };
   if (!ok(row_threads) || !ok(col_threads))
     return fail(c, FCSPH_EINVAL, "fcsph_set_cta_threads: widths must be 32, 64 or 128");
-  if (c->prec.fft_prec != FCSPH_F32 && (row_threads != 32 || col_threads != 32))
-    return fail(c, FCSPH_EUNSUPPORTED, "fcsph_set_cta_threads: only FP32 contexts have wide CTAs");
   if (row_threads != c->row_threads || col_threads != c->col_threads) drop_graph(c);
   c->row_threads = row_threads;
   c->col_threads = col_threads;
@@ -785,10 +801,10 @@ fcsph_status fcsph_autotune(fcsph_ctx* c, const fcsph_step_params* prm, int step
       }
     }
   if (st == FCSPH_OK) st = fcsph_set_tiling(c, best_r, best_c);
-  // FP32: then the CTA widths at the chosen tiling
+  // then the CTA widths at the chosen tiling
   int best_rt = c->row_threads, best_ct = c->col_threads;
   const int widths[3] = {32, 64, 128};
-  for (int ri = 0; ri < 3 && st == FCSPH_OK && c->prec.fft_prec == FCSPH_F32; ++ri)
+  for (int ri = 0; ri < 3 && st == FCSPH_OK; ++ri)
     for (int ci = 0; ci < 3 && st == FCSPH_OK; ++ci) {
       if ((st = fcsph_set_cta_threads(c, widths[ri], widths[ci])) != FCSPH_OK) break;
       if ((st = isph_step(c, &s, 1, prm)) != FCSPH_OK) break;

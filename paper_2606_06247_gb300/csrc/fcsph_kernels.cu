@@ -27,19 +27,19 @@ using namespace fcsph;
 namespace {
 
 constexpr int kThreads = 256;
-// FFT kernels are templated on their CTA width NT.  One warp per CTA is the
-// default: every barrier of the shared-memory FFT is then a warp barrier and
-// no warp waits on another.  FP32 kernels also come with 2- and 4-warp CTAs
-// (NT = 64, 128) that share one set of lines: long lines (~1000 points) then
-// hold less shared memory per warp, so more warps fit on an SM.
+// FFT kernels are templated on their CTA width NT = 32, 64 or 128 threads;
+// the threads of a CTA share its lines.  One warp per CTA keeps every barrier
+// of the shared-memory FFT a warp barrier, and is fastest when the pass has
+// CTAs enough to fill the GPU.  Wider CTAs carry each line with more threads:
+// they cut the latency of passes with few lines (small grids and batches),
+// and for long FP32 lines (~1000 points) they hold less shared memory per
+// warp, so more warps fit on an SM.
 // Minimum resident CTAs per SM asked of the register allocator: FP32-pair
 // code would otherwise take all 255 registers (8 one-warp CTAs per SM).
-// One-warp CTAs: FP64 and FP32x2 <= 168 registers, FP32 <= 128; FP32 with
-// 64 threads <= 128, with 128 threads <= 64 (more resident warps beat the
-// few spills this costs in the column and row passes).
-template <typename T, int NT> struct MinCtas { static constexpr int v = 1; };
-template <> struct MinCtas<ff, 32> { static constexpr int v = 12; };
-template <> struct MinCtas<double, 32> { static constexpr int v = 12; };
+// FP64 and FP32x2: <= 168 registers at every width; FP32: <= 128 at 32 and
+// 64 threads, <= 64 at 128 (more resident warps beat the few spills this
+// costs in the column and row passes).
+template <typename T, int NT> struct MinCtas { static constexpr int v = 384 / NT; };
 template <> struct MinCtas<float, 32> { static constexpr int v = 16; };
 template <> struct MinCtas<float, 64> { static constexpr int v = 8; };
 template <> struct MinCtas<float, 128> { static constexpr int v = 8; };
@@ -49,13 +49,10 @@ template <> struct MinCtas<float, 128> { static constexpr int v = 8; };
 template <typename T, int NT> struct LineMinCtas { static constexpr int v = MinCtas<T, NT>::v; };
 template <> struct LineMinCtas<float, 128> { static constexpr int v = 4; };
 
-// Calls f(std::integral_constant<int, NT>) for the CTA width nt: 32, 64 or
-// 128 threads for FP32 kernels, 32 for the others.
-template <typename T, typename F> cudaError_t with_width(int nt, F&& f) {
-  if constexpr (std::is_same<T, float>::value) {
-    if (nt == 64) return f(std::integral_constant<int, 64>{});
-    if (nt == 128) return f(std::integral_constant<int, 128>{});
-  }
+// Calls f(std::integral_constant<int, NT>) for the CTA width nt (32, 64, 128).
+template <typename F> cudaError_t with_width(int nt, F&& f) {
+  if (nt == 64) return f(std::integral_constant<int, 64>{});
+  if (nt == 128) return f(std::integral_constant<int, 128>{});
   if (nt != 32) return cudaErrorInvalidValue;
   return f(std::integral_constant<int, 32>{});
 }
@@ -920,18 +917,6 @@ cudaError_t init_kernel_attributes() {
   cudaError_t e = cudaSuccess;
 #define FCSPH_RAISE(K)                           \
   if ((e = raise_smem(K)) != cudaSuccess) return e;
-  FCSPH_RAISE((k_col_fwd<double, double, 32>))
-  FCSPH_RAISE((k_col_fwd<ff, double, 32>))
-  FCSPH_RAISE((k_row_sym<ff, 32>))
-  FCSPH_RAISE((k_row_ppe<ff, 32>))
-  FCSPH_RAISE((k_col_inv<ff, 32>))
-  FCSPH_RAISE((k_zlines<ff, 32>))
-  FCSPH_RAISE((k_line_op<ff, double, 32>))
-  FCSPH_RAISE((k_row_sym<double, 32>))
-  FCSPH_RAISE((k_row_ppe<double, 32>))
-  FCSPH_RAISE((k_col_inv<double, 32>))
-  FCSPH_RAISE((k_zlines<double, 32>))
-  FCSPH_RAISE((k_line_op<double, double, 32>))
   FCSPH_RAISE((k_dft_lines<double, false>))
   FCSPH_RAISE((k_dft_lines<double, true>))
   FCSPH_RAISE((k_dft_lines<float, false>))
@@ -939,16 +924,28 @@ cudaError_t init_kernel_attributes() {
   FCSPH_RAISE((k_dft_lines<ff, false, double2>))
   FCSPH_RAISE((k_dft_lines<ff, true, double2>))
   for (int nt : {32, 64, 128}) {
-    e = with_width<float>(nt, [](auto w) {
+    e = with_width(nt, [](auto w) {
       constexpr int NT = decltype(w)::value;
       cudaError_t r = cudaSuccess;
+      if ((r = raise_smem(k_col_fwd<double, double, NT>)) != cudaSuccess) return r;
+      if ((r = raise_smem(k_col_fwd<ff, double, NT>)) != cudaSuccess) return r;
       if ((r = raise_smem(k_col_fwd<float, double, NT>)) != cudaSuccess) return r;
       if ((r = raise_smem(k_col_fwd<float, float, NT>)) != cudaSuccess) return r;
+      if ((r = raise_smem(k_line_op<double, double, NT>)) != cudaSuccess) return r;
+      if ((r = raise_smem(k_line_op<ff, double, NT>)) != cudaSuccess) return r;
+      if ((r = raise_smem(k_line_op<float, float, NT>)) != cudaSuccess) return r;
+      if ((r = raise_smem(k_row_sym<double, NT>)) != cudaSuccess) return r;
+      if ((r = raise_smem(k_row_sym<ff, NT>)) != cudaSuccess) return r;
       if ((r = raise_smem(k_row_sym<float, NT>)) != cudaSuccess) return r;
+      if ((r = raise_smem(k_row_ppe<double, NT>)) != cudaSuccess) return r;
+      if ((r = raise_smem(k_row_ppe<ff, NT>)) != cudaSuccess) return r;
       if ((r = raise_smem(k_row_ppe<float, NT>)) != cudaSuccess) return r;
+      if ((r = raise_smem(k_col_inv<double, NT>)) != cudaSuccess) return r;
+      if ((r = raise_smem(k_col_inv<ff, NT>)) != cudaSuccess) return r;
       if ((r = raise_smem(k_col_inv<float, NT>)) != cudaSuccess) return r;
-      if ((r = raise_smem(k_zlines<float, NT>)) != cudaSuccess) return r;
-      return raise_smem(k_line_op<float, float, NT>);
+      if ((r = raise_smem(k_zlines<double, NT>)) != cudaSuccess) return r;
+      if ((r = raise_smem(k_zlines<ff, NT>)) != cudaSuccess) return r;
+      return raise_smem(k_zlines<float, NT>);
     });
     if (e != cudaSuccess) return e;
   }
@@ -1006,7 +1003,7 @@ static cudaError_t col_fwd_t(fcsph_ctx* c, int prec, int nf, const void* const* 
   const size_t fstride = (size_t)g.rows * g.ncol;
   const size_t bstride = (dct ? 1 : spec_in_fields(c)) * fstride;
   ProfScope ps(c, FCSPH_PROF_COL_FWD);
-  return with_width<T>(c->col_threads, [&](auto w) {
+  return with_width(c->col_threads, [&](auto w) {
     constexpr int NT = decltype(w)::value;
     k_col_fwd<T, U, NT><<<grid, NT, smem, c->stream>>>(g, (const U*)fields[0],
                                                        (const U*)(nf > 1 ? fields[1] : fields[0]),
@@ -1046,7 +1043,7 @@ static cudaError_t row_sym_t(fcsph_ctx* c, int prec, const void* sp_in, void* sp
   const size_t fs = (size_t)g.rows * g.ncol;
   dim3 grid((g.hy * g.nz + Rr - 1) / Rr, g.batch);
   ProfScope ps(c, kind);
-  return with_width<T>(c->row_threads, [&](auto w) {
+  return with_width(c->row_threads, [&](auto w) {
     constexpr int NT = decltype(w)::value;
     k_row_sym<T, NT><<<grid, NT, smem, c->stream>>>(g, (const typename CT<T>::t*)sp_in, (typename CT<T>::t*)sp_out,
                                                     fs, spec_in_fields(c) * fs, fs, spec_out_fields(c) * fs, ops, E,
@@ -1085,7 +1082,7 @@ static cudaError_t line_op_t(fcsph_ctx* c, int prec, const void* f, const int* o
   const long long blocks = (ncols + 2 * Pp - 1) / (2 * Pp);
   const auto* E = static_cast<const typename FcTab<T>::t*>(fc_table(c, prec, bc));
   ProfScope ps(c, FCSPH_PROF_COL_OUT);
-  return with_width<T>(c->col_threads, [&](auto w) {
+  return with_width(c->col_threads, [&](auto w) {
     constexpr int NT = decltype(w)::value;
     k_line_op<T, U, NT><<<(unsigned)blocks, NT, smem, c->stream>>>(g, (const U*)f, ncols, E, P, PoolOf<T>::get(c),
                                                                    lo, Pp, ls);
@@ -1115,7 +1112,7 @@ static cudaError_t zpass_t(fcsph_ctx* c, void* spec, int nf, size_t bstride, int
   const int lines = rows_used * g.nx;
   dim3 grid((lines + L - 1) / L, nf, g.batch);
   ProfScope ps(c, FCSPH_PROF_OTHER);
-  return with_width<T>(c->row_threads, [&](auto w) {
+  return with_width(c->row_threads, [&](auto w) {
     constexpr int NT = decltype(w)::value;
     k_zlines<T, NT><<<grid, NT, smem, c->stream>>>((typename CT<T>::t*)spec, lines, (size_t)g.rows * g.ncol, bstride,
                                                    P, PoolOf<T>::get(c), L, ls, inv);
@@ -1157,7 +1154,7 @@ static cudaError_t col_inv_common(fcsph_ctx* c, int epi, const void* spec, int n
   ProfScope ps(c, kinds[epi]);
   cudaError_t e = check_smem(smem);
   if (e != cudaSuccess) return e;
-  return with_width<T>(c->col_threads, [&](auto w) {
+  return with_width(c->col_threads, [&](auto w) {
     constexpr int NT = decltype(w)::value;
     k_col_inv<T, NT><<<grid, NT, smem, c->stream>>>(g, (const typename CT<T>::t*)spec, fs, bs, nout, nacc, P, pool,
                                                     ea, Pp, ls, epi);
@@ -1195,7 +1192,7 @@ static cudaError_t row_ppe_t(fcsph_ctx* c, void* spec, int apply) {
   if (e != cudaSuccess) return e;
   dim3 grid((g.ny * g.nz + Rr - 1) / Rr, g.batch);
   ProfScope ps(c, FCSPH_PROF_ROW_PPE);
-  return with_width<T>(c->row_threads, [&](auto w) {
+  return with_width(c->row_threads, [&](auto w) {
     constexpr int NT = decltype(w)::value;
     k_row_ppe<T, NT><<<grid, NT, smem, c->stream>>>(g, (typename CT<T>::t*)spec, (size_t)g.rows * g.ncol, c->plan_px,
                                                     PoolOf<T>::get(c), apply, Rr, ls);

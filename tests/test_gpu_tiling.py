@@ -97,19 +97,21 @@ def _same_across_widths(ctx, run):
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("prec", ["f32", "f32x2", "f64"])
 @pytest.mark.parametrize("nx,ny,x_walls", [(37, 30, True), (64, 256, False), (40, 512, False)])
-def test_every_cta_width_gives_the_same_fp32_results(nx, ny, x_walls):
-    """FP32 operators, line operator, pressure solve and RK3 steps: bitwise
-    equal for every pair of CTA widths.  The lengths cover a direct plan
-    (55 = 5 * 11), Rader (281) and Bluestein (537) columns."""
+def test_every_cta_width_gives_the_same_results(nx, ny, x_walls, prec):
+    """Operators, line operator, pressure solve and RK3 steps: bitwise equal
+    for every pair of CTA widths, in every precision.  The lengths cover a
+    direct plan (55 = 5 * 11), Rader (281) and Bluestein (537) columns."""
     torch = torch_cuda()
     b = binding()
     batch = 2
     lx, ly = grid_lengths(nx, ny, x_walls)
     fam = "G8" if x_walls else "G4"
-    ctx = b.Context(nx, ny, lx, ly, x_walls=x_walls, batch=batch, family=fam, h_over_dx=1.3, prec="f32")
+    ctx = b.Context(nx, ny, lx, ly, x_walls=x_walls, batch=batch, family=fam, h_over_dx=1.3, prec=prec)
     rng = np.random.default_rng(5)
-    f = torch.tensor(rng.standard_normal((batch, nx, ny)), dtype=torch.float32, device="cuda")
+    dt = torch.float32 if prec == "f32" else torch.float64
+    f = torch.tensor(rng.standard_normal((batch, nx, ny)), dtype=dt, device="cuda")
     rhs = f - f.mean(dim=(1, 2), keepdim=True)
 
     def ops():
@@ -135,12 +137,13 @@ def test_every_cta_width_gives_the_same_fp32_results(nx, ny, x_walls):
 
 
 @pytest.mark.gpu
-def test_every_cta_width_gives_the_same_fp32_3d_step():
+@pytest.mark.parametrize("prec", ["f32", "f32x2", "f64"])
+def test_every_cta_width_gives_the_same_3d_step(prec):
     torch = torch_cuda()
     b = binding()
     nx, nz, ny = 8, 6, 20
     dy = 1.0 / (ny - 1)
-    ctx = b.Context(nx, ny, nx * dy, 1.0, family="G4", h_over_dx=1.3, prec="f32", nz=nz, lz=nz * dy)
+    ctx = b.Context(nx, ny, nx * dy, 1.0, family="G4", h_over_dx=1.3, prec=prec, nz=nz, lz=nz * dy)
     rng = np.random.default_rng(9)
     init = [1e-3 * rng.standard_normal((1, nx, nz, ny)) for _ in range(3)]
 
@@ -156,19 +159,23 @@ def test_every_cta_width_gives_the_same_fp32_3d_step():
 
 @pytest.mark.gpu
 def test_cta_widths_are_checked():
+    """Defaults: 4-warp CTAs for passes that fill at most a quarter of the GPU
+    with one-warp CTAs, 2-warp for at most half; long FP32 lines at least 64
+    (row) and 128 (column)."""
     torch_cuda()
     b = binding()
+    for prec in ("f64", "f32x2", "f32"):
+        small = b.Context(64, 64, 64 / 63, 1.0, batch=1, prec=prec)  # 32 column pairs, 45 rows
+        assert small.get_cta_threads() == (128, 128)
+        full = b.Context(256, 256, 1.0, 1.0, x_walls=True, batch=32, prec=prec)  # 4096 pairs, 4512 rows
+        assert full.get_cta_threads() == (32, 32)
+        mid = b.Context(256, 256, 1.0, 1.0, x_walls=True, batch=6, prec=prec)  # 768 pairs, 846 rows
+        assert mid.get_cta_threads() == (64, 64)
+        for bad in [(0, 32), (32, 96), (256, 32)]:
+            with pytest.raises(b.FcsphError) as e:
+                small.set_cta_threads(*bad)
+            assert e.value.status == 1
+        small.set_cta_threads(64, 32)
+        assert small.get_cta_threads() == (64, 32)
     big = b.Context(1024, 1024, 1024 / 1023, 1.0, batch=1, prec="f32")
     assert big.get_cta_threads() == (64, 128)      # FP32, lines of >= 768 points
-    small = b.Context(64, 64, 64 / 63, 1.0, batch=1, prec="f32")
-    assert small.get_cta_threads() == (32, 32)
-    for bad in [(0, 32), (32, 96), (256, 32)]:
-        with pytest.raises(b.FcsphError) as e:
-            small.set_cta_threads(*bad)
-        assert e.value.status == 1
-    for prec in ("f64", "f32x2"):
-        ctx = b.Context(64, 64, 64 / 63, 1.0, batch=1, prec=prec)
-        assert ctx.get_cta_threads() == (32, 32)
-        with pytest.raises(b.FcsphError) as e:
-            ctx.set_cta_threads(64, 32)
-        assert e.value.status == 6
