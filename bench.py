@@ -57,6 +57,9 @@ def parse():
                     help="cavity: the 256^2 lid cavity (default); uneven: 64 solves of sizes 64^2..512^2 "
                          "submitted together; serve: a Poisson request stream (2D part)")
     ap.add_argument("--serve-seconds", type=float, default=1.0)
+    ap.add_argument("--fc-cont", default="25",
+                    help="uneven/serve: FC continuation length of every size class, an integer or 'smooth' (per size "
+                         "the length nearest 25 in [20, 40] whose extended line the engine transforms directly)")
     ap.add_argument("--profile-case", action="store_true",
                     help="no timing: 2 eager RK3 steps of the cavity, or (--workload planes) 3 spectral_op calls "
                          "on --batch planes of 1024^2, for ncu captures on a small batch")
@@ -240,11 +243,11 @@ def ff_peak_tflops(sm_mhz=2070.0):
 # profiles/), keyed by (precision, kind, batch).  Valid only for the kernel sources they were taken on:
 # KERNEL_SOURCES_SHA256 is the hash of csrc/ at capture time, and a different hash reports null.
 MEASURED_TRAFFIC = {
-    ("f32x2", "row_mom", 32): 91668224, ("f32x2", "col_mom", 32): 237278464,
-    ("f64", "row_mom", 32): 83464704, ("f64", "col_mom", 32): 242213888,
-    ("f32", "row_mom", 32): 21289216, ("f32", "col_mom", 32): 162235904,
+    ("f32x2", "row_mom", 32): 91517952, ("f32x2", "col_mom", 32): 236587008,
+    ("f64", "row_mom", 32): 83504640, ("f64", "col_mom", 32): 241349888,
+    ("f32", "row_mom", 32): 21483776, ("f32", "col_mom", 32): 159032576,
 }
-KERNEL_SOURCES_SHA256 = "233ea5a043d056a90f0ef14cd3f1d17232de5579b89e9712f1c04df08934942e"
+KERNEL_SOURCES_SHA256 = "e9ab77ad1e0dcc7fdf8aceea312e26c39b3230465426dd0a8074dabf39564275"
 
 
 def kernel_sources_sha256():
@@ -571,8 +574,9 @@ def run_reference(args):
 
 
 def run_serving(args):
-    """Configurations 4 and 5 through the continuous-batching server, and the same
-    requests run one at a time on the plain FP64 path (batch 1)."""
+    """The uneven batch and the Poisson request stream through the continuous-
+    batching server, and the same requests run one at a time on the plain FP64
+    path (batch 1), both with the same FC continuation lengths."""
     import numpy as np
     import torch
     import __graft_entry__
@@ -592,8 +596,9 @@ def run_serving(args):
                                 max(1, d["steps"] * steps // 500), d["t"]) for i, d in enumerate(spec)]
         desc = (f"Poisson arrivals 200/s for {args.serve_seconds} s, 80% 2D cavity/channel of 64^2..1024^2, "
                 f"20% 3D channel of 64^3..128^3, each 50-500 RK3 steps scaled by {steps}/500")
+    fc_cont = args.fc_cont if args.fc_cont == "smooth" else int(args.fc_cont)
     torch.cuda.synchronize()
-    srv = Server(prec=args.prec, capacity=8)
+    srv = Server(prec=args.prec, capacity=8, fc_cont=fc_cont)
     rs = reqs()
     wall = srv.run(rs)
     torch.cuda.synchronize()
@@ -602,7 +607,7 @@ def run_serving(args):
     base = reqs()
     t0 = time.perf_counter()
     for r in base:
-        s1 = Server(prec="f64", capacity=1)
+        s1 = Server(prec="f64", capacity=1, fc_cont=fc_cont)
         r.arrival = 0.0
         s1.submit(r)
         while not s1.idle():
@@ -613,7 +618,7 @@ def run_serving(args):
         "metric": METRIC, "value": served["particle_updates_per_s"], "unit": "particle-updates/s", "n_gpus": 1,
         "steps": steps, "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
-        "config": {"workload": desc, "precision": args.prec, "slots_per_size_class": 8},
+        "config": {"workload": desc, "precision": args.prec, "slots_per_size_class": 8, "fc_cont": args.fc_cont},
         "latency_ms": {"p50": served["step_latency_ms_p50"], "p99": served["step_latency_ms_p99"]},
         "served": served, "serial_plain_fp64": serial,
         "speedup_vs_serial": served["particle_updates_per_s"] / serial["particle_updates_per_s"]}))

@@ -20,6 +20,13 @@ request's result is the same alone and in the mix (bitwise, same precision).
 The per-request Reynolds number enters through per-instance viscosity (and,
 for the channels, body force): cavity nu = 1/Re (lid speed 1, side 1);
 channel (2D and 3D) u_max = 1, nu = 1/Re, F = 8 nu.
+
+FC continuation length: 25 points for every size (fc_cont=25), or per size
+the length nearest 25 in [20, 40] whose extended line n + C the FFT engine
+transforms directly (fc_cont="smooth"; see smooth_n_cont).  The continuation
+length is a free parameter of FC(Gram) (Sec. 4: the Gram fit sets the
+accuracy, C the period); with 25, sizes such as 512 (537 = 3 * 179) or 1024
+(1049, prime) need Bluestein transforms of about twice the length.
 """
 import collections
 import time
@@ -49,6 +56,31 @@ class Request:
     t_done: float = None
 
 
+# Radices the FFT engine runs as register butterflies.
+_DIRECT_PRIMES = (2, 3, 5, 7, 11, 13, 17)
+
+
+def _factors_over(m, primes):
+    for q in primes:
+        while m % q == 0:
+            m //= q
+    return m == 1
+
+
+def smooth_n_cont(n, base=25, lo=20, hi=40):
+    """FC continuation length for n wall-normal nodes: `base` if n + base
+    factors into the engine's register radices (2..17); else the length in
+    [lo, hi] nearest `base` (the smaller on a tie) with n + C 7-smooth; else
+    `base`."""
+    if _factors_over(n + base, _DIRECT_PRIMES):
+        return base
+    for d in range(1, max(base - lo, hi - base) + 1):
+        for c in (base - d, base + d):
+            if lo <= c <= hi and _factors_over(n + c, (2, 3, 5, 7)):
+                return c
+    return base
+
+
 def family_for(kind, re):
     """Kernel family per the paper's guidance: G4 at low Re, G8 at high Re (cavity always G8)."""
     if kind == "cavity":
@@ -64,10 +96,10 @@ def particles(req):
     return req.n ** 3 if req.kind == "channel3d" else req.n ** 2
 
 
-def footprint_bytes(n, capacity, prec, d3=False):
+def footprint_bytes(n, capacity, prec, d3=False, n_cont=25):
     """Device bytes of one class: state, workspace and spectra per slot
     (2D: 5 + 6 fields, 8 spectra; 3D: 7 + 7 fields, 15 spectra)."""
-    my = n + 25
+    my = n + n_cont
     hy = my // 2 + 1
     rows = max(hy, n)
     cb = 8 if prec == "f32" else 16
@@ -77,17 +109,18 @@ def footprint_bytes(n, capacity, prec, d3=False):
 
 
 class SizeClass:
-    def __init__(self, key, capacity, prec, device):
+    def __init__(self, key, capacity, prec, device, n_cont=25):
         kind, n, fam = key
         self.key, self.kind, self.n, self.capacity, self.prec = key, kind, n, capacity, prec
+        self.n_cont = n_cont
         self.d3 = kind == "channel3d"
         x_walls = kind == "cavity"
         dy = 1.0 / (n - 1)
         lx = 1.0 if x_walls else n * dy
         self.stream = torch.cuda.Stream(device=device)
         with torch.cuda.stream(self.stream):
-            self.ctx = b.Context(n, n, lx, 1.0, x_walls=x_walls, batch=capacity, family=fam, h_over_dx=1.3,
-                                 prec=prec, stream=self.stream.cuda_stream, nz=n if self.d3 else 1,
+            self.ctx = b.Context(n, n, lx, 1.0, x_walls=x_walls, batch=capacity, n_cont=n_cont, family=fam,
+                                 h_over_dx=1.3, prec=prec, stream=self.stream.cuda_stream, nz=n if self.d3 else 1,
                                  lz=n * dy if self.d3 else 0.0)
             shape = (capacity, n, n, n) if self.d3 else (capacity, n, n)
             z = torch.zeros(shape, dtype=torch.float64, device=device)
@@ -149,10 +182,12 @@ class SizeClass:
 
 
 class Server:
-    def __init__(self, prec="f64", capacity=8, mem_budget=None, device=None):
+    def __init__(self, prec="f64", capacity=8, mem_budget=None, device=None, fc_cont=25):
         self.device = device if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.prec = prec
         self.capacity = capacity
+        assert fc_cont == "smooth" or isinstance(fc_cont, int)
+        self.fc_cont = fc_cont
         if mem_budget is None:
             free, _ = torch.cuda.mem_get_info(self.device)
             mem_budget = int(0.8 * free)
@@ -161,8 +196,11 @@ class Server:
         self.queue = collections.deque()
         self.done = []
 
+    def n_cont(self, n):
+        return smooth_n_cont(n) if self.fc_cont == "smooth" else self.fc_cont
+
     def used_bytes(self):
-        return sum(footprint_bytes(c.n, c.capacity, c.prec, c.d3) for c in self.classes.values())
+        return sum(footprint_bytes(c.n, c.capacity, c.prec, c.d3, c.n_cont) for c in self.classes.values())
 
     def submit(self, req):
         self.queue.append(req)
@@ -174,11 +212,11 @@ class Server:
             key = class_key(req)
             cls = self.classes.get(key)
             if cls is None:
-                need = footprint_bytes(req.n, self.capacity, self.prec, req.kind == "channel3d")
+                need = footprint_bytes(req.n, self.capacity, self.prec, req.kind == "channel3d", self.n_cont(req.n))
                 if self.used_bytes() + need > self.mem_budget:
                     waiting.append(req)
                     continue
-                cls = SizeClass(key, self.capacity, self.prec, self.device)
+                cls = SizeClass(key, self.capacity, self.prec, self.device, self.n_cont(req.n))
                 self.classes[key] = cls
             free = cls.free_slots()
             if not free or cls.pending_event:
