@@ -106,6 +106,13 @@ typedef struct {
   const double* nu_inst;   /* device [batch] or NULL: per-instance viscosity (overrides nu) */
   const double* fx_inst;   /* device [batch] or NULL: per-instance body force x (overrides force_x) */
   double force_z;      /* 3D: body force in z                                  */
+  /* device [batch] or NULL (every instance): instance b advances only where
+   * active[b] != 0; the state of the others is not read or written (their
+   * CTAs return at once).  The contents may change between calls and between
+   * replays of the captured graph (the pointer is part of the graph's key).
+   * Not with FP32 PPE refinement (FCSPH_EUNSUPPORTED).  Lets a batch hold
+   * empty slots (serving) without computing them. */
+  const unsigned char* active;
 } fcsph_step_params;
 
 /* Create a context for one grid shape: builds the FC tables (Sec. 4; FP64,

@@ -58,7 +58,13 @@ class fcsph_step_params(ctypes.Structure):
                 ("force_x", ctypes.c_double), ("force_y", ctypes.c_double),
                 ("u_bottom", ctypes.c_double), ("u_top", ctypes.c_double),
                 ("scheme", ctypes.c_int), ("use_graph", ctypes.c_int),
-                ("nu_inst", ctypes.c_void_p), ("fx_inst", ctypes.c_void_p), ("force_z", ctypes.c_double)]
+                ("nu_inst", ctypes.c_void_p), ("fx_inst", ctypes.c_void_p), ("force_z", ctypes.c_double),
+                ("active", ctypes.c_void_p)]
+
+
+def torch_uint8():
+    import torch
+    return torch.uint8
 
 
 def _load():
@@ -241,20 +247,24 @@ class Context:
         return r.value if want_resid else None
 
     @staticmethod
-    def _params(nu, rho, dt, force, u_bottom, u_top, scheme, use_graph, nu_inst, fx_inst):
+    def _params(nu, rho, dt, force, u_bottom, u_top, scheme, use_graph, nu_inst, fx_inst, active=None):
         fz = force[2] if len(force) > 2 else 0.0
+        if active is not None:
+            assert active.is_cuda and active.dtype == torch_uint8() and active.is_contiguous()
         return fcsph_step_params(nu, rho, dt, force[0], force[1], u_bottom, u_top, SCHEME[scheme], 1 if use_graph else 0,
                                  nu_inst.data_ptr() if nu_inst is not None else None,
-                                 fx_inst.data_ptr() if fx_inst is not None else None, fz)
+                                 fx_inst.data_ptr() if fx_inst is not None else None, fz,
+                                 active.data_ptr() if active is not None else None)
 
     def isph_step(self, u, v, p, fu, fv, nsteps, nu, rho=1.0, dt=1e-3, force=(0.0, 0.0), u_bottom=0.0, u_top=0.0,
-                  scheme="fop", use_graph=True, nu_inst=None, fx_inst=None, w=None, fw=None):
+                  scheme="fop", use_graph=True, nu_inst=None, fx_inst=None, w=None, fw=None, active=None):
         """nu_inst / fx_inst: optional CUDA float64 tensors [batch] of per-instance
         viscosity and x body force (override nu / force[0]).  3D grids: w, fw (z
-        velocity and its F^{k-1}) and force = (fx, fy, fz)."""
+        velocity and its F^{k-1}) and force = (fx, fy, fz).  active: optional CUDA
+        uint8 tensor [batch]; only instances with a nonzero flag advance."""
         st = fcsph_state(u.data_ptr(), v.data_ptr(), p.data_ptr(), fu.data_ptr(), fv.data_ptr(),
                          w.data_ptr() if w is not None else None, fw.data_ptr() if fw is not None else None)
-        prm = self._params(nu, rho, dt, force, u_bottom, u_top, scheme, use_graph, nu_inst, fx_inst)
+        prm = self._params(nu, rho, dt, force, u_bottom, u_top, scheme, use_graph, nu_inst, fx_inst, active)
         self._ck(lib.isph_step(self.h, ctypes.byref(st), nsteps, ctypes.byref(prm)))
 
     def set_tiling(self, row_lines, col_pairs):

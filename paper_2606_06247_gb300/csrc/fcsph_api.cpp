@@ -614,8 +614,24 @@ static fcsph_status one_step(fcsph_ctx* c, const fcsph_state* s, const fcsph_ste
   return FCSPH_OK;
 }
 
+// Sets the context's instance mask for the duration of one isph_step call.
+struct ActiveScope {
+  fcsph_ctx* c;
+  ActiveScope(fcsph_ctx* ctx, const unsigned char* active) : c(ctx) { c->gd.active = active; }
+  ~ActiveScope() { c->gd.active = nullptr; }
+};
+
+static fcsph_status isph_step_masked(fcsph_ctx* c, const fcsph_state* s, int nsteps, const fcsph_step_params* prm);
+
 fcsph_status isph_step(fcsph_ctx* c, const fcsph_state* s, int nsteps, const fcsph_step_params* prm) {
   if (!c || !s || !prm || nsteps < 0) return fail(c, FCSPH_EINVAL, "isph_step: bad argument");
+  if (prm->active && c->prec.fft_prec == FCSPH_F32 && c->prec.ppe_refine_iters > 0)
+    return fail(c, FCSPH_EUNSUPPORTED, "isph_step: an instance mask with PPE refinement");
+  ActiveScope scope(c, prm->active);
+  return isph_step_masked(c, s, nsteps, prm);
+}
+
+static fcsph_status isph_step_masked(fcsph_ctx* c, const fcsph_state* s, int nsteps, const fcsph_step_params* prm) {
   if (!s->u || !s->v || !s->p || !s->fu || !s->fv) return fail(c, FCSPH_EINVAL, "isph_step: null state pointer");
   if (c->gd.nz > 1 && (!s->w || !s->fw)) return fail(c, FCSPH_EINVAL, "isph_step: a 3D grid needs w and fw");
   if (prm->scheme != FCSPH_SCHEME_FOP && prm->scheme != FCSPH_SCHEME_RK3)
@@ -636,7 +652,8 @@ fcsph_status isph_step(fcsph_ctx* c, const fcsph_state* s, int nsteps, const fcs
                              (double)(uintptr_t)s->fu, (double)(uintptr_t)s->fv, prm->nu, prm->rho, prm->dt,
                              prm->force_x, prm->force_y, prm->u_bottom, prm->u_top, (double)prm->scheme,
                              (double)(uintptr_t)prm->nu_inst, (double)(uintptr_t)prm->fx_inst,
-                             (double)(uintptr_t)s->w, (double)(uintptr_t)s->fw, prm->force_z};
+                             (double)(uintptr_t)s->w, (double)(uintptr_t)s->fw, prm->force_z,
+                             (double)(uintptr_t)prm->active};
   if (!c->gexec || key != c->graph_key) {
     if (c->gexec) {
       cudaGraphExecDestroy(c->gexec);

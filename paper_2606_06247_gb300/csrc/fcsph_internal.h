@@ -136,7 +136,14 @@ struct GridDev {
   int ex_off, ey_off;
   // pool offsets of the PPE eigenvalues lam_k^2 (k < nx) and lam_l^2 (l < ny)
   int lx2_off, ly2_off;
+  // isph_step only: device [batch] flags, instance b is advanced where
+  // active[b] != 0 (null: every instance); null outside isph_step
+  const unsigned char* active = nullptr;
 };
+
+// CTAs of an instance left out of the step return at once (uniform per CTA,
+// before any barrier).
+__host__ __device__ inline bool inactive(const GridDev& g, int b) { return g.active && !g.active[b]; }
 
 struct StepDev {
   double nu, rho, dt, fx, fy, fz, u_bottom, u_top;
@@ -159,7 +166,7 @@ struct fcsph_ctx {
   void* dEff = nullptr;         // the same in FP32 pairs (FP32x2 contexts)
   int row_lines = 1;            // rows per CTA of the row passes
   int col_pairs = 1;            // column pairs per CTA of the column passes
-  int row_threads = 32;         // CTA width of the row (and z) passes: 32, 64, 128 (FP32 only > 32)
+  int row_threads = 32;         // CTA width of the row (and z) passes: 32, 64 or 128
   int col_threads = 32;         // CTA width of the column passes
   std::vector<double> hE[2];    // host copies
   double2* pool64 = nullptr;

@@ -250,6 +250,7 @@ __global__ void __launch_bounds__(NT, MinCtas<T, NT>::v) k_col_fwd(GridDev g, co
   V* lines = reinterpret_cast<V*>(smem_raw);
   V* scratch = lines + (size_t)Pp * ls;
   const int b = blockIdx.z, f = blockIdx.y;
+  if (inactive(g, b)) return;
   const int i0 = blockIdx.x * 2 * Pp;
   const U* src = f == 0 ? f0 : (f == 1 ? f1 : f2);
   const int W = 2 * Pp;
@@ -319,6 +320,7 @@ __global__ void __launch_bounds__(NT, MinCtas<T, NT>::v) k_row_sym(GridDev g, co
   V* A = reinterpret_cast<V*>(smem_raw);
   V* B = A + (size_t)nin * Rr * ls;
   const int b = blockIdx.y;
+  if (inactive(g, b)) return;
   const int q0 = blockIdx.x * Rr;
   const int nx = g.nx, mx = g.mx, nz = g.nz;
   const int nq = g.hy * nz;
@@ -456,15 +458,17 @@ __global__ void __launch_bounds__(NT, LineMinCtas<T, NT>::v) k_line_op(GridDev g
 // ---------------------------------------------------------------------------
 // z pass of the 3D channel: in the spectra [b][field][row][x][z] every run of
 // nz values (fixed b, field, row, x) is one periodic z line; L lines per CTA
-// are transformed in place, forward or (inv) unnormalised inverse.
+// are transformed in place, forward or (inv) unnormalised inverse.  Instances
+// with active[b] == 0 (isph_step's mask, when given) are left alone.
 template <typename T, int NT>
 __global__ void __launch_bounds__(NT, MinCtas<T, NT>::v) k_zlines(typename CT<T>::t* __restrict__ spec,
                                                                       int lines_per_field, size_t fstride,
                                                                       size_t bstride, const __grid_constant__ FftPlan P,
                                                                       const typename CT<T>::t* __restrict__ pool, int L,
-                                                                      int ls, int inv) {
+                                                                      int ls, int inv, const unsigned char* active) {
   typedef typename CT<T>::t V;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (active && !active[blockIdx.z]) return;
   V* A = reinterpret_cast<V*>(smem_raw);
   V* B = A + (size_t)L * ls;
   const int n = P.base.n;
@@ -503,6 +507,7 @@ __global__ void __launch_bounds__(NT, MinCtas<T, NT>::v) k_row_ppe(GridDev g, ty
   V* A = reinterpret_cast<V*>(smem_raw);
   V* B = A + (size_t)Rr * ls;
   const int b = blockIdx.y;
+  if (inactive(g, b)) return;
   const int q0 = blockIdx.x * Rr;
   const int nx = g.nx, ny = g.ny, nz = g.nz;
   const int nq = ny * nz;
@@ -615,6 +620,7 @@ __global__ void __launch_bounds__(NT, MinCtas<T, NT>::v) k_col_inv(GridDev g, co
   V* S = Z + (size_t)Pp * ls;
   double2* acc = reinterpret_cast<double2*>(S + (size_t)Pp * ls);
   const int b = blockIdx.y;
+  if (inactive(g, b)) return;
   const int i0 = blockIdx.x * 2 * Pp;
   const int ny = g.ny;
   const bool ppe = (EPI == EPI_PPE_SOLVE || EPI == EPI_PPE_RESID || EPI == EPI_PPE_ADD);
@@ -1115,7 +1121,7 @@ static cudaError_t zpass_t(fcsph_ctx* c, void* spec, int nf, size_t bstride, int
   return with_width(c->row_threads, [&](auto w) {
     constexpr int NT = decltype(w)::value;
     k_zlines<T, NT><<<grid, NT, smem, c->stream>>>((typename CT<T>::t*)spec, lines, (size_t)g.rows * g.ncol, bstride,
-                                                   P, PoolOf<T>::get(c), L, ls, inv);
+                                                   P, PoolOf<T>::get(c), L, ls, inv, g.active);
     c->launches++;
     return cudaGetLastError();
   });

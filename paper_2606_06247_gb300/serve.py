@@ -10,7 +10,8 @@ overlap on the GPU.  Classes run independently: the host polls each class's
 end-of-step event and, when a class's step is done, retires its finished
 requests (state copied to the host), admits queued requests into the freed
 slots and launches its next step, without waiting for the other classes.
-New classes are admitted only while the estimated device footprint of all
+The step runs only the occupied slots (isph_step's instance mask): an empty
+slot costs its CTAs an early return.  New classes are admitted only while the estimated device footprint of all
 classes fits the memory budget.
 
 Every slot is an independent instance of the step: its result does not
@@ -128,6 +129,8 @@ class SizeClass:
             self.w, self.fw = (z.clone(), z.clone()) if self.d3 else (None, None)
             self.nu = torch.full((capacity,), 1e-2, dtype=torch.float64, device=device)
             self.fx = torch.zeros((capacity,), dtype=torch.float64, device=device)
+            # slots holding a request; empty slots are skipped by the step's kernels
+            self.active_mask = torch.zeros((capacity,), dtype=torch.uint8, device=device)
         self.slots = [None] * capacity
         self.ev0 = torch.cuda.Event(enable_timing=True)
         self.ev1 = torch.cuda.Event(enable_timing=True)
@@ -147,6 +150,7 @@ class SizeClass:
                     t[slot].zero_()
             self.nu[slot] = nu
             self.fx[slot] = 8.0 * nu if self.kind in ("channel", "channel3d") else 0.0
+            self.active_mask[slot] = 1
         self.slots[slot] = req
 
     def step(self):
@@ -155,7 +159,7 @@ class SizeClass:
             self.ev0.record(self.stream)
             self.ctx.isph_step(self.u, self.v, self.p, self.fu, self.fv, 1, nu=1e-2, rho=1.0, dt=DT,
                                u_top=1.0 if self.kind == "cavity" else 0.0, scheme="rk3", use_graph=True,
-                               nu_inst=self.nu, fx_inst=self.fx, w=self.w, fw=self.fw)
+                               nu_inst=self.nu, fx_inst=self.fx, w=self.w, fw=self.fw, active=self.active_mask)
             self.ev1.record(self.stream)
         self.pending_event = True
 
@@ -177,6 +181,8 @@ class SizeClass:
                     r.result["w"] = self.w[i].cpu().numpy()
                 r.t_done = now
                 self.slots[i] = None
+                with torch.cuda.stream(self.stream):
+                    self.active_mask[i] = 0
                 retired.append(r)
         return retired
 
