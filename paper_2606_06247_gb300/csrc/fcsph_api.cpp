@@ -314,6 +314,28 @@ fcsph_status fcsph_create(const fcsph_grid* grid, const fcsph_fc* fc, const fcsp
       CREATE_CK(cudaMalloc(&c->dEff, 2 * ne * sizeof(float2)), "cudaMalloc(Eff)");
       CREATE_CK(cudaMemcpy(c->dEff, hf.data(), 2 * ne * sizeof(float2), cudaMemcpyHostToDevice), "Eff upload");
     }
+    {  // W_hat on the extended grid (Eq. 16), rounded once to the transform type
+      const std::vector<double> W = what_table(g.mx, g.my, g.nz, g.hy, g.dx, g.dy, g.dz, g.h, g.family);
+      std::vector<float2> wf;
+      std::vector<float> w32;
+      const void* src = W.data();
+      size_t bytes = W.size() * sizeof(double);
+      if (prec->fft_prec == FCSPH_F32X2) {
+        wf.resize(W.size());
+        for (size_t i = 0; i < W.size(); ++i) {
+          const float h = (float)W[i];
+          wf[i] = make_float2(h, (float)(W[i] - (double)h));
+        }
+        src = wf.data();
+        bytes = wf.size() * sizeof(float2);
+      } else if (prec->fft_prec == FCSPH_F32) {
+        w32.assign(W.begin(), W.end());
+        src = w32.data();
+        bytes = w32.size() * sizeof(float);
+      }
+      CREATE_CK(cudaMalloc(&c->dW, bytes), "cudaMalloc(W)");
+      CREATE_CK(cudaMemcpy(c->dW, src, bytes, cudaMemcpyHostToDevice), "W upload");
+    }
     const size_t fs = (size_t)g.rows * g.ncol * g.batch;
     const size_t cb = cplx_bytes(prec->fft_prec);
     const bool d3 = g.nz > 1;
@@ -348,6 +370,7 @@ fcsph_status fcsph_destroy(fcsph_ctx* c) {
   cudaFree(c->poolff);
   cudaFree(c->dE);
   cudaFree(c->dEff);
+  cudaFree(c->dW);
   cudaFree(c->spec_in);
   cudaFree(c->spec_out);
   cudaFree(c->spec_ppe);

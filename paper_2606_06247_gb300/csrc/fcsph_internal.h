@@ -102,6 +102,7 @@ int smooth_at_least(int n);
 FftPlan make_plan(int n, Pool* pool, std::vector<double>* bhat_src_re, std::vector<double>* bhat_src_im);
 int fc_table_build(const fcsph_fc* fc, int bc, std::vector<double>* E, std::string* err);
 std::vector<double> gauss_axis(int m, double d, double h, int count);
+std::vector<double> what_table(int mx, int my, int nz, int hy, double dx, double dy, double dz, double h, int family);
 
 }  // namespace fcsph
 
@@ -164,6 +165,7 @@ struct fcsph_ctx {
   fcsph::FftPlan plan_z;                            // 3D: periodic z (operators and PPE)
   double* dE = nullptr;         // device [2][n_cont][2 n_match] (Dirichlet, Neumann)
   void* dEff = nullptr;         // the same in FP32 pairs (FP32x2 contexts)
+  void* dW = nullptr;           // W_hat on the extended grid, [hy * nz][mx], in the transform type
   int row_lines = 1;            // rows per CTA of the row passes
   int col_pairs = 1;            // column pairs per CTA of the column passes
   int row_threads = 32;         // CTA width of the row (and z) passes: 32, 64 or 128

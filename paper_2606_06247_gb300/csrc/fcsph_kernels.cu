@@ -303,6 +303,8 @@ template <typename T> __device__ __forceinline__ T kernel_poly(int family, T s) 
 // nz.  For Rr lines of one instance: load nin input lines, FC-extend in x
 // (walled x), FFT (length mx); then for each output in turn form
 // sum_t S_t * F_t times `scale`, inverse FFT, truncate to nx and store.
+// The symbols S_t are W_hat (Wt: the context's [hy nz][mx] table of Eq. 16 in
+// the transform type) times 1, i kx, i ky, i kz or -|k|^2.
 // Shared memory: the nin input lines and their scratch (2 nin Rr lines; one
 // half holds the spectra, the other serves the outputs), plus Rr lines when
 // nin = 1.
@@ -313,7 +315,7 @@ __global__ void __launch_bounds__(NT, MinCtas<T, NT>::v) k_row_sym(GridDev g, co
                                                          const __grid_constant__ RowOps ops,
                                                          const typename FcTab<T>::t* __restrict__ E,
                                                          const __grid_constant__ FftPlan P, const typename CT<T>::t* __restrict__ pool,
-                                                         double scale, int Rr, int ls) {
+                                                         const T* __restrict__ Wt, double scale, int Rr, int ls) {
   typedef typename CT<T>::t V;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nin = ops.nin, nout = ops.nout;
@@ -339,7 +341,6 @@ __global__ void __launch_bounds__(NT, MinCtas<T, NT>::v) k_row_sym(GridDev g, co
   V* X = fft_any<T, false>(A, B, nin * Rr, ls, P, pool);
   V* Cq = (X == A) ? B : A;
   V* D = nin >= 2 ? Cq + (size_t)Rr * ls : B + (size_t)Rr * ls;
-  const T hh = (T)(g.h * g.h * 0.25);
   const T ckx = (T)(2.0 * 3.14159265358979323846 / (mx * g.dx));
   const T cky = (T)(2.0 * 3.14159265358979323846 / (g.my * g.dy));
   const T ckz = (T)(2.0 * 3.14159265358979323846 / (nz * g.dz));
@@ -352,14 +353,13 @@ __global__ void __launch_bounds__(NT, MinCtas<T, NT>::v) k_row_sym(GridDev g, co
       const T kyw = cky * (T)ky, kz = ckz * (T)kzeta;
       const bool nyq_y = (g.my % 2 == 0) && (2 * ky == g.my);
       const bool nyq_z = (nz % 2 == 0) && (2 * kq == nz);
-      // e^{-s} = e^{-kx^2 h^2/4} e^{-ky^2 h^2/4} e^{-kz^2 h^2/4} from the per-axis tables
-      const T Wyz = pool[g.ey_off + ky].x * pool[g.ez_off + kq].x;
-      const T kyz2 = kyw * kyw + kz * kz;
+      // W_hat of row q from the context's table (Eq. 16, built once in quad precision)
+      const T* Wq = Wt + (size_t)q * mx;
       for (int kxi = threadIdx.x; kxi < mx; kxi += blockDim.x) {
         const int kappa = (2 * kxi <= mx) ? kxi : kxi - mx;
         const T kx = ckx * (T)kappa;
         const bool nyq_x = (mx % 2 == 0) && (2 * kxi == mx);
-        const T What = pool[g.ex_off + kxi].x * Wyz * kernel_poly<T>(g.family, (kx * kx + kyz2) * hh);
+        const T What = Wq[kxi];
         V acc = mk<V>(0.0, 0.0);
         for (int t = 0; t < ops.nterm[o]; ++t) {
           const V s = symbol<T>(ops.op[o][t], kx, kyw, kz, nyq_x, nyq_y, nyq_z, What);
@@ -1053,7 +1053,8 @@ static cudaError_t row_sym_t(fcsph_ctx* c, int prec, const void* sp_in, void* sp
     constexpr int NT = decltype(w)::value;
     k_row_sym<T, NT><<<grid, NT, smem, c->stream>>>(g, (const typename CT<T>::t*)sp_in, (typename CT<T>::t*)sp_out,
                                                     fs, spec_in_fields(c) * fs, fs, spec_out_fields(c) * fs, ops, E,
-                                                    c->plan_x, PoolOf<T>::get(c), scale, Rr, ls);
+                                                    c->plan_x, PoolOf<T>::get(c), static_cast<const T*>(c->dW),
+                                                    scale, Rr, ls);
     c->launches++;
     return cudaGetLastError();
   });

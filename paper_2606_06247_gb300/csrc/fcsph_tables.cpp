@@ -259,6 +259,38 @@ std::vector<double> gauss_axis(int m, double d, double h, int count) {
   return out;
 }
 
+// Eq. 16 closed form on the extended grid: W_hat = e^{-s} sum_{m<family}
+// s^m / m!, s = |k|^2 h^2 / 4, for every row q = ky nz + kq (ky < hy, the y
+// half-spectrum; kq < nz) and kx index < mx; kx and kz signed (Nyquist
+// positive), ky >= 0.  Quad precision, rounded once.  Entry q mx + kx.
+std::vector<double> what_table(int mx, int my, int nz, int hy, double dx, double dy, double dz, double h, int family) {
+  std::vector<double> out((size_t)hy * nz * mx);
+  const qreal ckx = 2 * QPI / ((qreal)mx * (qreal)dx), cky = 2 * QPI / ((qreal)my * (qreal)dy);
+  const qreal ckz = nz > 1 ? 2 * QPI / ((qreal)nz * (qreal)dz) : 0;
+  const qreal hh = (qreal)h * (qreal)h / 4;
+  for (int ky = 0; ky < hy; ++ky)
+    for (int kq = 0; kq < nz; ++kq) {
+      const int kz = (2 * kq <= nz) ? kq : kq - nz;
+      const qreal syz = (cky * ky) * (cky * ky) + (ckz * kz) * (ckz * kz);
+      for (int a = 0; a < mx; ++a) {
+        const int kx = (2 * a <= mx) ? a : a - mx;
+        const qreal sx = (ckx * kx) * (ckx * kx);
+        const qreal s = (sx + syz) * hh;
+        qreal term = 1, sum = 1;
+        for (int m = 1; m < family; ++m) {
+          term = term * s / m;
+          sum += term;
+        }
+#if defined(__x86_64__)
+        out[((size_t)ky * nz + kq) * mx + a] = (double)(expq(-s) * sum);
+#else
+        out[((size_t)ky * nz + kq) * mx + a] = (double)(expl(-s) * sum);
+#endif
+      }
+    }
+  return out;
+}
+
 int smooth_at_least(int n) {
   for (int m = n;; ++m) {
     int r = m;
