@@ -596,6 +596,29 @@ struct EpiArgs {
   int* status;
 };
 
+// L2 prefetch hints for the column pass.  Only addresses the kernel reads
+// later are named, so every one lies inside its buffer.
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
+// Rows k < hy of one field's half-spectrum at the CTA's column pairs.
+template <typename V>
+__device__ void prefetch_spec_pairs(const GridDev& g, int i0, int Pp, const V* spec) {
+  for (int t = threadIdx.x; t < g.hy * Pp; t += blockDim.x) {
+    const int k = t / Pp, p = t - k * Pp;
+    if (i0 + 2 * p < g.ncol) prefetch_l2(spec + (size_t)k * g.ncol + i0 + 2 * p);
+  }
+}
+
+// The CTA's columns of one FP64 field of instance b, 128-byte lines.
+__device__ void prefetch_field_cols(const GridDev& g, int b, int i0, int Pp, const double* f) {
+  const int per = (g.ny + 15) / 16 + 1;  // lines of one column, one more for an unaligned start
+  const int nc = min(2 * Pp, g.ncol - i0);
+  for (int t = threadIdx.x; t < nc * per; t += blockDim.x) {
+    const int c = t / per, l = t - c * per;
+    prefetch_l2(f + fidx(g, b, i0 + c, min(16 * l, g.ny - 1)));
+  }
+}
+
 // The epilogue kind is a runtime argument (uniform across the grid): one
 // instantiation per precision keeps the build small.
 //
@@ -632,6 +655,16 @@ __global__ void __launch_bounds__(NT, MinCtas<T, NT>::v) k_col_inv(GridDev g, co
       R = fft_any<T, false>(Z, S, Pp, ls, P, pool);
     } else {
       col_gather_hermitian<T>(Z, Pp, ls, g, i0, spec + b * bstride + o * fstride, fstride, 1, P.base.n);
+      // while this output is transformed, bring the next one's spectrum and
+      // this output's FP64 epilogue operands (state columns) into L2
+      if (o + 1 < nout) prefetch_spec_pairs(g, i0, Pp, spec + b * bstride + (o + 1) * fstride);
+      if (EPI == EPI_MOM) {
+        const int nt = ea.mom_terms, comp = o / nt, term = o - comp * nt;
+        prefetch_field_cols(g, b, i0, Pp, ea.vel[term < nt - 1 ? term : comp]);
+        if (term == nt - 1) prefetch_field_cols(g, b, i0, Pp, ea.Fp[comp]);
+      } else if (EPI == EPI_CORR) {
+        prefetch_field_cols(g, b, i0, Pp, ea.vs[o]);
+      }
       __syncthreads();
       R = fft_any<T, true>(Z, S, Pp, ls, P, pool);
     }
