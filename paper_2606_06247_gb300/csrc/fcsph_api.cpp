@@ -122,6 +122,18 @@ int default_width(long long ctas) {
   return 32;
 }
 
+// FP64 / FP32x2 CTA width for a pass whose CTAs hold smem_cta bytes of shared
+// memory: registers (<= 168 a thread) allow 12 resident warps per SM at any
+// width; when shared memory fits fewer one-warp CTAs than that (long lines),
+// the narrowest width that reaches 12 warps.
+int smem_width(size_t smem_cta) {
+  const size_t per_sm = 228 * 1024, reserved = 1024;
+  const long long fit = (long long)(per_sm / (smem_cta + reserved));
+  for (int w : {32, 64, 128})
+    if (fit * (w / 32) >= 12) return w;
+  return 128;
+}
+
 RowOps ops_none() {
   RowOps o;
   memset(&o, 0, sizeof(o));
@@ -241,15 +253,18 @@ fcsph_status fcsph_create(const fcsph_grid* grid, const fcsph_fc* fc, const fcsp
   c->plan_x = plan_for(g.mx, &pool, &fills);
   c->plan_py = plan_for(2 * (g.ny - 1), &pool, &fills);
   c->plan_px = plan_for(g.x_walls ? 2 * (g.nx - 1) : g.nx, &pool, &fills);
-  g.ex_off = pool.add(gauss_axis(g.mx, g.dx, g.h, g.mx), std::vector<double>(g.mx, 0.0));
-  g.ey_off = pool.add(gauss_axis(g.my, g.dy, g.h, g.hy), std::vector<double>(g.hy, 0.0));
-  g.ez_off = pool.add(gauss_axis(nz, g.dz, g.h, nz), std::vector<double>(nz, 0.0));
+  const std::vector<double> gx = gauss_axis(g.mx, g.dx, g.h, g.mx), gy = gauss_axis(g.my, g.dy, g.h, g.hy),
+                            gz = gauss_axis(nz, g.dz, g.h, nz);
+  g.ex_off = pool.add(gx, std::vector<double>(g.mx, 0.0));
+  g.ey_off = pool.add(gy, std::vector<double>(g.hy, 0.0));
+  g.ez_off = pool.add(gz, std::vector<double>(nz, 0.0));
   if (nz > 1) c->plan_z = plan_for(nz, &pool, &fills);
   {
     // Passes with fewer one-warp CTAs than the GPU holds leave SMs idle: give
-    // each CTA 2 or 4 warps instead.  FP32 lines of ~1000 points and more:
-    // one warp per CTA leaves too few warps per SM (shared memory bound), so
-    // those passes share each CTA's lines among 2 (row) or 4 (column) warps.
+    // each CTA 2 or 4 warps instead.  Long lines: one warp per CTA leaves too
+    // few warps per SM (shared memory bound), so those passes share each
+    // CTA's lines among more warps (FP32 lines of >= 768 points: 2 (row) or 4
+    // (column); FP64 / FP32x2: the narrowest width that reaches 12 warps).
     const long long col_ctas = (long long)((g.ncol + 1) / 2) * g.batch;
     const long long row_ctas = (long long)g.hy * g.nz * g.batch;
     c->row_threads = default_width(row_ctas);
@@ -257,6 +272,13 @@ fcsph_status fcsph_create(const fcsph_grid* grid, const fcsph_fc* fc, const fcsp
     if (prec->fft_prec == FCSPH_F32) {
       if (c->plan_x.line_len() >= kWideLine) c->row_threads = std::max(c->row_threads, 64);
       if (c->plan_y.line_len() >= kWideLine) c->col_threads = 128;
+    } else {
+      // shared memory of the momentum passes, the largest of each kind: one
+      // row CTA (2 nc lines) and one column-pair CTA (2 lines + the FP64
+      // accumulators of nc components)
+      const size_t cb = 16, nc = g.nz > 1 ? 3 : 2;
+      c->row_threads = std::max(c->row_threads, smem_width(2 * nc * c->plan_x.line_len() * cb));
+      c->col_threads = std::max(c->col_threads, smem_width(2 * (size_t)c->plan_y.line_len() * cb + nc * g.ny * 16));
     }
   }
   {
@@ -315,7 +337,7 @@ fcsph_status fcsph_create(const fcsph_grid* grid, const fcsph_fc* fc, const fcsp
       CREATE_CK(cudaMemcpy(c->dEff, hf.data(), 2 * ne * sizeof(float2), cudaMemcpyHostToDevice), "Eff upload");
     }
     {  // W_hat on the extended grid (Eq. 16), rounded once to the transform type
-      const std::vector<double> W = what_table(g.mx, g.my, g.nz, g.hy, g.dx, g.dy, g.dz, g.h, g.family);
+      const std::vector<double> W = what_table(gx, gy, gz, g.mx, g.my, g.nz, g.hy, g.dx, g.dy, g.dz, g.h, g.family);
       std::vector<float2> wf;
       std::vector<float> w32;
       const void* src = W.data();

@@ -102,7 +102,9 @@ int smooth_at_least(int n);
 FftPlan make_plan(int n, Pool* pool, std::vector<double>* bhat_src_re, std::vector<double>* bhat_src_im);
 int fc_table_build(const fcsph_fc* fc, int bc, std::vector<double>* E, std::string* err);
 std::vector<double> gauss_axis(int m, double d, double h, int count);
-std::vector<double> what_table(int mx, int my, int nz, int hy, double dx, double dy, double dz, double h, int family);
+std::vector<double> what_table(const std::vector<double>& ex, const std::vector<double>& ey,
+                               const std::vector<double>& ez, int mx, int my, int nz, int hy, double dx, double dy,
+                               double dz, double h, int family);
 
 }  // namespace fcsph
 

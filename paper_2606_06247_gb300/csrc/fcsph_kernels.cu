@@ -353,7 +353,7 @@ __global__ void __launch_bounds__(NT, MinCtas<T, NT>::v) k_row_sym(GridDev g, co
       const T kyw = cky * (T)ky, kz = ckz * (T)kzeta;
       const bool nyq_y = (g.my % 2 == 0) && (2 * ky == g.my);
       const bool nyq_z = (nz % 2 == 0) && (2 * kq == nz);
-      // W_hat of row q from the context's table (Eq. 16, built once in quad precision)
+      // W_hat of row q from the context's table (Eq. 16, built once on the host)
       const T* Wq = Wt + (size_t)q * mx;
       for (int kxi = threadIdx.x; kxi < mx; kxi += blockDim.x) {
         const int kappa = (2 * kxi <= mx) ? kxi : kxi - mx;

@@ -262,30 +262,33 @@ std::vector<double> gauss_axis(int m, double d, double h, int count) {
 // Eq. 16 closed form on the extended grid: W_hat = e^{-s} sum_{m<family}
 // s^m / m!, s = |k|^2 h^2 / 4, for every row q = ky nz + kq (ky < hy, the y
 // half-spectrum; kq < nz) and kx index < mx; kx and kz signed (Nyquist
-// positive), ky >= 0.  Quad precision, rounded once.  Entry q mx + kx.
-std::vector<double> what_table(int mx, int my, int nz, int hy, double dx, double dy, double dz, double h, int family) {
+// positive), ky >= 0.  e^{-s} is the product of the per-axis factors ex, ey,
+// ez (gauss_axis, quad precision, rounded once each); s and the series are
+// evaluated in FP64, so the table is within a few FP64 ulps and identical on
+// every host.  Entry q mx + kx.
+std::vector<double> what_table(const std::vector<double>& ex, const std::vector<double>& ey,
+                               const std::vector<double>& ez, int mx, int my, int nz, int hy, double dx, double dy,
+                               double dz, double h, int family) {
   std::vector<double> out((size_t)hy * nz * mx);
-  const qreal ckx = 2 * QPI / ((qreal)mx * (qreal)dx), cky = 2 * QPI / ((qreal)my * (qreal)dy);
-  const qreal ckz = nz > 1 ? 2 * QPI / ((qreal)nz * (qreal)dz) : 0;
-  const qreal hh = (qreal)h * (qreal)h / 4;
+  const double pi = 3.14159265358979323846;
+  const double ckx = 2.0 * pi / (mx * dx), cky = 2.0 * pi / (my * dy), ckz = nz > 1 ? 2.0 * pi / (nz * dz) : 0.0;
+  const double hh = h * h * 0.25;
   for (int ky = 0; ky < hy; ++ky)
     for (int kq = 0; kq < nz; ++kq) {
       const int kz = (2 * kq <= nz) ? kq : kq - nz;
-      const qreal syz = (cky * ky) * (cky * ky) + (ckz * kz) * (ckz * kz);
+      const double kyw = cky * ky, kzw = ckz * kz;
+      const double kyz2 = kyw * kyw + kzw * kzw;
+      const double eyz = ey[ky] * ez[kq];
       for (int a = 0; a < mx; ++a) {
         const int kx = (2 * a <= mx) ? a : a - mx;
-        const qreal sx = (ckx * kx) * (ckx * kx);
-        const qreal s = (sx + syz) * hh;
-        qreal term = 1, sum = 1;
+        const double kxw = ckx * kx;
+        const double s = (kxw * kxw + kyz2) * hh;
+        double term = 1.0, sum = 1.0;
         for (int m = 1; m < family; ++m) {
           term = term * s / m;
           sum += term;
         }
-#if defined(__x86_64__)
-        out[((size_t)ky * nz + kq) * mx + a] = (double)(expq(-s) * sum);
-#else
-        out[((size_t)ky * nz + kq) * mx + a] = (double)(expl(-s) * sum);
-#endif
+        out[((size_t)ky * nz + kq) * mx + a] = ex[a] * eyz * sum;
       }
     }
   return out;

@@ -161,7 +161,8 @@ def test_every_cta_width_gives_the_same_3d_step(prec):
 def test_cta_widths_are_checked():
     """Defaults: 4-warp CTAs for passes that fill at most a quarter of the GPU
     with one-warp CTAs, 2-warp for at most half; long FP32 lines at least 64
-    (row) and 128 (column)."""
+    (row) and 128 (column); FP64 / FP32x2 passes whose shared memory fits
+    fewer than 12 one-warp CTAs per SM the narrowest width reaching 12 warps."""
     torch_cuda()
     b = binding()
     for prec in ("f64", "f32x2", "f32"):
@@ -179,3 +180,6 @@ def test_cta_widths_are_checked():
         assert small.get_cta_threads() == (64, 32)
     big = b.Context(1024, 1024, 1024 / 1023, 1.0, batch=1, prec="f32")
     assert big.get_cta_threads() == (64, 128)      # FP32, lines of >= 768 points
+    # FP32-pair 540-point lines: ~34 KB per one-warp CTA, 6 fit an SM; 2 warps reach 12
+    long = b.Context(512, 512, 1.0, 1.0, x_walls=True, batch=32, n_cont=28, prec="f32x2")
+    assert long.get_cta_threads() == (64, 64)
