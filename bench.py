@@ -312,7 +312,12 @@ def oracle_rate(seconds, n=N):
 
 
 def cpu_cores():
-    return os.cpu_count() or 1
+    """Host cores this process may run on: the oracle's dense DFT products go
+    through numpy's BLAS, whose thread pool spans them."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
 
 
 # ---------------------------------------------------------------- main (ours)
