@@ -139,3 +139,72 @@ def test_double_float_step_matches_oracle(case):
     assert rel_l2(ug[0], uo) < _ff_tol(fu)
     assert rel_l2(vg[0], vo) < _ff_tol(fv)
     assert rel_l2(pg[0], po) < _ff_tol(fp)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", ["f64", "f32x2"])
+def test_resume_from_a_host_copy_is_bitwise_equal(prec):
+    """Checkpoint/resume: the whole step state is the caller's (u, v, p, F^{k-1});
+    copying it to the host, into a fresh context and on is bitwise the same as
+    running straight through."""
+    torch = torch_cuda()
+    b = binding()
+    nx, ny = 32, 32
+    lx, ly = grid_lengths(nx, ny, True)
+    prm = dict(nu=1e-3, rho=1.0, dt=1e-3, u_top=1.0, scheme="rk3")
+    u0, v0 = inputs.cavity_initial(nx, ny, seed=8, sigma=1e-3)
+
+    def fresh():
+        return b.Context(nx, ny, lx, ly, x_walls=True, batch=1, family="G8", h_over_dx=1.3, prec=prec)
+
+    def state():
+        u, v = to_dev(u0[None]), to_dev(v0[None])
+        return [u, v, torch.zeros_like(u), torch.zeros_like(u), torch.zeros_like(u)]
+
+    straight = state()
+    c1 = fresh()
+    c1.isph_step(*straight, 6, **prm)
+    c1.sync()
+    half = state()
+    c2 = fresh()
+    c2.isph_step(*half, 3, **prm)
+    c2.sync()
+    saved = [x.cpu().numpy().copy() for x in half]
+    del c2
+    resumed = [to_dev(a) for a in saved]
+    c3 = fresh()
+    c3.isph_step(*resumed, 3, **prm)
+    c3.sync()
+    for a, r in zip(straight, resumed):
+        np.testing.assert_array_equal(a.cpu().numpy(), r.cpu().numpy())
+
+
+@pytest.mark.gpu
+def test_nonfinite_state_is_reported_and_the_context_recovers():
+    """Failure detection with a host-made fault: a NaN planted in one instance's
+    velocity makes fcsph_sync return FCSPH_ENONFINITE (5); masking that instance
+    out, or restoring a finite state, steps cleanly again on the same context."""
+    torch = torch_cuda()
+    b = binding()
+    nx, ny, batch = 32, 32, 2
+    lx, ly = grid_lengths(nx, ny, True)
+    prm = dict(nu=1e-3, rho=1.0, dt=1e-3, u_top=1.0, scheme="rk3")
+    ctx = b.Context(nx, ny, lx, ly, x_walls=True, batch=batch, family="G8", h_over_dx=1.3, prec="f32x2")
+    z = torch.zeros((batch, nx, ny), dtype=torch.float64, device="cuda")
+    st = [z.clone() for _ in range(5)]
+    st[0][1, nx // 2, ny // 2] = float("nan")
+    ctx.isph_step(*st, 1, **prm)
+    with pytest.raises(b.FcsphError) as e:
+        ctx.sync()
+    assert e.value.status == 5
+    # the flag was consumed: a clean state on the same context steps without error
+    st = [z.clone() for _ in range(5)]
+    st[0][1, nx // 2, ny // 2] = float("nan")
+    mask = torch.tensor([1, 0], dtype=torch.uint8, device="cuda")
+    ctx.isph_step(*st, 2, active=mask, **prm)
+    ctx.sync()
+    assert torch.isfinite(st[0][0]).all()
+    st = [z.clone() for _ in range(5)]
+    ctx.isph_step(*st, 2, **prm)
+    ctx.sync()
+    assert all(torch.isfinite(x).all() for x in st)
