@@ -57,6 +57,7 @@ def parse():
                     help="cavity: the 256^2 lid cavity (default); uneven: 64 solves of sizes 64^2..512^2 "
                          "submitted together; serve: a Poisson request stream (2D part)")
     ap.add_argument("--serve-seconds", type=float, default=1.0)
+    ap.add_argument("--slots", type=int, default=8, help="uneven/serve: slots (batch) per size class")
     ap.add_argument("--fc-cont", default="25",
                     help="uneven/serve: FC continuation length of every size class, an integer or 'smooth' (per size "
                          "the length nearest 25 in [20, 40] whose extended line the engine transforms directly)")
@@ -603,7 +604,7 @@ def run_serving(args):
                 f"20% 3D channel of 64^3..128^3, each 50-500 RK3 steps scaled by {steps}/500")
     fc_cont = args.fc_cont if args.fc_cont == "smooth" else int(args.fc_cont)
     torch.cuda.synchronize()
-    srv = Server(prec=args.prec, capacity=8, fc_cont=fc_cont)
+    srv = Server(prec=args.prec, capacity=args.slots, fc_cont=fc_cont)
     rs = reqs()
     wall = srv.run(rs)
     torch.cuda.synchronize()
@@ -623,7 +624,7 @@ def run_serving(args):
         "metric": METRIC, "value": served["particle_updates_per_s"], "unit": "particle-updates/s", "n_gpus": 1,
         "steps": steps, "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
-        "config": {"workload": desc, "precision": args.prec, "slots_per_size_class": 8, "fc_cont": args.fc_cont},
+        "config": {"workload": desc, "precision": args.prec, "slots_per_size_class": args.slots, "fc_cont": args.fc_cont},
         "latency_ms": {"p50": served["step_latency_ms_p50"], "p99": served["step_latency_ms_p99"]},
         "served": served, "serial_plain_fp64": serial,
         "speedup_vs_serial": served["particle_updates_per_s"] / serial["particle_updates_per_s"]}))
