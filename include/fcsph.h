@@ -44,7 +44,7 @@ typedef enum {
   FCSPH_ECUDA = 3,       /* a CUDA runtime call failed                        */
   FCSPH_ETIMEOUT = 4,    /* a bounded device-side wait gave up                */
   FCSPH_ENONFINITE = 5,  /* a non-finite value reached the time-step state    */
-  FCSPH_EUNSUPPORTED = 6 /* valid request this build does not implement       */
+  FCSPH_EUNSUPPORTED = 6 /* valid request the library does not implement      */
 } fcsph_status;
 
 /* arithmetic of FFTs and symbols: FP64; FP32; FP32x2 = double-float (value =
