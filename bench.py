@@ -241,14 +241,15 @@ def ff_peak_tflops(sm_mhz=2070.0):
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of a kernel kind, from one ncu
 # capture of `bench.py --profile-case --batch B --prec P` (first RK3 substep; command and table in
-# profiles/), keyed by (precision, kind, batch).  Valid only for the kernel sources they were taken on:
-# KERNEL_SOURCES_SHA256 is the hash of csrc/ at capture time, and a different hash reports null.
+# profiles/), keyed by (precision, kind, batch).  Valid only for the device code they were taken on:
+# KERNEL_SOURCES_SHA256 is the hash of the kernel sources in csrc/ (.cu, .cuh, .h) at capture time, and a
+# different hash reports null.
 MEASURED_TRAFFIC = {
     ("f32x2", "row_mom", 32): 92215808, ("f32x2", "col_mom", 32): 238394112,
     ("f64", "row_mom", 32): 84306688, ("f64", "col_mom", 32): 242745600,
     ("f32", "row_mom", 32): 21776640, ("f32", "col_mom", 32): 160495360,
 }
-KERNEL_SOURCES_SHA256 = "578fffa6ef74b68cb8b7b7ede3e17aabcc5241d09dc9ebec19f5222bf5e392fe"
+KERNEL_SOURCES_SHA256 = "549b562461e750e9be30b3d4656fc40e3de5ecf334af2c54aa84de3781e91d4e"
 
 
 def kernel_sources_sha256():
@@ -256,7 +257,7 @@ def kernel_sources_sha256():
     d = os.path.join(ROOT, "paper_2606_06247_gb300", "csrc")
     h = hashlib.sha256()
     for name in sorted(os.listdir(d)):
-        if name.endswith((".cu", ".cuh", ".h", ".cpp")):
+        if name.endswith((".cu", ".cuh", ".h")):
             with open(os.path.join(d, name), "rb") as f:
                 h.update(name.encode() + b"\0" + f.read())
     return h.hexdigest()

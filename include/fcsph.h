@@ -62,7 +62,7 @@ typedef struct {
   int nx, ny;      /* physical nodes per instance (nx >= 4, ny >= 2*n_match)    */
   double lx, ly;   /* domain lengths (see Grid above)                          */
   int x_walls;     /* 0: x periodic; 1: walls at both x ends                   */
-  int batch;       /* independent instances per call (>= 1)                    */
+  int batch;       /* independent instances per call (1 .. 65535)              */
   int nz;          /* 3D channel: nodes in z (periodic, like x); <= 1 = 2D     */
   double lz;       /* 3D channel: z period (dz = lz / nz)                      */
 } fcsph_grid;

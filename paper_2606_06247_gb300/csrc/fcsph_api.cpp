@@ -196,6 +196,8 @@ fcsph_status fcsph_create(const fcsph_grid* grid, const fcsph_fc* fc, const fcsp
     return fail(nullptr, FCSPH_EINVAL, "fcsph_create: need nx >= 4, ny >= 2*n_match, batch >= 1, lx, ly > 0");
   if (grid->nx > 8192 || grid->ny > 8192)
     return fail(nullptr, FCSPH_EINVAL, "fcsph_create: nx, ny > 8192 not supported");
+  if (grid->batch > 65535)  // instances index the y (or z) dimension of every launch grid
+    return fail(nullptr, FCSPH_EINVAL, "fcsph_create: batch > 65535 not supported");
   if (kernel->family < FCSPH_G2 || kernel->family > FCSPH_G10 || !(kernel->h_over_dx >= 0))
     return fail(nullptr, FCSPH_EINVAL, "fcsph_create: bad kernel");
   if (prec->fft_prec != FCSPH_F64 && prec->fft_prec != FCSPH_F32 && prec->fft_prec != FCSPH_F32X2)

@@ -91,4 +91,5 @@ def test_create_rejects_bad_grids_before_touching_the_gpu(lib):
     assert create(prec=7) == 1                     # unknown precision
     assert create(family=0) == 1                   # unknown kernel family
     assert create(nx=9000) == 1                    # beyond the supported size
+    assert create(batch=70000) == 1                # more instances than a launch grid dimension holds
     assert create(nz=4, lz=1.0, prec=1, refine=2) == 6  # PPE refinement is 2D only
