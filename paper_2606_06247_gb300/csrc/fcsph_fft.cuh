@@ -51,6 +51,11 @@ template <typename V> __device__ __forceinline__ V csub(V a, V b) {
   r.y = a.y - b.y;
   return r;
 }
+// Sums inside one butterfly: plain sums here; FP32-pair values skip the
+// renormalisation (fcsph_ff.cuh) and cnorm restores it at the store.
+template <typename V> __device__ __forceinline__ V cadd_nr(V a, V b) { return cadd(a, b); }
+template <typename V> __device__ __forceinline__ V csub_nr(V a, V b) { return csub(a, b); }
+template <typename V> __device__ __forceinline__ V cnorm(V a) { return a; }
 template <typename V, typename S> __device__ __forceinline__ V cscale(V a, S s) {
   V r;
   r.x = a.x * s;
@@ -212,13 +217,13 @@ __device__ __forceinline__ void dft_odd(typename CT<T>::t* v) {
   V A[h], B[h];
 #pragma unroll
   for (int r = 1; r <= h; ++r) {
-    A[r - 1] = cadd(v[r], v[R - r]);
-    B[r - 1] = csub(v[r], v[R - r]);
+    A[r - 1] = cadd_nr(v[r], v[R - r]);
+    B[r - 1] = csub_nr(v[r], v[R - r]);
   }
   V o[R];
   V y0 = v[0];
 #pragma unroll
-  for (int r = 0; r < h; ++r) y0 = cadd(y0, A[r]);
+  for (int r = 0; r < h; ++r) y0 = cadd_nr(y0, A[r]);
   o[0] = y0;
 #pragma unroll
   for (int q = 1; q <= h; ++q) {
@@ -234,8 +239,8 @@ __device__ __forceinline__ void dft_odd(typename CT<T>::t* v) {
       im.y = madd(im.y, B[r - 1].y, s);
     }
     const V ri = rot<V, INV>(im);  // -i * im (forward)
-    o[q] = cadd(re, ri);
-    o[R - q] = csub(re, ri);
+    o[q] = cadd_nr(re, ri);
+    o[R - q] = csub_nr(re, ri);
   }
 #pragma unroll
   for (int q = 0; q < R; ++q) v[q] = o[q];
@@ -245,12 +250,12 @@ template <typename T, bool INV>
 __device__ __forceinline__ void dft4(typename CT<T>::t& a0, typename CT<T>::t& a1, typename CT<T>::t& a2,
                                      typename CT<T>::t& a3) {
   typedef typename CT<T>::t V;
-  const V t0 = cadd(a0, a2), t1 = csub(a0, a2);
-  const V t2 = cadd(a1, a3), t3 = rot<V, INV>(csub(a1, a3));
-  a0 = cadd(t0, t2);
-  a2 = csub(t0, t2);
-  a1 = cadd(t1, t3);
-  a3 = csub(t1, t3);
+  const V t0 = cadd_nr(a0, a2), t1 = csub_nr(a0, a2);
+  const V t2 = cadd_nr(a1, a3), t3 = rot<V, INV>(csub_nr(a1, a3));
+  a0 = cadd_nr(t0, t2);
+  a2 = csub_nr(t0, t2);
+  a1 = cadd_nr(t1, t3);
+  a3 = csub_nr(t1, t3);
 }
 
 template <typename T, bool INV>
@@ -268,8 +273,8 @@ __device__ __forceinline__ void dft_reg(typename CT<T>::t* v) {
   typedef typename CT<T>::t V;
   if constexpr (R == 2) {
     const V a = v[0], b = v[1];
-    v[0] = cadd(a, b);
-    v[1] = csub(a, b);
+    v[0] = cadd_nr(a, b);
+    v[1] = csub_nr(a, b);
   } else if constexpr (R == 4) {
     dft4<T, INV>(v[0], v[1], v[2], v[3]);
   } else if constexpr (R == 8) {
@@ -283,14 +288,14 @@ __device__ __forceinline__ void dft_reg(typename CT<T>::t* v) {
     const V p1 = INV ? mk<V>(h * (o1.x - o1.y), h * (o1.x + o1.y)) : mk<V>(h * (o1.x + o1.y), h * (o1.y - o1.x));
     const V p2 = rot<V, INV>(o2);
     const V p3 = INV ? mk<V>(-h * (o3.x + o3.y), h * (o3.x - o3.y)) : mk<V>(h * (o3.y - o3.x), -h * (o3.x + o3.y));
-    v[0] = cadd(e0, o0);
-    v[4] = csub(e0, o0);
-    v[1] = cadd(e1, p1);
-    v[5] = csub(e1, p1);
-    v[2] = cadd(e2, p2);
-    v[6] = csub(e2, p2);
-    v[3] = cadd(e3, p3);
-    v[7] = csub(e3, p3);
+    v[0] = cadd_nr(e0, o0);
+    v[4] = csub_nr(e0, o0);
+    v[1] = cadd_nr(e1, p1);
+    v[5] = csub_nr(e1, p1);
+    v[2] = cadd_nr(e2, p2);
+    v[6] = csub_nr(e2, p2);
+    v[3] = cadd_nr(e3, p3);
+    v[7] = csub_nr(e3, p3);
   } else if constexpr (R == 9) {
     // r = 3a + b: Z_b = DFT3_a(x_{3a+b}); T_b(q1) = w9^{b q1} Z_b(q1); y_{q1+3 q2} = DFT3_b(T)(q2)
     V z[9];
@@ -348,7 +353,7 @@ __device__ void stage_reg(const typename CT<T>::t* __restrict__ src, typename CT
     dft_reg<T, R, INV>(v);
     V* out = dst + (size_t)line * ls + g * Ns * R + k;
 #pragma unroll
-    for (int r = 0; r < R; ++r) out[r * Ns] = v[r];
+    for (int r = 0; r < R; ++r) out[r * Ns] = cnorm(v[r]);
   }
 }
 
