@@ -56,6 +56,7 @@ template <typename V> __device__ __forceinline__ V csub(V a, V b) {
 template <typename V> __device__ __forceinline__ V cadd_nr(V a, V b) { return cadd(a, b); }
 template <typename V> __device__ __forceinline__ V csub_nr(V a, V b) { return csub(a, b); }
 template <typename V> __device__ __forceinline__ V cnorm(V a) { return a; }
+template <typename V> __device__ __forceinline__ V cmul_nr(V a, V b) { return cmul(a, b); }
 template <typename V, typename S> __device__ __forceinline__ V cscale(V a, S s) {
   V r;
   r.x = a.x * s;
@@ -233,10 +234,10 @@ __device__ __forceinline__ void dft_odd(typename CT<T>::t* v) {
     for (int r = 1; r <= h; ++r) {
       const T c = (T)cosk<R>((r * q) % R);
       const T s = (T)sink<R>((r * q) % R);
-      re.x = madd(re.x, A[r - 1].x, c);
-      re.y = madd(re.y, A[r - 1].y, c);
-      im.x = madd(im.x, B[r - 1].x, s);
-      im.y = madd(im.y, B[r - 1].y, s);
+      re.x = madd_nr(re.x, A[r - 1].x, c);
+      re.y = madd_nr(re.y, A[r - 1].y, c);
+      im.x = madd_nr(im.x, B[r - 1].x, s);
+      im.y = madd_nr(im.y, B[r - 1].y, s);
     }
     const V ri = rot<V, INV>(im);  // -i * im (forward)
     o[q] = cadd_nr(re, ri);
@@ -348,7 +349,7 @@ __device__ void stage_reg(const typename CT<T>::t* __restrict__ src, typename CT
     if (k > 0) {
       const int ks = k * s;
 #pragma unroll
-      for (int r = 1; r < R; ++r) v[r] = cmul(v[r], root<V, INV>(tw, r * ks));
+      for (int r = 1; r < R; ++r) v[r] = cmul_nr(v[r], root<V, INV>(tw, r * ks));
     }
     dft_reg<T, R, INV>(v);
     V* out = dst + (size_t)line * ls + g * Ns * R + k;
