@@ -211,7 +211,7 @@ fcsph_status fcsph_dft(int n, int nlines, int dir, int prec, const void* in, voi
 #define FCSPH_NOALLOC_SCRATCH_BYTES (1u << 20)
 fcsph_status fcsph_dft_noalloc(int n, int nlines, int dir, int prec, const void* in, void* out, void* stream);
 
-/* Tiling of the one-warp FFT passes: row_lines rows per CTA of the x
+/* Tiling of the FFT passes: row_lines rows per CTA of the x
  * passes, col_pairs column pairs per CTA of the wall-normal passes (each
  * 1..8).  More lines per CTA fill more lanes of each butterfly stage but hold
  * more shared memory, so fewer CTAs fit on an SM; the best choice depends on

@@ -7,8 +7,10 @@
 // The FC-extended grid is never materialised in HBM on the hot path: the
 // continuation is computed in shared memory inside the transform kernels.
 //
-// Every transform kernel runs one warp per CTA, so each barrier of the
-// shared-memory FFT is a warp barrier.  Column kernels (y direction) handle
+// Transform kernels run 32, 64 or 128 threads per CTA (one warp, whose
+// barriers are warp barriers, for full batches; more where a pass has few
+// lines or long ones), the threads of a CTA sharing its lines.  Column
+// kernels (y direction) handle
 // 2*Pp adjacent columns of one instance: two real columns are packed into
 // one complex line (a + i b), transformed together, and separated with the
 // Hermitian split
