@@ -1,0 +1,61 @@
+"""Host logic of bench.py that needs no GPU: the device-code hash that keys
+the recorded DRAM counters (comment edits keep it, code edits change it),
+the lookup that reports null for stale or missing counters, the per-launch
+cost model's scaling, and the whole-job rate over ranks."""
+import os
+import shutil
+
+import pytest
+
+import bench
+
+
+def _tree(tmp_path, kernel_src):
+    d = tmp_path / "paper_2606_06247_gb300" / "csrc"
+    d.mkdir(parents=True)
+    (d / "k.cu").write_text(kernel_src)
+    (d / "api.cpp").write_text("int host_only = 1;\n")
+    return str(tmp_path)
+
+
+def test_source_hash_ignores_comments_and_host_code(tmp_path, monkeypatch):
+    a = _tree(tmp_path / "a", "// header\n__global__ void k(float* x) { x[0] = 1.f; /* set */ }\n")
+    b = _tree(tmp_path / "b", "/* other\n words */ __global__ void k(float* x) {\n  x[0] = 1.f;  // set\n}\n")
+    c = _tree(tmp_path / "c", "__global__ void k(float* x) { x[0] = 2.f; }\n")
+    hashes = []
+    for root in (a, b, c):
+        monkeypatch.setattr(bench, "ROOT", root)
+        hashes.append(bench.kernel_sources_sha256())
+    assert hashes[0] == hashes[1] != hashes[2]
+    # host sources are not part of the key
+    (tmp_path / "a" / "paper_2606_06247_gb300" / "csrc" / "api.cpp").write_text("int host_only = 2;\n")
+    monkeypatch.setattr(bench, "ROOT", a)
+    assert bench.kernel_sources_sha256() == hashes[0]
+
+
+def test_recorded_traffic_is_reported_only_for_matching_code(monkeypatch):
+    key = next(iter(bench.MEASURED_TRAFFIC))
+    monkeypatch.setattr(bench, "kernel_sources_sha256", lambda: bench.KERNEL_SOURCES_SHA256)
+    v, note = bench.measured_traffic(*key)
+    assert v == bench.MEASURED_TRAFFIC[key] and "ncu" in note
+    monkeypatch.setattr(bench, "kernel_sources_sha256", lambda: "0" * 64)
+    v, note = bench.measured_traffic(*key)
+    assert v is None and "changed" in note
+    v, note = bench.measured_traffic("f32x2", "col_mom", 7)
+    assert v is None
+
+
+def test_cost_model_scales_with_the_batch():
+    N, C = 256, 25
+    hy = (N + C) // 2 + 1
+    for kind in bench.PROF_KINDS:
+        by1 = bench.kernel_bytes(kind, N, N, hy, 16, 1)
+        fl1 = bench.kernel_flops(kind, N, N, N + C, N + C, hy, 2 * (N - 1), 1, False)
+        assert bench.kernel_bytes(kind, N, N, hy, 16, 32) == 32 * by1
+        assert bench.kernel_flops(kind, N, N, N + C, N + C, hy, 2 * (N - 1), 32, False) == pytest.approx(32 * fl1)
+    # FP32 spectra are half the FP32-pair size; FP64 fields are not
+    assert bench.kernel_bytes("row_mom", N, N, hy, 8, 1) * 2 == bench.kernel_bytes("row_mom", N, N, hy, 16, 1)
+
+
+def test_job_rate_counts_every_rank():
+    assert bench.job_rate(1000, 4, 2.0) == pytest.approx(4 * 1000 / 2e-3)
