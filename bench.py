@@ -374,6 +374,8 @@ def run_ours(args):
                 ctx.isph_step(u, v, p, fu, fv, 1, use_graph=True, **prm)
                 ev[k + 1].record(stream)
             torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
         launches = ctx.launch_count - n0
         per = [ev[k].elapsed_time(ev[k + 1]) for k in range(steps)]
         total = ev[0].elapsed_time(ev[steps])
