@@ -189,22 +189,29 @@ fcsph_status fcsph_sync(fcsph_ctx* ctx);
 fcsph_status fcsph_dft(int n, int nlines, int dir, int prec, const void* in, void* out, void* stream);
 
 /* fcsph_dft without any allocation.  For callers that cannot allocate device
- * memory -- a CUDA graph being captured, an application whose memory pool
- * owns all device memory, a plugin that must not touch the CUDA allocator --
- * this variant keeps its scratch (roots of unity, Bluestein chirp and filter)
- * in one fixed file-scope device array of FCSPH_NOALLOC_SCRATCH_BYTES per
- * GPU instead of allocating it.  The paper has no counterpart: this is a
+ * memory -- an application whose memory pool owns all device memory, a
+ * plugin or a host thread that must not call into the CUDA allocator -- this
+ * variant keeps its scratch (roots of unity, Bluestein chirp and filter) in
+ * one fixed file-scope device array of FCSPH_NOALLOC_SCRATCH_BYTES per GPU
+ * instead of allocating it.  The paper has no counterpart: this is a
  * deployment convenience, not part of the method.
- *   Same arguments, layout and results as fcsph_dft (up to rounding of the
- *   roots, which are computed on the device).
- *   Limit: the scratch holds 24 bytes per pool entry; the pool has n entries
+ *   Arguments, layout and results as fcsph_dft (up to rounding of the roots,
+ *   which are computed on the device), for prec FCSPH_F64 or FCSPH_F32 only
+ *   (FCSPH_F32X2 returns FCSPH_EINVAL).  The caller allocates in and out.
+ *   Limits: the scratch holds 24 bytes per pool entry; the pool has n entries
  *   when n factors into primes <= 31, else 2m + n (Bluestein, m the smallest
- *   2^a 3^b 5^c 7^d >= 2n - 1).  Larger n returns FCSPH_EINVAL and queues
- *   nothing (any direct length n <= 43690 fits; Bluestein lengths up to about
- *   8000 fit).
- *   Set-up: the first call on each device looks up the array's device
- *   address (cudaGetSymbolAddress) with that device current; make that first
- *   call before any stream capture.
+ *   2^a 3^b 5^c 7^d >= 2n - 1).  Every transform line must also fit in one
+ *   CTA's 227 KB of shared memory: direct lengths n <= 7264 (FCSPH_F64) or
+ *   n <= 14528 (FCSPH_F32); Bluestein m <= 7264 in both precisions (its
+ *   filter is transformed in FP64), i.e. n up to about 3600.  Any other n
+ *   returns FCSPH_EINVAL before anything is queued.
+ *   Errors: FCSPH_ECUDA for a failed launch, or when a CUDA error from
+ *   earlier work is already pending on the calling thread (reported, not
+ *   cleared); fcsph_last_error(NULL, ...) gives the text.
+ *   Set-up: the first call on each device, with that device current, looks
+ *   up the array's device address (cudaGetSymbolAddress) and raises the
+ *   kernels' shared-memory limits; neither allocates.  Make that first call
+ *   before any stream capture.
  *   Sharing: all calls use the same array and every call rewrites the parts
  *   it reads, so calls whose work overlaps on the GPU race; serialise them.
  *   The array stays resident on every GPU that loaded the library until exit. */

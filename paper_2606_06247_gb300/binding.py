@@ -159,11 +159,8 @@ def fcsph_dft_noalloc(x, out, direction=-1, stream=None):
     assert x.is_cuda and x.is_complex() and x.is_contiguous() and out.shape == x.shape and out.dtype == x.dtype
     prec = F64 if x.dtype == torch.complex128 else F32
     n = x.shape[-1]
-    st = lib.fcsph_dft_noalloc(n, x.numel() // n if n else 0, direction, prec, _ptr(x), _ptr(out), _stream(stream))
-    if st == 1:
-        raise FcsphError(st, f"fcsph_dft_noalloc: length {n} needs more than the fixed scratch of "
-                             "FCSPH_NOALLOC_SCRATCH_BYTES (or bad arguments)")
-    _check(st)
+    _check(lib.fcsph_dft_noalloc(n, x.numel() // n if n else 0, direction, prec, _ptr(x), _ptr(out),
+                                 _stream(stream)))
     return out
 
 

@@ -149,6 +149,8 @@ static size_t out_bstride(const fcsph_ctx* c) { return (c->gd.nz > 1 ? 12 : 6) *
 
 }  // namespace
 
+void set_global_error(const std::string& msg) { set_global_err(msg); }
+
 ProfScope::ProfScope(fcsph_ctx* ctx, int k) : c(ctx), kind(k) {
   if (!c || !c->prof_on) return;
   cudaEvent_t a;

@@ -234,6 +234,12 @@ cudaError_t launch_step_corr(fcsph_ctx* c, const StepDev& s, const void* spec_gr
 cudaError_t launch_zpass(fcsph_ctx* c, int prec, void* spec, int nf, size_t bstride, int rows_used, int inv);
 cudaError_t launch_dft_lines(int n, int nlines, int dir, int prec, const void* in, void* out, cudaStream_t st,
                              const fcsph::FftPlan& plan, const void* pool);
+// Dynamic shared memory launch_dft_lines asks for with this plan and precision,
+// and the most any CTA may have; a launch beyond it fails.
+size_t dft_lines_smem(int prec, const fcsph::FftPlan& plan);
+size_t dft_smem_max();
+// Text returned by fcsph_last_error(NULL, ...) (context-free calls).
+void set_global_error(const std::string& msg);
 // out2[0] = sum over instances of sum (r - instance mean)^2, out2[1] = sum b^2
 cudaError_t launch_resid_norm(fcsph_ctx* c, const double* r, const double* b, double* out2);
 cudaError_t launch_axpy(fcsph_ctx* c, double* y, const double* x, const float* xf, int n, double a);

@@ -1357,6 +1357,15 @@ cudaError_t dft_lines_t(int n, int nlines, int dir, const void* in, void* out, c
   return cudaGetLastError();
 }
 
+size_t dft_lines_smem(int prec, const FftPlan& plan) {
+  const size_t cb = prec == FCSPH_F32 ? sizeof(CT<float>::t) : prec == FCSPH_F32X2 ? sizeof(CT<ff>::t)
+                                                                                 : sizeof(CT<double>::t);
+  const size_t per = 2 * (size_t)plan.line_len() * cb;
+  return per * fit_units(per, kSmemBudget, 16);
+}
+
+size_t dft_smem_max() { return kSmemMax; }
+
 cudaError_t launch_dft_lines(int n, int nlines, int dir, int prec, const void* in, void* out, cudaStream_t st,
                              const FftPlan& plan, const void* pool) {
   if (prec == FCSPH_F64) return dft_lines_t<double, double2>(n, nlines, dir, in, out, st, plan, pool);

@@ -1,9 +1,8 @@
 // fcsph_dft_noalloc: the batched DFT of fcsph_dft for callers that may not
-// allocate device memory, e.g. code running inside a CUDA graph capture, a
-// memory pool that forbids outside allocations, or a host process that must
-// not touch the CUDA allocator at all.  Its scratch (roots of unity, the
-// Bluestein chirp and filter) lives in one file-scope device array instead of
-// a cudaMalloc'd buffer.
+// allocate device memory, e.g. an application whose memory pool owns all
+// device memory, or a host thread that must not call into the CUDA allocator
+// at all.  Its scratch (roots of unity, the Bluestein chirp and filter) lives
+// in one file-scope device array instead of a cudaMalloc'd buffer.
 //
 // Sharing and lifetime: every call, on every stream, uses the same array, and
 // the array keeps the last call's contents; each call rewrites all of the
@@ -11,7 +10,12 @@
 // before using it.  Two calls whose work overlaps on the GPU therefore race
 // on the array: serialise them (same stream, or events).  Each GPU that loads
 // the library holds the array (kNoallocScratchBytes) until the process exits.
+//
+// Set-up: the first call on a device, with that device current, looks up the
+// array's device address and raises the kernels' shared-memory limits; both
+// allocate nothing.
 #include <mutex>
+#include <string>
 
 #include <cuda_runtime.h>
 
@@ -30,15 +34,21 @@ void* g_noalloc_ptr[kMaxDevices] = {nullptr};
 
 // Device address of the scratch array on the current device, looked up once
 // per device (the host-side symbol is only a stand-in and must not be passed
-// to a kernel).
-cudaError_t scratch_address(void** out) {
+// to a kernel).  The same first call raises the dynamic shared-memory limit
+// of every kernel on that device, which the transform launches need.
+cudaError_t scratch_address(void** out, const char** where) {
   int dev = 0;
+  *where = "cudaGetDevice";
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lk(g_noalloc_mu);
   if (!g_noalloc_ptr[dev]) {
+    *where = "kernel attributes";
+    e = init_kernel_attributes();
+    if (e != cudaSuccess) return e;
     void* p = nullptr;
+    *where = "cudaGetSymbolAddress";
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
     g_noalloc_ptr[dev] = p;
@@ -61,12 +71,16 @@ bool factor_fixed(int n, Plan1* p) {
       ++cnt[q];
       r /= q;
     }
-  for (int q = 11; r > 1; q += 2) {
+  for (int q = 11; r > 1 && q * q <= r; q += 2) {
     while (r % q == 0) {
       if (q > kMaxDirectPrime || nbig == kMaxStages) return false;
       big[nbig++] = q;
       r /= q;
     }
+  }
+  if (r > 1) {  // the prime left over once q^2 > r
+    if (r > kMaxDirectPrime || nbig == kMaxStages) return false;
+    big[nbig++] = r;
   }
   int rad[kMaxStages];
   int nr = 0;
@@ -166,36 +180,61 @@ __global__ void k_finish_pool(double2* pool, float2* pool32, int total, int bs, 
 
 }  // namespace
 
+namespace {
+
+fcsph_status reject(fcsph_status st, const std::string& msg) {
+  set_global_error("fcsph_dft_noalloc: " + msg);
+  return st;
+}
+
+fcsph_status cuda_reject(cudaError_t e, const char* where) {
+  return reject(FCSPH_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+}  // namespace
+
 extern "C" fcsph_status fcsph_dft_noalloc(int n, int nlines, int dir, int prec, const void* in, void* out,
                                           void* stream) {
-  if (n < 1 || nlines < 0 || (dir != -1 && dir != 1) || (prec != FCSPH_F64 && prec != FCSPH_F32) || !in || !out)
-    return FCSPH_EINVAL;
+  if (n < 1 || nlines < 0 || (dir != -1 && dir != 1) || !in || !out) return reject(FCSPH_EINVAL, "bad argument");
+  if (prec != FCSPH_F64 && prec != FCSPH_F32)
+    return reject(FCSPH_EINVAL, "precision must be FCSPH_F64 or FCSPH_F32 (FCSPH_F32X2 is not supported)");
+  constexpr size_t kEntry = sizeof(double2) + sizeof(float2);
+  if ((size_t)n > kNoallocScratchBytes / kEntry)  // the pool holds at least n entries
+    return reject(FCSPH_EINVAL, "length " + std::to_string(n) + " needs more than the fixed scratch");
   FftPlan P;
   int pool_len = 0;
-  if (!plan_fixed(n, &P, &pool_len)) return FCSPH_EINVAL;
-  const size_t need = (size_t)pool_len * (sizeof(double2) + sizeof(float2));
-  if (need > kNoallocScratchBytes) return FCSPH_EINVAL;  // n too large for the fixed scratch
+  if (!plan_fixed(n, &P, &pool_len)) return reject(FCSPH_EINVAL, "no plan for length " + std::to_string(n));
+  if ((size_t)pool_len * kEntry > kNoallocScratchBytes)
+    return reject(FCSPH_EINVAL, "length " + std::to_string(n) + " needs more than the fixed scratch");
+  // Every transform line must fit in one CTA's shared memory: the main
+  // transform (length n, or m for Bluestein) and, for Bluestein, the FP64
+  // transform of the length-m filter.
+  FftPlan filt;
+  filt.base = P.sub;
+  filt.bs = 0;
+  if (dft_lines_smem(prec, P) > dft_smem_max() || (P.bs && dft_lines_smem(FCSPH_F64, filt) > dft_smem_max()))
+    return reject(FCSPH_EINVAL, "length " + std::to_string(n) + ": a transform line exceeds one CTA's shared memory");
   if (nlines == 0) return FCSPH_OK;
+  // An error pending from earlier work on this thread is not this call's; it
+  // is reported and left in place for its owner.
+  cudaError_t e = cudaPeekAtLastError();
+  if (e != cudaSuccess) return cuda_reject(e, "CUDA error pending before the call");
   void* base = nullptr;
-  if (scratch_address(&base) != cudaSuccess) return FCSPH_ECUDA;
+  const char* where = "";
+  if ((e = scratch_address(&base, &where)) != cudaSuccess) return cuda_reject(e, where);
   double2* pool64 = reinterpret_cast<double2*>(base);
   float2* pool32 = reinterpret_cast<float2*>(reinterpret_cast<unsigned char*>(base) + (size_t)pool_len * sizeof(double2));
   cudaStream_t st = (cudaStream_t)stream;
   const int L = P.bs ? P.sub.n : n;
   k_fill_pool<<<64, 256, 0, st>>>(pool64, L, P.bs, n, P.bs ? P.sub.n : 0, P.chirp, P.bhat);
-  if (cudaGetLastError() != cudaSuccess) return FCSPH_ECUDA;
-  if (P.bs) {
-    FftPlan direct;
-    direct.base = P.sub;
-    direct.bs = 0;
-    if (launch_dft_lines(P.sub.n, 1, -1, FCSPH_F64, pool64 + P.bhat, pool64 + P.bhat, st, direct, pool64) !=
-        cudaSuccess)
-      return FCSPH_ECUDA;
-  }
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_reject(e, "fill pool");
+  if (P.bs && (e = launch_dft_lines(P.sub.n, 1, -1, FCSPH_F64, pool64 + P.bhat, pool64 + P.bhat, st, filt, pool64)) !=
+                  cudaSuccess)
+    return cuda_reject(e, "Bluestein filter");
   k_finish_pool<<<64, 256, 0, st>>>(pool64, pool32, pool_len, P.bs, P.bhat, P.bs ? P.sub.n : 1);
-  if (cudaGetLastError() != cudaSuccess) return FCSPH_ECUDA;
-  if (launch_dft_lines(n, nlines, dir, prec, in, out, st, P,
-                       prec == FCSPH_F64 ? (const void*)pool64 : (const void*)pool32) != cudaSuccess)
-    return FCSPH_ECUDA;
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_reject(e, "finish pool");
+  if ((e = launch_dft_lines(n, nlines, dir, prec, in, out, st, P,
+                            prec == FCSPH_F64 ? (const void*)pool64 : (const void*)pool32)) != cudaSuccess)
+    return cuda_reject(e, "transform");
   return FCSPH_OK;
 }
