@@ -104,16 +104,23 @@ def gram_params(n_match, n_cont):
     return T, K
 
 
-def gram_table(n_match, n_cont, bc=DIRICHLET, dps=80):
+def gram_table(n_match, n_cont, bc=DIRICHLET, dps=80, modes=None, ridge=0.0):
     """E for FC(Gram) (Sec. 4.5), construction in the module docstring.
 
     bc is accepted for interface symmetry; the Gram continuation treats
     Dirichlet and Neumann data alike (the Neumann condition is carried by the
-    data themselves)."""
+    data themselves).
+
+    modes, ridge: alternatives kept only to measure the conditioning/accuracy
+    trade-off of the construction (the tables in use take the defaults):
+    `modes` trig modes instead of floor(T/4), and a ridge (Tikhonov) term
+    ridge^2 * max_i (A^T A)_ii * I added to the normal equations."""
     import mpmath as mp
 
     d, C = n_match, n_cont
     T, K = gram_params(d, C)
+    if modes is not None:
+        K = modes
     with mp.workdps(dps):
         ovs = GRAM_OVERSAMPLE
         u_match = [mp.mpf(i) / ovs for i in range((d - 1) * ovs + 1)]
@@ -142,6 +149,9 @@ def gram_table(n_match, n_cont, bc=DIRICHLET, dps=80):
         # Least squares by the normal equations, exact enough at this precision.
         AtA = A.T * A
         Atb = A.T * rhs
+        if ridge:
+            scale = max(AtA[i, i] for i in range(AtA.rows))
+            AtA = AtA + (mp.mpf(ridge) ** 2 * scale) * mp.eye(AtA.rows)
         B = mp.matrix([trig_row(mp.mpf(u)) for u in range(d, d + C)])
         Er = np.zeros((C, d))
         for a in range(d):

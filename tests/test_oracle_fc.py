@@ -120,3 +120,55 @@ def test_extend2d_tensor_product_commutes():
     b = fc.extend_last_axis(fc.extend_last_axis(f.T, E).T.T, E).T  # x first, then y
     b = fc.extend_last_axis(fc.extend_last_axis(f.T, E).T, E)
     np.testing.assert_allclose(a, b, rtol=0, atol=1e-9 * np.abs(a).max())
+
+
+# ||E||_inf (largest row sum of |E|) of the FC(Gram) tables, d = 5: the
+# continuation of the degree-4 Gram polynomial across a C-node gap at the
+# table's bandwidth (floor(T/4) modes over period T) needs excursions of a few
+# thousand times the data; this bound pins the conditioning of the tables in
+# use (a construction change that worsens it fails here).
+GRAM_NORM_BOUND = {22: 1.1e4, 24: 1.5e4, 25: 1.75e4, 26: 2.0e4, 28: 2.7e4, 32: 4.5e4}
+
+
+@pytest.mark.parametrize("n_cont", sorted(GRAM_NORM_BOUND))
+def test_gram_table_norm_is_bounded(n_cont):
+    E = gram_golden(5, n_cont)
+    assert np.abs(E).sum(axis=1).max() <= GRAM_NORM_BOUND[n_cont]
+    # ... and it grows with the gap: longer continuations at a fixed bandwidth
+    # per node swing further
+    if n_cont > 22:
+        assert np.abs(E).sum(axis=1).max() > np.abs(gram_golden(5, 22)).sum(axis=1).max()
+
+
+def _poly_derivative_error(E, N=64):
+    y = np.linspace(0, 1, N)
+    dy = y[1] - y[0]
+    worst = 0.0
+    for deg in range(5):
+        c = np.random.default_rng(deg).uniform(-1, 1, deg + 1)
+        f = sum(c[i] * y ** i for i in range(deg + 1))
+        fp = sum(i * c[i] * y ** (i - 1) for i in range(1, deg + 1)) if deg > 0 else 0 * y
+        F = fc.extend_last_axis(f, E)
+        worst = max(worst, np.abs(_spectral_derivative(F, dy)[:N] - fp).max())
+    return worst
+
+
+def test_gram_norm_accuracy_trade_off():
+    # Lowering ||E|| costs accuracy.  The same blend-to-zero fit with twice the
+    # bandwidth (T/2 - 1 modes) and a ridge term of 1e-16 relative has a 13x
+    # smaller norm, but its continuation carries content near the grid's
+    # Nyquist frequency: the Fourier derivative of extended polynomials is
+    # then wrong by ~5e-4 instead of ~2e-10, and refinement no longer helps.
+    E0 = gram_golden(5, 25)
+    T, _ = fc.gram_params(5, 25)
+    E1 = fc.gram_table(5, 25, dps=60, modes=T // 2 - 1, ridge=1e-16)
+    n0 = np.abs(E0).sum(axis=1).max()
+    n1 = np.abs(E1).sum(axis=1).max()
+    assert n1 < n0 / 10
+    e0, e1 = _poly_derivative_error(E0), _poly_derivative_error(E1)
+    assert e0 < 2e-9 and e1 > 1e-4, (e0, e1)
+    # and it no longer continues constants: with the wider band the ridge term
+    # prefers a continuation that sags between the two fit intervals (the
+    # smallest-norm trig polynomial equal to 1 on both is not the constant)
+    assert np.abs(E0 @ np.ones(10) - 1.0).max() < 1e-11
+    assert np.abs(E1 @ np.ones(10) - 1.0).max() > 0.1
