@@ -66,6 +66,8 @@ def parse():
                          "on --batch planes of 1024^2, for ncu captures on a small batch")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-microbench", action="store_true",
+                    help="skip the plane and line operator microbenchmarks of the default run")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     return ap.parse_args()
 
@@ -227,16 +229,30 @@ def fp64_peak_tflops(sm_mhz=2070.0):
     return 152 * 2 * 2 * sm_mhz * 1e6 / 1e12
 
 
+def fp32_peak_tflops(sm_mhz=2070.0):
+    """GB300 FP32 FMA rate: 152 SMs x 128 FP32 lanes x 2 flops x clock."""
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
 # FP32 instructions per algorithmic flop of FP32-pair arithmetic, counted on
 # the radix-2 butterfly (1 complex multiply + 2 complex adds = 10 flops): a
 # pair add is 11 FP32 instructions (TwoSum 6, low-part adds 2, Fast2Sum 3), a
 # pair multiply 7 (product, 3 FMAs, Fast2Sum 3); 4 multiplies + 6 adds = 94.
+# Used only for the issue-efficiency figure (FP32 instructions the achieved
+# pair-flop rate implies, over the FP32 lane issue rate), not as a peak.
 FF_INST_PER_FLOP = 94 / 10
 
 
-def ff_peak_tflops(sm_mhz=2070.0):
-    """FP32-pair flop rate: 152 SMs x 128 FP32 lanes x clock / FF_INST_PER_FLOP."""
-    return 152 * 128 * sm_mhz * 1e6 / FF_INST_PER_FLOP / 1e12
+def fp32_lane_inst_rate(sm_mhz=2070.0):
+    """FP32 instructions per second over all lanes: 152 SMs x 128 lanes x clock."""
+    return 152 * 128 * sm_mhz * 1e6
+
+
+# Algorithmic bytes per particle-update of one FOP substep (the four fused
+# passes u,v -> u*,v*; u*,v* -> b; b -> phi; phi,u*,v* -> u,v, each reading
+# and writing its fields once): 72 B with FP32 transforms and spectra held
+# on chip, 112 B for plain FP64.  An RK3 step is three substeps.
+STEP_BYTES_PER_UPDATE = {"f32": 72, "f32x2": 72, "f64": 112}
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of a kernel kind, from one ncu
@@ -417,24 +433,37 @@ def run_ours(args):
         d["alg_gflop"] = fl / 1e9
         d["gflops"] = fl / (d["avg_ms"] * 1e-3) / 1e9 if fl else None
     traffic, traffic_note = measured_traffic(args.prec, dom, B)
+    clk_mhz = peaks.get("sm_max_mhz", 2070.0)
     if args.prec in ("f64", "f32x2"):
         if args.prec == "f64":
-            pk = fp64_peak_tflops(peaks.get("sm_max_mhz", 2070.0)) * 1e3
-            src = "derived: 152 SMs x 2 FP64 lanes x 2 flop x max SM clock"
+            pk = fp64_peak_tflops(clk_mhz) * 1e3
+            src = "derived: 152 SMs x 2 FP64 FMA lanes x 2 flop x max SM clock"
         else:
-            pk = ff_peak_tflops(peaks.get("sm_max_mhz", 2070.0)) * 1e3
-            src = (f"derived: 152 SMs x 128 FP32 lanes x max SM clock / {FF_INST_PER_FLOP} FP32 instructions "
-                   "per FP32-pair flop")
+            pk = fp32_peak_tflops(clk_mhz) * 1e3
+            src = ("derived: 152 SMs x 128 FP32 FMA lanes x 2 flop x max SM clock (FP32-pair flops counted as "
+                   "flops, 5 n log2 n per transform)")
         roof = {"kernel": dom, "bound": "alu", "achieved": kinds[dom]["gflops"], "peak": pk, "unit": "GFLOP/s",
                 "frac": (kinds[dom]["gflops"] or 0) / pk, "traffic": traffic, "traffic_source": traffic_note,
                 "peak_source": src,
                 "alg_gflop_per_launch": kinds[dom]["alg_gflop"], "avg_launch_ms": kinds[dom]["avg_ms"],
                 "hbm_gbs_alg": kinds[dom]["gbs"], "hbm_frac_of_measured": (kinds[dom]["gbs"] or 0) / peaks["hbm_gbs"]}
+        if args.prec == "f32x2":
+            roof["issue_efficiency"] = ((kinds[dom]["gflops"] or 0) * 1e9 * FF_INST_PER_FLOP
+                                        / fp32_lane_inst_rate(clk_mhz))
+            roof["issue_efficiency_note"] = (f"FP32 instructions implied by the achieved pair-flop rate at "
+                                             f"{FF_INST_PER_FLOP} per flop (radix-2 butterfly count), over 152 x 128 "
+                                             "FP32 lanes x max SM clock")
     else:
         roof = {"kernel": dom, "bound": "hbm", "achieved": kinds[dom]["gbs"], "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": (kinds[dom]["gbs"] or 0) / peaks["hbm_gbs"], "traffic": traffic, "traffic_source": traffic_note,
                 "peak_source": peak_src + " hbm_gbs", "alg_bytes_per_launch": kinds[dom]["alg_bytes"],
                 "avg_launch_ms": kinds[dom]["avg_ms"]}
+    step_bytes = B * N * N * 3 * STEP_BYTES_PER_UPDATE[args.prec]
+    step_gbs = step_bytes / (t_max / args.steps * 1e-3) / 1e9
+    roof["step"] = {"alg_bytes_per_particle_update": 3 * STEP_BYTES_PER_UPDATE[args.prec],
+                    "alg_bytes_per_step": step_bytes, "alg_GBps": step_gbs, "frac_of_hbm": step_gbs / peaks["hbm_gbs"],
+                    "note": (f"{STEP_BYTES_PER_UPDATE[args.prec]} B per particle-update per FOP substep x 3 RK3 "
+                             "substeps over ms_per_step, against the measured HBM copy rate")}
     prof_total = sum(d["ms"] for d in kinds.values())
     for d in kinds.values():
         d["share"] = d["ms"] / prof_total
@@ -521,6 +550,19 @@ def run_ours(args):
         if args.prec != "f64":
             compare["headline_equal_l2"] = compare.get(f"{args.prec}_equal_l2")
 
+    # ---- the operator microbenchmarks (FP32 fields) at full size, rank 0 at N = 1:
+    # 256 planes of 1024^2 (spectral_op DX+DY+LAP, per-pass algorithmic GB/s) and
+    # 4096 lines of 512 (line_op DY+LAP, one fused kernel)
+    micro = None
+    if rank == 0 and ws == 1 and not args.no_microbench:
+        torch.cuda.empty_cache()
+        planes, _ = measure_planes(max(3, min(args.steps, 5)), 3)
+        lines, _ = measure_lines(max(8, args.steps), 3, precs=(("f32", 25), ("f32", 28)))
+        micro = {"planes_256x1024x1024_f32": planes, "lines_4096x512_f32": lines,
+                 "peak": peaks["hbm_gbs"], "peak_source": peak_src + " hbm_gbs",
+                 "note": ("algorithmic bytes: planes 4 B in + 3 x 4 B out per node per call and each pass's own "
+                          "reads and writes; lines 4 B in + 2 x 4 B out per node")}
+
     # ---- CPU baseline (oracle), rank 0 only
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -550,6 +592,7 @@ def run_ours(args):
             "gpu_launches": launches,
             "clocks": clocks,
             "compare": compare,
+            "operator_microbench": micro,
         }
         print(json.dumps(line))
     if ws > 1:
@@ -628,6 +671,25 @@ def run_serving(args):
             s1.tick(0.0)
     torch.cuda.synchronize()
     serial = summarize(base, time.perf_counter() - t0)
+    # per-instance error of the served (mixed) result against the same request
+    # on the plain FP64 path (which is at parity with the FP64 oracle): relative
+    # L2 and L-infinity of the velocity
+    per_inst = []
+    for r, r0 in zip(rs, base):
+        if r.result is None or r0.result is None:
+            continue
+        comps = ("u", "v", "w") if "w" in r.result else ("u", "v")
+        a = np.stack([r.result[c] for c in comps])
+        ref = np.stack([r0.result[c] for c in comps])
+        nrm = max(float(np.linalg.norm(ref)), 1e-300)
+        per_inst.append({"rid": r.rid, "kind": r.kind, "n": r.n, "re": r.re, "steps": r.steps,
+                         "rel_l2_velocity": float(np.linalg.norm(a - ref)) / nrm,
+                         "linf_velocity": float(np.abs(a - ref).max())})
+    errs = sorted(d["rel_l2_velocity"] for d in per_inst)
+    err_summary = {"instances": len(errs), "max_rel_l2": errs[-1] if errs else None,
+                   "median_rel_l2": errs[len(errs) // 2] if errs else None,
+                   "max_linf": max((d["linf_velocity"] for d in per_inst), default=None),
+                   "reference": "the same request run alone on the plain FP64 path (batch 1)"}
     print(json.dumps({
         "metric": METRIC, "value": served["particle_updates_per_s"], "unit": "particle-updates/s", "n_gpus": 1,
         "steps": steps, "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
@@ -635,20 +697,33 @@ def run_serving(args):
         "config": {"workload": desc, "precision": args.prec, "slots_per_size_class": args.slots, "fc_cont": args.fc_cont},
         "latency_ms": {"p50": served["step_latency_ms_p50"], "p99": served["step_latency_ms_p99"]},
         "served": served, "serial_plain_fp64": serial,
+        "error_vs_fp64": err_summary, "per_instance": per_inst,
         "speedup_vs_serial": served["particle_updates_per_s"] / serial["particle_updates_per_s"]}))
 
 
 WIDTH_SWEEP = [(r, c) for r in (32, 64, 128) for c in (32, 64, 128)]
 
 
-def run_planes(args):
-    """FC-extended operator microbench on 256 planes of
-    1024 x 1024 (x periodic, walls in y), FP32 fields, d/dx, d/dy and the
-    Laplacian per call.  Algorithmic bytes: 4 B in + 3 x 4 B out per node."""
+def plane_kernel_bytes(kind, P, nx, ny, hy, nout=3):
+    """Algorithmic bytes of one launch of each pass of the FP32 plane operator
+    (whole batch of P planes): the FP32 field in (col_fwd), the half-spectrum
+    (hy rows of nx complex FP32) out of the y pass, into and nout spectra out
+    of the x pass, and nout spectra in and FP32 fields out of the inverse y
+    pass."""
+    S = P * hy * nx * 8
+    F = P * nx * ny * 4
+    return {"col_fwd": F + S, "row_op": S + nout * S, "col_out": nout * S + nout * F}.get(kind, 0)
+
+
+def measure_planes(steps, warmup, sweep_widths=True):
+    """FC-extended operator microbench on 256 planes of 1024 x 1024 (x periodic,
+    walls in y), FP32 fields, d/dx, d/dy and the Laplacian per call, for
+    n_cont = 25 (n_e = 1049, Bluestein) and 26 (n_e = 1050).  Algorithmic bytes
+    per call: 4 B in + 3 x 4 B out per node; per pass: each kernel's own
+    reads and writes (plane_kernel_bytes), from CUDA events on the launching
+    stream around every eager launch."""
     import numpy as np
     import torch
-    import __graft_entry__
-    __graft_entry__.build()
     from paper_2606_06247_gb300 import binding as b
     from paper_2606_06247_gb300 import inputs
     P, n = 256, 1024
@@ -656,7 +731,8 @@ def run_planes(args):
     f = torch.tensor(np.tile(base, (P // 4, 1, 1)), dtype=torch.float32, device="cuda")
     outs = [torch.empty_like(f) for _ in range(3)]
     peaks, src = load_peaks()
-    lines = {}
+    res = {}
+
     def call_ms(ctx, calls):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
@@ -668,22 +744,44 @@ def run_planes(args):
 
     for n_cont in (25, 26):
         ctx = b.Context(n, n, n / (n - 1), 1.0, batch=P, n_cont=n_cont, family="G4", h_over_dx=1.3, prec="f32")
-        # CTA widths: a short sweep (row, column threads), then the timed calls at the fastest
         sweep = {}
-        for w in WIDTH_SWEEP:
-            ctx.set_cta_threads(*w)
-            call_ms(ctx, 1)
-            sweep[f"{w[0]},{w[1]}"] = call_ms(ctx, 2)
-        best_w = min(sweep, key=sweep.get)
-        ctx.set_cta_threads(*[int(x) for x in best_w.split(",")])
-        call_ms(ctx, max(3, args.warmup))
-        ms = call_ms(ctx, args.steps)
+        if sweep_widths:  # CTA widths: a short sweep (row, column threads), then the timed calls at the fastest
+            for w in WIDTH_SWEEP:
+                ctx.set_cta_threads(*w)
+                call_ms(ctx, 1)
+                sweep[f"{w[0]},{w[1]}"] = call_ms(ctx, 2)
+            best_w = min(sweep, key=sweep.get)
+            ctx.set_cta_threads(*[int(x) for x in best_w.split(",")])
+        call_ms(ctx, max(3, warmup))
+        ms = call_ms(ctx, max(3, steps))
         gbs = P * n * n * 16 / (ms * 1e-3) / 1e9
-        lines[f"n_cont={n_cont} (n_e={n + n_cont})"] = {"ms_per_call": ms, "alg_GBps": gbs, "frac_of_hbm": gbs / peaks["hbm_gbs"],
-                                                        "launches_per_call": 3, "cta_threads": best_w,
-                                                        "width_sweep_ms": sweep}
+        # per-pass durations (eager, events on the launching stream)
+        ctx.set_profiling(True)
+        for _ in range(3):
+            ctx.spectral_op(f, ["DX", "DY", "LAP"], outs)
+        prof = ctx.get_profile()
+        ctx.set_profiling(False)
+        hy = (n + n_cont) // 2 + 1
+        passes = {}
+        for k, (tms, cnt) in prof.items():
+            by = plane_kernel_bytes(k, P, n, n, hy)
+            avg = tms / cnt
+            passes[k] = {"avg_ms": avg, "alg_bytes": by, "alg_GBps": by / (avg * 1e-3) / 1e9,
+                         "frac_of_hbm": by / (avg * 1e-3) / 1e9 / peaks["hbm_gbs"]}
+        res[f"n_cont={n_cont} (n_e={n + n_cont})"] = {
+            "ms_per_call": ms, "alg_GBps": gbs, "frac_of_hbm": gbs / peaks["hbm_gbs"], "launches_per_call": 3,
+            "cta_threads": list(ctx.get_cta_threads()), "width_sweep_ms": sweep, "passes": passes}
         del ctx
         torch.cuda.empty_cache()
+    del f, outs
+    torch.cuda.empty_cache()
+    return res, src
+
+
+def run_planes(args):
+    import __graft_entry__
+    __graft_entry__.build()
+    lines, src = measure_planes(args.steps, args.warmup)
     best = max(v["alg_GBps"] for v in lines.values())
     print(json.dumps({"metric": "FC-extended spectral operator throughput (algorithmic HBM GB/s)", "value": best,
                       "unit": "GB/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
@@ -693,23 +791,21 @@ def run_planes(args):
                       "variants": lines}))
 
 
-def run_lines(args):
-    """Line-operator microbench: 4096 independent wall-normal lines of 512 nodes (walls
-    at both ends), band-limited trig sums plus degree-4 polynomials, d/dy and
-    d^2/dy^2 per call through line_op (one fused kernel).  Algorithmic bytes:
-    4 B in + 2 x 4 B out per node (FP32 fields).  One call moves 25 MB, which
-    fits in L2, so the timed calls rotate through 8 input/output sets (200 MB)."""
-    import numpy as np
+def measure_lines(steps, warmup, precs=(("f32", 25), ("f32", 28), ("f32x2", 25), ("f64", 25))):
+    """Line-operator microbench: 4096 independent wall-normal lines of 512 nodes
+    (walls at both ends), band-limited trig sums plus degree-4 polynomials,
+    d/dy and d^2/dy^2 per call through line_op (one fused kernel).
+    Algorithmic bytes: 4 B in + 2 x 4 B out per node (FP32 fields; 8 B for
+    FP64 I/O).  One call moves 25 MB, which fits in L2, so the timed calls
+    rotate through 8 input/output sets (200 MB)."""
     import torch
-    import __graft_entry__
-    __graft_entry__.build()
     from paper_2606_06247_gb300 import binding as b
     from paper_2606_06247_gb300 import inputs
     L, n, sets = 4096, 512, 8
     base = inputs.band_limited_lines(L, n, seed=12345)
     peaks, src = load_peaks()
     variants = {}
-    for prec, n_cont in (("f32", 25), ("f32", 28), ("f32x2", 25), ("f64", 25)):
+    for prec, n_cont in precs:
         dt = torch.float32 if prec == "f32" else torch.float64
         dy = 1.0 / (n - 1)
         ctx = b.Context(L, n, L * dy, 1.0, batch=1, n_cont=n_cont, family="G4", h_over_dx=1.3, prec=prec)
@@ -732,8 +828,8 @@ def run_lines(args):
                 call_ms(sets)
                 sweep[w] = call_ms(2 * sets)
             ctx.set_cta_threads(32, min(sweep, key=sweep.get))
-        call_ms(max(3, args.warmup, sets))
-        calls = max(args.steps, sets)
+        call_ms(max(3, warmup, sets))
+        calls = max(steps, sets)
         ms = call_ms(calls)
         es = 4 if prec == "f32" else 8
         gbs = L * n * 3 * es / (ms * 1e-3) / 1e9
@@ -742,6 +838,14 @@ def run_lines(args):
             "lines_per_s": L / (ms * 1e-3), "cta_threads": ctx.get_cta_threads()[1], "width_sweep_ms": sweep}
         del ctx, fs, outs
         torch.cuda.empty_cache()
+    return variants, src
+
+
+def run_lines(args):
+    import __graft_entry__
+    __graft_entry__.build()
+    variants, src = measure_lines(args.steps, args.warmup)
+    peaks, _ = load_peaks()
     head = variants["f32 n_cont=25 (n_e=537)"]
     print(json.dumps({"metric": "FC-extended line operator throughput (algorithmic HBM GB/s)", "value": head["alg_GBps"],
                       "unit": "GB/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,

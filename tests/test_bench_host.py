@@ -59,3 +59,17 @@ def test_cost_model_scales_with_the_batch():
 
 def test_job_rate_counts_every_rank():
     assert bench.job_rate(1000, 4, 2.0) == pytest.approx(4 * 1000 / 2e-3)
+
+
+def test_hardware_peaks_and_plane_pass_bytes():
+    import bench
+    assert abs(bench.fp32_peak_tflops(2070.0) - 80.55) < 0.01     # 152 x 128 x 2 x 2.07 GHz
+    assert abs(bench.fp64_peak_tflops(2070.0) - 1.2586) < 1e-3    # 152 x 2 x 2 x 2.07 GHz
+    assert bench.fp32_lane_inst_rate(2070.0) * 2 / 1e12 == bench.fp32_peak_tflops(2070.0)
+    P, n, hy = 256, 1024, 526
+    passes = {k: bench.plane_kernel_bytes(k, P, n, n, hy) for k in ("col_fwd", "row_op", "col_out")}
+    # every pass moves at least the call's own input or output; together they move
+    # more than the call's 16 B per node (the spectra round-trip HBM between passes)
+    assert passes["col_fwd"] > P * n * n * 4 and passes["col_out"] > P * n * n * 12
+    assert sum(passes.values()) > P * n * n * 16
+    assert bench.STEP_BYTES_PER_UPDATE == {"f32": 72, "f32x2": 72, "f64": 112}
