@@ -288,3 +288,51 @@ def summarize(requests, wall_s):
             "particle_updates": updates, "wall_s": wall_s, "particle_updates_per_s": updates / wall_s if wall_s else None,
             "step_latency_ms_p50": float(np.percentile(lat, 50)) if lat.size else None,
             "step_latency_ms_p99": float(np.percentile(lat, 99)) if lat.size else None}
+
+
+# ---------------------------------------------------------------- several GPUs
+def place_requests(requests, world_size, prec="f64", fc_cont=25):
+    """Placement of independent requests on `world_size` ranks (one GPU each):
+    in arrival order, each request goes to the rank whose placed device
+    footprint (one slot of the request's size class per request) is
+    smallest, the lower rank on a tie.  Returns (per-rank request lists,
+    per-rank footprint bytes).  The solves are independent, so ranks
+    exchange nothing while they run."""
+    load = [0] * world_size
+    out = [[] for _ in range(world_size)]
+    for r in sorted(requests, key=lambda q: (q.arrival, q.rid)):
+        nc = smooth_n_cont(r.n) if fc_cont == "smooth" else fc_cont
+        need = footprint_bytes(r.n, 1, prec, r.kind == "channel3d", nc)
+        k = min(range(world_size), key=lambda i: (load[i], i))
+        out[k].append(r)
+        load[k] += need
+    return out, load
+
+
+def serve_on_ranks(requests, rank, world_size, make_server, time_scale=1.0):
+    """Serves this rank's share of `requests` (place_requests) with its own
+    Server (make_server() builds it on this rank's device) and gathers every
+    rank's finished requests on rank 0 through torch.distributed (host
+    objects, once at the end).  Rank 0 returns (all requests ordered by rid,
+    per-rank wall seconds); the other ranks return (None, None)."""
+    import torch.distributed as dist
+    srv = make_server()
+    parts, _ = place_requests(requests, world_size, srv.prec, srv.fc_cont)
+    mine = parts[rank]
+    wall = srv.run(mine, time_scale=time_scale) if mine else 0.0
+    payload = {"wall_s": wall,
+               "requests": [dict(rid=r.rid, kind=r.kind, n=r.n, re=r.re, steps=r.steps, arrival=r.arrival,
+                                 done_steps=r.done_steps, latencies_ms=list(r.latencies_ms), result=r.result,
+                                 rank=rank) for r in mine]}
+    gathered = [None] * world_size if rank == 0 else None
+    dist.gather_object(payload, gathered, dst=0)
+    if rank != 0:
+        return None, None
+    done = []
+    for g in gathered:
+        for d in g["requests"]:
+            r = Request(d["rid"], d["kind"], d["n"], d["re"], d["steps"], d["arrival"])
+            r.done_steps, r.latencies_ms, r.result = d["done_steps"], d["latencies_ms"], d["result"]
+            r.rank = d["rank"]
+            done.append(r)
+    return sorted(done, key=lambda r: r.rid), [g["wall_s"] for g in gathered]
