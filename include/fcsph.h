@@ -162,6 +162,22 @@ fcsph_status line_op(fcsph_ctx* ctx, const void* f, unsigned op_mask, int bc, vo
  * 2D grids only (FCSPH_EUNSUPPORTED on a 3D grid). */
 fcsph_status spectral_div(fcsph_ctx* ctx, const void* fx, const void* fy, void* out);
 
+/* The projection on the FC-extended periodic grid, the alternative to the
+ * physical-domain PPE of Sec. 5.1 that Sec. 5.2 names and leaves for future
+ * work.  Both components are FC-extended (Dirichlet table) and transformed;
+ * with g = (kx, ky) the wavevector of the gradient symbols S_x = i kx W_hat,
+ * S_y = i ky W_hat (each component zero on its own Nyquist line), every mode
+ * is projected onto the null space of the extended divergence S_x U + S_y V:
+ *   (U, V) <- (U, V) - g (g . (U, V)) / |g|^2     (modes with g = 0 kept),
+ * i.e. phi_hat = (S_x U + S_y V)/(S_x^2 + S_y^2) and (U, V) -= (S_x, S_y) phi_hat;
+ * then inverse transforms and truncation to the physical nodes.  The
+ * extended field it truncates has zero discrete divergence at round-off.
+ * fx, fy, out_x, out_y: [batch][nx][ny] in the context's I/O type (out may
+ * not alias the inputs).  2D grids only (FCSPH_EUNSUPPORTED on a 3D grid).
+ * Note: used inside a time step (truncate, reset the walls, re-extend) this
+ * projection is unstable; isph_step keeps the physical-domain solve. */
+fcsph_status spectral_project(fcsph_ctx* ctx, const void* fx, const void* fy, void* out_x, void* out_y);
+
 /* Eqs. 31-33: phi with lap(phi) = rhs under the DFT(x) x DCT-I(y) (periodic x)
  * or DCT-I x DCT-I (walled x) diagonalisation; the (0,0) mode of phi is 0.
  * With ppe_refine_iters > 0 (F32 contexts) each sweep forms the residual in

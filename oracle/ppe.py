@@ -15,7 +15,8 @@ lap(phi) = b.  The (0,0) mode is set to zero (Neumann solvability).
 """
 import numpy as np
 
-from .dft import dft_matrix, idft_matrix, dct1_matrix, idct1_matrix, signed_wavenumbers
+from .dft import dct1_matrix, dft2, dft_matrix, idct1_matrix, idft2, idft_matrix, signed_wavenumbers
+from .fc import extend2d
 
 
 def eigenvalues(nx, ny, Lx, Ly, x_walls):
@@ -60,3 +61,34 @@ def laplacian(phi, Lx, Ly, x_walls):
     lam_k, lam_l = eigenvalues(nx, ny, Lx, Ly, x_walls)
     ph = Tx @ np.asarray(phi, dtype=np.float64) @ Ty.T
     return np.real(Txi @ (-(lam_k[:, None] ** 2 + lam_l[None, :] ** 2) * ph) @ Tyi.T).copy()
+
+
+def extended_projection(us, vs, Sx, Sy, E_y, E_x=None, return_extended=False):
+    """The projection on the FC-extended periodic grid (the alternative to the
+    physical-domain solve that Sec. 5.2 names and leaves for future work).
+
+    With the gradient symbols G = (Sx, Sy) of the operators (Eq. 13/16; they
+    are i k W_hat with the odd symbols zero on their Nyquist lines), the
+    pressure is the Fourier multiplier solve of div(grad phi) = div(u*) on the
+    extended grid, and the corrected spectrum is
+
+        phi_hat = (Sx U + Sy V) / (Sx^2 + Sy^2),   (U, V) <- (U, V) - (Sx, Sy) phi_hat
+
+    (modes where Sx^2 + Sy^2 = 0 are left as they are; their divergence is
+    zero).  The extended divergence Sx U + Sy V of the result is zero at every
+    mode.  Returns the corrected fields on the physical nodes (and the
+    corrected extended fields when return_extended)."""
+    nx, ny = us.shape
+    U = dft2(extend2d(np.asarray(us, dtype=np.float64), E_y, E_x))
+    V = dft2(extend2d(np.asarray(vs, dtype=np.float64), E_y, E_x))
+    GG = Sx * Sx + Sy * Sy
+    nz = np.abs(GG) > 0
+    phi = np.zeros_like(U)
+    phi[nz] = (Sx[nz] * U[nz] + Sy[nz] * V[nz]) / GG[nz]
+    Un = U - Sx * phi
+    Vn = V - Sy * phi
+    ue, ve = np.real(idft2(Un)), np.real(idft2(Vn))
+    out = (ue[:nx, :ny].copy(), ve[:nx, :ny].copy())
+    if return_extended:
+        return out + (ue, ve)
+    return out

@@ -26,7 +26,7 @@ import numpy as np
 
 from . import fc as fcmod
 from . import ops
-from .ppe import ppe_solve
+from .ppe import extended_projection, ppe_solve
 from .symbols import symbol_closed
 
 RK3_A = (8.0 / 15.0, 2.0 / 15.0, 1.0 / 3.0)
@@ -65,6 +65,10 @@ class Problem:
     u_bottom: float = 0.0
     u_top: float = 0.0
     scheme: str = "fop"
+    # "dct": the physical-domain spectral PPE of Sec. 5.1 (the method);
+    # "extended": the projection on the FC-extended periodic grid that Sec. 5.2
+    # leaves for future work (ppe.extended_projection), kept to measure it
+    proj: str = "dct"
     sym: dict = field(default_factory=dict)
 
     @property
@@ -133,6 +137,10 @@ def substep(p, u, v, Fu_prev, Fv_prev, a, g, z):
     us = momentum_update(u, Fu, Fu_prev, p.force[0], p.dt, a, g, z)
     vs = momentum_update(v, Fv, Fv_prev, p.force[1], p.dt, a, g, z)
     us, vs = wall_reset(p, us, vs)
+    if p.proj == "extended":
+        un, vn = extended_projection(us, vs, S["DX"], S["DY"], p.E_y(D), p.E_x(D))
+        un, vn = wall_reset(p, un, vn)
+        return un, vn, np.zeros_like(u), Fu, Fv
     div = ops.divergence(us, vs, S["DX"], S["DY"], p.E_y(D), p.E_x(D))
     b = (p.rho / (a * p.dt)) * div
     phi = ppe_solve(b, p.Lx, p.Ly, p.x_walls)

@@ -81,6 +81,7 @@ def _load():
         "fc_extend": [P, P, P, I],
         "spectral_op": [P, P, U, I, P],
         "spectral_div": [P, P, P, P],
+        "spectral_project": [P, P, P, P, P],
         "line_op": [P, P, U, I, P],
         "ppe_solve": [P, P, P, ctypes.POINTER(D)],
         "isph_step": [P, ctypes.POINTER(fcsph_state), I, ctypes.POINTER(fcsph_step_params)],
@@ -237,6 +238,13 @@ class Context:
 
     def spectral_div(self, fx, fy, out):
         self._ck(lib.spectral_div(self.h, _ptr(fx), _ptr(fy), _ptr(out)))
+
+    def spectral_project(self, fx, fy, out_x, out_y):
+        """Projection on the FC-extended grid (see include/fcsph.h)."""
+        for t in (fx, fy, out_x, out_y):
+            assert t.is_cuda and t.is_contiguous()
+        assert out_x.data_ptr() not in (fx.data_ptr(), fy.data_ptr()) and out_y.data_ptr() not in (fx.data_ptr(), fy.data_ptr())
+        self._ck(lib.spectral_project(self.h, _ptr(fx), _ptr(fy), _ptr(out_x), _ptr(out_y)))
 
     def ppe_solve(self, rhs, phi, want_resid=False):
         r = ctypes.c_double(0.0)

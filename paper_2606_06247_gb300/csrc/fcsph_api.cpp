@@ -485,6 +485,32 @@ fcsph_status spectral_div(fcsph_ctx* c, const void* fx, const void* fy, void* ou
   return FCSPH_OK;
 }
 
+fcsph_status spectral_project(fcsph_ctx* c, const void* fx, const void* fy, void* out_x, void* out_y) {
+  if (!c || !fx || !fy || !out_x || !out_y) return fail(c, FCSPH_EINVAL, "spectral_project: bad argument");
+  if (c->gd.nz > 1) return fail(c, FCSPH_EUNSUPPORTED, "spectral_project: 2D grids only");
+  // out_x = U - (gx^2 U + gx gy V)/|g|^2, out_y = V - (gx gy U + gy^2 V)/|g|^2
+  RowOps ops = ops_none();
+  ops.nin = 2;
+  ops.nout = 2;
+  const int terms[2][3][2] = {{{0, SYM_ONE}, {0, SYM_NPXX}, {1, SYM_NPXY}}, {{1, SYM_ONE}, {0, SYM_NPXY}, {1, SYM_NPYY}}};
+  for (int o = 0; o < 2; ++o) {
+    ops.nterm[o] = 3;
+    for (int t = 0; t < 3; ++t) {
+      ops.field[o][t] = terms[o][t][0];
+      ops.op[o][t] = terms[o][t][1];
+    }
+  }
+  const int p = c->prec.fft_prec;
+  const void* fl[2] = {fx, fy};
+  void* outs[2] = {out_x, out_y};
+  FCSPH_CK(launch_col_fwd(c, p, 2, fl, p != FCSPH_F32, FCSPH_DIRICHLET, c->spec_in, 0), "spectral_project fwd");
+  FCSPH_CK(launch_row_sym(c, p, c->spec_in, c->spec_out, ops, 1.0 / ((double)c->gd.mx * c->gd.my), FCSPH_DIRICHLET,
+                          FCSPH_PROF_ROW_OP),
+           "spectral_project row");
+  FCSPH_CK(launch_col_out(c, c->spec_out, 2, outs), "spectral_project inv");
+  return FCSPH_OK;
+}
+
 // Iterative refinement of the PPE solution phi64 (double, device) for the
 // right-hand side b64: b0 = b64 without its (0,0) transform mode (FP64), then
 // `iters` sweeps of r = b0 - L phi (FP64) and phi += solve(r) (context

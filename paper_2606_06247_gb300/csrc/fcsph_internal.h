@@ -110,7 +110,11 @@ std::vector<double> what_table(const std::vector<double>& ex, const std::vector<
 
 // Operator descriptors for the spectral row pass: output o is
 // sum_{t < nterm[o]} symbol(op[o][t]) * spectrum(field[o][t]).
-enum { SYM_W = 0, SYM_DX = 1, SYM_DY = 2, SYM_LAP = 3, SYM_DZ = 4 };
+enum { SYM_W = 0, SYM_DX = 1, SYM_DY = 2, SYM_LAP = 3, SYM_DZ = 4,
+       // Leray projection on the extended grid (spectral_project): 1, and
+       // -gx^2/|g|^2, -gx gy/|g|^2, -gy^2/|g|^2 with g the gradient symbols'
+       // wavevector (each component zero on its own Nyquist line), 0 where g = 0
+       SYM_ONE = 5, SYM_NPXX = 6, SYM_NPXY = 7, SYM_NPYY = 8 };
 constexpr int kMaxRowOut = 12;   // 3D momentum: 3 components x (3 gradients + Laplacian)
 constexpr int kMaxRowTerms = 3;  // 3D divergence
 struct RowOps {

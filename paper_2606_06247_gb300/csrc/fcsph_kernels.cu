@@ -272,17 +272,40 @@ __global__ void __launch_bounds__(NT, MinCtas<T, NT>::v) k_col_fwd(GridDev g, co
 // Symbols (Eq. 16 reading): W_hat(s) = e^{-s} sum_{m<n} s^m/m!, s = |k|^2 h^2/4;
 // DX = i kx W_hat, DY = i ky W_hat, DZ = i kz W_hat (each zero on its own
 // axis' Nyquist plane), LAP = -|k|^2 W_hat, W = W_hat (kz = 0 in 2D).
-// Returned as (re, im) in the compute type.
+// Returned as (re, im) in the compute type.  Products and sums of the
+// wavenumbers use round-to-nearest intrinsics, which the compiler never
+// contracts into FMAs: every CTA width then evaluates the same expression.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float div_rn(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double div_rn(double a, double b) { return __ddiv_rn(a, b); }
+__device__ __forceinline__ ff mul_rn(ff a, ff b) { return a * b; }
+__device__ __forceinline__ ff add_rn(ff a, ff b) { return a + b; }
+__device__ __forceinline__ ff div_rn(ff a, ff b) { return a / b; }
+
 template <typename T>
 __device__ __forceinline__ typename CT<T>::t symbol(int op, T kx, T ky, T kz, bool nyq_x, bool nyq_y, bool nyq_z,
                                                     T What) {
   typedef typename CT<T>::t V;
   switch (op) {
     case SYM_W: return mk<V>(What, 0.0);
-    case SYM_DX: return mk<V>(0.0, nyq_x ? (T)0 : kx * What);
-    case SYM_DY: return mk<V>(0.0, nyq_y ? (T)0 : ky * What);
-    case SYM_DZ: return mk<V>(0.0, nyq_z ? (T)0 : kz * What);
-    default: return mk<V>(-(kx * kx + ky * ky + kz * kz) * What, 0.0);
+    case SYM_DX: return mk<V>(0.0, nyq_x ? (T)0 : mul_rn(kx, What));
+    case SYM_DY: return mk<V>(0.0, nyq_y ? (T)0 : mul_rn(ky, What));
+    case SYM_DZ: return mk<V>(0.0, nyq_z ? (T)0 : mul_rn(kz, What));
+    case SYM_LAP: {
+      const T k2 = add_rn(add_rn(mul_rn(kx, kx), mul_rn(ky, ky)), mul_rn(kz, kz));
+      return mk<V>(-mul_rn(k2, What), 0.0);
+    }
+    case SYM_ONE: return mk<V>((T)1.0, 0.0);
+    default: {  // projection terms: g = (i kx W_hat, i ky W_hat) up to the common factor i W_hat
+      const T gx = nyq_x ? (T)0 : kx, gy = nyq_y ? (T)0 : ky;
+      const T g2 = add_rn(mul_rn(gx, gx), mul_rn(gy, gy));
+      if (!(static_cast<float>(g2) > 0.f)) return mk<V>(0.0, 0.0);
+      const T num = op == SYM_NPXX ? mul_rn(gx, gx) : op == SYM_NPXY ? mul_rn(gx, gy) : mul_rn(gy, gy);
+      return mk<V>(-div_rn(num, g2), 0.0);
+    }
   }
 }
 
@@ -365,7 +388,10 @@ __global__ void __launch_bounds__(NT, MinCtas<T, NT>::v) k_row_sym(GridDev g, co
         V acc = mk<V>(0.0, 0.0);
         for (int t = 0; t < ops.nterm[o]; ++t) {
           const V s = symbol<T>(ops.op[o][t], kx, kyw, kz, nyq_x, nyq_y, nyq_z, What);
-          acc = cadd(acc, cmul(s, X[((size_t)ops.field[o][t] * Rr + r) * ls + kxi]));
+          const V x = X[((size_t)ops.field[o][t] * Rr + r) * ls + kxi];
+          // acc += s x, rounded step by step (no contraction: the same result at every CTA width)
+          acc.x = add_rn(acc.x, add_rn(mul_rn(s.x, x.x), -mul_rn(s.y, x.y)));
+          acc.y = add_rn(acc.y, add_rn(mul_rn(s.x, x.y), mul_rn(s.y, x.x)));
         }
         Cq[(size_t)r * ls + kxi] = cscale(acc, tscale);
       }
