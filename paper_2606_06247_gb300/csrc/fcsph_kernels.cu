@@ -22,6 +22,7 @@
 #include <type_traits>
 
 #include "fcsph_fft.cuh"
+#include "fcsph_warpfft.cuh"
 #include "fcsph_internal.h"
 
 using namespace fcsph;
@@ -406,6 +407,123 @@ __global__ void __launch_bounds__(NT, MinCtas<T, NT>::v) k_row_sym(GridDev g, co
       for (int i = threadIdx.x; i < nx; i += blockDim.x) S[(size_t)i * nz] = Yl[i];
     }
     __syncthreads();
+  }
+}
+
+// Per-lane constants of the register row pass for one row: lane k1 owns the
+// frequencies kxi = k1 + M k2 (k2 < 32) of row q (Wq: its W_hat row).
+struct WRowSym {
+  float ckx, kyw, kz;
+  bool nyq_y, nyq_z;
+  int mx, k1;
+  const float* Wq;
+};
+
+// v[k2] += symbol OP (kx of k1 + M k2) x spectrum value ([k2][lane] at xr, xi).
+template <int OP, int M>
+__device__ __forceinline__ void w_accumulate(float2* v, const float* xr, const float* xi, const WRowSym& r) {
+#pragma unroll
+  for (int k2 = 0; k2 < 32; ++k2) {
+    const int kxi = r.k1 + M * k2;
+    const int kappa = (2 * kxi <= r.mx) ? kxi : kxi - r.mx;
+    const float kx = r.ckx * (float)kappa;
+    const bool nyq_x = (r.mx % 2 == 0) && (2 * kxi == r.mx);
+    const float What = (OP == SYM_ONE || OP == SYM_NPXX || OP == SYM_NPXY || OP == SYM_NPYY) ? 1.f : r.Wq[kxi];
+    const float2 sy = symbol<float>(OP, kx, r.kyw, r.kz, nyq_x, r.nyq_y, r.nyq_z, What);
+    const float2 x = make_float2(xr[k2 * 32], xi[k2 * 32]);
+    v[k2].x = add_rn(v[k2].x, add_rn(mul_rn(sy.x, x.x), -mul_rn(sy.y, x.y)));
+    v[k2].y = add_rn(v[k2].y, add_rn(mul_rn(sy.x, x.y), mul_rn(sy.y, x.x)));
+  }
+}
+
+// Row pass of FP32 contexts with periodic x lines of mx = nx = 32 M points
+// (M = 2 .. 32): the same operation as k_row_sym, with the register FFT of
+// fcsph_warpfft.cuh.  One warp carries 32 / M rows through every transform;
+// a CTA holds 4 warps.  The forward spectra of the nin inputs wait in shared
+// memory ([field][k2][lane] of this warp, conflict-free) while the outputs are
+// formed one at a time, each in the registers of the lane that owns its
+// frequencies kx = k1 + M k2 (lane = l M + k1).
+template <int M>
+__global__ void __launch_bounds__(128, 3) k_row_sym_w(GridDev g, const float2* __restrict__ sp_in,
+                                                      float2* __restrict__ sp_out, size_t fstride_in,
+                                                      size_t bstride_in, size_t fstride_out, size_t bstride_out,
+                                                      const __grid_constant__ RowOps ops,
+                                                      const float2* __restrict__ roots,
+                                                      const float* __restrict__ Wt, double scale) {
+  constexpr int LPW = 32 / M;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nin = ops.nin, nout = ops.nout;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float* xs = reinterpret_cast<float*>(smem_raw) + (size_t)warp * (kWarpXchgFloats + nin * 2 * 32 * 32);
+  float* spre = xs + kWarpXchgFloats;
+  float* spim = spre + nin * 32 * 32;
+  const int b = blockIdx.y;
+  if (inactive(g, b)) return;
+  const int mx = g.mx, nz = g.nz;
+  const int nq = g.hy * nz;
+  const int q0 = (blockIdx.x * 4 + warp) * LPW;
+  if (q0 >= nq) return;  // whole warp beyond the last row (uniform)
+  for (int f = 0; f < nin; ++f) {
+    float2 v[32];
+#pragma unroll
+    for (int l = 0; l < LPW; ++l) {
+      const int q = q0 + l;
+      const float2* S = sp_in + b * bstride_in + f * fstride_in + (size_t)(q / nz) * g.ncol + (q % nz);
+#pragma unroll
+      for (int j = 0; j < M; ++j) v[l * M + j] = q < nq ? S[(size_t)(lane + 32 * j) * nz] : make_float2(0.f, 0.f);
+    }
+    warp_fft_fwd<M>(v, xs, roots, lane);
+#pragma unroll
+    for (int k2 = 0; k2 < 32; ++k2) {
+      spre[(f * 32 + k2) * 32 + lane] = v[k2].x;
+      spim[(f * 32 + k2) * 32 + lane] = v[k2].y;
+    }
+  }
+  __syncwarp();
+  const int l = lane / M, k1 = lane - (lane / M) * M;
+  const int q = q0 + l < nq ? q0 + l : q0;
+  const float ckx = (float)(2.0 * 3.14159265358979323846 / (mx * g.dx));
+  const float cky = (float)(2.0 * 3.14159265358979323846 / (g.my * g.dy));
+  const float ckz = (float)(2.0 * 3.14159265358979323846 / (nz * g.dz));
+  const int ky = q / nz, kq = q - (q / nz) * nz;
+  const int kzeta = (2 * kq <= nz) ? kq : kq - nz;
+  const float kyw = cky * (float)ky, kz = ckz * (float)kzeta;
+  const bool nyq_y = (g.my % 2 == 0) && (2 * ky == g.my);
+  const bool nyq_z = (nz % 2 == 0) && (2 * kq == nz);
+  const float* Wq = Wt + (size_t)q * mx;
+  const float tscale = (float)scale;
+  const WRowSym rs{ckx, kyw, kz, nyq_y, nyq_z, mx, k1, Wq};
+  for (int o = 0; o < nout; ++o) {
+    float2 v[32];
+#pragma unroll
+    for (int k2 = 0; k2 < 32; ++k2) v[k2] = make_float2(0.f, 0.f);
+    for (int t = 0; t < ops.nterm[o]; ++t) {
+      const float* xr = spre + ops.field[o][t] * 32 * 32 + lane;
+      const float* xi = spim + ops.field[o][t] * 32 * 32 + lane;
+      switch (ops.op[o][t]) {  // uniform over the warp: one unrolled loop per symbol
+        case SYM_W: w_accumulate<SYM_W, M>(v, xr, xi, rs); break;
+        case SYM_DX: w_accumulate<SYM_DX, M>(v, xr, xi, rs); break;
+        case SYM_DY: w_accumulate<SYM_DY, M>(v, xr, xi, rs); break;
+        case SYM_LAP: w_accumulate<SYM_LAP, M>(v, xr, xi, rs); break;
+        case SYM_DZ: w_accumulate<SYM_DZ, M>(v, xr, xi, rs); break;
+        case SYM_ONE: w_accumulate<SYM_ONE, M>(v, xr, xi, rs); break;
+        case SYM_NPXX: w_accumulate<SYM_NPXX, M>(v, xr, xi, rs); break;
+        case SYM_NPXY: w_accumulate<SYM_NPXY, M>(v, xr, xi, rs); break;
+        default: w_accumulate<SYM_NPYY, M>(v, xr, xi, rs); break;
+      }
+    }
+#pragma unroll
+    for (int k2 = 0; k2 < 32; ++k2) v[k2] = cscale(v[k2], tscale);
+    warp_fft_inv<M>(v, xs, roots, lane);
+#pragma unroll
+    for (int l2 = 0; l2 < LPW; ++l2) {
+      const int qq = q0 + l2;
+      if (qq < nq) {
+        float2* S = sp_out + b * bstride_out + o * fstride_out + (size_t)(qq / nz) * g.ncol + (qq % nz);
+#pragma unroll
+        for (int j = 0; j < M; ++j) S[(size_t)(lane + 32 * j) * nz] = v[l2 * M + j];
+      }
+    }
   }
 }
 
@@ -990,6 +1108,11 @@ cudaError_t init_kernel_attributes() {
   FCSPH_RAISE((k_dft_lines<float, true>))
   FCSPH_RAISE((k_dft_lines<ff, false, double2>))
   FCSPH_RAISE((k_dft_lines<ff, true, double2>))
+  FCSPH_RAISE((k_row_sym_w<2>))
+  FCSPH_RAISE((k_row_sym_w<4>))
+  FCSPH_RAISE((k_row_sym_w<8>))
+  FCSPH_RAISE((k_row_sym_w<16>))
+  FCSPH_RAISE((k_row_sym_w<32>))
   for (int nt : {32, 64, 128}) {
     e = with_width(nt, [](auto w) {
       constexpr int NT = decltype(w)::value;
@@ -1096,10 +1219,50 @@ cudaError_t launch_col_fwd(fcsph_ctx* c, int prec, int nf, const void* const* fi
   return col_fwd_t<float, float>(c, prec, nf, fields, bc, spec, dct);
 }
 
+// Shared memory of k_row_sym_w: per warp the exchange block and nin spectra.
+size_t row_w_smem(int nin) { return 4 * ((size_t)kWarpXchgFloats + (size_t)nin * 2 * 32 * 32) * sizeof(float); }
+
+// M = mx / 32 when the FP32 row pass can take the register FFT (periodic x,
+// direct plan, mx = 32 M with M a power of two in 2 .. 32), else 0.
+int row_w_m(const fcsph_ctx* c) {
+  const GridDev& g = c->gd;
+  if (c->prec.fft_prec != FCSPH_F32 || g.x_walls || g.mx != g.nx || c->plan_x.bs || c->plan_x.rd) return 0;
+  for (int m = 2; m <= 32; m *= 2)
+    if (g.mx == 32 * m) return m;
+  return 0;
+}
+
+template <int M>
+static cudaError_t row_sym_w(fcsph_ctx* c, const void* sp_in, void* sp_out, const RowOps& ops, double scale, int kind) {
+  const GridDev& g = c->gd;
+  const size_t smem = row_w_smem(ops.nin);
+  cudaError_t e = check_smem(smem);
+  if (e != cudaSuccess) return e;
+  constexpr int rows_per_cta = 4 * (32 / M);
+  dim3 grid((g.hy * g.nz + rows_per_cta - 1) / rows_per_cta, g.batch);
+  const size_t fs = (size_t)g.rows * g.ncol;
+  ProfScope ps(c, kind);
+  k_row_sym_w<M><<<grid, 128, smem, c->stream>>>(g, (const float2*)sp_in, (float2*)sp_out, fs, spec_in_fields(c) * fs,
+                                                 fs, spec_out_fields(c) * fs, ops, c->pool32 + c->plan_x.base.tw,
+                                                 static_cast<const float*>(c->dW), scale);
+  c->launches++;
+  return cudaGetLastError();
+}
+
 template <typename T>
 static cudaError_t row_sym_t(fcsph_ctx* c, int prec, const void* sp_in, void* sp_out, const RowOps& ops, double scale,
                              int bc, int kind) {
   const GridDev& g = c->gd;
+  if (prec == FCSPH_F32) {
+    switch (row_w_m(c)) {
+      case 2: return row_sym_w<2>(c, sp_in, sp_out, ops, scale, kind);
+      case 4: return row_sym_w<4>(c, sp_in, sp_out, ops, scale, kind);
+      case 8: return row_sym_w<8>(c, sp_in, sp_out, ops, scale, kind);
+      case 16: return row_sym_w<16>(c, sp_in, sp_out, ops, scale, kind);
+      case 32: return row_sym_w<32>(c, sp_in, sp_out, ops, scale, kind);
+      default: break;
+    }
+  }
   const int ls = c->plan_x.line_len();
   const int Rr = c->row_lines;
   const int nlines = 2 * ops.nin + (ops.nin == 1 ? 1 : 0);
