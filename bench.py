@@ -58,6 +58,8 @@ def parse():
                          "submitted together; serve: a Poisson request stream (2D part)")
     ap.add_argument("--serve-seconds", type=float, default=1.0)
     ap.add_argument("--slots", type=int, default=8, help="uneven/serve: slots (batch) per size class")
+    ap.add_argument("--server", default="native", choices=["native", "python"],
+                    help="uneven/serve: the library's scheduler (fcsph_batch_*) or the Python one")
     ap.add_argument("--fc-cont", default="25",
                     help="uneven/serve: FC continuation length of every size class, an integer or 'smooth' (per size "
                          "the length nearest 25 in [20, 40] whose extended line the engine transforms directly)")
@@ -639,7 +641,8 @@ def run_serving(args):
     import __graft_entry__
     __graft_entry__.build()
     from paper_2606_06247_gb300 import inputs
-    from paper_2606_06247_gb300.serve import Request, Server, summarize
+    from paper_2606_06247_gb300.serve import NativeServer, Request, Server, summarize
+    ServerCls = NativeServer if args.server == "native" else Server
     steps = args.steps
     if args.workload == "uneven":
         spec = inputs.uneven_batch(64, seed=2024)
@@ -655,7 +658,7 @@ def run_serving(args):
                 f"20% 3D channel of 64^3..128^3, each 50-500 RK3 steps scaled by {steps}/500")
     fc_cont = args.fc_cont if args.fc_cont == "smooth" else int(args.fc_cont)
     torch.cuda.synchronize()
-    srv = Server(prec=args.prec, capacity=args.slots, fc_cont=fc_cont)
+    srv = ServerCls(prec=args.prec, capacity=args.slots, fc_cont=fc_cont)
     rs = reqs()
     wall = srv.run(rs)
     torch.cuda.synchronize()
@@ -664,7 +667,7 @@ def run_serving(args):
     base = reqs()
     t0 = time.perf_counter()
     for r in base:
-        s1 = Server(prec="f64", capacity=1, fc_cont=fc_cont)
+        s1 = ServerCls(prec="f64", capacity=1, fc_cont=fc_cont)
         r.arrival = 0.0
         s1.submit(r)
         while not s1.idle():
@@ -694,7 +697,8 @@ def run_serving(args):
         "metric": METRIC, "value": served["particle_updates_per_s"], "unit": "particle-updates/s", "n_gpus": 1,
         "steps": steps, "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
-        "config": {"workload": desc, "precision": args.prec, "slots_per_size_class": args.slots, "fc_cont": args.fc_cont},
+        "config": {"workload": desc, "precision": args.prec, "slots_per_size_class": args.slots, "fc_cont": args.fc_cont,
+                   "scheduler": args.server},
         "latency_ms": {"p50": served["step_latency_ms_p50"], "p99": served["step_latency_ms_p99"]},
         "served": served, "serial_plain_fp64": serial,
         "error_vs_fp64": err_summary, "per_instance": per_inst,

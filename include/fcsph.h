@@ -113,6 +113,10 @@ typedef struct {
    * Not with FP32 PPE refinement (FCSPH_EUNSUPPORTED).  Lets a batch hold
    * empty slots (serving) without computing them. */
   const unsigned char* active;
+  /* device [batch] or NULL: per-instance time step (overrides dt); lets
+   * instances of one grid but different viscosity each run within their own
+   * explicit viscous limit */
+  const double* dt_inst;
 } fcsph_step_params;
 
 /* Create a context for one grid shape: builds the FC tables (Sec. 4; FP64,
@@ -203,6 +207,75 @@ fcsph_status fcsph_sync(fcsph_ctx* ctx);
  * (prec FCSPH_F64, or FCSPH_F32X2: double-float arithmetic, double I/O) or
  * floats (FCSPH_F32); in-place allowed. */
 fcsph_status fcsph_dft(int n, int nlines, int dir, int prec, const void* in, void* out, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Continuous batching of independent solves (serving).  Not part of the
+ * paper's method: a scheduling layer over isph_step for many requests of
+ * different sizes.  Requests are grouped into size classes (kind, n, kernel
+ * family); a class owns one context of `slots` instances on its own stream,
+ * with device-resident state for every slot.  The library allocates and owns
+ * all device memory of the classes and copies each finished request's state
+ * to host memory it owns.  A request's result does not depend on the other
+ * requests in its class or in the batch (same precision: bitwise).
+ *   Per request: Re -> nu = 1/Re; lid cavity on [0,1]^2 with lid speed 1
+ *   (G8); channel (2D, or 3D with x and z periodic) with u_max = 1, body
+ *   force 8 nu, G4 below Re 625 else G8; h = 1.3 dx; low-storage RK3 from
+ *   the fluid at rest with dt = min(1e-3, 0.25 dx^2 Re) (the explicit
+ *   viscous limit of the smoothed Laplacian is about 0.6 dx^2 / nu at
+ *   h = 1.3 dx); FC(Gram) d = 5.
+ * Not thread-safe: one batch is driven by one host thread. */
+enum { FCSPH_REQ_CAVITY = 0, FCSPH_REQ_CHANNEL = 1, FCSPH_REQ_CHANNEL3D = 2 };
+enum { FCSPH_REQ_QUEUED = 0, FCSPH_REQ_RUNNING = 1, FCSPH_REQ_DONE = 2, FCSPH_REQ_CANCELLED = 3 };
+typedef struct {
+  int kind;      /* FCSPH_REQ_CAVITY, _CHANNEL or _CHANNEL3D                    */
+  int n;         /* particles per axis: n x n (3D n^3); 16..4096 (3D 16..256)   */
+  double re;     /* Reynolds number, > 0                                        */
+  int steps;     /* RK3 steps to run, >= 1                                      */
+} fcsph_request;
+typedef struct {
+  int state;             /* FCSPH_REQ_*                                         */
+  int done_steps;        /* steps completed                                     */
+  double last_step_ms;   /* device time of its class's last step (CUDA events)  */
+  double total_step_ms;  /* sum over its steps                                  */
+} fcsph_request_info;
+typedef struct fcsph_batch fcsph_batch;
+
+/* prec: FCSPH_F64, FCSPH_F32 or FCSPH_F32X2.  slots: instances per size
+ * class (1..1024).  mem_budget_bytes: a new class is created only while the
+ * estimated device footprint of all classes stays within it (0: 80 % of the
+ * device memory free at this call).  n_cont: FC continuation length of every
+ * class (>= 4), or 0 for the per-size choice (25 where n + 25 has only prime
+ * factors <= 17, else the length in [20, 40] nearest 25 with n + C 7-smooth).
+ * Touches the device only when mem_budget_bytes is 0. */
+fcsph_status fcsph_batch_create(int prec, int slots, double mem_budget_bytes, int n_cont, fcsph_batch** out);
+/* Waits for every class's stream and frees all device and host memory. */
+fcsph_status fcsph_batch_destroy(fcsph_batch* batch);
+/* Queues a request; *id receives its handle (> 0).  No device work. */
+fcsph_status fcsph_batch_add(fcsph_batch* batch, const fcsph_request* req, long long* id);
+/* Cancels a request: a queued one at once, a running one when its class's
+ * step in flight is done (its slot then frees); finished requests stay. */
+fcsph_status fcsph_batch_remove(fcsph_batch* batch, long long id);
+/* One scheduling tick: classes whose step is done (block = 1: wait for every
+ * class in flight first) count the step for their occupied slots, copy the
+ * finished requests' u, v (w), p to host and free their slots; queued
+ * requests are admitted into free slots of classes not in flight (new
+ * classes within the budget; classes with no occupied slot are dropped when
+ * requests wait); every class with occupied slots that is not in flight
+ * launches its next RK3 step (one graph replay) on its stream.  Returns
+ * without waiting for those steps; *in_flight (nullable) receives the number
+ * of classes with a step in flight.  FCSPH_ENONFINITE if a retired step
+ * flagged a non-finite value (the batch stays usable). */
+fcsph_status fcsph_batch_run(fcsph_batch* batch, int block, int* in_flight);
+fcsph_status fcsph_batch_poll(fcsph_batch* batch, long long id, fcsph_request_info* info);
+/* Host copies of a finished request's fields, each n_each >= n^2 (3D n^3)
+ * doubles in [x][y] ([x][z][y]) order; any pointer may be NULL; w only for
+ * 3D requests.  FCSPH_EINVAL unless the request is FCSPH_REQ_DONE. */
+fcsph_status fcsph_batch_result(fcsph_batch* batch, long long id, double* u, double* v, double* w, double* p,
+                                size_t n_each);
+/* Classes alive, requests queued, estimated device bytes of the classes. */
+fcsph_status fcsph_batch_info(const fcsph_batch* batch, int* classes, int* queued, double* used_bytes);
+/* Message of the last failure of this batch (NULL: of fcsph_batch_create). */
+fcsph_status fcsph_batch_last_error(const fcsph_batch* batch, char* buf, size_t n);
 
 /* fcsph_dft without any allocation.  For callers that cannot allocate device
  * memory -- an application whose memory pool owns all device memory, a

@@ -59,7 +59,20 @@ class fcsph_step_params(ctypes.Structure):
                 ("u_bottom", ctypes.c_double), ("u_top", ctypes.c_double),
                 ("scheme", ctypes.c_int), ("use_graph", ctypes.c_int),
                 ("nu_inst", ctypes.c_void_p), ("fx_inst", ctypes.c_void_p), ("force_z", ctypes.c_double),
-                ("active", ctypes.c_void_p)]
+                ("active", ctypes.c_void_p), ("dt_inst", ctypes.c_void_p)]
+
+
+class fcsph_request(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("n", ctypes.c_int), ("re", ctypes.c_double), ("steps", ctypes.c_int)]
+
+
+class fcsph_request_info(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int), ("done_steps", ctypes.c_int), ("last_step_ms", ctypes.c_double),
+                ("total_step_ms", ctypes.c_double)]
+
+
+REQ_KIND = {"cavity": 0, "channel": 1, "channel3d": 2}
+REQ_STATE = {0: "queued", 1: "running", 2: "done", 3: "cancelled"}
 
 
 def torch_uint8():
@@ -97,6 +110,15 @@ def _load():
         "fcsph_set_cta_threads": [P, I, I],
         "fcsph_get_cta_threads": [P, ctypes.POINTER(I), ctypes.POINTER(I)],
         "fcsph_autotune": [P, ctypes.POINTER(fcsph_step_params), I, ctypes.POINTER(D)],
+        "fcsph_batch_create": [I, I, D, I, ctypes.POINTER(P)],
+        "fcsph_batch_destroy": [P],
+        "fcsph_batch_add": [P, ctypes.POINTER(fcsph_request), ctypes.POINTER(ctypes.c_longlong)],
+        "fcsph_batch_remove": [P, ctypes.c_longlong],
+        "fcsph_batch_run": [P, I, ctypes.POINTER(I)],
+        "fcsph_batch_poll": [P, ctypes.c_longlong, ctypes.POINTER(fcsph_request_info)],
+        "fcsph_batch_result": [P, ctypes.c_longlong, P, P, P, P, S],
+        "fcsph_batch_info": [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(D)],
+        "fcsph_batch_last_error": [P, ctypes.c_char_p, S],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -252,24 +274,27 @@ class Context:
         return r.value if want_resid else None
 
     @staticmethod
-    def _params(nu, rho, dt, force, u_bottom, u_top, scheme, use_graph, nu_inst, fx_inst, active=None):
+    def _params(nu, rho, dt, force, u_bottom, u_top, scheme, use_graph, nu_inst, fx_inst, active=None, dt_inst=None):
         fz = force[2] if len(force) > 2 else 0.0
         if active is not None:
             assert active.is_cuda and active.dtype == torch_uint8() and active.is_contiguous()
         return fcsph_step_params(nu, rho, dt, force[0], force[1], u_bottom, u_top, SCHEME[scheme], 1 if use_graph else 0,
                                  nu_inst.data_ptr() if nu_inst is not None else None,
                                  fx_inst.data_ptr() if fx_inst is not None else None, fz,
-                                 active.data_ptr() if active is not None else None)
+                                 active.data_ptr() if active is not None else None,
+                                 dt_inst.data_ptr() if dt_inst is not None else None)
 
     def isph_step(self, u, v, p, fu, fv, nsteps, nu, rho=1.0, dt=1e-3, force=(0.0, 0.0), u_bottom=0.0, u_top=0.0,
-                  scheme="fop", use_graph=True, nu_inst=None, fx_inst=None, w=None, fw=None, active=None):
-        """nu_inst / fx_inst: optional CUDA float64 tensors [batch] of per-instance
-        viscosity and x body force (override nu / force[0]).  3D grids: w, fw (z
-        velocity and its F^{k-1}) and force = (fx, fy, fz).  active: optional CUDA
-        uint8 tensor [batch]; only instances with a nonzero flag advance."""
+                  scheme="fop", use_graph=True, nu_inst=None, fx_inst=None, w=None, fw=None, active=None,
+                  dt_inst=None):
+        """nu_inst / fx_inst / dt_inst: optional CUDA float64 tensors [batch] of
+        per-instance viscosity, x body force and time step (override nu /
+        force[0] / dt).  3D grids: w, fw (z velocity and its F^{k-1}) and force =
+        (fx, fy, fz).  active: optional CUDA uint8 tensor [batch]; only instances
+        with a nonzero flag advance."""
         st = fcsph_state(u.data_ptr(), v.data_ptr(), p.data_ptr(), fu.data_ptr(), fv.data_ptr(),
                          w.data_ptr() if w is not None else None, fw.data_ptr() if fw is not None else None)
-        prm = self._params(nu, rho, dt, force, u_bottom, u_top, scheme, use_graph, nu_inst, fx_inst, active)
+        prm = self._params(nu, rho, dt, force, u_bottom, u_top, scheme, use_graph, nu_inst, fx_inst, active, dt_inst)
         self._ck(lib.isph_step(self.h, ctypes.byref(st), nsteps, ctypes.byref(prm)))
 
     def set_tiling(self, row_lines, col_pairs):
@@ -316,3 +341,72 @@ class Context:
         self._ck(lib.fcsph_get_profile(self.h, ms.ctypes.data_as(ctypes.c_void_p),
                                        cnt.ctypes.data_as(ctypes.c_void_p), len(PROF_KINDS)))
         return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(PROF_KINDS) if cnt[i] > 0}
+
+
+class Batch:
+    """fcsph_batch_*: continuous batching of independent solves in the
+    library (argument marshalling only; the scheduler is native)."""
+
+    def __init__(self, prec="f32x2", slots=8, mem_budget=0.0, n_cont=25):
+        """n_cont: continuation length of every class, or "smooth" (per-size choice)."""
+        h = ctypes.c_void_p()
+        nc = 0 if n_cont == "smooth" else int(n_cont)
+        st = lib.fcsph_batch_create(PREC[prec], slots, float(mem_budget), nc, ctypes.byref(h))
+        if st != 0:
+            raise FcsphError(st, self._err(None))
+        self.h = h
+        self.prec = prec
+
+    @staticmethod
+    def _err(h):
+        buf = ctypes.create_string_buffer(512)
+        lib.fcsph_batch_last_error(h, buf, 512)
+        return buf.value.decode()
+
+    def _ck(self, st):
+        if st != 0:
+            raise FcsphError(st, self._err(self.h))
+
+    def add(self, kind, n, re, steps):
+        req = fcsph_request(REQ_KIND[kind], n, re, steps)
+        rid = ctypes.c_longlong()
+        self._ck(lib.fcsph_batch_add(self.h, ctypes.byref(req), ctypes.byref(rid)))
+        return rid.value
+
+    def remove(self, rid):
+        self._ck(lib.fcsph_batch_remove(self.h, rid))
+
+    def run(self, block=False):
+        """One scheduling tick; returns the number of classes in flight."""
+        k = ctypes.c_int()
+        self._ck(lib.fcsph_batch_run(self.h, 1 if block else 0, ctypes.byref(k)))
+        return k.value
+
+    def poll(self, rid):
+        info = fcsph_request_info()
+        self._ck(lib.fcsph_batch_poll(self.h, rid, ctypes.byref(info)))
+        return {"state": REQ_STATE[info.state], "done_steps": info.done_steps, "last_step_ms": info.last_step_ms,
+                "total_step_ms": info.total_step_ms}
+
+    def result(self, rid, kind, n):
+        shape = (n, n, n) if kind == "channel3d" else (n, n)
+        out = {k: np.zeros(shape) for k in (("u", "v", "w", "p") if kind == "channel3d" else ("u", "v", "p"))}
+        ptr = lambda k: out[k].ctypes.data_as(ctypes.c_void_p) if k in out else None
+        self._ck(lib.fcsph_batch_result(self.h, rid, ptr("u"), ptr("v"), ptr("w"), ptr("p"), out["u"].size))
+        return out
+
+    def info(self):
+        c, q, u = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        self._ck(lib.fcsph_batch_info(self.h, ctypes.byref(c), ctypes.byref(q), ctypes.byref(u)))
+        return {"classes": c.value, "queued": q.value, "used_bytes": u.value}
+
+    def close(self):
+        if self.h:
+            lib.fcsph_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -30,7 +30,7 @@ def _cuda_home():
 
 
 def _sources():
-    return [os.path.join(CSRC, f) for f in ("fcsph_tables.cpp", "fcsph_api.cpp", "fcsph_kernels.cu", "fcsph_noalloc.cu")]
+    return [os.path.join(CSRC, f) for f in ("fcsph_tables.cpp", "fcsph_api.cpp", "fcsph_batch.cpp", "fcsph_kernels.cu", "fcsph_noalloc.cu")]
 
 
 def _needs_build():

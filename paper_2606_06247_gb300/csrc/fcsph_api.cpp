@@ -673,6 +673,7 @@ static fcsph_status one_step(fcsph_ctx* c, const fcsph_state* s, const fcsph_ste
     sd.u_bottom = prm->u_bottom;
     sd.u_top = prm->u_top;
     sd.nu_inst = prm->nu_inst;
+    sd.dt_inst = prm->dt_inst;
     sd.fx_inst = prm->fx_inst;
     if (nsub == 3) {
       sd.a = A3[k];
@@ -728,7 +729,7 @@ static fcsph_status isph_step_masked(fcsph_ctx* c, const fcsph_state* s, int nst
                              prm->force_x, prm->force_y, prm->u_bottom, prm->u_top, (double)prm->scheme,
                              (double)(uintptr_t)prm->nu_inst, (double)(uintptr_t)prm->fx_inst,
                              (double)(uintptr_t)s->w, (double)(uintptr_t)s->fw, prm->force_z,
-                             (double)(uintptr_t)prm->active};
+                             (double)(uintptr_t)prm->active, (double)(uintptr_t)prm->dt_inst};
   if (!c->gexec || key != c->graph_key) {
     if (c->gexec) {
       cudaGraphExecDestroy(c->gexec);

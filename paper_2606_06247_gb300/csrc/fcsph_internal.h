@@ -157,6 +157,7 @@ struct StepDev {
   double a, g, z;        // substep coefficients
   const double* nu_inst; // per-instance overrides (device) or null
   const double* fx_inst;
+  const double* dt_inst; // per-instance time step (device) or null
 };
 
 struct fcsph_ctx {

@@ -849,7 +849,8 @@ __global__ void __launch_bounds__(NT, MinCtas<T, NT>::v) k_col_inv(GridDev g, co
             const double nu = ea.s.nu_inst ? ea.s.nu_inst[b] : ea.s.nu;
             const double F = *a - nu * val;
             const double f = comp == 0 ? (ea.s.fx_inst ? ea.s.fx_inst[b] : ea.s.fx) : (comp == 1 ? ea.s.fy : ea.s.fz);
-            double cs = ea.vel[comp][id] + ea.s.dt * (-ea.s.g * F - ea.s.z * ea.Fp[comp][id] + ea.s.a * f);
+            const double dt = ea.s.dt_inst ? ea.s.dt_inst[b] : ea.s.dt;
+            double cs = ea.vel[comp][id] + dt * (-ea.s.g * F - ea.s.z * ea.Fp[comp][id] + ea.s.a * f);
             // y walls: the tangential x velocity takes the wall speeds, the others 0
             if (j == 0) cs = comp == 0 ? ea.s.u_bottom : 0.0;
             if (j == ny - 1) cs = comp == 0 ? ea.s.u_top : 0.0;
@@ -860,12 +861,12 @@ __global__ void __launch_bounds__(NT, MinCtas<T, NT>::v) k_col_inv(GridDev g, co
             *a = cs;
           }
         } else if (EPI == EPI_DIV) {
-          nv = ea.s.rho / (ea.s.a * ea.s.dt) * val;
+          nv = ea.s.rho / (ea.s.a * (ea.s.dt_inst ? ea.s.dt_inst[b] : ea.s.dt)) * val;
           ea.bvec[id] = nv;
           slot = 0;
         } else if (EPI == EPI_CORR) {
           // output o: d phi / d(axis o) -> component o
-          const double c = ea.s.a * ea.s.dt / ea.s.rho;
+          const double c = ea.s.a * (ea.s.dt_inst ? ea.s.dt_inst[b] : ea.s.dt) / ea.s.rho;
           double cn = ea.vs[o][id] - c * val;
           if (j == 0) cn = o == 0 ? ea.s.u_bottom : 0.0;
           if (j == ny - 1) cn = o == 0 ? ea.s.u_top : 0.0;

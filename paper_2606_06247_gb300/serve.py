@@ -82,6 +82,15 @@ def smooth_n_cont(n, base=25, lo=20, hi=40):
     return base
 
 
+def request_dt(req):
+    """Time step of a request: dt = min(1e-3, 0.25 dx^2 Re).  The explicit
+    viscous limit of the smoothed Laplacian at h = 1.3 dx is about
+    0.6 dx^2 / nu (RK3), so low-Re requests on fine grids need less than
+    1e-3."""
+    dx = 1.0 / (req.n - 1)
+    return min(DT, 0.25 * dx * dx * req.re)
+
+
 def family_for(kind, re):
     """Kernel family per the paper's guidance: G4 at low Re, G8 at high Re (cavity always G8)."""
     if kind == "cavity":
@@ -129,6 +138,7 @@ class SizeClass:
             self.w, self.fw = (z.clone(), z.clone()) if self.d3 else (None, None)
             self.nu = torch.full((capacity,), 1e-2, dtype=torch.float64, device=device)
             self.fx = torch.zeros((capacity,), dtype=torch.float64, device=device)
+            self.dt = torch.full((capacity,), DT, dtype=torch.float64, device=device)
             # slots holding a request; empty slots are skipped by the step's kernels
             self.active_mask = torch.zeros((capacity,), dtype=torch.uint8, device=device)
         self.slots = [None] * capacity
@@ -150,6 +160,7 @@ class SizeClass:
                     t[slot].zero_()
             self.nu[slot] = nu
             self.fx[slot] = 8.0 * nu if self.kind in ("channel", "channel3d") else 0.0
+            self.dt[slot] = request_dt(req)
             self.active_mask[slot] = 1
         self.slots[slot] = req
 
@@ -159,7 +170,8 @@ class SizeClass:
             self.ev0.record(self.stream)
             self.ctx.isph_step(self.u, self.v, self.p, self.fu, self.fv, 1, nu=1e-2, rho=1.0, dt=DT,
                                u_top=1.0 if self.kind == "cavity" else 0.0, scheme="rk3", use_graph=True,
-                               nu_inst=self.nu, fx_inst=self.fx, w=self.w, fw=self.fw, active=self.active_mask)
+                               nu_inst=self.nu, fx_inst=self.fx, w=self.w, fw=self.fw, active=self.active_mask,
+                               dt_inst=self.dt)
             self.ev1.record(self.stream)
         self.pending_event = True
 
@@ -279,6 +291,69 @@ class Server:
             if max_wall and time.perf_counter() - t0 > max_wall:
                 break
         return time.perf_counter() - t0
+
+
+class NativeServer:
+    """The same serving loop run by the library's own scheduler (fcsph_batch_*
+    in include/fcsph.h): size classes, slots, admission by footprint and the
+    per-class streams live in C++; this class only submits requests, ticks
+    the batch and collects results and step latencies (same interface as
+    Server)."""
+
+    def __init__(self, prec="f64", capacity=8, mem_budget=None, device=None, fc_cont=25):
+        self.prec = prec
+        self.capacity = capacity
+        self.fc_cont = fc_cont
+        self.batch = b.Batch(prec=prec, slots=capacity, mem_budget=0.0 if mem_budget is None else mem_budget,
+                             n_cont=fc_cont)
+        self.live = {}     # library id -> Request
+        self.done = []
+
+    def submit(self, req):
+        rid = self.batch.add(req.kind, req.n, req.re, req.steps)
+        req.t_admit = None
+        self.live[rid] = req
+
+    def tick(self, now, block=False):
+        inflight = self.batch.run(block=block)
+        for rid in list(self.live):
+            req = self.live[rid]
+            info = self.batch.poll(rid)
+            while req.done_steps < info["done_steps"]:
+                req.done_steps += 1
+                req.latencies_ms.append(info["last_step_ms"])
+            if req.t_admit is None and info["state"] != "queued":
+                req.t_admit = now
+            if info["state"] == "done":
+                req.result = self.batch.result(rid, req.kind, req.n)
+                req.t_done = now
+                self.done.append(req)
+                del self.live[rid]
+        return inflight
+
+    def idle(self):
+        return not self.live
+
+    def run(self, requests, time_scale=1.0, max_wall=None):
+        pending = sorted(requests, key=lambda r: r.arrival)
+        t0 = time.perf_counter()
+        k = 0
+        while k < len(pending) or not self.idle():
+            now = (time.perf_counter() - t0) / time_scale
+            while k < len(pending) and pending[k].arrival <= now:
+                self.submit(pending[k])
+                k += 1
+            inflight = self.tick(now)
+            if inflight == 0 and k < len(pending) and self.idle():
+                time.sleep(max(0.0, (pending[k].arrival - now) * time_scale))
+            elif inflight:
+                time.sleep(5e-5)
+            if max_wall and time.perf_counter() - t0 > max_wall:
+                break
+        return time.perf_counter() - t0
+
+    def close(self):
+        self.batch.close()
 
 
 def summarize(requests, wall_s):
