@@ -330,10 +330,12 @@ __device__ __forceinline__ void dft_reg(typename CT<T>::t* v) {
   }
 }
 
+// cin / cout: conjugate the values as they are loaded / stored (the first and
+// last stage of an inverse transform computed as conj(DFT(conj x))).
 template <typename T, int R, bool INV>
 __device__ void stage_reg(const typename CT<T>::t* __restrict__ src, typename CT<T>::t* __restrict__ dst, int nl,
                           int ls, int n, int Ns, const FastDiv& dnb, const FastDiv& dns,
-                          const typename CT<T>::t* __restrict__ tw) {
+                          const typename CT<T>::t* __restrict__ tw, bool cin, bool cout) {
   typedef typename CT<T>::t V;
   const int nb = n / R;
   const int s = n / (Ns * R);
@@ -346,6 +348,10 @@ __device__ void stage_reg(const typename CT<T>::t* __restrict__ src, typename CT
     V v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = in[j + r * nb];
+    if (cin) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[r].y = -v[r].y;
+    }
     if (k > 0) {
       const int ks = k * s;
 #pragma unroll
@@ -353,6 +359,10 @@ __device__ void stage_reg(const typename CT<T>::t* __restrict__ src, typename CT
     }
     dft_reg<T, R, INV>(v);
     V* out = dst + (size_t)line * ls + g * Ns * R + k;
+    if (cout) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[r].y = -v[r].y;
+    }
 #pragma unroll
     for (int r = 0; r < R; ++r) out[r * Ns] = cnorm(v[r]);
   }
@@ -361,7 +371,8 @@ __device__ void stage_reg(const typename CT<T>::t* __restrict__ src, typename CT
 // Large prime radix: one thread per output element.
 template <typename T, bool INV>
 __device__ void stage_big(const typename CT<T>::t* __restrict__ src, typename CT<T>::t* __restrict__ dst, int nl,
-                          int ls, int n, int Ns, int R, const FastDiv& dn, const typename CT<T>::t* __restrict__ tw) {
+                          int ls, int n, int Ns, int R, const FastDiv& dn, const typename CT<T>::t* __restrict__ tw,
+                          bool cin, bool cout) {
   typedef typename CT<T>::t V;
   const int nb = n / R;
   const int NsR = Ns * R;
@@ -375,13 +386,17 @@ __device__ void stage_big(const typename CT<T>::t* __restrict__ src, typename CT
     const int j = g * Ns + k;
     const V* in = src + (size_t)line * ls;
     V acc = in[j];
+    if (cin) acc.y = -acc.y;
     const int estep = (mm * s) % n;  // exponent increment per r
     int e = 0;
     for (int r = 1; r < R; ++r) {
       e += estep;
       if (e >= n) e -= n;
-      acc = cadd(acc, cmul(in[j + r * nb], root<V, INV>(tw, e)));
+      V x = in[j + r * nb];
+      if (cin) x.y = -x.y;
+      acc = cadd(acc, cmul(x, root<V, INV>(tw, e)));
     }
+    if (cout) acc.y = -acc.y;
     dst[(size_t)line * ls + o] = acc;
   }
 }
@@ -389,26 +404,31 @@ __device__ void stage_big(const typename CT<T>::t* __restrict__ src, typename CT
 // Runs the forward stages of p on nl lines held in a (stride ls), b is
 // scratch of the same shape.  All threads of the block must call it.
 // Returns the buffer holding the result (a or b).
+// conj_io: conjugate the input as the first stage loads it and the output as
+// the last stage stores it (the inverse as conj(DFT(conj x))); no-op if the
+// plan has no stage.
 template <typename T>
 __device__ __forceinline__ typename CT<T>::t* fft_run(typename CT<T>::t* a, typename CT<T>::t* b, int nl, int ls,
-                                                      const Plan1& p, const typename CT<T>::t* __restrict__ tw) {
+                                                      const Plan1& p, const typename CT<T>::t* __restrict__ tw,
+                                                      bool conj_io) {
   typedef typename CT<T>::t V;
   int Ns = 1;
   const int n = p.n;
   for (int s = 0; s < p.nst; ++s) {
     const int R = p.radix[s];
+    const bool ci = conj_io && s == 0, co = conj_io && s == p.nst - 1;
     switch (R) {
-      case 2: stage_reg<T, 2, false>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw); break;
-      case 3: stage_reg<T, 3, false>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw); break;
-      case 4: stage_reg<T, 4, false>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw); break;
-      case 5: stage_reg<T, 5, false>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw); break;
-      case 7: stage_reg<T, 7, false>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw); break;
-      case 8: stage_reg<T, 8, false>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw); break;
-      case 9: stage_reg<T, 9, false>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw); break;
-      case 11: stage_reg<T, 11, false>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw); break;
-      case 13: stage_reg<T, 13, false>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw); break;
-      case 17: stage_reg<T, 17, false>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw); break;
-      default: stage_big<T, false>(a, b, nl, ls, n, Ns, R, p.dn, tw); break;
+      case 2: stage_reg<T, 2, false>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw, ci, co); break;
+      case 3: stage_reg<T, 3, false>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw, ci, co); break;
+      case 4: stage_reg<T, 4, false>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw, ci, co); break;
+      case 5: stage_reg<T, 5, false>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw, ci, co); break;
+      case 7: stage_reg<T, 7, false>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw, ci, co); break;
+      case 8: stage_reg<T, 8, false>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw, ci, co); break;
+      case 9: stage_reg<T, 9, false>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw, ci, co); break;
+      case 11: stage_reg<T, 11, false>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw, ci, co); break;
+      case 13: stage_reg<T, 13, false>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw, ci, co); break;
+      case 17: stage_reg<T, 17, false>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw, ci, co); break;
+      default: stage_big<T, false>(a, b, nl, ls, n, Ns, R, p.dn, tw, ci, co); break;
     }
     __syncthreads();
     V* t = a;
@@ -474,19 +494,14 @@ __device__ __noinline__ typename CT<T>::t* fft_any_rt(typename CT<T>::t* a, type
         *x = mk<V>(0.0, 0.0);
       }
     }
-  } else if (inv) {
-    for (int t = threadIdx.x; t < nl * n; t += blockDim.x) {
-      const int line = fdiv(t, P.base.dn);
-      V* x = a + (size_t)line * ls + (t - line * n);
-      x->y = -x->y;
-    }
   }
   __syncthreads();
-  // ---- one or two forward passes through a single call site
+  // ---- one or two forward passes through a single call site (a direct
+  // inverse conjugates in its first and last stage)
   V* r = src;
 #pragma unroll 1
   for (int pass = 0; pass < (two ? 2 : 1); ++pass) {
-    r = fft_run<T>(src, dst, nl, ls, sp, pool + sp.tw);
+    r = fft_run<T>(src, dst, nl, ls, sp, pool + sp.tw, !two && inv);
     V* o = (r == src) ? dst : src;
     if (pass == 0 && two) {
       for (int t = threadIdx.x; t < nl * m; t += blockDim.x) {
@@ -543,14 +558,6 @@ __device__ __noinline__ typename CT<T>::t* fft_any_rt(typename CT<T>::t* a, type
     }
     __syncthreads();
     return r;
-  }
-  if (inv) {
-    for (int t = threadIdx.x; t < nl * n; t += blockDim.x) {
-      const int line = fdiv(t, P.base.dn);
-      V* x = r + (size_t)line * ls + (t - line * n);
-      x->y = -x->y;
-    }
-    __syncthreads();
   }
   return r;
 }

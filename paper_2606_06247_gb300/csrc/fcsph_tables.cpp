@@ -5,6 +5,7 @@
 // (condition number ~1e16), so it is solved with Householder QR in IEEE
 // binary128 (x86-64: __float128/libquadmath; aarch64: long double), and the
 // twiddles/chirps are evaluated there too, then rounded once to FP64.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -204,7 +205,11 @@ static void roots(int n, std::vector<double>* re, std::vector<double>* im) {
 }
 
 bool factor_direct(int n, Plan1* p) {
-  // radix order: 8s, then a 4 or 2; 9s, then a 3; 5s; 7s; larger primes
+  // radix order: larger primes, 7s, 5s, a 3 then 9s, a 4 or 2 then 8s.  The
+  // first Stockham stages store at a stride of their radix; odd radices
+  // first keep those stores free of shared-memory bank conflicts, and the
+  // radix-8 stages come last, when consecutive threads store consecutive
+  // elements.
   int cnt[32] = {0};
   std::vector<int> big;
   int r = n;
@@ -238,6 +243,7 @@ bool factor_direct(int n, Plan1* p) {
   for (int i = 0; i < cnt[7]; ++i) rad.push_back(7);
   for (int q : big) rad.push_back(q);
   if ((int)rad.size() > kMaxStages) return false;
+  std::reverse(rad.begin(), rad.end());
   plan_set_radices(p, n, rad.data(), (int)rad.size());
   return true;
 }

@@ -83,7 +83,7 @@ def test_fp32_register_rows_channel_step():
     uo, vo, _ = ostep.isph_steps(prob, u0, v0, 3)
     eu, ev = rel_l2(u[0].cpu().numpy(), uo), rel_l2(v[0].cpu().numpy(), vo)
     print(f"register rows, channel {nx}x{ny} RK3 x3: FP32 rel L2 u {eu:.2e} v {ev:.2e}")
-    assert eu < 1e-4 and ev < 1e-2
+    assert eu < 5e-4 and ev < 1e-2
 
 
 @pytest.mark.gpu
