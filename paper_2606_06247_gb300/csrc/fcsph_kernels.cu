@@ -23,6 +23,7 @@
 
 #include "fcsph_fft.cuh"
 #include "fcsph_warpfft.cuh"
+#include "fcsph_regfft.cuh"
 #include "fcsph_internal.h"
 
 using namespace fcsph;
@@ -136,6 +137,10 @@ __device__ __forceinline__ void fc_append(typename CT<T>::t* lines, int nl, int 
   }
 }
 
+template <typename T>
+__device__ void col_store_spectrum(const typename CT<T>::t* R, int Pp, int ls, const GridDev& g, int i0, int n,
+                                   int dct, typename CT<T>::t* __restrict__ spec);
+
 // ---------------------------------------------------------------------------
 // Forward transform of packed column pairs held in shared memory.
 // lines: Pp lines of stride ls, line p has column i0+2p in .x and i0+2p+1 in
@@ -161,7 +166,17 @@ __device__ void col_forward_store(typename CT<T>::t* lines, typename CT<T>::t* s
   }
   __syncthreads();
   V* R = fft_any<T, false>(lines, scratch, Pp, ls, P, pool);
-  const int n = P.base.n;
+  col_store_spectrum<T>(R, Pp, ls, g, i0, P.base.n, dct, spec);
+}
+
+// Half spectrum (or, dct = 1, the ny real DCT-I coefficients as (c, 0)) of
+// the Pp transformed packed column pairs in R (stride ls, length n) into
+// spec[ky][i] of columns i0 + 2p, i0 + 2p + 1.
+template <typename T>
+__device__ void col_store_spectrum(const typename CT<T>::t* R, int Pp, int ls, const GridDev& g, int i0, int n,
+                                   int dct, typename CT<T>::t* __restrict__ spec) {
+  typedef typename CT<T>::t V;
+  const int ny = g.ny;
   const int nk = dct ? ny : g.hy;
   const T h = (T)0.5;
   for (int p = 0; p < Pp; ++p) {
@@ -431,8 +446,13 @@ __device__ __forceinline__ void w_accumulate(float2* v, const float* xr, const f
     const float What = (OP == SYM_ONE || OP == SYM_NPXX || OP == SYM_NPXY || OP == SYM_NPYY) ? 1.f : r.Wq[kxi];
     const float2 sy = symbol<float>(OP, kx, r.kyw, r.kz, nyq_x, r.nyq_y, r.nyq_z, What);
     const float2 x = make_float2(xr[k2 * 32], xi[k2 * 32]);
-    v[k2].x = add_rn(v[k2].x, add_rn(mul_rn(sy.x, x.x), -mul_rn(sy.y, x.y)));
-    v[k2].y = add_rn(v[k2].y, add_rn(mul_rn(sy.x, x.y), mul_rn(sy.y, x.x)));
+    if (OP == SYM_DX || OP == SYM_DY || OP == SYM_DZ) {  // purely imaginary symbol i sy.y
+      v[k2].x = add_rn(v[k2].x, -mul_rn(sy.y, x.y));
+      v[k2].y = add_rn(v[k2].y, mul_rn(sy.y, x.x));
+    } else {  // real symbol sy.x
+      v[k2].x = add_rn(v[k2].x, mul_rn(sy.x, x.x));
+      v[k2].y = add_rn(v[k2].y, mul_rn(sy.x, x.y));
+    }
   }
 }
 
@@ -918,6 +938,87 @@ __global__ void __launch_bounds__(NT, MinCtas<T, NT>::v) k_col_inv(GridDev g, co
 }
 
 // ---------------------------------------------------------------------------
+// Wall-normal passes of FP32 contexts with the register team FFT of
+// fcsph_regfft.cuh, for extended lengths n = N1 N2 with a direct plan: one
+// column pair per CTA of TeamFFT<N1, N2>::THREADS threads.  k_col_fwd_r does
+// what k_col_fwd does for FP32 fields (load, FC, forward transform, half
+// spectrum); k_col_out_r what k_col_inv does with EPI_OUT into FP32 outputs
+// (Hermitian gather, inverse transform, store), for every output.
+template <int N1, int N2>
+__global__ void __launch_bounds__(TeamFFT<N1, N2>::THREADS) k_col_fwd_r(
+    GridDev g, const float* __restrict__ f0, const float* __restrict__ f1, const float* __restrict__ f2,
+    const typename FcTab<float>::t* __restrict__ E, const float2* __restrict__ roots, float2* __restrict__ spec,
+    size_t fstride, size_t bstride) {
+  typedef TeamFFT<N1, N2> TF;
+  constexpr int n = N1 * N2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* L = reinterpret_cast<float2*>(smem_raw);
+  float2* xs = L + n;
+  const int b = blockIdx.z, f = blockIdx.y;
+  if (inactive(g, b)) return;
+  const int i0 = blockIdx.x * 2;
+  const float* src = f == 0 ? f0 : (f == 1 ? f1 : f2);
+  const int ny = g.ny, t = threadIdx.x;
+  const size_t base = ((size_t)b * g.ncol + i0) * ny;
+  for (int col = 0; col < 2; ++col) {
+    float* Lc = reinterpret_cast<float*>(L) + col;
+    const bool in = i0 + col < g.ncol;
+    for (int j = t; j < ny; j += blockDim.x) Lc[2 * j] = in ? src[base + (size_t)col * ny + j] : 0.f;
+  }
+  __syncthreads();
+  fc_append<float>(L, 1, n, ny, g.n_cont, g.n_match, E);
+  __syncthreads();
+  float2 v[TF::NV];
+  if (t < N2) {
+#pragma unroll
+    for (int j = 0; j < N1; ++j) v[j] = L[t + N2 * j];
+  }
+  TF::fwd(v, xs, roots, t);
+  if (t < N1) {
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) L[t + N1 * k2] = v[k2];
+  }
+  __syncthreads();
+  col_store_spectrum<float>(L, 1, n, g, i0, n, 0, spec + b * bstride + f * fstride);
+}
+
+template <int N1, int N2>
+__global__ void __launch_bounds__(TeamFFT<N1, N2>::THREADS) k_col_out_r(
+    GridDev g, const float2* __restrict__ spec, size_t fstride, size_t bstride, int nout, const EpiArgs ea,
+    const float2* __restrict__ roots) {
+  typedef TeamFFT<N1, N2> TF;
+  constexpr int n = N1 * N2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* L = reinterpret_cast<float2*>(smem_raw);
+  float2* xs = L + n;
+  const int b = blockIdx.y;
+  if (inactive(g, b)) return;
+  const int i0 = blockIdx.x * 2;
+  const int ny = g.ny, t = threadIdx.x;
+  for (int o = 0; o < nout; ++o) {
+    col_gather_hermitian<float>(L, 1, n, g, i0, spec + b * bstride + o * fstride, fstride, 1, n);
+    __syncthreads();
+    float2 v[TF::NV];
+    if (t < N1) {
+#pragma unroll
+      for (int k2 = 0; k2 < N2; ++k2) v[k2] = L[t + N1 * k2];
+    }
+    TF::inv(v, xs, roots, t);
+    if (t < N2) {
+      float* out = reinterpret_cast<float*>(ea.outs[o]);
+#pragma unroll
+      for (int j = 0; j < N1; ++j) {
+        const int row = t + N2 * j;
+        if (row < ny) {
+          out[fidx(g, b, i0, row)] = v[j].x;
+          if (i0 + 1 < g.ncol) out[fidx(g, b, i0 + 1, row)] = v[j].y;
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // fc_extend (Eq. 30) as a standalone kernel: y continuation of every column,
 // then x continuation of every extended row (walled x).
 template <typename U>
@@ -1109,6 +1210,10 @@ cudaError_t init_kernel_attributes() {
   FCSPH_RAISE((k_dft_lines<float, true>))
   FCSPH_RAISE((k_dft_lines<ff, false, double2>))
   FCSPH_RAISE((k_dft_lines<ff, true, double2>))
+  FCSPH_RAISE((k_col_fwd_r<20, 27>))
+  FCSPH_RAISE((k_col_fwd_r<30, 35>))
+  FCSPH_RAISE((k_col_out_r<20, 27>))
+  FCSPH_RAISE((k_col_out_r<30, 35>))
   FCSPH_RAISE((k_row_sym_w<2>))
   FCSPH_RAISE((k_row_sym_w<4>))
   FCSPH_RAISE((k_row_sym_w<8>))
@@ -1180,9 +1285,67 @@ cudaError_t launch_fc_extend(fcsph_ctx* c, const void* f, void* fext, int bc) {
 }
 
 
+// Register column FFT for FP32 contexts: the split n = N1 N2 of the extended
+// wall-normal length when the plan is direct and the length is one of the
+// supported ones, else 0.
+int col_r_split(const fcsph_ctx* c) {
+  const FftPlan& P = c->plan_y;
+  if (c->prec.fft_prec != FCSPH_F32 || P.bs || P.rd) return 0;
+  switch (P.base.n) {
+    case 540: return 20;
+    case 1050: return 30;
+    default: return 0;
+  }
+}
+
+template <int N1, int N2>
+static cudaError_t col_fwd_r(fcsph_ctx* c, int nf, const void* const* fields, int bc, void* spec) {
+  typedef TeamFFT<N1, N2> TF;
+  const GridDev& g = c->gd;
+  const size_t smem = ((size_t)N1 * N2 + TF::XCHG) * sizeof(float2);
+  cudaError_t e = check_smem(smem);
+  if (e != cudaSuccess) return e;
+  const auto* E = static_cast<const typename FcTab<float>::t*>(fc_table(c, FCSPH_F32, bc));
+  dim3 grid((g.ncol + 1) / 2, nf, g.batch);
+  const size_t fstride = (size_t)g.rows * g.ncol;
+  const size_t bstride = spec_in_fields(c) * fstride;
+  ProfScope ps(c, FCSPH_PROF_COL_FWD);
+  const float* f0 = (const float*)fields[0];
+  k_col_fwd_r<N1, N2><<<grid, TF::THREADS, smem, c->stream>>>(
+      g, f0, (const float*)(nf > 1 ? fields[1] : fields[0]), (const float*)(nf > 2 ? fields[2] : fields[0]), E,
+      c->pool32 + c->plan_y.base.tw, (float2*)spec, fstride, bstride);
+  c->launches++;
+  return cudaGetLastError();
+}
+
+template <int N1, int N2>
+static cudaError_t col_out_r(fcsph_ctx* c, const void* spec, int nout, EpiArgs& ea) {
+  typedef TeamFFT<N1, N2> TF;
+  const GridDev& g = c->gd;
+  const size_t smem = ((size_t)N1 * N2 + TF::XCHG) * sizeof(float2);
+  cudaError_t e = check_smem(smem);
+  if (e != cudaSuccess) return e;
+  const size_t fs = (size_t)g.rows * g.ncol;
+  dim3 grid((g.ncol + 1) / 2, g.batch);
+  ProfScope ps(c, FCSPH_PROF_COL_OUT);
+  k_col_out_r<N1, N2><<<grid, TF::THREADS, smem, c->stream>>>(g, (const float2*)spec, fs, spec_out_fields(c) * fs,
+                                                             nout, ea, c->pool32 + c->plan_y.base.tw);
+  c->launches++;
+  return cudaGetLastError();
+}
+
 template <typename T, typename U>
 static cudaError_t col_fwd_t(fcsph_ctx* c, int prec, int nf, const void* const* fields, int bc, void* spec, int dct) {
   const GridDev& g = c->gd;
+  if constexpr (sizeof(T) == sizeof(float) && sizeof(U) == sizeof(float)) {
+    if (!dct) {
+      switch (col_r_split(c)) {
+        case 20: return col_fwd_r<20, 27>(c, nf, fields, bc, spec);
+        case 30: return col_fwd_r<30, 35>(c, nf, fields, bc, spec);
+        default: break;
+      }
+    }
+  }
   const FftPlan& P = dct ? c->plan_py : c->plan_y;
   const int ls = P.line_len();
   const int Pp = c->col_pairs;
@@ -1411,6 +1574,13 @@ cudaError_t launch_col_out(fcsph_ctx* c, const void* spec, int nout, void* const
   EpiArgs ea = epi_defaults();
   for (int o = 0; o < nout; ++o) ea.outs[o] = outs[o];
   ea.out_double = c->prec.fft_prec != FCSPH_F32;
+  if (!ea.out_double) {
+    switch (col_r_split(c)) {
+      case 20: return col_out_r<20, 27>(c, spec, nout, ea);
+      case 30: return col_out_r<30, 35>(c, spec, nout, ea);
+      default: break;
+    }
+  }
   return col_inv(c, c->prec.fft_prec, EPI_OUT, spec, nout, ea);
 }
 

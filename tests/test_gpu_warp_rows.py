@@ -105,3 +105,38 @@ def test_fp32_register_rows_3d_channel_step():
     errs = [rel_l2(a, r) for a, r in zip(res["f32"], res["f64"])]
     print("register rows, 3D channel RK3 x2: FP32 vs FP64 rel L2 (u, v, w)", errs)
     assert max(errs) < 5e-4
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("nx,ny,n_cont", [(16, 1024, 26), (15, 512, 28), (64, 512, 28)])
+def test_fp32_register_columns_spectral_op(nx, ny, n_cont):
+    """The register column FFT of FP32 contexts (fcsph_regfft.cuh: 1050 = 30 x 35
+    and 540 = 20 x 27 extended points): forward pass with FC and inverse pass
+    into FP32 outputs, against the FP64 oracle; an odd nx leaves the last
+    column pair half empty."""
+    torch = torch_cuda()
+    b = binding()
+    batch = 2
+    lx, ly = grid_lengths(nx, ny, False)
+    ctx = b.Context(nx, ny, lx, ly, batch=batch, n_cont=n_cont, family="G4", h_over_dx=1.3, prec="f32")
+    p = oracle_problem(nx, ny, False, "G4", 1.3, n_cont=n_cont)
+    from oracle.symbols import symbol_closed
+    mx, my = p.extended_shape()
+    names = ["W", "DX", "DY", "LAP"]
+    S = [symbol_closed(op, "G4", p.h, mx, my, p.dx, p.dy) for op in names]
+    f = _fields(nx, ny, batch, 5)
+    outs = [torch.zeros((batch, nx, ny), dtype=torch.float32, device="cuda") for _ in names]
+    ctx.spectral_op(to_dev(f, "f32"), names, outs)
+    div = torch.zeros((batch, nx, ny), dtype=torch.float32, device="cuda")
+    ctx.spectral_div(to_dev(f, "f32"), to_dev(f[:, ::-1].copy(), "f32"), div)
+    ctx.sync()
+    worst = 0.0
+    for k in range(batch):
+        fk = f[k].astype(np.float32).astype(np.float64)
+        refs = oops.apply_symbols(fk, S, p.E_dir)
+        for o, r in zip(outs, refs):
+            worst = max(worst, rel_l2(o[k].double().cpu().numpy(), r))
+        rd = oops.divergence(fk, fk[::-1].copy(), S[1], S[2], p.E_dir)
+        worst = max(worst, rel_l2(div[k].double().cpu().numpy(), rd))
+    print(f"register columns {nx}x{ny} C={n_cont}: worst FP32 rel L2 vs FP64 oracle {worst:.2e}")
+    assert worst < 2e-4
