@@ -621,6 +621,81 @@ __global__ void __launch_bounds__(NT, LineMinCtas<T, NT>::v) k_line_op(GridDev g
   }
 }
 
+// The line operator of FP32 contexts with the register team FFT
+// (fcsph_regfft.cuh) for extended lengths n = N1 N2: one column pair per CTA;
+// the forward spectrum waits in shared memory, each value where the thread
+// that owns its frequency (k = t + N1 k2) reads it back, while the outputs are
+// formed one at a time.
+template <int N1, int N2>
+__global__ void __launch_bounds__(TeamFFT<N1, N2>::THREADS, TeamFFT<N1, N2>::MIN_CTAS) k_line_op_r(
+    GridDev g, const float* __restrict__ f, long long ncols, const typename FcTab<float>::t* __restrict__ E,
+    const float2* __restrict__ pool, const float2* __restrict__ roots, const __grid_constant__ LineOuts lo) {
+  typedef TeamFFT<N1, N2> TF;
+  constexpr int n = N1 * N2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* L = reinterpret_cast<float2*>(smem_raw);
+  float2* xs = L + n;
+  const long long c0 = (long long)blockIdx.x * 2;
+  const int ny = g.ny, t = threadIdx.x;
+  for (int col = 0; col < 2; ++col) {
+    const long long cc = c0 + col;
+    float* Lc = reinterpret_cast<float*>(L) + col;
+    for (int j = t; j < ny; j += blockDim.x) Lc[2 * j] = cc < ncols ? f[cc * ny + j] : 0.f;
+  }
+  __syncthreads();
+  fc_append<float>(L, 1, n, ny, g.n_cont, g.n_match, E);
+  __syncthreads();
+  float2 x[TF::NV];
+  if (t < N2) {
+#pragma unroll
+    for (int j = 0; j < N1; ++j) x[j] = L[t + N2 * j];
+  }
+  TF::fwd(x, xs, roots, t);
+  if (t < N1) {
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) L[t + N1 * k2] = x[k2];
+  }
+  const float hh = (float)(g.h * g.h * 0.25);
+  const float cky = (float)(2.0 * 3.14159265358979323846 / (n * g.dy));
+  const float tscale = (float)(1.0 / n);
+  for (int o = 0; o < lo.nout; ++o) {
+    const int op = lo.op[o];
+    float2 y[TF::NV];
+    if (t < N1) {
+#pragma unroll
+      for (int k2 = 0; k2 < N2; ++k2) {
+        const int k = t + N1 * k2;
+        const int kappa = (2 * k <= n) ? k : k - n;
+        const float ky = cky * (float)kappa;
+        const float What = pool[g.ey_off + (kappa < 0 ? -kappa : kappa)].x * kernel_poly<float>(g.family, ky * ky * hh);
+        const bool nyq = (n % 2 == 0) && (2 * k == n);
+        float2 sy;
+        if (op == SYM_W)
+          sy = make_float2(What, 0.f);
+        else if (op == SYM_DY)
+          sy = make_float2(0.f, nyq ? 0.f : ky * What);
+        else if (op == SYM_LAP)
+          sy = make_float2(-(ky * ky) * What, 0.f);
+        else
+          sy = make_float2(0.f, 0.f);
+        y[k2] = cscale(cmul(sy, L[k]), tscale);
+      }
+    }
+    TF::inv(y, xs, roots, t);
+    if (t < N2) {
+      float* out = reinterpret_cast<float*>(lo.out[o]);
+#pragma unroll
+      for (int j = 0; j < N1; ++j) {
+        const int row = t + N2 * j;
+        if (row < ny) {
+          if (c0 < ncols) out[c0 * ny + row] = y[j].x;
+          if (c0 + 1 < ncols) out[(c0 + 1) * ny + row] = y[j].y;
+        }
+      }
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // z pass of the 3D channel: in the spectra [b][field][row][x][z] every run of
 // nz values (fixed b, field, row, x) is one periodic z line; L lines per CTA
@@ -945,7 +1020,7 @@ __global__ void __launch_bounds__(NT, MinCtas<T, NT>::v) k_col_inv(GridDev g, co
 // spectrum); k_col_out_r what k_col_inv does with EPI_OUT into FP32 outputs
 // (Hermitian gather, inverse transform, store), for every output.
 template <int N1, int N2>
-__global__ void __launch_bounds__(TeamFFT<N1, N2>::THREADS) k_col_fwd_r(
+__global__ void __launch_bounds__(TeamFFT<N1, N2>::THREADS, TeamFFT<N1, N2>::MIN_CTAS) k_col_fwd_r(
     GridDev g, const float* __restrict__ f0, const float* __restrict__ f1, const float* __restrict__ f2,
     const typename FcTab<float>::t* __restrict__ E, const float2* __restrict__ roots, float2* __restrict__ spec,
     size_t fstride, size_t bstride) {
@@ -983,7 +1058,7 @@ __global__ void __launch_bounds__(TeamFFT<N1, N2>::THREADS) k_col_fwd_r(
 }
 
 template <int N1, int N2>
-__global__ void __launch_bounds__(TeamFFT<N1, N2>::THREADS) k_col_out_r(
+__global__ void __launch_bounds__(TeamFFT<N1, N2>::THREADS, TeamFFT<N1, N2>::MIN_CTAS) k_col_out_r(
     GridDev g, const float2* __restrict__ spec, size_t fstride, size_t bstride, int nout, const EpiArgs ea,
     const float2* __restrict__ roots) {
   typedef TeamFFT<N1, N2> TF;
@@ -1210,6 +1285,8 @@ cudaError_t init_kernel_attributes() {
   FCSPH_RAISE((k_dft_lines<float, true>))
   FCSPH_RAISE((k_dft_lines<ff, false, double2>))
   FCSPH_RAISE((k_dft_lines<ff, true, double2>))
+  FCSPH_RAISE((k_line_op_r<20, 27>))
+  FCSPH_RAISE((k_line_op_r<30, 35>))
   FCSPH_RAISE((k_col_fwd_r<20, 27>))
   FCSPH_RAISE((k_col_fwd_r<30, 35>))
   FCSPH_RAISE((k_col_out_r<20, 27>))
@@ -1457,9 +1534,39 @@ cudaError_t launch_row_sym(fcsph_ctx* c, int prec, const void* sp_in, void* sp_o
   return row_sym_t<float>(c, prec, sp_in, sp_out, ops, scale, bc, kind);
 }
 
+template <int N1, int N2>
+static cudaError_t line_op_r(fcsph_ctx* c, const void* f, const LineOuts& lo, int bc) {
+  typedef TeamFFT<N1, N2> TF;
+  const GridDev& g = c->gd;
+  const size_t smem = ((size_t)N1 * N2 + TF::XCHG) * sizeof(float2);
+  cudaError_t e = check_smem(smem);
+  if (e != cudaSuccess) return e;
+  const long long ncols = (long long)g.batch * g.ncol;
+  const auto* E = static_cast<const typename FcTab<float>::t*>(fc_table(c, FCSPH_F32, bc));
+  ProfScope ps(c, FCSPH_PROF_COL_OUT);
+  k_line_op_r<N1, N2><<<(unsigned)((ncols + 1) / 2), TF::THREADS, smem, c->stream>>>(
+      g, (const float*)f, ncols, E, c->pool32, c->pool32 + c->plan_y.base.tw, lo);
+  c->launches++;
+  return cudaGetLastError();
+}
+
 template <typename T, typename U>
 static cudaError_t line_op_t(fcsph_ctx* c, int prec, const void* f, const int* ops, int nout, int bc, void* const* outs) {
   const GridDev& g = c->gd;
+  if constexpr (sizeof(T) == sizeof(float) && sizeof(U) == sizeof(float)) {
+    const int split = col_r_split(c);
+    if (split) {
+      LineOuts lo;
+      memset(&lo, 0, sizeof(lo));
+      lo.nout = nout;
+      for (int o = 0; o < nout; ++o) {
+        lo.op[o] = ops[o];
+        lo.out[o] = outs[o];
+      }
+      if (split == 20) return line_op_r<20, 27>(c, f, lo, bc);
+      if (split == 30) return line_op_r<30, 35>(c, f, lo, bc);
+    }
+  }
   const FftPlan& P = c->plan_y;
   const int ls = P.line_len();
   const int Pp = c->col_pairs;

@@ -75,6 +75,7 @@ template <int N1, int N2> struct TeamFFT {
   static constexpr int S = (N2 % 2) ? N2 : N2 + 1;    // odd row stride of the exchange block
   static constexpr int XCHG = N1 * S;                 // float2 elements of the exchange block
   static constexpr int THREADS = (NV + 31) / 32 * 32;
+  static constexpr int MIN_CTAS = 512 / THREADS;      // <= 128 registers per thread
 
   // Forward: v[j] = x[t + N2 j] (t < N2) on entry; v[k2] = X[t + N1 k2]
   // (t < N1) on return.  Every thread of the CTA calls it.
