@@ -621,6 +621,27 @@ __global__ void __launch_bounds__(NT, LineMinCtas<T, NT>::v) k_line_op(GridDev g
   }
 }
 
+// Two adjacent FP32 columns (c0 = src[0..ny), c1 = src[ny..2 ny); c1 absent:
+// zeros) packed into the complex line L[j] = (c0[j], c1[j]).  With ny a
+// multiple of 4 and a 16-byte aligned start every thread issues its float4
+// loads of both columns back to back; otherwise plain loads.
+__device__ __forceinline__ void load_pair_f32(float2* L, const float* __restrict__ src, bool has1, int ny) {
+  const int t = threadIdx.x, nt = blockDim.x;
+  if ((ny & 3) == 0 && ((reinterpret_cast<uintptr_t>(src) & 15) == 0)) {
+    const float4* c0 = reinterpret_cast<const float4*>(src);
+    const float4* c1 = reinterpret_cast<const float4*>(src + ny);
+    for (int m = t; m < ny / 4; m += nt) {
+      const float4 a = c0[m];
+      const float4 b = has1 ? c1[m] : make_float4(0.f, 0.f, 0.f, 0.f);
+      float4* d = reinterpret_cast<float4*>(L + 4 * m);
+      d[0] = make_float4(a.x, b.x, a.y, b.y);
+      d[1] = make_float4(a.z, b.z, a.w, b.w);
+    }
+  } else {
+    for (int j = t; j < ny; j += nt) L[j] = make_float2(src[j], has1 ? src[ny + j] : 0.f);
+  }
+}
+
 // The line operator of FP32 contexts with the register team FFT
 // (fcsph_regfft.cuh) for extended lengths n = N1 N2: one column pair per CTA;
 // the forward spectrum waits in shared memory, each value where the thread
@@ -637,11 +658,7 @@ __global__ void __launch_bounds__(TeamFFT<N1, N2>::THREADS, TeamFFT<N1, N2>::MIN
   float2* xs = L + n;
   const long long c0 = (long long)blockIdx.x * 2;
   const int ny = g.ny, t = threadIdx.x;
-  for (int col = 0; col < 2; ++col) {
-    const long long cc = c0 + col;
-    float* Lc = reinterpret_cast<float*>(L) + col;
-    for (int j = t; j < ny; j += blockDim.x) Lc[2 * j] = cc < ncols ? f[cc * ny + j] : 0.f;
-  }
+  load_pair_f32(L, f + c0 * ny, c0 + 1 < ncols, ny);
   __syncthreads();
   fc_append<float>(L, 1, n, ny, g.n_cont, g.n_match, E);
   __syncthreads();
@@ -1034,12 +1051,7 @@ __global__ void __launch_bounds__(TeamFFT<N1, N2>::THREADS, TeamFFT<N1, N2>::MIN
   const int i0 = blockIdx.x * 2;
   const float* src = f == 0 ? f0 : (f == 1 ? f1 : f2);
   const int ny = g.ny, t = threadIdx.x;
-  const size_t base = ((size_t)b * g.ncol + i0) * ny;
-  for (int col = 0; col < 2; ++col) {
-    float* Lc = reinterpret_cast<float*>(L) + col;
-    const bool in = i0 + col < g.ncol;
-    for (int j = t; j < ny; j += blockDim.x) Lc[2 * j] = in ? src[base + (size_t)col * ny + j] : 0.f;
-  }
+  load_pair_f32(L, src + ((size_t)b * g.ncol + i0) * ny, i0 + 1 < g.ncol, ny);
   __syncthreads();
   fc_append<float>(L, 1, n, ny, g.n_cont, g.n_match, E);
   __syncthreads();
@@ -1072,6 +1084,8 @@ __global__ void __launch_bounds__(TeamFFT<N1, N2>::THREADS, TeamFFT<N1, N2>::MIN
   const int ny = g.ny, t = threadIdx.x;
   for (int o = 0; o < nout; ++o) {
     col_gather_hermitian<float>(L, 1, n, g, i0, spec + b * bstride + o * fstride, fstride, 1, n);
+    // the next output's half spectrum into L2 while this one is transformed
+    if (o + 1 < nout) prefetch_spec_pairs(g, i0, 1, spec + b * bstride + (o + 1) * fstride);
     __syncthreads();
     float2 v[TF::NV];
     if (t < N1) {

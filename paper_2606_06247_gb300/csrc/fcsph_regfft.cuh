@@ -36,8 +36,8 @@ template <> struct RegSplit<35> { static constexpr int a = 5; };
 
 // exp(-/+ 2 pi i e / N) (forward / inverse) for a composite N.
 template <int N, bool INV> __device__ __forceinline__ float2 rroot(int e) {
-  const float s = (float)rsin<N>(e);
-  return make_float2((float)rcos<N>(e), INV ? s : -s);
+  const float s = rsin<N>(e);
+  return make_float2(rcos<N>(e), INV ? s : -s);
 }
 
 // In-register N-point DFT, natural order in and out:

@@ -18,16 +18,16 @@ def main():
     out = ["// Generated by gen_roots.py: cos and sin of 2 pi e / N for the composite",
            "// register-DFT sizes N.  Do not edit by hand.",
            "#pragma once", "", "namespace fcsph {", "",
-           "template <int N> __device__ __forceinline__ double rcos(int e);",
-           "template <int N> __device__ __forceinline__ double rsin(int e);", ""]
+           "template <int N> __device__ __forceinline__ float rcos(int e);",
+           "template <int N> __device__ __forceinline__ float rsin(int e);", ""]
     for n in SIZES:
         for name, fn in (("rcos", mp.cos), ("rsin", mp.sin)):
-            out.append(f"template <> __device__ __forceinline__ double {name}<{n}>(int e) {{")
+            out.append(f"template <> __device__ __forceinline__ float {name}<{n}>(int e) {{")
             out.append(f"  switch (((e % {n}) + {n}) % {n}) {{")
             for e in range(n):
                 v = fn(2 * mp.pi * e / n)
-                out.append(f"    case {e}: return {mp.nstr(v, 17, min_fixed=-2, max_fixed=2)};")
-            out.append("    default: return 0.0;")
+                out.append(f"    case {e}: return {mp.nstr(v, 17, min_fixed=-2, max_fixed=2)}f;")
+            out.append("    default: return 0.0f;")
             out.append("  }")
             out.append("}")
         out.append("")

@@ -140,3 +140,31 @@ def test_fp32_register_columns_spectral_op(nx, ny, n_cont):
         worst = max(worst, rel_l2(div[k].double().cpu().numpy(), rd))
     print(f"register columns {nx}x{ny} C={n_cont}: worst FP32 rel L2 vs FP64 oracle {worst:.2e}")
     assert worst < 2e-4
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("ny,n_cont", [(1024, 26), (512, 28)])
+def test_fp32_register_line_op(ny, n_cont):
+    """line_op of FP32 contexts on the register team FFT (1050 and 540 extended
+    points), an odd number of lines, against the FP64 oracle."""
+    torch = torch_cuda()
+    b = binding()
+    from oracle.symbols import symbol_closed
+    from tables import gram_golden
+    nl = 5
+    dy = 1.0 / (ny - 1)
+    ctx = b.Context(nl, ny, nl * dy, 1.0, batch=1, n_cont=n_cont, family="G4", h_over_dx=1.3, prec="f32")
+    f = inputs.band_limited_lines(nl, ny, seed=3, n_modes=32).reshape(1, nl, ny)
+    names = ["W", "DY", "LAP"]
+    outs = [torch.zeros((1, nl, ny), dtype=torch.float32, device="cuda") for _ in names]
+    ctx.line_op(to_dev(f, "f32"), names, outs)
+    ctx.sync()
+    E = gram_golden(5, n_cont)
+    S = [symbol_closed(op, "G4", 1.3 * dy, 1, ny + n_cont, 1.0, dy) for op in names]
+    worst = 0.0
+    for i in range(nl):
+        refs = oops.apply_symbols(f[0, i].astype(np.float32).astype(np.float64)[None, :], S, E)
+        for o, r in zip(outs, refs):
+            worst = max(worst, rel_l2(o[0, i].double().cpu().numpy(), r[0]))
+    print(f"register line_op ny={ny} C={n_cont}: worst FP32 rel L2 {worst:.2e}")
+    assert worst < 1e-4
