@@ -432,6 +432,7 @@ struct WRowSym {
   bool nyq_y, nyq_z;
   int mx, k1;
   const float* Wq;
+  float kx0, wrap;  // ckx k1 and ckx mx: kx = kx0 + ckx M k2 (- wrap past mx/2), no int-to-float per element
 };
 
 // v[k2] += symbol OP (kx of k1 + M k2) x spectrum value ([k2][lane] at xr, xi).
@@ -440,8 +441,8 @@ __device__ __forceinline__ void w_accumulate(float2* v, const float* xr, const f
 #pragma unroll
   for (int k2 = 0; k2 < 32; ++k2) {
     const int kxi = r.k1 + M * k2;
-    const int kappa = (2 * kxi <= r.mx) ? kxi : kxi - r.mx;
-    const float kx = r.ckx * (float)kappa;
+    const float kxu = fmaf(r.ckx, (float)(M * k2), r.kx0);  // M k2 is a compile-time constant
+    const float kx = (2 * kxi <= r.mx) ? kxu : kxu - r.wrap;
     const bool nyq_x = (r.mx % 2 == 0) && (2 * kxi == r.mx);
     const float What = (OP == SYM_ONE || OP == SYM_NPXX || OP == SYM_NPXY || OP == SYM_NPYY) ? 1.f : r.Wq[kxi];
     const float2 sy = symbol<float>(OP, kx, r.kyw, r.kz, nyq_x, r.nyq_y, r.nyq_z, What);
@@ -512,7 +513,7 @@ __global__ void __launch_bounds__(128, 3) k_row_sym_w(GridDev g, const float2* _
   const bool nyq_z = (nz % 2 == 0) && (2 * kq == nz);
   const float* Wq = Wt + (size_t)q * mx;
   const float tscale = (float)scale;
-  const WRowSym rs{ckx, kyw, kz, nyq_y, nyq_z, mx, k1, Wq};
+  const WRowSym rs{ckx, kyw, kz, nyq_y, nyq_z, mx, k1, Wq, ckx * (float)k1, ckx * (float)mx};
   for (int o = 0; o < nout; ++o) {
     float2 v[32];
 #pragma unroll
@@ -675,6 +676,7 @@ __global__ void __launch_bounds__(TeamFFT<N1, N2>::THREADS, TeamFFT<N1, N2>::MIN
   const float hh = (float)(g.h * g.h * 0.25);
   const float cky = (float)(2.0 * 3.14159265358979323846 / (n * g.dy));
   const float tscale = (float)(1.0 / n);
+  const float ky0 = cky * (float)t;
   for (int o = 0; o < lo.nout; ++o) {
     const int op = lo.op[o];
     float2 y[TF::NV];
@@ -683,7 +685,8 @@ __global__ void __launch_bounds__(TeamFFT<N1, N2>::THREADS, TeamFFT<N1, N2>::MIN
       for (int k2 = 0; k2 < N2; ++k2) {
         const int k = t + N1 * k2;
         const int kappa = (2 * k <= n) ? k : k - n;
-        const float ky = cky * (float)kappa;
+        const float kyu = fmaf(cky, (float)(N1 * k2), ky0);  // N1 k2 is a compile-time constant
+        const float ky = (2 * k <= n) ? kyu : kyu - cky * (float)n;
         const float What = pool[g.ey_off + (kappa < 0 ? -kappa : kappa)].x * kernel_poly<float>(g.family, ky * ky * hh);
         const bool nyq = (n % 2 == 0) && (2 * k == n);
         float2 sy;
