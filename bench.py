@@ -513,6 +513,7 @@ def run_ours(args):
                 compare[f"{pr}_ms_per_step"] = t2 / n2
                 compare[f"{pr}_tiling"] = list(c2.get_tiling())
                 compare[f"{pr}_cta_threads"] = list(c2.get_cta_threads())
+                compare[f"{pr}_step_groups"] = c2.get_step_groups()
             sa = state()
             c2.isph_step(*sa, nsteps_cmp, use_graph=True, **prm)
             torch.cuda.synchronize()
@@ -585,7 +586,8 @@ def run_ours(args):
                                               f"{args.refine} refinement sweeps"),
                                       "f32x2": "FP32-pair (double-float) FFT/symbols/FC sums, FP64 state",
                                       "f64": "FP64"}[args.prec],
-                           tiling=list(ctx.get_tiling()), cta_threads=list(ctx.get_cta_threads())),
+                           tiling=list(ctx.get_tiling()), cta_threads=list(ctx.get_cta_threads()),
+                           step_groups=ctx.get_step_groups()),
             "latency_ms": {"p50": per_sorted[len(per_sorted) // 2], "p99": per_sorted[min(len(per_sorted) - 1, int(0.99 * len(per_sorted)))]},
             "roofline": roof,
             "kernels": kinds,

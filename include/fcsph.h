@@ -333,12 +333,25 @@ fcsph_status fcsph_get_tiling(const fcsph_ctx* ctx, int* row_lines, int* col_pai
 fcsph_status fcsph_set_cta_threads(fcsph_ctx* ctx, int row_threads, int col_threads);
 fcsph_status fcsph_get_cta_threads(const fcsph_ctx* ctx, int* row_threads, int* col_threads);
 
+/* Instance groups of the isph_step graph (use_graph = 1): the batch is split
+ * into `groups` (1..16) groups of nearly equal size whose kernels run as
+ * parallel branches of the step graph, so that one group's launch fills the
+ * SMs left idle by the last, partial wave of CTAs of another group's launch.
+ * Results do not depend on it (each instance's arithmetic is unchanged).
+ * Default 1; eager steps (use_graph = 0) and FP32 contexts with PPE
+ * refinement always run one chain.  A change drops the captured graph.
+ * Engineering choice of this library; the paper has no counterpart. */
+fcsph_status fcsph_set_step_groups(fcsph_ctx* ctx, int groups);
+fcsph_status fcsph_get_step_groups(const fcsph_ctx* ctx, int* groups);
+
 /* Autotuner: times `steps` isph_step calls with *prm for every tiling with
  * row_lines, col_pairs in {1, 2, 4} that fits, on a zero state the call
  * allocates and frees (5 fields of the context's batch), then keeps the
  * fastest (2D: 5 fields, 3D: 7); then it times every pair of CTA widths in
- * {32, 64, 128} at that tiling and keeps the fastest.  best_ms_out
- * (nullable, host): its milliseconds per step.
+ * {32, 64, 128} at that tiling and keeps the fastest; then the instance
+ * groups 1, 2, 4 (at most the batch) of the step graph at that tiling and
+ * width, and keeps the fastest.  best_ms_out (nullable, host): its
+ * milliseconds per step.
  * Synchronises the context's stream.  Engineering choice of this library;
  * the paper has no counterpart. */
 fcsph_status fcsph_autotune(fcsph_ctx* ctx, const fcsph_step_params* prm, int steps, double* best_ms_out);

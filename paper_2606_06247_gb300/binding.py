@@ -109,6 +109,8 @@ def _load():
         "fcsph_get_tiling": [P, ctypes.POINTER(I), ctypes.POINTER(I)],
         "fcsph_set_cta_threads": [P, I, I],
         "fcsph_get_cta_threads": [P, ctypes.POINTER(I), ctypes.POINTER(I)],
+        "fcsph_set_step_groups": [P, I],
+        "fcsph_get_step_groups": [P, ctypes.POINTER(I)],
         "fcsph_autotune": [P, ctypes.POINTER(fcsph_step_params), I, ctypes.POINTER(D)],
         "fcsph_batch_create": [I, I, D, I, ctypes.POINTER(P)],
         "fcsph_batch_destroy": [P],
@@ -314,10 +316,19 @@ class Context:
         self._ck(lib.fcsph_get_cta_threads(self.h, ctypes.byref(r), ctypes.byref(c)))
         return r.value, c.value
 
+    def set_step_groups(self, groups):
+        """fcsph_set_step_groups: instance groups run as parallel branches of the step graph (1..16)."""
+        self._ck(lib.fcsph_set_step_groups(self.h, groups))
+
+    def get_step_groups(self):
+        g = ctypes.c_int()
+        self._ck(lib.fcsph_get_step_groups(self.h, ctypes.byref(g)))
+        return g.value
+
     def autotune(self, steps=3, nu=1e-3, rho=1.0, dt=1e-3, force=(0.0, 0.0), u_bottom=0.0, u_top=0.0, scheme="rk3",
                  use_graph=True, nu_inst=None, fx_inst=None):
-        """fcsph_autotune: keeps the fastest tiling (and, FP32, CTA widths); returns (row_lines, col_pairs,
-        ms per step)."""
+        """fcsph_autotune: keeps the fastest tiling, then CTA widths, then step groups; returns (row_lines,
+        col_pairs, ms per step)."""
         prm = self._params(nu, rho, dt, force, u_bottom, u_top, scheme, use_graph, nu_inst, fx_inst)
         ms = ctypes.c_double()
         self._ck(lib.fcsph_autotune(self.h, ctypes.byref(prm), steps, ctypes.byref(ms)))

@@ -237,6 +237,7 @@ fcsph_status fcsph_create(const fcsph_grid* grid, const fcsph_fc* fc, const fcsp
   g.ncol = g.nx * nz;
   g.dz = nz > 1 ? grid->lz / nz : 1.0;
   g.batch = grid->batch;
+  g.nb = grid->batch;
   g.x_walls = grid->x_walls ? 1 : 0;
   g.n_match = fc->n_match;
   g.n_cont = fc->n_cont;
@@ -404,6 +405,8 @@ fcsph_status fcsph_destroy(fcsph_ctx* c) {
   cudaFree(c->dred);
   cudaFree(c->dstatus);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  for (cudaStream_t gs : c->grp_streams) cudaStreamDestroy(gs);
+  for (cudaEvent_t ge : c->grp_events) cudaEventDestroy(ge);
   delete c;
   return FCSPH_OK;
 }
@@ -690,6 +693,69 @@ static fcsph_status one_step(fcsph_ctx* c, const fcsph_state* s, const fcsph_ste
   return FCSPH_OK;
 }
 
+// Instance groups of the step graph: the batch is split into G groups of
+// nearly equal size, and each group's kernels form their own chain (a branch
+// of the graph on its own capture stream).  A pass of one group then runs
+// while another group's previous pass is still draining, so the partial last
+// wave of CTAs of one launch overlaps with the next launch of another group.
+// PPE refinement reduces over the whole batch between passes and keeps one
+// chain.
+static int step_groups(const fcsph_ctx* c, const fcsph_step_params* prm) {
+  (void)prm;
+  int G = c->groups;
+  if (c->prec.fft_prec == FCSPH_F32 && c->prec.ppe_refine_iters > 0) G = 1;
+  if (G > c->gd.batch) G = c->gd.batch;
+  return G < 1 ? 1 : G;
+}
+
+static fcsph_status ensure_group_streams(fcsph_ctx* c, int G) {
+  while ((int)c->grp_streams.size() < G) {
+    cudaStream_t st = nullptr;
+    FCSPH_CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking), "group stream");
+    c->grp_streams.push_back(st);
+  }
+  while ((int)c->grp_events.size() < G + 1) {
+    cudaEvent_t ev = nullptr;
+    FCSPH_CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "group event");
+    c->grp_events.push_back(ev);
+  }
+  return FCSPH_OK;
+}
+
+// Inside a capture on c->cap_stream: forks G group streams off it, records one
+// step of instances [b0, b0 + nb) on each, and joins them back.  Every forked
+// stream is joined even when a launch fails, so the capture can end.
+static fcsph_status capture_groups(fcsph_ctx* c, const fcsph_state* s, const fcsph_step_params* prm, int G) {
+  const int B = c->gd.batch;
+  cudaEvent_t fork = c->grp_events[0];
+  fcsph_status st = FCSPH_OK;
+  if (cudaEventRecord(fork, c->cap_stream) != cudaSuccess) return fail(c, FCSPH_ECUDA, "group fork");
+  int forked = 0;
+  for (int k = 0; k < G; ++k) {
+    if (cudaStreamWaitEvent(c->grp_streams[k], fork, 0) != cudaSuccess) {
+      st = fail(c, FCSPH_ECUDA, "group fork wait");
+      break;
+    }
+    forked = k + 1;
+    const int b0 = (int)((long long)B * k / G), b1 = (int)((long long)B * (k + 1) / G);
+    c->stream = c->grp_streams[k];
+    c->gd.b0 = b0;
+    c->gd.nb = b1 - b0;
+    st = one_step(c, s, prm);
+    if (st != FCSPH_OK) break;
+  }
+  c->gd.b0 = 0;
+  c->gd.nb = B;
+  c->stream = c->cap_stream;
+  for (int k = 0; k < forked; ++k) {
+    cudaEvent_t join = c->grp_events[k + 1];
+    if ((cudaEventRecord(join, c->grp_streams[k]) != cudaSuccess ||
+         cudaStreamWaitEvent(c->cap_stream, join, 0) != cudaSuccess) && st == FCSPH_OK)
+      st = fail(c, FCSPH_ECUDA, "group join");
+  }
+  return st;
+}
+
 // Sets the context's instance mask for the duration of one isph_step call.
 struct ActiveScope {
   fcsph_ctx* c;
@@ -738,10 +804,18 @@ static fcsph_status isph_step_masked(fcsph_ctx* c, const fcsph_state* s, int nst
     cudaStream_t user = c->stream;
     const int prof = c->prof_on;
     c->prof_on = 0;
+    const int G = step_groups(c, prm);
+    if (G > 1) {
+      fcsph_status gst = ensure_group_streams(c, G);
+      if (gst != FCSPH_OK) {
+        c->prof_on = prof;
+        return gst;
+      }
+    }
     c->stream = c->cap_stream;
     FCSPH_CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeRelaxed), "begin capture");
     const long long before = c->launches;
-    fcsph_status st = one_step(c, s, prm);
+    fcsph_status st = G > 1 ? capture_groups(c, s, prm, G) : one_step(c, s, prm);
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
     c->stream = user;
@@ -856,6 +930,20 @@ fcsph_status fcsph_get_tiling(const fcsph_ctx* c, int* row_lines, int* col_pairs
   return FCSPH_OK;
 }
 
+fcsph_status fcsph_set_step_groups(fcsph_ctx* c, int groups) {
+  if (!c) return fail(nullptr, FCSPH_EINVAL, "fcsph_set_step_groups: null context");
+  if (groups < 1 || groups > 16) return fail(c, FCSPH_EINVAL, "fcsph_set_step_groups: groups must be in 1..16");
+  if (groups != c->groups) drop_graph(c);
+  c->groups = groups;
+  return FCSPH_OK;
+}
+
+fcsph_status fcsph_get_step_groups(const fcsph_ctx* c, int* groups) {
+  if (!c || !groups) return fail(nullptr, FCSPH_EINVAL, "fcsph_get_step_groups: bad argument");
+  *groups = c->groups;
+  return FCSPH_OK;
+}
+
 fcsph_status fcsph_autotune(fcsph_ctx* c, const fcsph_step_params* prm, int steps, double* best_ms_out) {
   if (!c || !prm || steps < 1) return fail(c, FCSPH_EINVAL, "fcsph_autotune: bad argument");
   const size_t n = field_elems(c);
@@ -914,6 +1002,25 @@ fcsph_status fcsph_autotune(fcsph_ctx* c, const fcsph_step_params* prm, int step
       }
     }
   if (st == FCSPH_OK) st = fcsph_set_cta_threads(c, best_rt, best_ct);
+  // then the instance groups of the step graph at that tiling and width
+  int best_g = c->groups;
+  const int gcand[3] = {1, 2, 4};
+  for (int gi = 0; gi < 3 && st == FCSPH_OK; ++gi) {
+    if (gcand[gi] > c->gd.batch) continue;
+    if ((st = fcsph_set_step_groups(c, gcand[gi])) != FCSPH_OK) break;
+    if ((st = isph_step(c, &s, 1, prm)) != FCSPH_OK) break;
+    if ((e = cudaEventRecord(e0, c->stream)) != cudaSuccess) { st = cuda_fail(c, e, "autotune event"); break; }
+    if ((st = isph_step(c, &s, steps, prm)) != FCSPH_OK) break;
+    if ((e = cudaEventRecord(e1, c->stream)) != cudaSuccess) { st = cuda_fail(c, e, "autotune event"); break; }
+    if ((e = cudaEventSynchronize(e1)) != cudaSuccess) { st = cuda_fail(c, e, "autotune sync"); break; }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) {
+      best = ms;
+      best_g = gcand[gi];
+    }
+  }
+  if (st == FCSPH_OK) st = fcsph_set_step_groups(c, best_g);
   drop_graph(c);
   cudaStreamSynchronize(c->stream);
   if (e0) cudaEventDestroy(e0);

@@ -146,6 +146,11 @@ struct GridDev {
   // isph_step only: device [batch] flags, instance b is advanced where
   // active[b] != 0 (null: every instance); null outside isph_step
   const unsigned char* active = nullptr;
+  // Instances b0 .. b0 + nb - 1 are the ones a launch covers (grid dimension
+  // nb, instance index b0 + block index).  isph_step captures the batch as
+  // several such groups on parallel branches of its graph; every other call
+  // covers the whole batch (b0 = 0, nb = batch).
+  int b0 = 0, nb = 0;
 };
 
 // CTAs of an instance left out of the step return at once (uniform per CTA,
@@ -177,6 +182,9 @@ struct fcsph_ctx {
   int col_pairs = 1;            // column pairs per CTA of the column passes
   int row_threads = 32;         // CTA width of the row (and z) passes: 32, 64 or 128
   int col_threads = 32;         // CTA width of the column passes
+  int groups = 1;               // instance groups of the isph_step graph (parallel branches)
+  std::vector<cudaStream_t> grp_streams;  // one capture stream per group
+  std::vector<cudaEvent_t> grp_events;    // fork event + one join event per group
   std::vector<double> hE[2];    // host copies
   double2* pool64 = nullptr;
   float2* pool32 = nullptr;

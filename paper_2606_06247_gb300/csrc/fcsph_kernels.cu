@@ -267,7 +267,7 @@ __global__ void __launch_bounds__(NT, MinCtas<T, NT>::v) k_col_fwd(GridDev g, co
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* lines = reinterpret_cast<V*>(smem_raw);
   V* scratch = lines + (size_t)Pp * ls;
-  const int b = blockIdx.z, f = blockIdx.y;
+  const int b = blockIdx.z + g.b0, f = blockIdx.y;
   if (inactive(g, b)) return;
   const int i0 = blockIdx.x * 2 * Pp;
   const U* src = f == 0 ? f0 : (f == 1 ? f1 : f2);
@@ -362,7 +362,7 @@ __global__ void __launch_bounds__(NT, MinCtas<T, NT>::v) k_row_sym(GridDev g, co
   const int nin = ops.nin, nout = ops.nout;
   V* A = reinterpret_cast<V*>(smem_raw);
   V* B = A + (size_t)nin * Rr * ls;
-  const int b = blockIdx.y;
+  const int b = blockIdx.y + g.b0;
   if (inactive(g, b)) return;
   const int q0 = blockIdx.x * Rr;
   const int nx = g.nx, mx = g.mx, nz = g.nz;
@@ -478,7 +478,7 @@ __global__ void __launch_bounds__(128, 3) k_row_sym_w(GridDev g, const float2* _
   float* xs = reinterpret_cast<float*>(smem_raw) + (size_t)warp * (kWarpXchgFloats + nin * 2 * 32 * 32);
   float* spre = xs + kWarpXchgFloats;
   float* spim = spre + nin * 32 * 32;
-  const int b = blockIdx.y;
+  const int b = blockIdx.y + g.b0;
   if (inactive(g, b)) return;
   const int mx = g.mx, nz = g.nz;
   const int nq = g.hy * nz;
@@ -726,14 +726,16 @@ __global__ void __launch_bounds__(NT, MinCtas<T, NT>::v) k_zlines(typename CT<T>
                                                                       int lines_per_field, size_t fstride,
                                                                       size_t bstride, const __grid_constant__ FftPlan P,
                                                                       const typename CT<T>::t* __restrict__ pool, int L,
-                                                                      int ls, int inv, const unsigned char* active) {
+                                                                      int ls, int inv, const unsigned char* active,
+                                                                      int b0) {
   typedef typename CT<T>::t V;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  if (active && !active[blockIdx.z]) return;
+  const int b = blockIdx.z + b0;
+  if (active && !active[b]) return;
   V* A = reinterpret_cast<V*>(smem_raw);
   V* B = A + (size_t)L * ls;
   const int n = P.base.n;
-  V* base = spec + blockIdx.z * bstride + blockIdx.y * fstride;
+  V* base = spec + b * bstride + blockIdx.y * fstride;
   const int l0 = blockIdx.x * L;
   for (int r = 0; r < L; ++r) {
     const bool in = l0 + r < lines_per_field;
@@ -767,7 +769,7 @@ __global__ void __launch_bounds__(NT, MinCtas<T, NT>::v) k_row_ppe(GridDev g, ty
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* A = reinterpret_cast<V*>(smem_raw);
   V* B = A + (size_t)Rr * ls;
-  const int b = blockIdx.y;
+  const int b = blockIdx.y + g.b0;
   if (inactive(g, b)) return;
   const int q0 = blockIdx.x * Rr;
   const int nx = g.nx, ny = g.ny, nz = g.nz;
@@ -903,7 +905,7 @@ __global__ void __launch_bounds__(NT, MinCtas<T, NT>::v) k_col_inv(GridDev g, co
   V* Z = reinterpret_cast<V*>(smem_raw);
   V* S = Z + (size_t)Pp * ls;
   double2* acc = reinterpret_cast<double2*>(S + (size_t)Pp * ls);
-  const int b = blockIdx.y;
+  const int b = blockIdx.y + g.b0;
   if (inactive(g, b)) return;
   const int i0 = blockIdx.x * 2 * Pp;
   const int ny = g.ny;
@@ -1049,7 +1051,7 @@ __global__ void __launch_bounds__(TeamFFT<N1, N2>::THREADS, TeamFFT<N1, N2>::MIN
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* L = reinterpret_cast<float2*>(smem_raw);
   float2* xs = L + n;
-  const int b = blockIdx.z, f = blockIdx.y;
+  const int b = blockIdx.z + g.b0, f = blockIdx.y;
   if (inactive(g, b)) return;
   const int i0 = blockIdx.x * 2;
   const float* src = f == 0 ? f0 : (f == 1 ? f1 : f2);
@@ -1081,7 +1083,7 @@ __global__ void __launch_bounds__(TeamFFT<N1, N2>::THREADS, TeamFFT<N1, N2>::MIN
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* L = reinterpret_cast<float2*>(smem_raw);
   float2* xs = L + n;
-  const int b = blockIdx.y;
+  const int b = blockIdx.y + g.b0;
   if (inactive(g, b)) return;
   const int i0 = blockIdx.x * 2;
   const int ny = g.ny, t = threadIdx.x;
@@ -1400,7 +1402,7 @@ static cudaError_t col_fwd_r(fcsph_ctx* c, int nf, const void* const* fields, in
   cudaError_t e = check_smem(smem);
   if (e != cudaSuccess) return e;
   const auto* E = static_cast<const typename FcTab<float>::t*>(fc_table(c, FCSPH_F32, bc));
-  dim3 grid((g.ncol + 1) / 2, nf, g.batch);
+  dim3 grid((g.ncol + 1) / 2, nf, g.nb);
   const size_t fstride = (size_t)g.rows * g.ncol;
   const size_t bstride = spec_in_fields(c) * fstride;
   ProfScope ps(c, FCSPH_PROF_COL_FWD);
@@ -1420,7 +1422,7 @@ static cudaError_t col_out_r(fcsph_ctx* c, const void* spec, int nout, EpiArgs& 
   cudaError_t e = check_smem(smem);
   if (e != cudaSuccess) return e;
   const size_t fs = (size_t)g.rows * g.ncol;
-  dim3 grid((g.ncol + 1) / 2, g.batch);
+  dim3 grid((g.ncol + 1) / 2, g.nb);
   ProfScope ps(c, FCSPH_PROF_COL_OUT);
   k_col_out_r<N1, N2><<<grid, TF::THREADS, smem, c->stream>>>(g, (const float2*)spec, fs, spec_out_fields(c) * fs,
                                                              nout, ea, c->pool32 + c->plan_y.base.tw);
@@ -1447,7 +1449,7 @@ static cudaError_t col_fwd_t(fcsph_ctx* c, int prec, int nf, const void* const* 
   cudaError_t e = check_smem(smem);
   if (e != cudaSuccess) return e;
   const auto* E = static_cast<const typename FcTab<T>::t*>(fc_table(c, prec, bc));
-  dim3 grid((g.ncol + 2 * Pp - 1) / (2 * Pp), nf, g.batch);
+  dim3 grid((g.ncol + 2 * Pp - 1) / (2 * Pp), nf, g.nb);
   const size_t fstride = (size_t)g.rows * g.ncol;
   const size_t bstride = (dct ? 1 : spec_in_fields(c)) * fstride;
   ProfScope ps(c, FCSPH_PROF_COL_FWD);
@@ -1497,7 +1499,7 @@ static cudaError_t row_sym_w(fcsph_ctx* c, const void* sp_in, void* sp_out, cons
   cudaError_t e = check_smem(smem);
   if (e != cudaSuccess) return e;
   constexpr int rows_per_cta = 4 * (32 / M);
-  dim3 grid((g.hy * g.nz + rows_per_cta - 1) / rows_per_cta, g.batch);
+  dim3 grid((g.hy * g.nz + rows_per_cta - 1) / rows_per_cta, g.nb);
   const size_t fs = (size_t)g.rows * g.ncol;
   ProfScope ps(c, kind);
   k_row_sym_w<M><<<grid, 128, smem, c->stream>>>(g, (const float2*)sp_in, (float2*)sp_out, fs, spec_in_fields(c) * fs,
@@ -1529,7 +1531,7 @@ static cudaError_t row_sym_t(fcsph_ctx* c, int prec, const void* sp_in, void* sp
   if (e != cudaSuccess) return e;
   const auto* E = static_cast<const typename FcTab<T>::t*>(fc_table(c, prec, bc));
   const size_t fs = (size_t)g.rows * g.ncol;
-  dim3 grid((g.hy * g.nz + Rr - 1) / Rr, g.batch);
+  dim3 grid((g.hy * g.nz + Rr - 1) / Rr, g.nb);
   ProfScope ps(c, kind);
   return with_width(c->row_threads, [&](auto w) {
     constexpr int NT = decltype(w)::value;
@@ -1629,12 +1631,12 @@ static cudaError_t zpass_t(fcsph_ctx* c, void* spec, int nf, size_t bstride, int
   cudaError_t e = check_smem(smem);
   if (e != cudaSuccess) return e;
   const int lines = rows_used * g.nx;
-  dim3 grid((lines + L - 1) / L, nf, g.batch);
+  dim3 grid((lines + L - 1) / L, nf, g.nb);
   ProfScope ps(c, FCSPH_PROF_OTHER);
   return with_width(c->row_threads, [&](auto w) {
     constexpr int NT = decltype(w)::value;
     k_zlines<T, NT><<<grid, NT, smem, c->stream>>>((typename CT<T>::t*)spec, lines, (size_t)g.rows * g.ncol, bstride,
-                                                   P, PoolOf<T>::get(c), L, ls, inv, g.active);
+                                                   P, PoolOf<T>::get(c), L, ls, inv, g.active, g.b0);
     c->launches++;
     return cudaGetLastError();
   });
@@ -1663,7 +1665,7 @@ static cudaError_t col_inv_common(fcsph_ctx* c, int epi, const void* spec, int n
   const size_t smem = ((size_t)2 * ls * sizeof(typename CT<T>::t) + (size_t)nacc * g.ny * sizeof(double2)) * Pp;
   const size_t fs = (size_t)g.rows * g.ncol;
   const size_t bs = (epi >= EPI_PPE_SOLVE ? 1 : spec_out_fields(c)) * fs;  // spec_ppe or spec_out
-  dim3 grid((g.ncol + 2 * Pp - 1) / (2 * Pp), g.batch);
+  dim3 grid((g.ncol + 2 * Pp - 1) / (2 * Pp), g.nb);
   const typename CT<T>::t* pool = PoolOf<T>::get(c);
   if (epi < EPI_OUT || epi > EPI_PPE_ADD) return cudaErrorInvalidValue;
   if (ea.fwd_nf > 3 || (epi == EPI_MOM && nout != ea.fwd_nf * ea.mom_terms)) return cudaErrorInvalidValue;
@@ -1716,7 +1718,7 @@ static cudaError_t row_ppe_t(fcsph_ctx* c, void* spec, int apply) {
   const size_t smem = 2 * (size_t)ls * sizeof(typename CT<T>::t) * Rr;
   cudaError_t e = check_smem(smem);
   if (e != cudaSuccess) return e;
-  dim3 grid((g.ny * g.nz + Rr - 1) / Rr, g.batch);
+  dim3 grid((g.ny * g.nz + Rr - 1) / Rr, g.nb);
   ProfScope ps(c, FCSPH_PROF_ROW_PPE);
   return with_width(c->row_threads, [&](auto w) {
     constexpr int NT = decltype(w)::value;

@@ -183,3 +183,68 @@ def test_cta_widths_are_checked():
     # FP32-pair 540-point lines: ~34 KB per one-warp CTA, 6 fit an SM; 2 warps reach 12
     long = b.Context(512, 512, 1.0, 1.0, x_walls=True, batch=32, n_cont=28, prec="f32x2")
     assert long.get_cta_threads() == (64, 64)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", ["f64", "f32x2", "f32"])
+def test_step_groups_give_the_same_step(prec):
+    """fcsph_set_step_groups splits the batch into groups whose kernels run as
+    parallel branches of the step graph; every instance's arithmetic is that
+    of the single chain, so the state after the steps is bitwise the same, for
+    groups of unequal size (5 instances in 2 or 3 groups) and with an instance
+    masked out."""
+    torch = torch_cuda()
+    b = binding()
+    nx, ny, batch = 37, 30, 5
+    lx, ly = grid_lengths(nx, ny, True)
+    ctx = b.Context(nx, ny, lx, ly, x_walls=True, batch=batch, family="G8", h_over_dx=1.3, prec=prec)
+    active = torch.tensor([1, 1, 0, 1, 1], dtype=torch.uint8, device="cuda")
+    for mask in (None, active):
+        ref = None
+        for groups in (1, 2, 3, 5, 8):
+            ctx.set_step_groups(groups)
+            assert ctx.get_step_groups() == groups
+            st = _state(torch, nx, ny, batch, 21)
+            ctx.isph_step(*st, 2, use_graph=True, active=mask, **CAVITY)
+            ctx.sync()
+            out = [x.cpu().numpy() for x in st]
+            if ref is None:
+                ref = out
+            else:
+                for a, r in zip(out, ref):
+                    np.testing.assert_array_equal(a, r, err_msg=f"groups {groups}")
+        if mask is not None:
+            init = [x.cpu().numpy() for x in _state(torch, nx, ny, batch, 21)]
+            for a, r in zip(ref, init):
+                np.testing.assert_array_equal(a[2], r[2])  # the masked instance is untouched
+    with pytest.raises(b.FcsphError) as e:
+        ctx.set_step_groups(0)
+    assert e.value.status == 1
+
+
+@pytest.mark.gpu
+def test_step_groups_in_3d():
+    torch = torch_cuda()
+    b = binding()
+    nx, ny, nz, batch = 16, 20, 8, 3
+    dy = 1.0 / (ny - 1)
+    ctx = b.Context(nx, ny, nx * dy, 1.0, batch=batch, family="G4", h_over_dx=1.3, prec="f32x2", nz=nz, lz=nz * dy)
+    ref = None
+    for groups in (1, 2, 3):
+        ctx.set_step_groups(groups)
+        st = [torch.zeros((batch, nx * nz, ny), dtype=torch.float64, device="cuda") for _ in range(7)]
+        g0 = np.random.default_rng(9)
+        for k in range(3):
+            st[k].copy_(torch.tensor(1e-3 * g0.standard_normal((batch, nx * nz, ny))))
+            st[k][:, :, 0] = 0
+            st[k][:, :, -1] = 0
+        u, v, w, p, fu, fv, fw = st
+        ctx.isph_step(u, v, p, fu, fv, 2, nu=0.01, rho=1.0, dt=1e-3, force=(0.08, 0.0, 0.0), scheme="rk3",
+                      use_graph=True, w=w, fw=fw)
+        ctx.sync()
+        out = [x.cpu().numpy() for x in (u, v, w, p)]
+        if ref is None:
+            ref = out
+        else:
+            for a, r in zip(out, ref):
+                np.testing.assert_array_equal(a, r, err_msg=f"groups {groups}")
