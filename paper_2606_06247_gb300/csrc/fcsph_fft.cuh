@@ -330,12 +330,35 @@ __device__ __forceinline__ void dft_reg(typename CT<T>::t* v) {
   }
 }
 
+// Work a Rader transform folds into the first and last register stage of its
+// two length-(p-1) passes (null pointers: none).  ldmap (first stage of the
+// first pass): input element e is loaded from position ldmap[e] (primitive-
+// root order g^e; real parts of pool entries).  mul (last stage of the first
+// pass): output e is stored as conj(y_e * mul[e]), and y_0 (= sum_{j>0} x_j)
+// goes to slot rn + 1 first.  stmap (last stage of the second pass): output e
+// is stored at position stmap[e] (g^-e) as x_0 + conj(y_e), x_0 from slot rn
+// of the line; position 0 gets x_0 + A_0, A_0 from slot rn + 1 of aux.
+// Folded only into the FP64 and FP32 engines: in the FP32-pair engine the
+// extra branches of the stage loop cost more registers (spills) than the
+// passes they save.
+template <typename T> struct RaderFold { static constexpr bool on = true; };
+template <> struct RaderFold<ff> { static constexpr bool on = false; };
+
+template <typename V> struct StageFx {
+  const V* ldmap = nullptr;
+  const V* mul = nullptr;
+  const V* stmap = nullptr;
+  const V* aux = nullptr;
+  int rn = 0;
+};
+
 // cin / cout: conjugate the values as they are loaded / stored (the first and
 // last stage of an inverse transform computed as conj(DFT(conj x))).
 template <typename T, int R, bool INV>
 __device__ void stage_reg(const typename CT<T>::t* __restrict__ src, typename CT<T>::t* __restrict__ dst, int nl,
                           int ls, int n, int Ns, const FastDiv& dnb, const FastDiv& dns,
-                          const typename CT<T>::t* __restrict__ tw, bool cin, bool cout) {
+                          const typename CT<T>::t* __restrict__ tw, bool cin, bool cout,
+                          const StageFx<typename CT<T>::t>& fx) {
   typedef typename CT<T>::t V;
   const int nb = n / R;
   const int s = n / (Ns * R);
@@ -346,8 +369,13 @@ __device__ void stage_reg(const typename CT<T>::t* __restrict__ src, typename CT
     const int k = j - g * Ns;
     const V* in = src + (size_t)line * ls;
     V v[R];
+    if (RaderFold<T>::on && fx.ldmap) {
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = in[j + r * nb];
+      for (int r = 0; r < R; ++r) v[r] = in[pool_index(fx.ldmap[j + r * nb].x)];
+    } else {
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[r] = in[j + r * nb];
+    }
     if (cin) {
 #pragma unroll
       for (int r = 0; r < R; ++r) v[r].y = -v[r].y;
@@ -358,13 +386,43 @@ __device__ void stage_reg(const typename CT<T>::t* __restrict__ src, typename CT
       for (int r = 1; r < R; ++r) v[r] = cmul_nr(v[r], root<V, INV>(tw, r * ks));
     }
     dft_reg<T, R, INV>(v);
-    V* out = dst + (size_t)line * ls + g * Ns * R + k;
-    if (cout) {
+    V* ol = dst + (size_t)line * ls;
+    const int p0 = g * Ns * R + k;
+    if (RaderFold<T>::on && fx.mul) {
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[r].y = -v[r].y;
+      for (int r = 0; r < R; ++r) {
+        const int pos = p0 + r * Ns;
+        V w = cnorm(v[r]);
+        if (pos == 0) ol[fx.rn + 1] = w;
+        w = cmul(w, fx.mul[pos]);
+        w.y = -w.y;
+        ol[pos] = w;
+      }
+    } else if (RaderFold<T>::on && fx.stmap) {
+      const V x0 = in[fx.rn];
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int pos = p0 + r * Ns;
+        const V y = cnorm(v[r]);
+        V o;
+        o.x = x0.x + y.x;
+        o.y = x0.y - y.y;
+        if (cout) o.y = -o.y;
+        ol[pool_index(fx.stmap[pos].x)] = o;
+        if (pos == 0) {
+          V z = cadd(x0, fx.aux[(size_t)line * ls + fx.rn + 1]);
+          if (cout) z.y = -z.y;
+          ol[0] = z;
+        }
+      }
+    } else {
+      if (cout) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r].y = -v[r].y;
+      }
+#pragma unroll
+      for (int r = 0; r < R; ++r) ol[p0 + r * Ns] = cnorm(v[r]);
     }
-#pragma unroll
-    for (int r = 0; r < R; ++r) out[r * Ns] = cnorm(v[r]);
   }
 }
 
@@ -401,33 +459,48 @@ __device__ void stage_big(const typename CT<T>::t* __restrict__ src, typename CT
   }
 }
 
+// Radices with a register butterfly (stage_reg); others run stage_big.
+__device__ __forceinline__ bool reg_radix(int R) {
+  return R == 2 || R == 3 || R == 4 || R == 5 || R == 7 || R == 8 || R == 9 || R == 11 || R == 13 || R == 17;
+}
+
 // Runs the forward stages of p on nl lines held in a (stride ls), b is
 // scratch of the same shape.  All threads of the block must call it.
 // Returns the buffer holding the result (a or b).
-// conj_io: conjugate the input as the first stage loads it and the output as
-// the last stage stores it (the inverse as conj(DFT(conj x))); no-op if the
-// plan has no stage.
+// conj_in / conj_out: conjugate the input as the first stage loads it and
+// the output as the last stage stores it (the inverse as conj(DFT(conj x)));
+// no-op if the plan has no stage.  fx: Rader work folded into the first
+// (ldmap) and last (mul, stmap) stage, which must then be register stages.
 template <typename T>
 __device__ __forceinline__ typename CT<T>::t* fft_run(typename CT<T>::t* a, typename CT<T>::t* b, int nl, int ls,
                                                       const Plan1& p, const typename CT<T>::t* __restrict__ tw,
-                                                      bool conj_io) {
+                                                      bool conj_in, bool conj_out,
+                                                      const StageFx<typename CT<T>::t>& fx) {
   typedef typename CT<T>::t V;
   int Ns = 1;
   const int n = p.n;
   for (int s = 0; s < p.nst; ++s) {
     const int R = p.radix[s];
-    const bool ci = conj_io && s == 0, co = conj_io && s == p.nst - 1;
+    const bool ci = conj_in && s == 0, co = conj_out && s == p.nst - 1;
+    StageFx<V> f;
+    if (s == 0) f.ldmap = fx.ldmap;
+    if (s == p.nst - 1) {
+      f.mul = fx.mul;
+      f.stmap = fx.stmap;
+      f.aux = fx.aux;
+      f.rn = fx.rn;
+    }
     switch (R) {
-      case 2: stage_reg<T, 2, false>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw, ci, co); break;
-      case 3: stage_reg<T, 3, false>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw, ci, co); break;
-      case 4: stage_reg<T, 4, false>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw, ci, co); break;
-      case 5: stage_reg<T, 5, false>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw, ci, co); break;
-      case 7: stage_reg<T, 7, false>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw, ci, co); break;
-      case 8: stage_reg<T, 8, false>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw, ci, co); break;
-      case 9: stage_reg<T, 9, false>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw, ci, co); break;
-      case 11: stage_reg<T, 11, false>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw, ci, co); break;
-      case 13: stage_reg<T, 13, false>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw, ci, co); break;
-      case 17: stage_reg<T, 17, false>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw, ci, co); break;
+      case 2: stage_reg<T, 2, false>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw, ci, co, f); break;
+      case 3: stage_reg<T, 3, false>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw, ci, co, f); break;
+      case 4: stage_reg<T, 4, false>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw, ci, co, f); break;
+      case 5: stage_reg<T, 5, false>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw, ci, co, f); break;
+      case 7: stage_reg<T, 7, false>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw, ci, co, f); break;
+      case 8: stage_reg<T, 8, false>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw, ci, co, f); break;
+      case 9: stage_reg<T, 9, false>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw, ci, co, f); break;
+      case 11: stage_reg<T, 11, false>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw, ci, co, f); break;
+      case 13: stage_reg<T, 13, false>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw, ci, co, f); break;
+      case 17: stage_reg<T, 17, false>(a, b, nl, ls, n, Ns, p.dnb[s], p.dns[s], tw, ci, co, f); break;
       default: stage_big<T, false>(a, b, nl, ls, n, Ns, R, p.dn, tw, ci, co); break;
     }
     __syncthreads();
@@ -462,8 +535,18 @@ __device__ __noinline__ typename CT<T>::t* fft_any_rt(typename CT<T>::t* a, type
   const V* bh = pool + P.bhat;
   V* src = a;
   V* dst = b;
+  // Rader whose length-(n-1) plan starts and ends with register stages: the
+  // gather, the kernel multiply and the scatter run inside those stages
+  const bool rfuse = RaderFold<T>::on && P.rd && reg_radix(sp.radix[0]) && reg_radix(sp.radix[sp.nst - 1]);
   // ---- input stage
-  if (P.rd) {
+  if (rfuse) {
+    for (int line = threadIdx.x; line < nl; line += blockDim.x) {
+      V x0 = a[(size_t)line * ls];
+      if (inv) x0.y = -x0.y;
+      a[(size_t)line * ls + n] = x0;
+      b[(size_t)line * ls + n] = x0;
+    }
+  } else if (P.rd) {
     const V* gi = pool + P.gidx;
     for (int t = threadIdx.x; t < nl * m; t += blockDim.x) {
       const int line = fdiv(t, sp.dn);
@@ -501,9 +584,23 @@ __device__ __noinline__ typename CT<T>::t* fft_any_rt(typename CT<T>::t* a, type
   V* r = src;
 #pragma unroll 1
   for (int pass = 0; pass < (two ? 2 : 1); ++pass) {
-    r = fft_run<T>(src, dst, nl, ls, sp, pool + sp.tw, !two && inv);
+    StageFx<V> fx;
+    bool ci = !two && inv, co = !two && inv;
+    if (rfuse) {
+      fx.rn = n;
+      if (pass == 0) {
+        fx.ldmap = pool + P.gidx;
+        fx.mul = bh;
+        ci = inv;
+      } else {
+        fx.stmap = pool + P.sidx;
+        fx.aux = src;  // the first pass's result: A_0 in slot n + 1
+        co = inv;
+      }
+    }
+    r = fft_run<T>(src, dst, nl, ls, sp, pool + sp.tw, ci, co, fx);
     V* o = (r == src) ? dst : src;
-    if (pass == 0 && two) {
+    if (pass == 0 && two && !rfuse) {
       for (int t = threadIdx.x; t < nl * m; t += blockDim.x) {
         const int line = fdiv(t, sp.dn);
         const int k = t - line * m;
@@ -522,6 +619,7 @@ __device__ __noinline__ typename CT<T>::t* fft_any_rt(typename CT<T>::t* a, type
     dst = o;
   }
   // ---- output stage (r holds the result of the last pass)
+  if (rfuse) return r;
   if (P.rd) {
     const V* si = pool + P.sidx;
     V* out = dst;
