@@ -60,6 +60,9 @@ def parse():
     ap.add_argument("--slots", type=int, default=8, help="uneven/serve: slots (batch) per size class")
     ap.add_argument("--server", default="native", choices=["native", "python"],
                     help="uneven/serve: the library's scheduler (fcsph_batch_*) or the Python one")
+    ap.add_argument("--persistent", action="store_true",
+                    help="uneven/serve (native scheduler, 2D requests): every tick steps all size classes in one "
+                         "persistent launch instead of one graph per class")
     ap.add_argument("--fc-cont", default="25",
                     help="uneven/serve: FC continuation length of every size class, an integer or 'smooth' (per size "
                          "the length nearest 25 in [20, 40] whose extended line the engine transforms directly)")
@@ -660,7 +663,12 @@ def run_serving(args):
                 f"20% 3D channel of 64^3..128^3, each 50-500 RK3 steps scaled by {steps}/500")
     fc_cont = args.fc_cont if args.fc_cont == "smooth" else int(args.fc_cont)
     torch.cuda.synchronize()
-    srv = ServerCls(prec=args.prec, capacity=args.slots, fc_cont=fc_cont)
+    if args.persistent:
+        if args.server != "native":
+            raise SystemExit("--persistent needs the native scheduler")
+        srv = ServerCls(prec=args.prec, capacity=args.slots, fc_cont=fc_cont, persistent=True)
+    else:
+        srv = ServerCls(prec=args.prec, capacity=args.slots, fc_cont=fc_cont)
     rs = reqs()
     wall = srv.run(rs)
     torch.cuda.synchronize()
@@ -700,7 +708,7 @@ def run_serving(args):
         "steps": steps, "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
         "config": {"workload": desc, "precision": args.prec, "slots_per_size_class": args.slots, "fc_cont": args.fc_cont,
-                   "scheduler": args.server},
+                   "scheduler": args.server + (" persistent" if args.persistent else "")},
         "latency_ms": {"p50": served["step_latency_ms_p50"], "p99": served["step_latency_ms_p99"]},
         "served": served, "serial_plain_fp64": serial,
         "error_vs_fp64": err_summary, "per_instance": per_inst,

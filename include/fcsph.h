@@ -266,6 +266,30 @@ fcsph_status fcsph_batch_remove(fcsph_batch* batch, long long id);
  * of classes with a step in flight.  FCSPH_ENONFINITE if a retired step
  * flagged a non-finite value (the batch stays usable). */
 fcsph_status fcsph_batch_run(fcsph_batch* batch, int block, int* in_flight);
+/* Persistent mode (on = 1; FP64 and FP32x2 batches of 2D requests): each
+ * tick of fcsph_batch_run steps every class in ONE launch of a persistent
+ * kernel (replayed from a CUDA graph) instead of one graph per class.  One RK3
+ * step of every class is recorded once per set of classes as pass
+ * descriptors; a work item is one CTA's share of one pass (one column pair
+ * or spectrum row of one instance), and the CTAs take the items of all
+ * classes pass by pass from an atomic counter.  An item waits until every
+ * tile of the previous pass of its own instance is done, so the passes of
+ * different instances and sizes overlap and no class runs alone.  Results
+ * equal those of the per-class graphs bitwise.  Every such wait is bounded by
+ * wait_limit_s (in (0, 60] seconds; and a spin count): a wait that runs out
+ * makes the rest of that launch skip its items and fcsph_batch_run return
+ * FCSPH_ETIMEOUT once, after which the batch stays usable (the requests of
+ * that step hold undefined state).  Switching needs no step in flight;
+ * on = 1 refuses FP32 batches and open 3D classes or queued 3D requests,
+ * and fcsph_batch_add then refuses 3D requests (FCSPH_EUNSUPPORTED).  The
+ * batching of uneven sizes is this library's serving layer; the paper has no
+ * counterpart. */
+fcsph_status fcsph_batch_set_persistent(fcsph_batch* batch, int on, double wait_limit_s);
+/* Fault injection for tests of the bounded wait (persistent mode): in the
+ * next launch the last work item waits for a count that never comes, so its
+ * wait runs out after wait_limit_s.  Plants nothing on the device that could
+ * fault: the wait gives up and the kernel returns. */
+fcsph_status fcsph_batch_inject_stall(fcsph_batch* batch);
 fcsph_status fcsph_batch_poll(fcsph_batch* batch, long long id, fcsph_request_info* info);
 /* Host copies of a finished request's fields, each n_each >= n^2 (3D n^3)
  * doubles in [x][y] ([x][z][y]) order; any pointer may be NULL; w only for
@@ -344,14 +368,29 @@ fcsph_status fcsph_get_cta_threads(const fcsph_ctx* ctx, int* row_threads, int* 
 fcsph_status fcsph_set_step_groups(fcsph_ctx* ctx, int groups);
 fcsph_status fcsph_get_step_groups(const fcsph_ctx* ctx, int* groups);
 
+/* Persistent step (on = 1; 2D FP64 or FP32x2 contexts, else
+ * FCSPH_EUNSUPPORTED): with use_graph = 1, every step of isph_step is ONE
+ * launch of a persistent kernel over the step's recorded passes instead of a
+ * graph of ~25 kernels.  A work item is one CTA's share of one pass for one
+ * instance; an item waits (bounded: 1 s, and a spin count) until every tile
+ * of the previous pass of its own instance is done, so the passes of
+ * different instances overlap and no launch ends in a partial wave.  Results
+ * equal the graph's bitwise.  A wait that runs out makes the rest of that
+ * launch skip its items and the next fcsph_sync return FCSPH_ETIMEOUT once.
+ * The recording is redone when isph_step's pointers or parameters change.
+ * Engineering choice of this library; the paper has no counterpart. */
+fcsph_status fcsph_set_step_persistent(fcsph_ctx* ctx, int on);
+fcsph_status fcsph_get_step_persistent(const fcsph_ctx* ctx, int* on);
+
 /* Autotuner: times `steps` isph_step calls with *prm for every tiling with
  * row_lines, col_pairs in {1, 2, 4} that fits, on a zero state the call
  * allocates and frees (5 fields of the context's batch), then keeps the
  * fastest (2D: 5 fields, 3D: 7); then it times every pair of CTA widths in
  * {32, 64, 128} at that tiling and keeps the fastest; then the instance
  * groups 1, 2, 4 (at most the batch) of the step graph at that tiling and
- * width, and keeps the fastest.  best_ms_out (nullable, host): its
- * milliseconds per step.
+ * width, and keeps the fastest; then (2D FP64 / FP32x2) the persistent step,
+ * kept if faster still.  best_ms_out (nullable, host): its milliseconds per
+ * step.
  * Synchronises the context's stream.  Engineering choice of this library;
  * the paper has no counterpart. */
 fcsph_status fcsph_autotune(fcsph_ctx* ctx, const fcsph_step_params* prm, int steps, double* best_ms_out);

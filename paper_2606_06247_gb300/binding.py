@@ -110,6 +110,8 @@ def _load():
         "fcsph_set_cta_threads": [P, I, I],
         "fcsph_get_cta_threads": [P, ctypes.POINTER(I), ctypes.POINTER(I)],
         "fcsph_set_step_groups": [P, I],
+        "fcsph_set_step_persistent": [P, I],
+        "fcsph_get_step_persistent": [P, ctypes.POINTER(I)],
         "fcsph_get_step_groups": [P, ctypes.POINTER(I)],
         "fcsph_autotune": [P, ctypes.POINTER(fcsph_step_params), I, ctypes.POINTER(D)],
         "fcsph_batch_create": [I, I, D, I, ctypes.POINTER(P)],
@@ -121,6 +123,8 @@ def _load():
         "fcsph_batch_result": [P, ctypes.c_longlong, P, P, P, P, S],
         "fcsph_batch_info": [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(D)],
         "fcsph_batch_last_error": [P, ctypes.c_char_p, S],
+        "fcsph_batch_set_persistent": [P, I, D],
+        "fcsph_batch_inject_stall": [P],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -325,6 +329,15 @@ class Context:
         self._ck(lib.fcsph_get_step_groups(self.h, ctypes.byref(g)))
         return g.value
 
+    def set_step_persistent(self, on=True):
+        """fcsph_set_step_persistent: each graph step as one persistent launch (2D FP64 / FP32x2)."""
+        self._ck(lib.fcsph_set_step_persistent(self.h, 1 if on else 0))
+
+    def get_step_persistent(self):
+        v = ctypes.c_int()
+        self._ck(lib.fcsph_get_step_persistent(self.h, ctypes.byref(v)))
+        return bool(v.value)
+
     def autotune(self, steps=3, nu=1e-3, rho=1.0, dt=1e-3, force=(0.0, 0.0), u_bottom=0.0, u_top=0.0, scheme="rk3",
                  use_graph=True, nu_inst=None, fx_inst=None):
         """fcsph_autotune: keeps the fastest tiling, then CTA widths, then step groups; returns (row_lines,
@@ -392,6 +405,14 @@ class Batch:
         k = ctypes.c_int()
         self._ck(lib.fcsph_batch_run(self.h, 1 if block else 0, ctypes.byref(k)))
         return k.value
+
+    def set_persistent(self, on=True, wait_limit_s=1.0):
+        """fcsph_batch_set_persistent: every tick steps all classes in one persistent launch."""
+        self._ck(lib.fcsph_batch_set_persistent(self.h, 1 if on else 0, float(wait_limit_s)))
+
+    def inject_stall(self):
+        """fcsph_batch_inject_stall: the next persistent launch has one wait that runs out (tests)."""
+        self._ck(lib.fcsph_batch_inject_stall(self.h))
 
     def poll(self, rid):
         info = fcsph_request_info()

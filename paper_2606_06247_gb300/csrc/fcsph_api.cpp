@@ -405,6 +405,7 @@ fcsph_status fcsph_destroy(fcsph_ctx* c) {
   cudaFree(c->dred);
   cudaFree(c->dstatus);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  persist_destroy(c->pplan);
   for (cudaStream_t gs : c->grp_streams) cudaStreamDestroy(gs);
   for (cudaEvent_t ge : c->grp_events) cudaEventDestroy(ge);
   delete c;
@@ -756,6 +757,44 @@ static fcsph_status capture_groups(fcsph_ctx* c, const fcsph_state* s, const fcs
   return st;
 }
 
+// The arguments a recorded step depends on (device pointers and parameters).
+static std::vector<double> step_key(const fcsph_state* s, const fcsph_step_params* prm) {
+  return {(double)(uintptr_t)s->u, (double)(uintptr_t)s->v, (double)(uintptr_t)s->p,
+          (double)(uintptr_t)s->fu, (double)(uintptr_t)s->fv, prm->nu, prm->rho, prm->dt,
+          prm->force_x, prm->force_y, prm->u_bottom, prm->u_top, (double)prm->scheme,
+          (double)(uintptr_t)prm->nu_inst, (double)(uintptr_t)prm->fx_inst,
+          (double)(uintptr_t)s->w, (double)(uintptr_t)s->fw, prm->force_z,
+          (double)(uintptr_t)prm->active, (double)(uintptr_t)prm->dt_inst};
+}
+
+// nsteps steps, each one launch of the persistent kernel over the recorded
+// passes of one step (after the forward transform isph_step launched).
+static fcsph_status persistent_steps(fcsph_ctx* c, const fcsph_state* s, int nsteps, const fcsph_step_params* prm) {
+  std::vector<double> key = step_key(s, prm);
+  if (!c->pplan || key != c->pplan_key) {
+    persist_destroy(c->pplan);
+    c->pplan = persist_create(c->prec.fft_prec);
+    fcsph_status st = record_isph_step(c, s, prm, persist_add_class(c->pplan, c->gd.batch), 0);
+    if (st != FCSPH_OK) {
+      persist_destroy(c->pplan);
+      c->pplan = nullptr;
+      return st;
+    }
+    std::string err;
+    cudaError_t e = persist_finalize(c->pplan, &err);
+    if (e != cudaSuccess) {
+      persist_destroy(c->pplan);
+      c->pplan = nullptr;
+      return fail(c, FCSPH_ECUDA, "isph_step: " + err + ": " + cudaGetErrorString(e));
+    }
+    c->pplan_key = key;
+  }
+  for (int it = 0; it < nsteps; ++it)
+    FCSPH_CK(persist_launch(c->pplan, c->stream, c->cap_stream, 1000000000ll, -1), "persistent step");
+  c->launches += nsteps;
+  return FCSPH_OK;
+}
+
 // Sets the context's instance mask for the duration of one isph_step call.
 struct ActiveScope {
   fcsph_ctx* c;
@@ -790,12 +829,8 @@ static fcsph_status isph_step_masked(fcsph_ctx* c, const fcsph_state* s, int nst
     }
     return FCSPH_OK;
   }
-  std::vector<double> key = {(double)(uintptr_t)s->u, (double)(uintptr_t)s->v, (double)(uintptr_t)s->p,
-                             (double)(uintptr_t)s->fu, (double)(uintptr_t)s->fv, prm->nu, prm->rho, prm->dt,
-                             prm->force_x, prm->force_y, prm->u_bottom, prm->u_top, (double)prm->scheme,
-                             (double)(uintptr_t)prm->nu_inst, (double)(uintptr_t)prm->fx_inst,
-                             (double)(uintptr_t)s->w, (double)(uintptr_t)s->fw, prm->force_z,
-                             (double)(uintptr_t)prm->active, (double)(uintptr_t)prm->dt_inst};
+  if (c->persist) return persistent_steps(c, s, nsteps, prm);
+  std::vector<double> key = step_key(s, prm);
   if (!c->gexec || key != c->graph_key) {
     if (c->gexec) {
       cudaGraphExecDestroy(c->gexec);
@@ -837,9 +872,34 @@ static fcsph_status isph_step_masked(fcsph_ctx* c, const fcsph_state* s, int nst
   return FCSPH_OK;
 }
 
+// One RK3 (or FOP) step of every instance recorded as pass descriptors for
+// the persistent multi-class launch (2D, FP64 or FP32x2).
+fcsph_status record_isph_step(fcsph_ctx* c, const fcsph_state* s, const fcsph_step_params* prm, PersistRec* rec,
+                              int with_fwd) {
+  if (!c || !s || !prm || !rec) return fail(c, FCSPH_EINVAL, "record_isph_step: bad argument");
+  if (c->gd.nz > 1 || c->prec.fft_prec == FCSPH_F32)
+    return fail(c, FCSPH_EUNSUPPORTED, "persistent step: 2D FP64 or FP32x2 contexts only");
+  if (!s->u || !s->v || !s->p || !s->fu || !s->fv) return fail(c, FCSPH_EINVAL, "record_isph_step: null state pointer");
+  ActiveScope scope(c, prm->active);
+  const int prof = c->prof_on;
+  c->prof_on = 0;
+  c->rec = rec;
+  const void* uvw[3] = {s->u, s->v, s->w};
+  cudaError_t e = with_fwd ? launch_col_fwd(c, c->prec.fft_prec, 2, uvw, 1, FCSPH_DIRICHLET, c->spec_in, 0) : cudaSuccess;
+  fcsph_status st = e == cudaSuccess ? one_step(c, s, prm) : cuda_fail(c, e, "record step");
+  c->rec = nullptr;
+  c->prof_on = prof;
+  return st;
+}
+
 fcsph_status fcsph_sync(fcsph_ctx* c) {
   if (!c) return fail(nullptr, FCSPH_EINVAL, "fcsph_sync: null context");
   FCSPH_CK(cudaStreamSynchronize(c->stream), "sync");
+  if (c->pplan) {
+    int ps = 0;
+    FCSPH_CK(persist_status(c->pplan, c->stream, &ps), "persistent status");
+    if (ps) return fail(c, FCSPH_ETIMEOUT, "a dependency wait of the persistent step ran out");
+  }
   int st = 0;
   FCSPH_CK(cudaMemcpy(&st, c->dstatus, sizeof(int), cudaMemcpyDeviceToHost), "status read");
   if (st & 1) {
@@ -938,6 +998,26 @@ fcsph_status fcsph_set_step_groups(fcsph_ctx* c, int groups) {
   return FCSPH_OK;
 }
 
+fcsph_status fcsph_set_step_persistent(fcsph_ctx* c, int on) {
+  if (!c) return fail(nullptr, FCSPH_EINVAL, "fcsph_set_step_persistent: null context");
+  if (on && (c->gd.nz > 1 || c->prec.fft_prec == FCSPH_F32))
+    return fail(c, FCSPH_EUNSUPPORTED, "fcsph_set_step_persistent: 2D FP64 or FP32x2 contexts only");
+  c->persist = on ? 1 : 0;
+  if (!on && c->pplan) {
+    cudaStreamSynchronize(c->stream);
+    persist_destroy(c->pplan);
+    c->pplan = nullptr;
+    c->pplan_key.clear();
+  }
+  return FCSPH_OK;
+}
+
+fcsph_status fcsph_get_step_persistent(const fcsph_ctx* c, int* on) {
+  if (!c || !on) return fail(nullptr, FCSPH_EINVAL, "fcsph_get_step_persistent: bad argument");
+  *on = c->persist;
+  return FCSPH_OK;
+}
+
 fcsph_status fcsph_get_step_groups(const fcsph_ctx* c, int* groups) {
   if (!c || !groups) return fail(nullptr, FCSPH_EINVAL, "fcsph_get_step_groups: bad argument");
   *groups = c->groups;
@@ -1021,6 +1101,26 @@ fcsph_status fcsph_autotune(fcsph_ctx* c, const fcsph_step_params* prm, int step
     }
   }
   if (st == FCSPH_OK) st = fcsph_set_step_groups(c, best_g);
+  // then one persistent launch per step instead of the graph (2D FP64 / FP32x2)
+  if (st == FCSPH_OK && c->gd.nz == 1 && c->prec.fft_prec != FCSPH_F32) {
+    bool keep = false;
+    if ((st = fcsph_set_step_persistent(c, 1)) == FCSPH_OK && (st = isph_step(c, &s, 1, prm)) == FCSPH_OK) {
+      if ((e = cudaEventRecord(e0, c->stream)) != cudaSuccess) st = cuda_fail(c, e, "autotune event");
+      if (st == FCSPH_OK) st = isph_step(c, &s, steps, prm);
+      if (st == FCSPH_OK && (e = cudaEventRecord(e1, c->stream)) != cudaSuccess) st = cuda_fail(c, e, "autotune event");
+      if (st == FCSPH_OK && (e = cudaEventSynchronize(e1)) != cudaSuccess) st = cuda_fail(c, e, "autotune sync");
+      float ms = 0.f;
+      if (st == FCSPH_OK) cudaEventElapsedTime(&ms, e0, e1);
+      if (st == FCSPH_OK && ms < best) {
+        best = ms;
+        keep = true;
+      }
+    }
+    // the autotuner's own state is freed below: the plan recorded for it goes
+    fcsph_status st2 = fcsph_set_step_persistent(c, 0);
+    if (st == FCSPH_OK) st = st2;
+    if (st == FCSPH_OK && keep) st = fcsph_set_step_persistent(c, 1);
+  }
   drop_graph(c);
   cudaStreamSynchronize(c->stream);
   if (e0) cudaEventDestroy(e0);

@@ -74,6 +74,15 @@ struct fcsph_batch {
   std::map<long long, Req> reqs;
   long long next_id = 1;
   std::string err;
+  // persistent mode: one launch steps every class (fcsph_batch_set_persistent)
+  bool persistent = false;
+  double wait_s = 1.0;
+  bool stall_next = false;
+  PersistPlan* plan = nullptr;
+  long long gen = 0, plan_gen = -1;  // class-set generation and the plan's
+  cudaStream_t tick_st = nullptr, cap_st = nullptr;
+  cudaEvent_t tick_end = nullptr;
+  bool tick_pending = false;
 };
 
 namespace {
@@ -312,10 +321,9 @@ fcsph_status finish_step(fcsph_batch* b, int ci) {
   return st;
 }
 
-fcsph_status launch_step(fcsph_batch* b, Class* c) {
-  cudaError_t e = cudaEventRecord(c->e0, c->st);
-  if (e != cudaSuccess) return bcuda(b, e, "fcsph_batch: event");
-  fcsph_state s = {c->u, c->v, c->p, c->fu, c->fv, c->w, c->fw};
+// Step parameters of a class: per-slot viscosity, body force and time step,
+// the slot mask, RK3.
+fcsph_step_params class_params(const Class* c) {
   fcsph_step_params prm;
   memset(&prm, 0, sizeof(prm));
   prm.nu = 1e-2;
@@ -328,6 +336,14 @@ fcsph_status launch_step(fcsph_batch* b, Class* c) {
   prm.fx_inst = c->fx;
   prm.active = c->active;
   prm.dt_inst = c->dt;
+  return prm;
+}
+
+fcsph_status launch_step(fcsph_batch* b, Class* c) {
+  cudaError_t e = cudaEventRecord(c->e0, c->st);
+  if (e != cudaSuccess) return bcuda(b, e, "fcsph_batch: event");
+  fcsph_state s = {c->u, c->v, c->p, c->fu, c->fv, c->w, c->fw};
+  fcsph_step_params prm = class_params(c);
   fcsph_status st = isph_step(c->ctx, &s, 1, &prm);
   if (st != FCSPH_OK) {
     char buf[256];
@@ -367,6 +383,7 @@ fcsph_status admit_queued(fcsph_batch* b) {
         return st;
       }
       b->classes.push_back(c);
+      b->gen++;
       ci = (int)b->classes.size() - 1;
     }
     Class* c = b->classes[ci];
@@ -401,10 +418,91 @@ void evict_idle(fcsph_batch* b) {
   }
   if (keep.size() != b->classes.size()) {
     b->classes.swap(keep);
+    b->gen++;
     for (size_t i = 0; i < b->classes.size(); ++i)
       for (int s = 0; s < b->classes[i]->capacity; ++s)
         if (b->classes[i]->slots[s] >= 0) b->reqs[b->classes[i]->slots[s]].cls = (int)i;
   }
+}
+
+// Records one step of every class into a new persistent plan.
+fcsph_status build_plan(fcsph_batch* b) {
+  if (b->plan) {
+    persist_destroy(b->plan);
+    b->plan = nullptr;
+  }
+  b->plan = persist_create(b->prec);
+  for (Class* c : b->classes) {
+    PersistRec* r = persist_add_class(b->plan, c->capacity);
+    fcsph_state s = {c->u, c->v, c->p, c->fu, c->fv, c->w, c->fw};
+    fcsph_step_params prm = class_params(c);
+    fcsph_status st = record_isph_step(c->ctx, &s, &prm, r, 1);
+    if (st != FCSPH_OK) {
+      char buf[256];
+      fcsph_last_error(c->ctx, buf, sizeof(buf));
+      return bfail(b, st, std::string("fcsph_batch: persistent step: ") + buf);
+    }
+  }
+  std::string err;
+  cudaError_t e = persist_finalize(b->plan, &err);
+  if (e != cudaSuccess) return bfail(b, FCSPH_ECUDA, "fcsph_batch: " + err + ": " + cudaGetErrorString(e));
+  b->plan_gen = b->gen;
+  return FCSPH_OK;
+}
+
+// One tick of the persistent mode: retire the finished launch, admit, and
+// step every class in one launch.
+fcsph_status run_persistent(fcsph_batch* b, int block, int* in_flight) {
+  fcsph_status first = FCSPH_OK;
+  auto pending_count = [&]() {
+    int k = 0;
+    for (const Class* c : b->classes) k += c->pending;
+    return k;
+  };
+  if (b->tick_pending) {
+    cudaError_t e = block ? cudaEventSynchronize(b->tick_end) : cudaEventQuery(b->tick_end);
+    if (e == cudaErrorNotReady) {
+      if (in_flight) *in_flight = pending_count();
+      return FCSPH_OK;
+    }
+    if (e != cudaSuccess) return bcuda(b, e, "fcsph_batch_run: persistent step event");
+    b->tick_pending = false;
+    int ps = 0;
+    if ((e = persist_status(b->plan, b->tick_st, &ps)) != cudaSuccess) return bcuda(b, e, "fcsph_batch_run: status");
+    if (ps)
+      first = bfail(b, FCSPH_ETIMEOUT, "fcsph_batch_run: a dependency wait of the persistent step ran out");
+    for (size_t i = 0; i < b->classes.size(); ++i) {
+      if (!b->classes[i]->pending) continue;
+      fcsph_status st = finish_step(b, (int)i);
+      if (st != FCSPH_OK && first == FCSPH_OK) first = st;
+    }
+  }
+  fcsph_status st = admit_queued(b);
+  if (st != FCSPH_OK) return st;
+  if (!b->queue.empty()) {
+    evict_idle(b);
+    if ((st = admit_queued(b)) != FCSPH_OK) return st;
+  }
+  bool any = false;
+  for (const Class* c : b->classes) any = any || c->occupied() > 0;
+  if (any) {
+    if (b->plan_gen != b->gen && (st = build_plan(b)) != FCSPH_OK) return st;
+    cudaError_t e = cudaSuccess;
+    for (Class* c : b->classes)
+      if ((e = cudaEventRecord(c->e0, b->tick_st)) != cudaSuccess) return bcuda(b, e, "fcsph_batch: event");
+    const int stall = b->stall_next ? (int)persist_items(b->plan) - 1 : -1;
+    b->stall_next = false;
+    e = persist_launch(b->plan, b->tick_st, b->cap_st, (long long)(b->wait_s * 1e9), stall);
+    if (e != cudaSuccess) return bcuda(b, e, "fcsph_batch: persistent launch");
+    for (Class* c : b->classes) {
+      if ((e = cudaEventRecord(c->e1, b->tick_st)) != cudaSuccess) return bcuda(b, e, "fcsph_batch: event");
+      c->pending = c->occupied() > 0;
+    }
+    if ((e = cudaEventRecord(b->tick_end, b->tick_st)) != cudaSuccess) return bcuda(b, e, "fcsph_batch: event");
+    b->tick_pending = true;
+  }
+  if (in_flight) *in_flight = pending_count();
+  return first;
 }
 
 }  // namespace
@@ -435,6 +533,11 @@ fcsph_status fcsph_batch_create(int prec, int slots, double mem_budget_bytes, in
 
 fcsph_status fcsph_batch_destroy(fcsph_batch* b) {
   if (!b) return FCSPH_EINVAL;
+  if (b->tick_st) cudaStreamSynchronize(b->tick_st);
+  persist_destroy(b->plan);
+  if (b->tick_end) cudaEventDestroy(b->tick_end);
+  if (b->tick_st) cudaStreamDestroy(b->tick_st);
+  if (b->cap_st) cudaStreamDestroy(b->cap_st);
   for (Class* c : b->classes) destroy_class(c);
   delete b;
   return FCSPH_OK;
@@ -446,6 +549,8 @@ fcsph_status fcsph_batch_add(fcsph_batch* b, const fcsph_request* req, long long
   if (req->kind < FCSPH_REQ_CAVITY || req->kind > FCSPH_REQ_CHANNEL3D || req->n < 16 || req->n > (d3 ? 256 : 4096) ||
       !(req->re > 0) || req->steps < 1)
     return bfail(b, FCSPH_EINVAL, "fcsph_batch_add: kind, n (16..4096; 3D 16..256), re > 0, steps >= 1");
+  if (d3 && b->persistent)
+    return bfail(b, FCSPH_EUNSUPPORTED, "fcsph_batch_add: the persistent step runs 2D requests only");
   const long long k = b->next_id++;
   Req r;
   r.r = *req;
@@ -472,8 +577,45 @@ fcsph_status fcsph_batch_remove(fcsph_batch* b, long long id) {
   return FCSPH_OK;  // a request in flight leaves its slot when its class's step is done
 }
 
+fcsph_status fcsph_batch_set_persistent(fcsph_batch* b, int on, double wait_limit_s) {
+  if (!b) return bfail(nullptr, FCSPH_EINVAL, "fcsph_batch_set_persistent: null batch");
+  if (!(wait_limit_s > 0) || wait_limit_s > 60)
+    return bfail(b, FCSPH_EINVAL, "fcsph_batch_set_persistent: wait limit must be in (0, 60] s");
+  if (b->tick_pending) return bfail(b, FCSPH_EINVAL, "fcsph_batch_set_persistent: a step is in flight");
+  for (const Class* c : b->classes)
+    if (c->pending) return bfail(b, FCSPH_EINVAL, "fcsph_batch_set_persistent: a step is in flight");
+  if (on) {
+    if (b->prec == FCSPH_F32)
+      return bfail(b, FCSPH_EUNSUPPORTED, "fcsph_batch_set_persistent: FP64 or FP32x2 batches only");
+    for (const Class* c : b->classes)
+      if (c->d3()) return bfail(b, FCSPH_EUNSUPPORTED, "fcsph_batch_set_persistent: a 3D class is open");
+    for (long long id : b->queue)
+      if (b->reqs[id].r.kind == FCSPH_REQ_CHANNEL3D)
+        return bfail(b, FCSPH_EUNSUPPORTED, "fcsph_batch_set_persistent: a 3D request is queued");
+    cudaError_t e = cudaSuccess;
+    if (!b->tick_st && (e = cudaStreamCreateWithFlags(&b->tick_st, cudaStreamNonBlocking)) != cudaSuccess)
+      return bcuda(b, e, "fcsph_batch_set_persistent: stream");
+    if (!b->cap_st && (e = cudaStreamCreateWithFlags(&b->cap_st, cudaStreamNonBlocking)) != cudaSuccess)
+      return bcuda(b, e, "fcsph_batch_set_persistent: stream");
+    if (!b->tick_end && (e = cudaEventCreateWithFlags(&b->tick_end, cudaEventDisableTiming)) != cudaSuccess)
+      return bcuda(b, e, "fcsph_batch_set_persistent: event");
+  }
+  b->persistent = on != 0;
+  b->wait_s = wait_limit_s;
+  b->plan_gen = -1;
+  return FCSPH_OK;
+}
+
+fcsph_status fcsph_batch_inject_stall(fcsph_batch* b) {
+  if (!b) return bfail(nullptr, FCSPH_EINVAL, "fcsph_batch_inject_stall: null batch");
+  if (!b->persistent) return bfail(b, FCSPH_EINVAL, "fcsph_batch_inject_stall: persistent mode only");
+  b->stall_next = true;
+  return FCSPH_OK;
+}
+
 fcsph_status fcsph_batch_run(fcsph_batch* b, int block, int* in_flight) {
   if (!b) return FCSPH_EINVAL;
+  if (b->persistent) return run_persistent(b, block, in_flight);
   fcsph_status first = FCSPH_OK;
   for (size_t i = 0; i < b->classes.size(); ++i) {
     Class* c = b->classes[i];

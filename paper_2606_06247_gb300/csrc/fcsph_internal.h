@@ -165,6 +165,11 @@ struct StepDev {
   const double* dt_inst; // per-instance time step (device) or null
 };
 
+// A recording of isph_step passes (fcsph_kernels.cu) and a persistent
+// multi-class step built from such recordings.
+struct PersistRec;
+struct PersistPlan;
+
 struct fcsph_ctx {
   fcsph_grid grid;
   fcsph_fc fc;
@@ -183,6 +188,10 @@ struct fcsph_ctx {
   int row_threads = 32;         // CTA width of the row (and z) passes: 32, 64 or 128
   int col_threads = 32;         // CTA width of the column passes
   int groups = 1;               // instance groups of the isph_step graph (parallel branches)
+  PersistRec* rec = nullptr;    // set: the step's launchers record pass descriptors instead of launching
+  int persist = 0;              // isph_step (use_graph = 1) as one persistent launch per step
+  PersistPlan* pplan = nullptr; // its plan, valid for pplan_key
+  std::vector<double> pplan_key;
   std::vector<cudaStream_t> grp_streams;  // one capture stream per group
   std::vector<cudaEvent_t> grp_events;    // fork event + one join event per group
   std::vector<double> hE[2];    // host copies
@@ -258,3 +267,20 @@ cudaError_t launch_resid_norm(fcsph_ctx* c, const double* r, const double* b, do
 cudaError_t launch_axpy(fcsph_ctx* c, double* y, const double* x, const float* xf, int n, double a);
 cudaError_t launch_sub(fcsph_ctx* c, double* r, const double* b, const double* lb, int n);
 cudaError_t launch_narrow(fcsph_ctx* c, float* y, const double* x, int n);
+
+// Persistent multi-class step (fcsph_kernels.cu).  persist_add_class returns
+// a recording owned by the plan; record_isph_step (fcsph_api.cpp) records one
+// step of a context into it; persist_finalize builds the work list on the
+// device; persist_launch enqueues one launch on st (cap: an idle stream for
+// the graph capture); persist_status reads and clears the status word (bit 1:
+// a dependency wait ran out).
+PersistPlan* persist_create(int prec);
+void persist_destroy(PersistPlan* p);
+PersistRec* persist_add_class(PersistPlan* p, int instances);
+cudaError_t persist_finalize(PersistPlan* p, std::string* err);
+cudaError_t persist_launch(PersistPlan* p, cudaStream_t st, cudaStream_t cap, long long wait_ns, int stall);
+cudaError_t persist_status(PersistPlan* p, cudaStream_t st, int* status);
+long long persist_items(const PersistPlan* p);
+int persist_grid(const PersistPlan* p);
+extern "C" fcsph_status record_isph_step(fcsph_ctx* c, const fcsph_state* s, const fcsph_step_params* prm,
+                                         PersistRec* rec, int with_fwd);

@@ -17,6 +17,7 @@
 //   A_k = (Z_k + conj Z_{-k}) / 2,  B_k = (Z_k - conj Z_{-k}) / (2i).
 // Row kernels (x direction) handle Rr x lines of one instance; outputs are
 // formed and inverted one at a time.
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <type_traits>
@@ -205,7 +206,7 @@ __device__ void col_store_spectrum(const typename CT<T>::t* R, int Pp, int ls, c
 // conj(A_k) + i conj(B_k); DC and Nyquist keep only the real parts.
 template <typename T>
 __device__ void col_gather_hermitian(typename CT<T>::t* lines, int Pp, int ls, const GridDev& g, int i0,
-                                     const typename CT<T>::t* __restrict__ spec, size_t fstride, int nout, int n) {
+                                     const typename CT<T>::t* spec, size_t fstride, int nout, int n) {
   typedef typename CT<T>::t V;
   const int hy = g.hy;
   for (int o = 0; o < nout; ++o)
@@ -238,7 +239,7 @@ __device__ void col_gather_hermitian(typename CT<T>::t* lines, int Pp, int ls, c
 // Packed DCT-I coefficient pairs (real parts of spec rows l < ny) into lines.
 template <typename T>
 __device__ void col_gather_dct(typename CT<T>::t* lines, int Pp, int ls, const GridDev& g, int i0,
-                               const typename CT<T>::t* __restrict__ spec) {
+                               const typename CT<T>::t* spec) {
   typedef typename CT<T>::t V;
   const int ny = g.ny, M = 2 * (ny - 1);
   for (int p = 0; p < Pp; ++p) {
@@ -257,19 +258,18 @@ __device__ void col_gather_dct(typename CT<T>::t* lines, int Pp, int ls, const G
 
 // ---------------------------------------------------------------------------
 // Column forward: load nf real fields, FC (or DCT) + FFT, store spectra.
-template <typename T, typename U, int NT>
-__global__ void __launch_bounds__(NT, MinCtas<T, NT>::v) k_col_fwd(GridDev g, const U* __restrict__ f0, const U* __restrict__ f1, const U* __restrict__ f2,
-                                                         const typename FcTab<T>::t* __restrict__ E, const __grid_constant__ FftPlan P,
-                                                      const typename CT<T>::t* __restrict__ pool, int dct,
-                                                      typename CT<T>::t* __restrict__ spec, size_t fstride,
-                                                      size_t bstride, int Pp, int ls) {
+template <typename T, typename U>
+__device__ __forceinline__ void col_fwd_body(const GridDev& g, const U* f0, const U* f1, const U* f2,
+                                             const typename FcTab<T>::t* E, const FftPlan& P,
+                                             const typename CT<T>::t* pool, int dct, typename CT<T>::t* spec,
+                                             size_t fstride, size_t bstride, int Pp, int ls, int bx, int by, int bz) {
   typedef typename CT<T>::t V;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* lines = reinterpret_cast<V*>(smem_raw);
   V* scratch = lines + (size_t)Pp * ls;
-  const int b = blockIdx.z + g.b0, f = blockIdx.y;
+  const int b = bz + g.b0, f = by;
   if (inactive(g, b)) return;
-  const int i0 = blockIdx.x * 2 * Pp;
+  const int i0 = bx * 2 * Pp;
   const U* src = f == 0 ? f0 : (f == 1 ? f1 : f2);
   const int W = 2 * Pp;
   const int ny = g.ny;
@@ -282,6 +282,15 @@ __global__ void __launch_bounds__(NT, MinCtas<T, NT>::v) k_col_fwd(GridDev g, co
   }
   __syncthreads();
   col_forward_store<T>(lines, scratch, Pp, ls, g, i0, E, P, pool, dct, spec + b * bstride + f * fstride);
+}
+
+template <typename T, typename U, int NT>
+__global__ void __launch_bounds__(NT, MinCtas<T, NT>::v) k_col_fwd(GridDev g, const U* __restrict__ f0, const U* __restrict__ f1, const U* __restrict__ f2,
+                                                         const typename FcTab<T>::t* __restrict__ E, const __grid_constant__ FftPlan P,
+                                                      const typename CT<T>::t* __restrict__ pool, int dct,
+                                                      typename CT<T>::t* __restrict__ spec, size_t fstride,
+                                                      size_t bstride, int Pp, int ls) {
+  col_fwd_body<T, U>(g, f0, f1, f2, E, P, pool, dct, spec, fstride, bstride, Pp, ls, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 // ---------------------------------------------------------------------------
@@ -349,22 +358,20 @@ template <typename T> __device__ __forceinline__ T kernel_poly(int family, T s) 
 // Shared memory: the nin input lines and their scratch (2 nin Rr lines; one
 // half holds the spectra, the other serves the outputs), plus Rr lines when
 // nin = 1.
-template <typename T, int NT>
-__global__ void __launch_bounds__(NT, MinCtas<T, NT>::v) k_row_sym(GridDev g, const typename CT<T>::t* __restrict__ sp_in,
-                                                         typename CT<T>::t* __restrict__ sp_out, size_t fstride_in,
-                                                         size_t bstride_in, size_t fstride_out, size_t bstride_out,
-                                                         const __grid_constant__ RowOps ops,
-                                                         const typename FcTab<T>::t* __restrict__ E,
-                                                         const __grid_constant__ FftPlan P, const typename CT<T>::t* __restrict__ pool,
-                                                         const T* __restrict__ Wt, double scale, int Rr, int ls) {
+template <typename T>
+__device__ __forceinline__ void row_sym_body(const GridDev& g, const typename CT<T>::t* sp_in, typename CT<T>::t* sp_out,
+                                             size_t fstride_in, size_t bstride_in, size_t fstride_out,
+                                             size_t bstride_out, const RowOps& ops, const typename FcTab<T>::t* E,
+                                             const FftPlan& P, const typename CT<T>::t* pool, const T* Wt,
+                                             double scale, int Rr, int ls, int bx, int by) {
   typedef typename CT<T>::t V;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nin = ops.nin, nout = ops.nout;
   V* A = reinterpret_cast<V*>(smem_raw);
   V* B = A + (size_t)nin * Rr * ls;
-  const int b = blockIdx.y + g.b0;
+  const int b = by + g.b0;
   if (inactive(g, b)) return;
-  const int q0 = blockIdx.x * Rr;
+  const int q0 = bx * Rr;
   const int nx = g.nx, mx = g.mx, nz = g.nz;
   const int nq = g.hy * nz;
   for (int f = 0; f < nin; ++f)
@@ -423,6 +430,18 @@ __global__ void __launch_bounds__(NT, MinCtas<T, NT>::v) k_row_sym(GridDev g, co
     }
     __syncthreads();
   }
+}
+
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT, MinCtas<T, NT>::v) k_row_sym(GridDev g, const typename CT<T>::t* __restrict__ sp_in,
+                                                         typename CT<T>::t* __restrict__ sp_out, size_t fstride_in,
+                                                         size_t bstride_in, size_t fstride_out, size_t bstride_out,
+                                                         const __grid_constant__ RowOps ops,
+                                                         const typename FcTab<T>::t* __restrict__ E,
+                                                         const __grid_constant__ FftPlan P, const typename CT<T>::t* __restrict__ pool,
+                                                         const T* __restrict__ Wt, double scale, int Rr, int ls) {
+  row_sym_body<T>(g, sp_in, sp_out, fstride_in, bstride_in, fstride_out, bstride_out, ops, E, P, pool, Wt, scale, Rr, ls,
+                  blockIdx.x, blockIdx.y);
 }
 
 // Per-lane constants of the register row pass for one row: lane k1 owns the
@@ -760,18 +779,16 @@ __global__ void __launch_bounds__(NT, MinCtas<T, NT>::v) k_zlines(typename CT<T>
 // transform back, store.  3D: line q is the l = q / nz row at z index
 // kq = q % nz of the DFT-z-transformed coefficients, elements at stride nz,
 // and lam_z^2 joins the denominator.
-template <typename T, int NT>
-__global__ void __launch_bounds__(NT, MinCtas<T, NT>::v) k_row_ppe(GridDev g, typename CT<T>::t* __restrict__ spec,
-                                                      size_t bstride, const __grid_constant__ FftPlan P,
-                                                      const typename CT<T>::t* __restrict__ pool, int apply, int Rr,
-                                                      int ls) {
+template <typename T>
+__device__ __forceinline__ void row_ppe_body(const GridDev& g, typename CT<T>::t* spec, size_t bstride, const FftPlan& P,
+                                             const typename CT<T>::t* pool, int apply, int Rr, int ls, int bx, int by) {
   typedef typename CT<T>::t V;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* A = reinterpret_cast<V*>(smem_raw);
   V* B = A + (size_t)Rr * ls;
-  const int b = blockIdx.y + g.b0;
+  const int b = by + g.b0;
   if (inactive(g, b)) return;
-  const int q0 = blockIdx.x * Rr;
+  const int q0 = bx * Rr;
   const int nx = g.nx, ny = g.ny, nz = g.nz;
   const int nq = ny * nz;
   const int n = P.base.n;  // nx or 2(nx-1)
@@ -828,6 +845,14 @@ __global__ void __launch_bounds__(NT, MinCtas<T, NT>::v) k_row_ppe(GridDev g, ty
     const V* Yl = Y + (size_t)r * ls;
     for (int i = threadIdx.x; i < nx; i += blockDim.x) S[(size_t)i * nz] = Yl[i];
   }
+}
+
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT, MinCtas<T, NT>::v) k_row_ppe(GridDev g, typename CT<T>::t* __restrict__ spec,
+                                                      size_t bstride, const __grid_constant__ FftPlan P,
+                                                      const typename CT<T>::t* __restrict__ pool, int apply, int Rr,
+                                                      int ls) {
+  row_ppe_body<T>(g, spec, bstride, P, pool, apply, Rr, ls, blockIdx.x, blockIdx.y);
 }
 
 // ---------------------------------------------------------------------------
@@ -893,21 +918,19 @@ __device__ void prefetch_field_cols(const GridDev& g, int b, int i0, int Pp, con
 // .x / .y): the momentum terms accumulate there (u.grad + nu lap per
 // component), the other epilogues leave the new field there.  The fused
 // forward then transforms acc[f] (f < fwd_nf) with Z and S as its lines.
-template <typename T, int NT>
-__global__ void __launch_bounds__(NT, MinCtas<T, NT>::v) k_col_inv(GridDev g, const typename CT<T>::t* __restrict__ spec,
-                                                         size_t fstride, size_t bstride, int nout, int nacc,
-                                                         const __grid_constant__ FftPlan P,
-                                                         const typename CT<T>::t* __restrict__ pool,
-                                                         const __grid_constant__ EpiArgs ea, int Pp, int ls,
-                                                         const int EPI) {
+template <typename T>
+__device__ __forceinline__ void col_inv_body(const GridDev& g, const typename CT<T>::t* spec, size_t fstride,
+                                             size_t bstride, int nout, int nacc, const FftPlan& P,
+                                             const typename CT<T>::t* pool, const EpiArgs& ea, int Pp, int ls,
+                                             const int EPI, int bx, int by) {
   typedef typename CT<T>::t V;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* Z = reinterpret_cast<V*>(smem_raw);
   V* S = Z + (size_t)Pp * ls;
   double2* acc = reinterpret_cast<double2*>(S + (size_t)Pp * ls);
-  const int b = blockIdx.y + g.b0;
+  const int b = by + g.b0;
   if (inactive(g, b)) return;
-  const int i0 = blockIdx.x * 2 * Pp;
+  const int i0 = bx * 2 * Pp;
   const int ny = g.ny;
   const bool ppe = (EPI == EPI_PPE_SOLVE || EPI == EPI_PPE_RESID || EPI == EPI_PPE_ADD);
   for (int o = 0; o < nout; ++o) {
@@ -1031,6 +1054,160 @@ __global__ void __launch_bounds__(NT, MinCtas<T, NT>::v) k_col_inv(GridDev g, co
     col_forward_store<T>(Z, S, Pp, ls, g, i0, reinterpret_cast<const typename FcTab<T>::t*>(ea.fwdE), ea.fwdP, pool,
                          ea.fwd_dct, reinterpret_cast<V*>(ea.fwd_spec) + b * ea.fwd_bstride + f * ea.fwd_fstride);
     __syncthreads();
+  }
+}
+
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT, MinCtas<T, NT>::v) k_col_inv(GridDev g, const typename CT<T>::t* __restrict__ spec,
+                                                         size_t fstride, size_t bstride, int nout, int nacc,
+                                                         const __grid_constant__ FftPlan P,
+                                                         const typename CT<T>::t* __restrict__ pool,
+                                                         const __grid_constant__ EpiArgs ea, int Pp, int ls,
+                                                         const int EPI) {
+  col_inv_body<T>(g, spec, fstride, bstride, nout, nacc, P, pool, ea, Pp, ls, EPI, blockIdx.x, blockIdx.y);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent step of several size classes in one launch.  Every pass of one
+// RK3 step of every class is recorded as a descriptor (the arguments its
+// launch would get); a work item is one CTA's share of one pass for one
+// instance: (descriptor, tile x, tile y, instance).  Items are listed pass by
+// pass (pass index p of every class, then p + 1, ...), and the CTAs of one
+// launch take them in that order from an atomic counter.  Item (c, b, p)
+// waits until every tile of pass p - 1 of the same instance has finished
+// (a per-(class, instance, pass) counter), so the classes' passes and their
+// instances interleave freely.  No deadlock is possible: an item only waits
+// for items taken before it, and the oldest unfinished item waits for nothing.
+// Waits are bounded (time and spin count); one that runs out sets bit 1 of
+// the plan's status word, and from then on every item is skipped (and
+// counted) so the launch drains at once.
+enum { PK_COL_FWD = 1, PK_ROW_SYM = 2, PK_COL_INV = 3, PK_ROW_PPE = 4 };
+
+struct PassDesc {
+  int kind;
+  int gx, gy, gz;  // the grid the pass's own launch would have
+  size_t smem;
+  int Pp, Rr, ls;
+  GridDev g;
+  FftPlan P;
+  const void* pool;
+  const void* E;
+  // column forward / column inverse
+  const void* f[3];
+  int dct;
+  void* spec;
+  size_t fstride, bstride;
+  // row passes
+  const void* sp_in;
+  void* sp_out;
+  size_t fs_in, bs_in, fs_out, bs_out;
+  RowOps ops;
+  const void* W;
+  double scale;
+  int apply;
+  // column inverse
+  int nout, nacc, epi;
+  EpiArgs ea;
+};
+
+struct WorkItem {
+  int desc, bx, by, b;
+  int dep;   // counter the item waits on (-1: none)
+  int need;  // value that counter must reach
+  int self;  // counter the item increments when done
+};
+
+constexpr int kPersistTimeout = 2;          // status bit: a dependency wait ran out
+constexpr long long kPersistMaxSpins = 1ll << 26;
+
+__device__ __forceinline__ long long global_ns() {
+  long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// One function per pass kind, each compiled (and register-allocated) on its
+// own rather than all four inlined into the persistent loop.
+template <typename T> __device__ __noinline__ void item_col_fwd(const PassDesc& d, int bx, int by, int b) {
+  typedef typename CT<T>::t V;
+  col_fwd_body<T, double>(d.g, (const double*)d.f[0], (const double*)d.f[1], (const double*)d.f[2],
+                          (const typename FcTab<T>::t*)d.E, d.P, (const V*)d.pool, d.dct, (V*)d.spec, d.fstride,
+                          d.bstride, d.Pp, d.ls, bx, by, b);
+}
+template <typename T> __device__ __noinline__ void item_row_sym(const PassDesc& d, int bx, int b) {
+  typedef typename CT<T>::t V;
+  row_sym_body<T>(d.g, (const V*)d.sp_in, (V*)d.sp_out, d.fs_in, d.bs_in, d.fs_out, d.bs_out, d.ops,
+                  (const typename FcTab<T>::t*)d.E, d.P, (const V*)d.pool, (const T*)d.W, d.scale, d.Rr, d.ls, bx, b);
+}
+template <typename T> __device__ __noinline__ void item_col_inv(const PassDesc& d, int bx, int b) {
+  typedef typename CT<T>::t V;
+  col_inv_body<T>(d.g, (const V*)d.spec, d.fstride, d.bstride, d.nout, d.nacc, d.P, (const V*)d.pool, d.ea, d.Pp, d.ls,
+                  d.epi, bx, b);
+}
+template <typename T> __device__ __noinline__ void item_row_ppe(const PassDesc& d, int bx, int b) {
+  typedef typename CT<T>::t V;
+  row_ppe_body<T>(d.g, (V*)d.spec, d.bstride, d.P, (const V*)d.pool, d.apply, d.Rr, d.ls, bx, b);
+}
+
+template <typename T>
+__device__ __forceinline__ void run_item(const PassDesc& d, int bx, int by, int b) {
+  switch (d.kind) {
+    case PK_COL_FWD: item_col_fwd<T>(d, bx, by, b); break;
+    case PK_ROW_SYM: item_row_sym<T>(d, bx, b); break;
+    case PK_COL_INV: item_col_inv<T>(d, bx, b); break;
+    case PK_ROW_PPE: item_row_ppe<T>(d, bx, b); break;
+    default: break;
+  }
+}
+
+// stall >= 0: item `stall` waits for a count that never comes (a test of the
+// bounded wait).
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT, MinCtas<T, NT>::v) k_persist(const PassDesc* descs, const WorkItem* items,
+                                                                  int n_items, unsigned* counters, unsigned* next,
+                                                                  int* status, long long wait_ns, int stall) {
+  __shared__ int s_idx, s_run;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const int idx = (int)atomicAdd(next, 1u);
+      int run = 1;
+      if (idx < n_items) {
+        const WorkItem it = items[idx];
+        if (it.dep >= 0) {
+          const unsigned need = idx == stall ? 0xffffffffu : (unsigned)it.need;
+          const unsigned* cnt = counters + it.dep;
+          const long long t0 = global_ns();
+          for (long long spin = 0;; ++spin) {
+            if (ld_acquire_gpu(cnt) >= need) break;
+            if ((*(volatile int*)status & kPersistTimeout) || spin > kPersistMaxSpins || global_ns() - t0 > wait_ns) {
+              atomicOr(status, kPersistTimeout);
+              run = 0;
+              break;
+            }
+            __nanosleep(100);
+          }
+        }
+        if (*(volatile int*)status & kPersistTimeout) run = 0;
+        __threadfence();
+      }
+      s_idx = idx;
+      s_run = run;
+    }
+    __syncthreads();
+    const int idx = s_idx, run = s_run;
+    if (idx >= n_items) return;
+    __threadfence();  // the dependency's writes before any load of this item
+    const WorkItem& it = items[idx];
+    if (run) run_item<T>(descs[it.desc], it.bx, it.by, it.b);
+    __threadfence();  // this item's writes before its count
+    __syncthreads();
+    if (threadIdx.x == 0 && it.self >= 0) atomicAdd(counters + it.self, 1u);
   }
 }
 
@@ -1294,6 +1471,32 @@ int col_ls(const fcsph_ctx* c) {
 // ===========================================================================
 // Launchers
 
+// Recording (fcsph_ctx::rec set): a pass of isph_step is appended to the
+// recording as a descriptor instead of being launched.  FP64 and FP32x2 only
+// (the persistent kernel's types).
+struct PersistRec {
+  std::vector<PassDesc> descs;
+};
+
+template <typename T> cudaError_t rec_push(fcsph_ctx* c, PassDesc& d) {
+  if (!std::is_same<T, double>::value && !std::is_same<T, ff>::value) return cudaErrorNotSupported;
+  d.pool = PoolOf<T>::get(c);
+  c->rec->descs.push_back(d);
+  return cudaSuccess;
+}
+
+static PassDesc new_desc(const fcsph_ctx* c, int kind, dim3 grid, size_t smem) {
+  PassDesc d;
+  memset(&d, 0, sizeof(d));
+  d.kind = kind;
+  d.gx = (int)grid.x;
+  d.gy = (int)grid.y;
+  d.gz = (int)grid.z;
+  d.smem = smem;
+  d.g = c->gd;
+  return d;
+}
+
 cudaError_t init_kernel_attributes() {
   cudaError_t e = cudaSuccess;
 #define FCSPH_RAISE(K)                           \
@@ -1315,6 +1518,18 @@ cudaError_t init_kernel_attributes() {
   FCSPH_RAISE((k_row_sym_w<8>))
   FCSPH_RAISE((k_row_sym_w<16>))
   FCSPH_RAISE((k_row_sym_w<32>))
+  // the persistent kernel holds two static shared words besides its dynamic
+  // shared memory
+  for (int nt : {32, 64, 128}) {
+    e = with_width(nt, [](auto w) {
+      constexpr int NT = decltype(w)::value;
+      const int lim = (int)kSmemMax - 64;
+      cudaError_t r = cudaFuncSetAttribute(k_persist<double, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+      if (r != cudaSuccess) return r;
+      return cudaFuncSetAttribute(k_persist<ff, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    });
+    if (e != cudaSuccess) return e;
+  }
   for (int nt : {32, 64, 128}) {
     e = with_width(nt, [](auto w) {
       constexpr int NT = decltype(w)::value;
@@ -1452,6 +1667,20 @@ static cudaError_t col_fwd_t(fcsph_ctx* c, int prec, int nf, const void* const* 
   dim3 grid((g.ncol + 2 * Pp - 1) / (2 * Pp), nf, g.nb);
   const size_t fstride = (size_t)g.rows * g.ncol;
   const size_t bstride = (dct ? 1 : spec_in_fields(c)) * fstride;
+  if (c->rec) {
+    if (!std::is_same<U, double>::value) return cudaErrorNotSupported;
+    PassDesc d = new_desc(c, PK_COL_FWD, grid, smem);
+    d.Pp = Pp;
+    d.ls = ls;
+    d.P = P;
+    d.E = E;
+    for (int k = 0; k < 3; ++k) d.f[k] = fields[k < nf ? k : 0];
+    d.dct = dct;
+    d.spec = spec;
+    d.fstride = fstride;
+    d.bstride = bstride;
+    return rec_push<T>(c, d);
+  }
   ProfScope ps(c, FCSPH_PROF_COL_FWD);
   return with_width(c->col_threads, [&](auto w) {
     constexpr int NT = decltype(w)::value;
@@ -1532,6 +1761,23 @@ static cudaError_t row_sym_t(fcsph_ctx* c, int prec, const void* sp_in, void* sp
   const auto* E = static_cast<const typename FcTab<T>::t*>(fc_table(c, prec, bc));
   const size_t fs = (size_t)g.rows * g.ncol;
   dim3 grid((g.hy * g.nz + Rr - 1) / Rr, g.nb);
+  if (c->rec) {
+    PassDesc d = new_desc(c, PK_ROW_SYM, grid, smem);
+    d.Rr = Rr;
+    d.ls = ls;
+    d.P = c->plan_x;
+    d.E = E;
+    d.sp_in = sp_in;
+    d.sp_out = sp_out;
+    d.fs_in = fs;
+    d.bs_in = spec_in_fields(c) * fs;
+    d.fs_out = fs;
+    d.bs_out = spec_out_fields(c) * fs;
+    d.ops = ops;
+    d.W = c->dW;
+    d.scale = scale;
+    return rec_push<T>(c, d);
+  }
   ProfScope ps(c, kind);
   return with_width(c->row_threads, [&](auto w) {
     constexpr int NT = decltype(w)::value;
@@ -1670,11 +1916,25 @@ static cudaError_t col_inv_common(fcsph_ctx* c, int epi, const void* spec, int n
   if (epi < EPI_OUT || epi > EPI_PPE_ADD) return cudaErrorInvalidValue;
   if (ea.fwd_nf > 3 || (epi == EPI_MOM && nout != ea.fwd_nf * ea.mom_terms)) return cudaErrorInvalidValue;
   ea.status = c->dstatus;
+  cudaError_t e = check_smem(smem);
+  if (e != cudaSuccess) return e;
+  if (c->rec) {
+    PassDesc d = new_desc(c, PK_COL_INV, grid, smem);
+    d.Pp = Pp;
+    d.ls = ls;
+    d.P = P;
+    d.spec = const_cast<void*>(spec);
+    d.fstride = fs;
+    d.bstride = bs;
+    d.nout = nout;
+    d.nacc = nacc;
+    d.epi = epi;
+    d.ea = ea;
+    return rec_push<T>(c, d);
+  }
   static const int kinds[7] = {FCSPH_PROF_COL_OUT, FCSPH_PROF_COL_MOM, FCSPH_PROF_COL_DIV, FCSPH_PROF_COL_CORR,
                                FCSPH_PROF_COL_PPE, FCSPH_PROF_COL_PPE, FCSPH_PROF_COL_PPE};
   ProfScope ps(c, kinds[epi]);
-  cudaError_t e = check_smem(smem);
-  if (e != cudaSuccess) return e;
   return with_width(c->col_threads, [&](auto w) {
     constexpr int NT = decltype(w)::value;
     k_col_inv<T, NT><<<grid, NT, smem, c->stream>>>(g, (const typename CT<T>::t*)spec, fs, bs, nout, nacc, P, pool,
@@ -1719,6 +1979,16 @@ static cudaError_t row_ppe_t(fcsph_ctx* c, void* spec, int apply) {
   cudaError_t e = check_smem(smem);
   if (e != cudaSuccess) return e;
   dim3 grid((g.ny * g.nz + Rr - 1) / Rr, g.nb);
+  if (c->rec) {
+    PassDesc d = new_desc(c, PK_ROW_PPE, grid, smem);
+    d.Rr = Rr;
+    d.ls = ls;
+    d.P = c->plan_px;
+    d.spec = spec;
+    d.bstride = (size_t)g.rows * g.ncol;
+    d.apply = apply;
+    return rec_push<T>(c, d);
+  }
   ProfScope ps(c, FCSPH_PROF_ROW_PPE);
   return with_width(c->row_threads, [&](auto w) {
     constexpr int NT = decltype(w)::value;
@@ -1887,3 +2157,202 @@ cudaError_t launch_narrow(fcsph_ctx* c, float* y, const double* x, int n) {
   c->launches++;
   return cudaGetLastError();
 }
+
+// ===========================================================================
+// Persistent multi-class step (see k_persist)
+
+struct PersistPlan {
+  int prec = FCSPH_F32X2;
+  std::vector<PersistRec*> recs;     // one recording per class
+  std::vector<int> inst;             // instances per class
+  PassDesc* d_descs = nullptr;
+  WorkItem* d_items = nullptr;
+  unsigned* d_counters = nullptr;    // counters, then the item dispenser
+  int* d_status = nullptr;
+  int n_items = 0, n_counters = 0, grid = 0, threads = 32;
+  size_t smem = 0;
+  cudaGraphExec_t gexec = nullptr;
+  long long graph_wait_ns = -1;
+};
+
+PersistPlan* persist_create(int prec) {
+  PersistPlan* p = new PersistPlan();
+  p->prec = prec;
+  return p;
+}
+
+void persist_destroy(PersistPlan* p) {
+  if (!p) return;
+  for (PersistRec* r : p->recs) delete r;
+  if (p->gexec) cudaGraphExecDestroy(p->gexec);
+  cudaFree(p->d_descs);
+  cudaFree(p->d_items);
+  cudaFree(p->d_counters);
+  cudaFree(p->d_status);
+  delete p;
+}
+
+PersistRec* persist_add_class(PersistPlan* p, int instances) {
+  PersistRec* r = new PersistRec();
+  p->recs.push_back(r);
+  p->inst.push_back(instances);
+  return r;
+}
+
+// Tiles of descriptor d per instance, and the instance count of its grid.
+static int desc_tiles(const PassDesc& d) { return d.kind == PK_COL_FWD ? d.gx * d.gy : d.gx; }
+static int desc_insts(const PassDesc& d) { return d.kind == PK_COL_FWD ? d.gz : d.gy; }
+
+cudaError_t persist_finalize(PersistPlan* p, std::string* err) {
+  std::vector<PassDesc> descs;
+  std::vector<int> first(p->recs.size()), npass(p->recs.size()), cbase(p->recs.size());
+  int maxp = 0, nc = 0;
+  for (size_t c = 0; c < p->recs.size(); ++c) {
+    first[c] = (int)descs.size();
+    npass[c] = (int)p->recs[c]->descs.size();
+    cbase[c] = nc;
+    for (const PassDesc& d : p->recs[c]->descs) {
+      if (desc_insts(d) != p->inst[c]) {
+        *err = "persistent plan: a pass does not cover the class's instances";
+        return cudaErrorInvalidValue;
+      }
+      descs.push_back(d);
+      if (d.smem > p->smem) p->smem = d.smem;
+    }
+    nc += p->inst[c] * npass[c];
+    if (npass[c] > maxp) maxp = npass[c];
+  }
+  // within a pass, the classes with the longest lines (most work per item)
+  // come first, so that the short items of small classes fill the end of it
+  std::vector<size_t> order(p->recs.size());
+  for (size_t c = 0; c < order.size(); ++c) order[c] = c;
+  auto weight = [&](size_t c) { return npass[c] ? descs[first[c]].g.my + descs[first[c]].g.mx : 0; };
+  std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b2) { return weight(a) > weight(b2); });
+  std::vector<WorkItem> items;
+  for (int ps = 0; ps < maxp; ++ps)
+    for (size_t c : order) {
+      if (ps >= npass[c]) continue;
+      const int di = first[c] + ps;
+      const PassDesc& d = descs[di];
+      const int prev_tiles = ps > 0 ? desc_tiles(descs[di - 1]) : 0;
+      for (int b = 0; b < p->inst[c]; ++b) {
+        const int self = cbase[c] + b * npass[c] + ps;
+        const int ny = d.kind == PK_COL_FWD ? d.gy : 1;
+        for (int by = 0; by < ny; ++by)
+          for (int bx = 0; bx < d.gx; ++bx) {
+            WorkItem it;
+            it.desc = di;
+            it.bx = bx;
+            it.by = by;
+            it.b = b;
+            it.dep = ps > 0 ? self - 1 : -1;
+            it.need = prev_tiles;
+            it.self = self;
+            items.push_back(it);
+          }
+      }
+    }
+  if (items.empty() || p->smem + 64 > kSmemMax) {  // 64: the kernel's own static shared words
+    *err = items.empty() ? "persistent plan: nothing to run" : "persistent plan: a pass exceeds shared memory";
+    return cudaErrorInvalidValue;
+  }
+  p->n_items = (int)items.size();
+  p->n_counters = nc;
+  cudaError_t e;
+  if ((e = cudaMalloc(&p->d_descs, descs.size() * sizeof(PassDesc))) != cudaSuccess ||
+      (e = cudaMalloc(&p->d_items, items.size() * sizeof(WorkItem))) != cudaSuccess ||
+      (e = cudaMalloc(&p->d_counters, (size_t)(nc + 1) * sizeof(unsigned))) != cudaSuccess ||
+      (e = cudaMalloc(&p->d_status, sizeof(int))) != cudaSuccess) {
+    *err = "persistent plan: device memory";
+    return e;
+  }
+  if ((e = cudaMemcpy(p->d_descs, descs.data(), descs.size() * sizeof(PassDesc), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(p->d_items, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemset(p->d_status, 0, sizeof(int))) != cudaSuccess) {
+    *err = "persistent plan: upload";
+    return e;
+  }
+  int dev = 0, sms = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+      (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+    return e;
+  // CTA width: the one with the most resident warps per SM (the narrowest on
+  // a tie): one warp per CTA unless shared memory (the largest pass of any
+  // class) caps the CTAs an SM holds
+  int best_warps = 0;
+  for (int nt : {32, 64, 128}) {
+    int occ = 0;
+    e = with_width(nt, [&](auto w) {
+      constexpr int NT = decltype(w)::value;
+      return p->prec == FCSPH_F64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_persist<double, NT>, NT, p->smem)
+                                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_persist<ff, NT>, NT, p->smem);
+    });
+    if (e != cudaSuccess) return e;
+    if (occ * nt / 32 > best_warps) {
+      best_warps = occ * nt / 32;
+      p->threads = nt;
+      p->grid = sms * occ;
+    }
+  }
+  if (best_warps == 0) {
+    *err = "persistent plan: no CTA fits an SM";
+    return cudaErrorInvalidValue;
+  }
+  return cudaSuccess;
+}
+
+static cudaError_t persist_enqueue(PersistPlan* p, cudaStream_t st, long long wait_ns, int stall) {
+  cudaError_t e = cudaMemsetAsync(p->d_counters, 0, (size_t)(p->n_counters + 1) * sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  unsigned* next = p->d_counters + p->n_counters;
+  return with_width(p->threads, [&](auto w) {
+    constexpr int NT = decltype(w)::value;
+    if (p->prec == FCSPH_F64)
+      k_persist<double, NT><<<p->grid, NT, p->smem, st>>>(p->d_descs, p->d_items, p->n_items, p->d_counters, next,
+                                                          p->d_status, wait_ns, stall);
+    else
+      k_persist<ff, NT><<<p->grid, NT, p->smem, st>>>(p->d_descs, p->d_items, p->n_items, p->d_counters, next,
+                                                      p->d_status, wait_ns, stall);
+    return cudaGetLastError();
+  });
+}
+
+// One persistent launch (counter reset + kernel).  Without a stall it replays
+// a CUDA graph of the two, captured on first use.
+cudaError_t persist_launch(PersistPlan* p, cudaStream_t st, cudaStream_t cap, long long wait_ns, int stall) {
+  if (stall >= 0) return persist_enqueue(p, st, wait_ns, stall);
+  if (!p->gexec || p->graph_wait_ns != wait_ns) {
+    if (p->gexec) {
+      cudaGraphExecDestroy(p->gexec);
+      p->gexec = nullptr;
+    }
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) return e;
+    cudaError_t le = persist_enqueue(p, cap, wait_ns, -1);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(cap, &g);
+    if (le != cudaSuccess || e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return le != cudaSuccess ? le : e;
+    }
+    e = cudaGraphInstantiate(&p->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return e;
+    p->graph_wait_ns = wait_ns;
+  }
+  return cudaGraphLaunch(p->gexec, st);
+}
+
+// Reads and clears the plan's status word (synchronises st).
+cudaError_t persist_status(PersistPlan* p, cudaStream_t st, int* status) {
+  *status = 0;
+  cudaError_t e = cudaMemcpyAsync(status, p->d_status, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess && *status) e = cudaMemsetAsync(p->d_status, 0, sizeof(int), st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return e;
+}
+
+long long persist_items(const PersistPlan* p) { return p ? p->n_items : 0; }
+int persist_grid(const PersistPlan* p) { return p ? p->grid : 0; }
+int persist_threads(const PersistPlan* p) { return p ? p->threads : 0; }

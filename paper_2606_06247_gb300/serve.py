@@ -300,12 +300,15 @@ class NativeServer:
     the batch and collects results and step latencies (same interface as
     Server)."""
 
-    def __init__(self, prec="f64", capacity=8, mem_budget=None, device=None, fc_cont=25):
+    def __init__(self, prec="f64", capacity=8, mem_budget=None, device=None, fc_cont=25, persistent=False):
+        """persistent: every tick steps all classes in one persistent launch (2D requests; FP64 / FP32x2)."""
         self.prec = prec
         self.capacity = capacity
         self.fc_cont = fc_cont
         self.batch = b.Batch(prec=prec, slots=capacity, mem_budget=0.0 if mem_budget is None else mem_budget,
                              n_cont=fc_cont)
+        if persistent:
+            self.batch.set_persistent(True)
         self.live = {}     # library id -> Request
         self.done = []
 

@@ -27,3 +27,28 @@ def test_create_and_add_validate_arguments():
     assert bt.poll(rid)["state"] == "cancelled"
     assert bt.info() == {"classes": 0, "queued": 1, "used_bytes": 0.0}
     bt.close()
+
+
+def test_persistent_mode_arguments_are_checked_before_any_device_call():
+    bt = b.Batch(prec="f32x2", slots=2, mem_budget=1e9)
+    for bad in (0.0, -1.0, 61.0):
+        with pytest.raises(b.FcsphError) as e:
+            bt.set_persistent(True, bad)
+        assert e.value.status == 1
+    with pytest.raises(b.FcsphError) as e:
+        bt.inject_stall()   # persistent mode only
+    assert e.value.status == 1
+    bt.add("channel3d", 32, 100.0, 5)
+    with pytest.raises(b.FcsphError) as e:
+        bt.set_persistent(True)   # a 3D request is queued
+    assert e.value.status == 6
+    bt.set_persistent(False)
+    bt.close()
+    f32 = b.Batch(prec="f32", slots=2, mem_budget=1e9)
+    with pytest.raises(b.FcsphError) as e:
+        f32.set_persistent(True)
+    assert e.value.status == 6
+    f32.close()
+    L = b.lib
+    assert L.fcsph_batch_set_persistent(None, 1, 1.0) == 1
+    assert L.fcsph_batch_inject_stall(None) == 1
