@@ -380,6 +380,17 @@ fcsph_status fcsph_get_step_groups(const fcsph_ctx* ctx, int* groups);
  * The recording is redone when isph_step's pointers or parameters change.
  * Engineering choice of this library; the paper has no counterpart. */
 fcsph_status fcsph_set_step_persistent(fcsph_ctx* ctx, int on);
+
+/* TMA staging (on = 1, the default) of the FP32 register column passes
+ * (extended wall-normal lengths 540 and 1050): the output pass gathers each
+ * column pair's half-spectrum rows with 2D tiled bulk copies
+ * (cp.async.bulk.tensor) one unit ahead of its inverse transform; on = 0
+ * keeps the per-thread loads.  Needs an even number of columns and no
+ * instance mask, else the per-thread path runs.  A copy whose wait runs out
+ * (bounded) makes fcsph_sync return FCSPH_ETIMEOUT.  Results are identical
+ * either way.  Engineering choice of this library; the paper has no
+ * counterpart. */
+fcsph_status fcsph_set_tma(fcsph_ctx* ctx, int on);
 fcsph_status fcsph_get_step_persistent(const fcsph_ctx* ctx, int* on);
 
 /* Autotuner: times `steps` isph_step calls with *prm for every tiling with

@@ -111,6 +111,7 @@ def _load():
         "fcsph_get_cta_threads": [P, ctypes.POINTER(I), ctypes.POINTER(I)],
         "fcsph_set_step_groups": [P, I],
         "fcsph_set_step_persistent": [P, I],
+        "fcsph_set_tma": [P, I],
         "fcsph_get_step_persistent": [P, ctypes.POINTER(I)],
         "fcsph_get_step_groups": [P, ctypes.POINTER(I)],
         "fcsph_autotune": [P, ctypes.POINTER(fcsph_step_params), I, ctypes.POINTER(D)],
@@ -332,6 +333,10 @@ class Context:
     def set_step_persistent(self, on=True):
         """fcsph_set_step_persistent: each graph step as one persistent launch (2D FP64 / FP32x2)."""
         self._ck(lib.fcsph_set_step_persistent(self.h, 1 if on else 0))
+
+    def set_tma(self, on=True):
+        """fcsph_set_tma: bulk-copy (TMA) staging of the FP32 register column passes."""
+        self._ck(lib.fcsph_set_tma(self.h, 1 if on else 0))
 
     def get_step_persistent(self):
         v = ctypes.c_int()

@@ -902,10 +902,20 @@ fcsph_status fcsph_sync(fcsph_ctx* c) {
   }
   int st = 0;
   FCSPH_CK(cudaMemcpy(&st, c->dstatus, sizeof(int), cudaMemcpyDeviceToHost), "status read");
+  if (st & 2) {
+    cudaMemset(c->dstatus, 0, sizeof(int));
+    return fail(c, FCSPH_ETIMEOUT, "a bulk-copy wait of a column pass ran out");
+  }
   if (st & 1) {
     cudaMemset(c->dstatus, 0, sizeof(int));
     return fail(c, FCSPH_ENONFINITE, "non-finite value in the time-step state");
   }
+  return FCSPH_OK;
+}
+
+fcsph_status fcsph_set_tma(fcsph_ctx* c, int on) {
+  if (!c) return fail(nullptr, FCSPH_EINVAL, "fcsph_set_tma: null context");
+  c->tma = on ? 1 : 0;
   return FCSPH_OK;
 }
 

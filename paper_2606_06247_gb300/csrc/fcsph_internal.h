@@ -190,6 +190,7 @@ struct fcsph_ctx {
   int groups = 1;               // instance groups of the isph_step graph (parallel branches)
   PersistRec* rec = nullptr;    // set: the step's launchers record pass descriptors instead of launching
   int persist = 0;              // isph_step (use_graph = 1) as one persistent launch per step
+  int tma = 1;                  // FP32 column passes stage their loads with bulk async copies (TMA)
   PersistPlan* pplan = nullptr; // its plan, valid for pplan_key
   std::vector<double> pplan_key;
   std::vector<cudaStream_t> grp_streams;  // one capture stream per group

@@ -25,6 +25,7 @@
 #include "fcsph_fft.cuh"
 #include "fcsph_warpfft.cuh"
 #include "fcsph_regfft.cuh"
+#include "fcsph_tma.cuh"
 #include "fcsph_internal.h"
 
 using namespace fcsph;
@@ -1289,6 +1290,94 @@ __global__ void __launch_bounds__(TeamFFT<N1, N2>::THREADS, TeamFFT<N1, N2>::MIN
   }
 }
 
+// k_col_out_r with TMA staging, persistent over (column pair, output) units:
+// while one unit's inverse transform runs, the next unit's half-spectrum rows
+// (the pair's two complex values of rows ky < hy, 16 bytes a row) arrive in
+// a staging buffer by 2D tiled bulk copies (nbox boxes of rows_box rows) on
+// one mbarrier, so the column pass no longer waits on its strided gather.
+// The wait for a copy is bounded: on a timeout the CTA sets bit 1 of the
+// status word, waits once more (bounded) for its copy in flight and returns.
+template <int N1, int N2>
+__global__ void __launch_bounds__(TeamFFT<N1, N2>::THREADS, TeamFFT<N1, N2>::MIN_CTAS) k_col_out_rt(
+    GridDev g, const __grid_constant__ CUtensorMap tmap, int rows_box, int nbox, int nfo, int nout,
+    const EpiArgs ea, const float2* __restrict__ roots, int npairs) {
+  typedef TeamFFT<N1, N2> TF;
+  constexpr int n = N1 * N2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  // bulk tensor copies land on 128-byte boundaries (the launch adds 128 bytes)
+  float4* stage = reinterpret_cast<float4*>(smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
+  float2* L = reinterpret_cast<float2*>(stage + (size_t)nbox * rows_box);
+  float2* xs = L + n;
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int s_ok;
+  const int t = threadIdx.x;
+  const int ny = g.ny, hy = g.hy;
+  const long long W = (long long)g.nb * npairs;
+  const uint32_t bytes = (uint32_t)(nbox * rows_box * 16);
+  auto pair_of = [&](long long k) { return (long long)blockIdx.x + (k / nout) * gridDim.x; };
+  auto issue = [&](long long k) {  // thread 0: copies of unit k into the stage
+    const long long w = pair_of(k);
+    const int o = (int)(k % nout);
+    const int b = g.b0 + (int)(w / npairs), i0 = (int)(w % npairs) * 2;
+    const int row0 = (b * nfo + o) * g.rows;
+    fence_proxy_async();
+    mbar_arrive_expect_tx(&bar, bytes);
+    for (int q = 0; q < nbox; ++q) tma_load_2d(stage + (size_t)q * rows_box, &tmap, 2 * i0, row0 + q * rows_box, &bar);
+  };
+  if (t == 0) {
+    mbar_init(&bar, 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  if (pair_of(0) >= W) return;
+  if (t == 0) issue(0);
+  for (long long k = 0; pair_of(k) < W; ++k) {
+    const long long w = pair_of(k);
+    const int o = (int)(k % nout);
+    const int b = g.b0 + (int)(w / npairs), i0 = (int)(w % npairs) * 2;
+    const uint32_t par = (uint32_t)(k & 1);
+    if (t == 0) s_ok = mbar_wait_bounded(&bar, par) ? 1 : 0;
+    __syncthreads();
+    if (!s_ok) {
+      if (t == 0) {
+        atomicOr(ea.status, 2);
+        mbar_wait_bounded(&bar, par);
+      }
+      return;
+    }
+    mbar_try_wait(&bar, par);  // every thread observes the completed phase
+    // Hermitian unpack: Z_k = A_k + i B_k, Z_{n-k} = conj(A_k) + i conj(B_k)
+    for (int kk = t; kk < hy; kk += blockDim.x) {
+      const float4 r = stage[kk];
+      if (kk == 0 || 2 * kk == n) {
+        L[kk] = make_float2(r.x, r.z);
+      } else {
+        L[kk] = make_float2(r.x - r.w, r.y + r.z);
+        L[n - kk] = make_float2(r.x + r.w, r.z - r.y);
+      }
+    }
+    __syncthreads();
+    if (t == 0 && pair_of(k + 1) < W) issue(k + 1);  // the stage is free again
+    float2 v[TF::NV];
+    if (t < N1) {
+#pragma unroll
+      for (int k2 = 0; k2 < N2; ++k2) v[k2] = L[t + N1 * k2];
+    }
+    TF::inv(v, xs, roots, t);
+    if (t < N2) {
+      float* out = reinterpret_cast<float*>(ea.outs[o]);
+#pragma unroll
+      for (int j = 0; j < N1; ++j) {
+        const int row = t + N2 * j;
+        if (row < ny) {
+          out[fidx(g, b, i0, row)] = v[j].x;
+          if (i0 + 1 < g.ncol) out[fidx(g, b, i0 + 1, row)] = v[j].y;
+        }
+      }
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // fc_extend (Eq. 30) as a standalone kernel: y continuation of every column,
 // then x continuation of every extended row (walled x).
@@ -1513,6 +1602,12 @@ cudaError_t init_kernel_attributes() {
   FCSPH_RAISE((k_col_fwd_r<30, 35>))
   FCSPH_RAISE((k_col_out_r<20, 27>))
   FCSPH_RAISE((k_col_out_r<30, 35>))
+  if ((e = cudaFuncSetAttribute(k_col_out_rt<20, 27>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax - 64)) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(k_col_out_rt<30, 35>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax - 64)) !=
+      cudaSuccess)
+    return e;
   FCSPH_RAISE((k_row_sym_w<2>))
   FCSPH_RAISE((k_row_sym_w<4>))
   FCSPH_RAISE((k_row_sym_w<8>))
@@ -1625,6 +1720,65 @@ static cudaError_t col_fwd_r(fcsph_ctx* c, int nf, const void* const* fields, in
   k_col_fwd_r<N1, N2><<<grid, TF::THREADS, smem, c->stream>>>(
       g, f0, (const float*)(nf > 1 ? fields[1] : fields[0]), (const float*)(nf > 2 ? fields[2] : fields[0]), E,
       c->pool32 + c->plan_y.base.tw, (float2*)spec, fstride, bstride);
+  c->launches++;
+  return cudaGetLastError();
+}
+
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+// The TMA column-output pass: needs an even number of columns (16-byte rows
+// of the tensor map and 16-byte aligned pair coordinates), a 16-byte aligned
+// spectrum buffer and no instance mask; returns cudaErrorNotSupported
+// otherwise (the caller then runs k_col_out_r).
+template <int N1, int N2>
+static cudaError_t col_out_rt(fcsph_ctx* c, const void* spec, int nout, EpiArgs& ea) {
+  typedef TeamFFT<N1, N2> TF;
+  const GridDev& g = c->gd;
+  EncodeTiledFn enc = encode_tiled();
+  if (!enc || g.ncol % 2 || ((uintptr_t)spec & 15) || g.active) return cudaErrorNotSupported;
+  const int nfo = spec_out_fields(c);
+  const int nbox = (g.hy + 255) / 256;
+  const int rows_box = ((g.hy + nbox - 1) / nbox + 7) / 8 * 8;
+  CUtensorMap map;
+  const cuuint64_t dims[2] = {(cuuint64_t)2 * g.ncol, (cuuint64_t)g.batch * nfo * g.rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)2 * g.ncol * sizeof(float)};
+  const cuuint32_t box[2] = {4, (cuuint32_t)rows_box};
+  const cuuint32_t es[2] = {1, 1};
+  if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(spec), dims, strides, box, es,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return cudaErrorNotSupported;
+  const size_t smem = 128 + (size_t)nbox * rows_box * 16 + ((size_t)N1 * N2 + TF::XCHG) * sizeof(float2);
+  cudaError_t e = check_smem(smem + 64);
+  if (e != cudaSuccess) return cudaErrorNotSupported;
+  int dev = 0, sms = 0, occ = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+      (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
+      (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_col_out_rt<N1, N2>, TF::THREADS, smem)) != cudaSuccess)
+    return e;
+  const int npairs = (g.ncol + 1) / 2;
+  const long long W = (long long)g.nb * npairs;
+  const long long grid = std::min<long long>(W, (long long)sms * (occ > 0 ? occ : 1));
+  ea.status = c->dstatus;
+  ProfScope ps(c, FCSPH_PROF_COL_OUT);
+  k_col_out_rt<N1, N2><<<(unsigned)grid, TF::THREADS, smem, c->stream>>>(g, map, rows_box, nbox, nfo, nout, ea,
+                                                                         c->pool32 + c->plan_y.base.tw, npairs);
   c->launches++;
   return cudaGetLastError();
 }
@@ -1961,9 +2115,14 @@ cudaError_t launch_col_out(fcsph_ctx* c, const void* spec, int nout, void* const
   for (int o = 0; o < nout; ++o) ea.outs[o] = outs[o];
   ea.out_double = c->prec.fft_prec != FCSPH_F32;
   if (!ea.out_double) {
+    cudaError_t e = cudaErrorNotSupported;
     switch (col_r_split(c)) {
-      case 20: return col_out_r<20, 27>(c, spec, nout, ea);
-      case 30: return col_out_r<30, 35>(c, spec, nout, ea);
+      case 20:
+        if (c->tma) e = col_out_rt<20, 27>(c, spec, nout, ea);
+        return e == cudaErrorNotSupported ? col_out_r<20, 27>(c, spec, nout, ea) : e;
+      case 30:
+        if (c->tma) e = col_out_rt<30, 35>(c, spec, nout, ea);
+        return e == cudaErrorNotSupported ? col_out_r<30, 35>(c, spec, nout, ea) : e;
       default: break;
     }
   }
