@@ -52,6 +52,10 @@ def parse():
     ap.add_argument("--refine", type=int, default=0)
     ap.add_argument("--tiling", default=None,
                     help="rows,pairs per CTA for the headline context instead of the autotuner (profiling runs)")
+    ap.add_argument("--cta-threads", default=None,
+                    help="with --tiling: row,column CTA widths of the headline context (profiling runs)")
+    ap.add_argument("--groups", type=int, default=None,
+                    help="with --tiling: instance groups of the step graph (profiling runs)")
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--workload", default="cavity", choices=["cavity", "uneven", "serve", "planes", "lines", "dipole", "channel3d"],
                     help="cavity: the 256^2 lid cavity (default); uneven: 64 solves of sizes 64^2..512^2 "
@@ -406,6 +410,10 @@ def run_ours(args):
     ctx = make(args.prec, args.refine if args.prec == "f32" else 0)
     if args.tiling:
         ctx.set_tiling(*[int(x) for x in args.tiling.split(",")])
+        if args.cta_threads:
+            ctx.set_cta_threads(*[int(x) for x in args.cta_threads.split(",")])
+        if args.groups:
+            ctx.set_step_groups(args.groups)
     else:
         ctx.autotune(steps=2, **prm)
     dtype_name = {"f64": "f64", "f32x2": "f32x2", "f32": "f32"}[args.prec]
@@ -590,7 +598,7 @@ def run_ours(args):
                                       "f32x2": "FP32-pair (double-float) FFT/symbols/FC sums, FP64 state",
                                       "f64": "FP64"}[args.prec],
                            tiling=list(ctx.get_tiling()), cta_threads=list(ctx.get_cta_threads()),
-                           step_groups=ctx.get_step_groups()),
+                           step_groups=ctx.get_step_groups(), step_persistent=ctx.get_step_persistent()),
             "latency_ms": {"p50": per_sorted[len(per_sorted) // 2], "p99": per_sorted[min(len(per_sorted) - 1, int(0.99 * len(per_sorted)))]},
             "roofline": roof,
             "kernels": kinds,
