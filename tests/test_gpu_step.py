@@ -83,10 +83,12 @@ def test_graph_replay_equals_eager_and_batch_equals_alone():
 
 @pytest.mark.gpu
 def test_mixed_precision_step_error_vs_fp64_oracle():
-    """Reports the FP32-transform path's error against the FP64 oracle.  Channel
-    (smooth wall data): asserted small.  Lid cavity: the impulsively started lid
-    makes the FC continuation ~4e3 times the data, which FP32 transforms cannot
-    resolve, so only a loose bound is asserted there."""
+    """The FP32-transform path's error against the FP64 oracle.  Channel (smooth
+    wall data): ~1e-4 relative L2, asserted below 1e-3 / 1e-2.  Lid cavity: the
+    tensor-product FC of the discontinuous lid corners reaches ~1e7 times the
+    data, which FP32 transforms cannot resolve: after 3 RK3 steps at 20^2 the
+    relative L2 is 0.12 (u) and 0.39 (v) on GB300, asserted below 0.3 and 0.8
+    (the FP32-pair path is the one at equal L2 there)."""
     b = binding()
     nx, ny = 24, 20
     u0, v0 = inputs.channel_initial(nx, ny, seed=1, sigma=1e-3)
@@ -107,7 +109,7 @@ def test_mixed_precision_step_error_vs_fp64_oracle():
                              **CAVITY)
     eu, ev = rel_l2(ug[0], uo), rel_l2(vg[0], vo)
     print(f"cavity mixed rel L2 vs FP64 oracle: u {eu:.2e} v {ev:.2e}")
-    assert np.isfinite(eu) and eu < 1.0
+    assert np.isfinite(eu) and eu < 0.3 and ev < 0.8
 
 
 # FP32-pair arithmetic rounds at about 2^-48, 32 times FP64's unit roundoff:
