@@ -81,7 +81,7 @@ template <typename V, bool INV> __device__ __forceinline__ V root(const V* __res
   return w;
 }
 
-__device__ __forceinline__ int fdiv(int x, const FastDiv& d) {
+__device__ __forceinline__ int fdiv(int x, const FastDiv d) {
   return (int)((__umulhi((unsigned)x, d.m) + (unsigned)x) >> d.l);
 }
 
@@ -356,7 +356,7 @@ template <typename V> struct StageFx {
 // last stage of an inverse transform computed as conj(DFT(conj x))).
 template <typename T, int R, bool INV>
 __device__ void stage_reg(const typename CT<T>::t* __restrict__ src, typename CT<T>::t* __restrict__ dst, int nl,
-                          int ls, int n, int Ns, const FastDiv& dnb, const FastDiv& dns,
+                          int ls, int n, int Ns, const FastDiv dnb, const FastDiv dns,
                           const typename CT<T>::t* __restrict__ tw, bool cin, bool cout,
                           const StageFx<typename CT<T>::t>& fx) {
   typedef typename CT<T>::t V;
@@ -429,7 +429,7 @@ __device__ void stage_reg(const typename CT<T>::t* __restrict__ src, typename CT
 // Large prime radix: one thread per output element.
 template <typename T, bool INV>
 __device__ void stage_big(const typename CT<T>::t* __restrict__ src, typename CT<T>::t* __restrict__ dst, int nl,
-                          int ls, int n, int Ns, int R, const FastDiv& dn, const typename CT<T>::t* __restrict__ tw,
+                          int ls, int n, int Ns, int R, const FastDiv dn, const typename CT<T>::t* __restrict__ tw,
                           bool cin, bool cout) {
   typedef typename CT<T>::t V;
   const int nb = n / R;
@@ -532,6 +532,9 @@ __device__ __noinline__ typename CT<T>::t* fft_any_rt(typename CT<T>::t* a, type
   const bool two = P.rd || P.bs;
   const Plan1& sp = two ? P.sub : P.base;
   const int m = sp.n;
+  // plan fields read inside loops, held in registers (the plan may live in
+  // global memory, where the loops' stores could alias it)
+  const FastDiv sdn = sp.dn, bdn = P.base.dn;
   const V* bh = pool + P.bhat;
   V* src = a;
   V* dst = b;
@@ -549,7 +552,7 @@ __device__ __noinline__ typename CT<T>::t* fft_any_rt(typename CT<T>::t* a, type
   } else if (P.rd) {
     const V* gi = pool + P.gidx;
     for (int t = threadIdx.x; t < nl * m; t += blockDim.x) {
-      const int line = fdiv(t, sp.dn);
+      const int line = fdiv(t, sdn);
       const int q = t - line * m;
       V v = a[(size_t)line * ls + pool_index(gi[q].x)];
       if (inv) v.y = -v.y;
@@ -566,7 +569,7 @@ __device__ __noinline__ typename CT<T>::t* fft_any_rt(typename CT<T>::t* a, type
   } else if (P.bs) {
     const V* ch = pool + P.chirp;
     for (int t = threadIdx.x; t < nl * m; t += blockDim.x) {
-      const int line = fdiv(t, sp.dn);
+      const int line = fdiv(t, sdn);
       const int j = t - line * m;
       V* x = a + (size_t)line * ls + j;
       if (j < n) {
@@ -602,7 +605,7 @@ __device__ __noinline__ typename CT<T>::t* fft_any_rt(typename CT<T>::t* a, type
     V* o = (r == src) ? dst : src;
     if (pass == 0 && two && !rfuse) {
       for (int t = threadIdx.x; t < nl * m; t += blockDim.x) {
-        const int line = fdiv(t, sp.dn);
+        const int line = fdiv(t, sdn);
         const int k = t - line * m;
         V* x = r + (size_t)line * ls + k;
         if (P.rd && k == 0) {  // A_0 = sum_{j>0} x_j, kept before the multiply overwrites it
@@ -624,7 +627,7 @@ __device__ __noinline__ typename CT<T>::t* fft_any_rt(typename CT<T>::t* a, type
     const V* si = pool + P.sidx;
     V* out = dst;
     for (int t = threadIdx.x; t < nl * m; t += blockDim.x) {
-      const int line = fdiv(t, sp.dn);
+      const int line = fdiv(t, sdn);
       const int q = t - line * m;
       const V* yl = r + (size_t)line * ls;
       V v;
@@ -645,7 +648,7 @@ __device__ __noinline__ typename CT<T>::t* fft_any_rt(typename CT<T>::t* a, type
   if (P.bs) {
     const V* ch = pool + P.chirp;
     for (int t = threadIdx.x; t < nl * n; t += blockDim.x) {
-      const int line = fdiv(t, P.base.dn);
+      const int line = fdiv(t, bdn);
       const int j = t - line * n;
       V* x = r + (size_t)line * ls + j;
       V z = *x;

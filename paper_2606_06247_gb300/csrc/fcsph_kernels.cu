@@ -1134,26 +1134,32 @@ __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
 }
 
 // One function per pass kind, each compiled (and register-allocated) on its
-// own rather than all four inlined into the persistent loop.
-template <typename T> __device__ __noinline__ void item_col_fwd(const PassDesc& d, int bx, int by, int b) {
+// own rather than all four inlined into the persistent loop.  The descriptor
+// is read-only for the whole launch and aliases nothing the pass writes
+// (__restrict__): its fields are loaded once, not again after every store.
+template <typename T> __device__ __noinline__ void item_col_fwd(const PassDesc& __restrict__ d, int bx, int by, int b) {
   typedef typename CT<T>::t V;
   col_fwd_body<T, double>(d.g, (const double*)d.f[0], (const double*)d.f[1], (const double*)d.f[2],
                           (const typename FcTab<T>::t*)d.E, d.P, (const V*)d.pool, d.dct, (V*)d.spec, d.fstride,
                           d.bstride, d.Pp, d.ls, bx, by, b);
 }
-template <typename T> __device__ __noinline__ void item_row_sym(const PassDesc& d, int bx, int b) {
+template <typename T> __device__ __noinline__ void item_row_sym(const PassDesc& __restrict__ d, int bx, int b) {
   typedef typename CT<T>::t V;
   row_sym_body<T>(d.g, (const V*)d.sp_in, (V*)d.sp_out, d.fs_in, d.bs_in, d.fs_out, d.bs_out, d.ops,
                   (const typename FcTab<T>::t*)d.E, d.P, (const V*)d.pool, (const T*)d.W, d.scale, d.Rr, d.ls, bx, b);
 }
-template <typename T> __device__ __noinline__ void item_col_inv(const PassDesc& d, int bx, int b) {
+template <typename T> __device__ __noinline__ void item_col_inv(const PassDesc& __restrict__ d, int bx, int b) {
   typedef typename CT<T>::t V;
   col_inv_body<T>(d.g, (const V*)d.spec, d.fstride, d.bstride, d.nout, d.nacc, d.P, (const V*)d.pool, d.ea, d.Pp, d.ls,
                   d.epi, bx, b);
 }
-template <typename T> __device__ __noinline__ void item_row_ppe(const PassDesc& d, int bx, int b) {
+template <typename T> __device__ __noinline__ void item_row_ppe(const PassDesc& __restrict__ d, int bx, int b) {
   typedef typename CT<T>::t V;
   row_ppe_body<T>(d.g, (V*)d.spec, d.bstride, d.P, (const V*)d.pool, d.apply, d.Rr, d.ls, bx, b);
+}
+
+__device__ __forceinline__ void red_release_gpu_add(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
 template <typename T>
@@ -1195,20 +1201,21 @@ __global__ void __launch_bounds__(NT, MinCtas<T, NT>::v) k_persist(const PassDes
           }
         }
         if (*(volatile int*)status & kPersistTimeout) run = 0;
-        __threadfence();
       }
       s_idx = idx;
       s_run = run;
     }
+    // thread 0's acquire of the dependency count, then the CTA barrier, orders
+    // the dependency's writes before every load of this item
     __syncthreads();
     const int idx = s_idx, run = s_run;
     if (idx >= n_items) return;
-    __threadfence();  // the dependency's writes before any load of this item
     const WorkItem& it = items[idx];
     if (run) run_item<T>(descs[it.desc], it.bx, it.by, it.b);
-    __threadfence();  // this item's writes before its count
+    // the barrier, then thread 0's release increment, orders every write of
+    // this item before its count
     __syncthreads();
-    if (threadIdx.x == 0 && it.self >= 0) atomicAdd(counters + it.self, 1u);
+    if (threadIdx.x == 0 && it.self >= 0) red_release_gpu_add(counters + it.self, 1u);
   }
 }
 
