@@ -391,6 +391,14 @@ fcsph_status fcsph_set_step_persistent(fcsph_ctx* ctx, int on);
  * either way.  Engineering choice of this library; the paper has no
  * counterpart. */
 fcsph_status fcsph_set_tma(fcsph_ctx* ctx, int on);
+
+/* Tracing (on = 1; default off): NVTX ranges ("fcsph <call>" around every
+ * call of this header that takes the context, "fcsph <pass>" around every
+ * kernel launch, named as the FCSPH_PROF_* kinds) for a profiler's timeline
+ * or for ncu --nvtx filters.  Host-side markers only: they cost nothing on
+ * the device, and nothing at all unless a tool is attached.  Engineering
+ * aid of this library; the paper has no counterpart. */
+fcsph_status fcsph_set_tracing(fcsph_ctx* ctx, int on);
 fcsph_status fcsph_get_step_persistent(const fcsph_ctx* ctx, int* on);
 
 /* Autotuner: times `steps` isph_step calls with *prm for every tiling with

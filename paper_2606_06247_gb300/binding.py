@@ -112,6 +112,7 @@ def _load():
         "fcsph_set_step_groups": [P, I],
         "fcsph_set_step_persistent": [P, I],
         "fcsph_set_tma": [P, I],
+        "fcsph_set_tracing": [P, I],
         "fcsph_get_step_persistent": [P, ctypes.POINTER(I)],
         "fcsph_get_step_groups": [P, ctypes.POINTER(I)],
         "fcsph_autotune": [P, ctypes.POINTER(fcsph_step_params), I, ctypes.POINTER(D)],
@@ -192,6 +193,29 @@ def fcsph_dft_noalloc(x, out, direction=-1, stream=None):
     _check(lib.fcsph_dft_noalloc(n, x.numel() // n if n else 0, direction, prec, _ptr(x), _ptr(out),
                                  _stream(stream)))
     return out
+
+
+def load_tune_cache(path):
+    """{key: launch shape} from the autotune cache file (empty if absent or unreadable)."""
+    import json
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return d if isinstance(d, dict) else {}
+    except (OSError, ValueError):
+        return {}
+
+
+def store_tune_cache(path, key, state):
+    """Adds or replaces one entry of the autotune cache file (written whole, through a temporary file)."""
+    import json
+    import os
+    d = load_tune_cache(path)
+    d[key] = state
+    tmp = f"{path}.tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump(d, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
 
 
 class Context:
@@ -334,6 +358,10 @@ class Context:
         """fcsph_set_step_persistent: each graph step as one persistent launch (2D FP64 / FP32x2)."""
         self._ck(lib.fcsph_set_step_persistent(self.h, 1 if on else 0))
 
+    def set_tracing(self, on=True):
+        """fcsph_set_tracing: NVTX ranges around every call and pass."""
+        self._ck(lib.fcsph_set_tracing(self.h, 1 if on else 0))
+
     def set_tma(self, on=True):
         """fcsph_set_tma: bulk-copy (TMA) staging of the FP32 register column passes."""
         self._ck(lib.fcsph_set_tma(self.h, 1 if on else 0))
@@ -343,13 +371,40 @@ class Context:
         self._ck(lib.fcsph_get_step_persistent(self.h, ctypes.byref(v)))
         return bool(v.value)
 
+    def tune_key(self, scheme="rk3", device_name=""):
+        """The autotune cache key of this context: grid, FC, kernel, precision, scheme and device."""
+        g, f, k, p = self.grid, self.fc, self.kernel, self.prec
+        return (f"{device_name}|{g.nx}x{g.ny}x{max(g.nz, 1)}|xw{g.x_walls}|b{g.batch}|fc{f.variant},{f.n_match},"
+                f"{f.n_cont},{f.poly_deg}|k{k.family},{k.h_over_dx}|p{p.fft_prec},{p.ppe_refine_iters}|{scheme}")
+
+    def tune_state(self):
+        """The launch shape the autotuner sets (tiling, CTA widths, step groups, persistent step)."""
+        return {"tiling": list(self.get_tiling()), "cta_threads": list(self.get_cta_threads()),
+                "groups": self.get_step_groups(), "persistent": self.get_step_persistent()}
+
+    def apply_tune_state(self, st):
+        self.set_tiling(*st["tiling"])
+        self.set_cta_threads(*st["cta_threads"])
+        self.set_step_groups(st["groups"])
+        self.set_step_persistent(st["persistent"])
+
     def autotune(self, steps=3, nu=1e-3, rho=1.0, dt=1e-3, force=(0.0, 0.0), u_bottom=0.0, u_top=0.0, scheme="rk3",
-                 use_graph=True, nu_inst=None, fx_inst=None):
-        """fcsph_autotune: keeps the fastest tiling, then CTA widths, then step groups; returns (row_lines,
-        col_pairs, ms per step)."""
+                 use_graph=True, nu_inst=None, fx_inst=None, cache=None, device_name=""):
+        """fcsph_autotune: keeps the fastest tiling, then CTA widths, then step groups, then (2D FP64 / FP32x2)
+        the persistent step; returns (row_lines, col_pairs, ms per step).  cache: path of a JSON file of launch
+        shapes by tune_key; a hit applies the stored shape without timing (ms None), a miss tunes and stores."""
+        key = self.tune_key(scheme, device_name)
+        if cache is not None:
+            hit = load_tune_cache(cache).get(key)
+            if hit is not None:
+                self.apply_tune_state(hit)
+                r, c = self.get_tiling()
+                return r, c, None
         prm = self._params(nu, rho, dt, force, u_bottom, u_top, scheme, use_graph, nu_inst, fx_inst)
         ms = ctypes.c_double()
         self._ck(lib.fcsph_autotune(self.h, ctypes.byref(prm), steps, ctypes.byref(ms)))
+        if cache is not None:
+            store_tune_cache(cache, key, self.tune_state())
         r, c = self.get_tiling()
         return r, c, ms.value
 

@@ -12,6 +12,8 @@
 
 #include "fcsph_internal.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 using namespace fcsph;
 
 namespace {
@@ -151,7 +153,16 @@ static size_t out_bstride(const fcsph_ctx* c) { return (c->gd.nz > 1 ? 12 : 6) *
 
 void set_global_error(const std::string& msg) { set_global_err(msg); }
 
+// NVTX range names of the pass kinds (FCSPH_PROF_*), for fcsph_set_tracing.
+static const char* const kPassNames[FCSPH_PROF_KINDS] = {
+    "fcsph col_fwd", "fcsph row_mom", "fcsph row_div", "fcsph row_grad", "fcsph row_op",  "fcsph col_mom",
+    "fcsph col_div", "fcsph col_corr", "fcsph col_out", "fcsph row_ppe", "fcsph col_ppe", "fcsph other"};
+
 ProfScope::ProfScope(fcsph_ctx* ctx, int k) : c(ctx), kind(k) {
+  if (c && c->trace_on && k >= 0 && k < FCSPH_PROF_KINDS) {
+    nvtxRangePushA(kPassNames[k]);
+    traced = true;
+  }
   if (!c || !c->prof_on) return;
   cudaEvent_t a;
   if (!c->ev_free.empty()) {
@@ -174,7 +185,19 @@ ProfScope::ProfScope(fcsph_ctx* ctx, int k) : c(ctx), kind(k) {
 
 ProfScope::~ProfScope() {
   if (b) cudaEventRecord(b, c->stream);
+  if (traced) nvtxRangePop();
 }
+
+// An NVTX range around one call of the C ABI when tracing is on.
+struct TraceRange {
+  bool on;
+  TraceRange(const fcsph_ctx* c, const char* name) : on(c && c->trace_on) {
+    if (on) nvtxRangePushA(name);
+  }
+  ~TraceRange() {
+    if (on) nvtxRangePop();
+  }
+};
 
 extern "C" {
 
@@ -420,12 +443,14 @@ fcsph_status fcsph_get_fc_table(const fcsph_ctx* c, int bc, double* out_host, si
 }
 
 fcsph_status fc_extend(fcsph_ctx* c, const void* f, void* f_ext, int bc) {
+  TraceRange tr(c, "fcsph fc_extend");
   if (!c || !f || !f_ext || (bc != 0 && bc != 1)) return fail(c, FCSPH_EINVAL, "fc_extend: bad argument");
   FCSPH_CK(launch_fc_extend(c, f, f_ext, bc), "fc_extend");
   return FCSPH_OK;
 }
 
 fcsph_status spectral_op(fcsph_ctx* c, const void* f, unsigned op_mask, int bc, void* const* outs) {
+  TraceRange tr(c, "fcsph spectral_op");
   if (!c || !f || !outs || (bc != 0 && bc != 1)) return fail(c, FCSPH_EINVAL, "spectral_op: bad argument");
   const unsigned all = c->gd.nz > 1 ? 31u : 15u;
   if (op_mask == 0 || (op_mask & ~all))
@@ -454,6 +479,7 @@ fcsph_status spectral_op(fcsph_ctx* c, const void* f, unsigned op_mask, int bc, 
 }
 
 fcsph_status line_op(fcsph_ctx* c, const void* f, unsigned op_mask, int bc, void* const* outs) {
+  TraceRange tr(c, "fcsph line_op");
   if (!c || !f || !outs || (bc != 0 && bc != 1)) return fail(c, FCSPH_EINVAL, "line_op: bad argument");
   if (op_mask == 0 || op_mask > 15u) return fail(c, FCSPH_EINVAL, "line_op: op_mask must be a nonempty subset of W|DX|DY|LAP");
   const int sym[4] = {SYM_W, SYM_DX, SYM_DY, SYM_LAP};
@@ -468,6 +494,7 @@ fcsph_status line_op(fcsph_ctx* c, const void* f, unsigned op_mask, int bc, void
 }
 
 fcsph_status spectral_div(fcsph_ctx* c, const void* fx, const void* fy, void* out) {
+  TraceRange tr(c, "fcsph spectral_div");
   if (!c || !fx || !fy || !out) return fail(c, FCSPH_EINVAL, "spectral_div: bad argument");
   if (c->gd.nz > 1) return fail(c, FCSPH_EUNSUPPORTED, "spectral_div: 2D grids only");
   RowOps ops = ops_none();
@@ -490,6 +517,7 @@ fcsph_status spectral_div(fcsph_ctx* c, const void* fx, const void* fy, void* ou
 }
 
 fcsph_status spectral_project(fcsph_ctx* c, const void* fx, const void* fy, void* out_x, void* out_y) {
+  TraceRange tr(c, "fcsph spectral_project");
   if (!c || !fx || !fy || !out_x || !out_y) return fail(c, FCSPH_EINVAL, "spectral_project: bad argument");
   if (c->gd.nz > 1) return fail(c, FCSPH_EUNSUPPORTED, "spectral_project: 2D grids only");
   // out_x = U - (gx^2 U + gx gy V)/|g|^2, out_y = V - (gx gy U + gy^2 V)/|g|^2
@@ -547,6 +575,7 @@ static fcsph_status ppe_refine(fcsph_ctx* c, const double* b64, double* phi64, i
 }
 
 fcsph_status ppe_solve(fcsph_ctx* c, const void* rhs, void* phi, double* resid_out) {
+  TraceRange tr(c, "fcsph ppe_solve");
   if (!c || !rhs || !phi) return fail(c, FCSPH_EINVAL, "ppe_solve: bad argument");
   const int p = c->prec.fft_prec;
   const size_t n = field_elems(c);
@@ -805,6 +834,7 @@ struct ActiveScope {
 static fcsph_status isph_step_masked(fcsph_ctx* c, const fcsph_state* s, int nsteps, const fcsph_step_params* prm);
 
 fcsph_status isph_step(fcsph_ctx* c, const fcsph_state* s, int nsteps, const fcsph_step_params* prm) {
+  TraceRange tr(c, "fcsph isph_step");
   if (!c || !s || !prm || nsteps < 0) return fail(c, FCSPH_EINVAL, "isph_step: bad argument");
   if (prm->active && c->prec.fft_prec == FCSPH_F32 && c->prec.ppe_refine_iters > 0)
     return fail(c, FCSPH_EUNSUPPORTED, "isph_step: an instance mask with PPE refinement");
@@ -910,6 +940,12 @@ fcsph_status fcsph_sync(fcsph_ctx* c) {
     cudaMemset(c->dstatus, 0, sizeof(int));
     return fail(c, FCSPH_ENONFINITE, "non-finite value in the time-step state");
   }
+  return FCSPH_OK;
+}
+
+fcsph_status fcsph_set_tracing(fcsph_ctx* c, int on) {
+  if (!c) return fail(nullptr, FCSPH_EINVAL, "fcsph_set_tracing: null context");
+  c->trace_on = on ? 1 : 0;
   return FCSPH_OK;
 }
 

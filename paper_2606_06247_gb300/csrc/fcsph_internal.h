@@ -214,6 +214,7 @@ struct fcsph_ctx {
   long long graph_kernels = 0;  // kernels in one replay of the step graph
   // per-kind event timing (eager launches only)
   int prof_on = 0;
+  int trace_on = 0;             // NVTX ranges around every call and pass
   std::vector<cudaEvent_t> ev_free;
   struct Pending {
     int kind;
@@ -229,6 +230,7 @@ struct ProfScope {
   fcsph_ctx* c;
   int kind;
   cudaEvent_t b = nullptr;
+  bool traced = false;
   ProfScope(fcsph_ctx* ctx, int k);
   ~ProfScope();
 };

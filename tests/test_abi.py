@@ -70,6 +70,7 @@ def test_bad_arguments_are_rejected(lib):
     assert L.fcsph_get_step_groups(None, ctypes.byref(r)) == 1
     assert L.fcsph_set_step_persistent(None, 1) == 1
     assert L.fcsph_set_tma(None, 1) == 1
+    assert L.fcsph_set_tracing(None, 1) == 1
     assert L.fcsph_get_step_persistent(None, ctypes.byref(r)) == 1
     prm = lib.fcsph_step_params(1e-3, 1.0, 1e-3, 0.0, 0.0, 0.0, 1.0, 1, 1, None, None)
     assert L.fcsph_autotune(None, ctypes.byref(prm), 3, None) == 1
