@@ -66,7 +66,8 @@ def parse():
                     help="uneven/serve: the library's scheduler (fcsph_batch_*) or the Python one")
     ap.add_argument("--persistent", action="store_true",
                     help="uneven/serve (native scheduler, 2D requests): every tick steps all size classes in one "
-                         "persistent launch instead of one graph per class")
+                         "persistent launch instead of one graph per class; with --profile-case: two cavity "
+                         "steps as persistent launches")
     ap.add_argument("--fc-cont", default="25",
                     help="uneven/serve: FC continuation length of every size class, an integer or 'smooth' (per size "
                          "the length nearest 25 in [20, 40] whose extended line the engine transforms directly)")
@@ -1033,6 +1034,12 @@ def run_profile_case(args):
                     h_over_dx=HDX, prec=args.prec, refine=args.refine if args.prec == "f32" else 0)
     z = torch.zeros((B, N, N), dtype=torch.float64, device="cuda")
     u, v, p, fu, fv = [z.clone() for _ in range(5)]
+    if args.persistent:  # two steps, each one launch of the persistent kernel
+        ctx.set_step_persistent(True)
+        ctx.isph_step(u, v, p, fu, fv, 2, nu=NU, rho=1.0, dt=DT, u_top=LID, scheme="rk3", use_graph=True)
+        ctx.sync()
+        print(json.dumps({"profile_case": "persistent", "prec": args.prec, "batch": B, "launches": ctx.launch_count}))
+        return
     ctx.isph_step(u, v, p, fu, fv, 2, nu=NU, rho=1.0, dt=DT, u_top=LID, scheme="rk3", use_graph=False)
     ctx.sync()
     print(json.dumps({"profile_case": True, "prec": args.prec, "batch": B, "launches": ctx.launch_count}))

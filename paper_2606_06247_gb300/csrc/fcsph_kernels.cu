@@ -1175,8 +1175,18 @@ __device__ __forceinline__ void run_item(const PassDesc& d, int bx, int by, int 
 
 // stall >= 0: item `stall` waits for a count that never comes (a test of the
 // bounded wait).
+// Register budget of the persistent kernel: its pass bodies read the grid,
+// plan and epilogue fields from the descriptor in global memory, where the
+// per-pass kernels take them as constant-bank operands, so the same code needs
+// more registers; the FP32-pair kernel gets up to 255 (8 warps per SM) rather
+// than spilling at 168.
+template <typename T, int NT> struct PersistMinCtas { static constexpr int v = MinCtas<T, NT>::v; };
+template <> struct PersistMinCtas<ff, 32> { static constexpr int v = 8; };
+template <> struct PersistMinCtas<ff, 64> { static constexpr int v = 4; };
+template <> struct PersistMinCtas<ff, 128> { static constexpr int v = 2; };
+
 template <typename T, int NT>
-__global__ void __launch_bounds__(NT, MinCtas<T, NT>::v) k_persist(const PassDesc* descs, const WorkItem* items,
+__global__ void __launch_bounds__(NT, PersistMinCtas<T, NT>::v) k_persist(const PassDesc* descs, const WorkItem* items,
                                                                   int n_items, unsigned* counters, unsigned* next,
                                                                   int* status, long long wait_ns, int stall) {
   __shared__ int s_idx, s_run;
