@@ -997,6 +997,7 @@ static void drop_graph(fcsph_ctx* c) {
     c->gexec = nullptr;
   }
   c->graph_key.clear();
+  c->pplan_key.clear();  // a persistent step is recorded again with the new launch shape
 }
 
 fcsph_status fcsph_set_tiling(fcsph_ctx* c, int row_lines, int col_pairs) {
