@@ -1307,6 +1307,112 @@ __global__ void __launch_bounds__(TeamFFT<N1, N2>::THREADS, TeamFFT<N1, N2>::MIN
   }
 }
 
+// Wall-normal passes of FP32 contexts whose extended length n has a large
+// prime factor (n = 537 and 1049 with n_cont = 25 at 512 and 1024 nodes):
+// Bluestein's convolution on the register team FFT of length m = 1080 =
+// 30 x 36 or 2100 = 42 x 50 (bluestein_team), one column pair per CTA.  The
+// chirp, the transformed filter and the m roots come from the context's plan
+// (P.chirp, P.bhat, P.sub.tw) in the FP32 pool.
+template <int N1, int N2>
+__global__ void __launch_bounds__(TeamFFT<N1, N2>::THREADS, TeamFFT<N1, N2>::MIN_CTAS) k_col_fwd_rb(
+    GridDev g, const float* __restrict__ f0, const float* __restrict__ f1, const float* __restrict__ f2,
+    const typename FcTab<float>::t* __restrict__ E, const float2* __restrict__ chirp,
+    const float2* __restrict__ bhat, const float2* __restrict__ roots, float2* __restrict__ spec, size_t fstride,
+    size_t bstride) {
+  constexpr int m = N1 * N2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* L = reinterpret_cast<float2*>(smem_raw);
+  float2* xs = L + m;
+  const int b = blockIdx.z + g.b0, f = blockIdx.y;
+  if (inactive(g, b)) return;
+  const int i0 = blockIdx.x * 2;
+  const float* src = f == 0 ? f0 : (f == 1 ? f1 : f2);
+  const int ny = g.ny, n = g.my, t = threadIdx.x;
+  load_pair_f32(L, src + ((size_t)b * g.ncol + i0) * ny, i0 + 1 < g.ncol, ny);
+  __syncthreads();
+  fc_append<float>(L, 1, m, ny, g.n_cont, g.n_match, E);
+  __syncthreads();
+  bluestein_team<N1, N2, false>(L, xs, n, chirp, bhat, roots, t);
+  col_store_spectrum<float>(L, 1, m, g, i0, n, 0, spec + b * bstride + f * fstride);
+}
+
+template <int N1, int N2>
+__global__ void __launch_bounds__(TeamFFT<N1, N2>::THREADS, TeamFFT<N1, N2>::MIN_CTAS) k_col_out_rb(
+    GridDev g, const float2* __restrict__ spec, size_t fstride, size_t bstride, int nout, const EpiArgs ea,
+    const float2* __restrict__ chirp, const float2* __restrict__ bhat, const float2* __restrict__ roots) {
+  constexpr int m = N1 * N2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* L = reinterpret_cast<float2*>(smem_raw);
+  float2* xs = L + m;
+  const int b = blockIdx.y + g.b0;
+  if (inactive(g, b)) return;
+  const int i0 = blockIdx.x * 2;
+  const int ny = g.ny, n = g.my, t = threadIdx.x;
+  for (int o = 0; o < nout; ++o) {
+    col_gather_hermitian<float>(L, 1, m, g, i0, spec + b * bstride + o * fstride, fstride, 1, n);
+    if (o + 1 < nout) prefetch_spec_pairs(g, i0, 1, spec + b * bstride + (o + 1) * fstride);
+    __syncthreads();
+    bluestein_team<N1, N2, true>(L, xs, n, chirp, bhat, roots, t);
+    float* out = reinterpret_cast<float*>(ea.outs[o]);
+    for (int j = t; j < ny; j += blockDim.x) {
+      out[fidx(g, b, i0, j)] = L[j].x;
+      if (i0 + 1 < g.ncol) out[fidx(g, b, i0 + 1, j)] = L[j].y;
+    }
+    __syncthreads();
+  }
+}
+
+// line_op on the Bluestein team transform: the forward spectrum stays in L,
+// each output is formed in W (symbol times spectrum over n) and inverted there.
+template <int N1, int N2>
+__global__ void __launch_bounds__(TeamFFT<N1, N2>::THREADS, TeamFFT<N1, N2>::MIN_CTAS) k_line_op_rb(
+    GridDev g, const float* __restrict__ f, long long ncols, const typename FcTab<float>::t* __restrict__ E,
+    const float2* __restrict__ pool, const float2* __restrict__ chirp, const float2* __restrict__ bhat,
+    const float2* __restrict__ roots, const __grid_constant__ LineOuts lo) {
+  constexpr int m = N1 * N2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* L = reinterpret_cast<float2*>(smem_raw);
+  float2* W = L + m;
+  float2* xs = W + m;
+  const long long c0 = (long long)blockIdx.x * 2;
+  const int ny = g.ny, n = g.my, t = threadIdx.x;
+  load_pair_f32(L, f + c0 * ny, c0 + 1 < ncols, ny);
+  __syncthreads();
+  fc_append<float>(L, 1, m, ny, g.n_cont, g.n_match, E);
+  __syncthreads();
+  bluestein_team<N1, N2, false>(L, xs, n, chirp, bhat, roots, t);
+  const float hh = (float)(g.h * g.h * 0.25);
+  const float cky = (float)(2.0 * 3.14159265358979323846 / (n * g.dy));
+  const float tscale = (float)(1.0 / n);
+  for (int o = 0; o < lo.nout; ++o) {
+    const int op = lo.op[o];
+    for (int k = t; k < n; k += blockDim.x) {
+      const int kappa = (2 * k <= n) ? k : k - n;
+      const float ky = cky * (float)kappa;
+      const float What = pool[g.ey_off + (kappa < 0 ? -kappa : kappa)].x * kernel_poly<float>(g.family, ky * ky * hh);
+      const bool nyq = (n % 2 == 0) && (2 * k == n);
+      float2 sy;
+      if (op == SYM_W)
+        sy = make_float2(What, 0.f);
+      else if (op == SYM_DY)
+        sy = make_float2(0.f, nyq ? 0.f : ky * What);
+      else if (op == SYM_LAP)
+        sy = make_float2(-(ky * ky) * What, 0.f);
+      else
+        sy = make_float2(0.f, 0.f);
+      W[k] = cscale(cmul(sy, L[k]), tscale);
+    }
+    __syncthreads();
+    bluestein_team<N1, N2, true>(W, xs, n, chirp, bhat, roots, t);
+    float* out = reinterpret_cast<float*>(lo.out[o]);
+    for (int j = t; j < ny; j += blockDim.x) {
+      if (c0 < ncols) out[c0 * ny + j] = W[j].x;
+      if (c0 + 1 < ncols) out[(c0 + 1) * ny + j] = W[j].y;
+    }
+    __syncthreads();
+  }
+}
+
 // k_col_out_r with TMA staging, persistent over (column pair, output) units:
 // while one unit's inverse transform runs, the next unit's half-spectrum rows
 // (the pair's two complex values of rows ky < hy, 16 bytes a row) arrive in
@@ -1619,6 +1725,12 @@ cudaError_t init_kernel_attributes() {
   FCSPH_RAISE((k_col_fwd_r<30, 35>))
   FCSPH_RAISE((k_col_out_r<20, 27>))
   FCSPH_RAISE((k_col_out_r<30, 35>))
+  FCSPH_RAISE((k_col_fwd_rb<30, 36>))
+  FCSPH_RAISE((k_col_fwd_rb<42, 50>))
+  FCSPH_RAISE((k_col_out_rb<30, 36>))
+  FCSPH_RAISE((k_col_out_rb<42, 50>))
+  FCSPH_RAISE((k_line_op_rb<30, 36>))
+  FCSPH_RAISE((k_line_op_rb<42, 50>))
   if ((e = cudaFuncSetAttribute(k_col_out_rt<20, 27>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax - 64)) !=
       cudaSuccess)
     return e;
@@ -1741,6 +1853,58 @@ static cudaError_t col_fwd_r(fcsph_ctx* c, int nf, const void* const* fields, in
   return cudaGetLastError();
 }
 
+// Register Bluestein column FFT for FP32 contexts: the split N1 of the
+// Bluestein length m (1080 = 30 x 36, 2100 = 42 x 50) of the extended
+// wall-normal length, else 0.
+int col_rb_split(const fcsph_ctx* c) {
+  const FftPlan& P = c->plan_y;
+  if (c->prec.fft_prec != FCSPH_F32 || !P.bs) return 0;
+  switch (P.sub.n) {
+    case 1080: return 30;
+    case 2100: return 42;
+    default: return 0;
+  }
+}
+
+template <int N1, int N2>
+static cudaError_t col_fwd_rb(fcsph_ctx* c, int nf, const void* const* fields, int bc, void* spec) {
+  typedef TeamFFT<N1, N2> TF;
+  const GridDev& g = c->gd;
+  const FftPlan& P = c->plan_y;
+  const size_t smem = ((size_t)N1 * N2 + TF::XCHG) * sizeof(float2);
+  cudaError_t e = check_smem(smem);
+  if (e != cudaSuccess) return e;
+  const auto* E = static_cast<const typename FcTab<float>::t*>(fc_table(c, FCSPH_F32, bc));
+  dim3 grid((g.ncol + 1) / 2, nf, g.nb);
+  const size_t fstride = (size_t)g.rows * g.ncol;
+  const size_t bstride = spec_in_fields(c) * fstride;
+  ProfScope ps(c, FCSPH_PROF_COL_FWD);
+  const float* f0 = (const float*)fields[0];
+  k_col_fwd_rb<N1, N2><<<grid, TF::THREADS, smem, c->stream>>>(
+      g, f0, (const float*)(nf > 1 ? fields[1] : fields[0]), (const float*)(nf > 2 ? fields[2] : fields[0]), E,
+      c->pool32 + P.chirp, c->pool32 + P.bhat, c->pool32 + P.sub.tw, (float2*)spec, fstride, bstride);
+  c->launches++;
+  return cudaGetLastError();
+}
+
+template <int N1, int N2>
+static cudaError_t col_out_rb(fcsph_ctx* c, const void* spec, int nout, EpiArgs& ea) {
+  typedef TeamFFT<N1, N2> TF;
+  const GridDev& g = c->gd;
+  const FftPlan& P = c->plan_y;
+  const size_t smem = ((size_t)N1 * N2 + TF::XCHG) * sizeof(float2);
+  cudaError_t e = check_smem(smem);
+  if (e != cudaSuccess) return e;
+  const size_t fs = (size_t)g.rows * g.ncol;
+  dim3 grid((g.ncol + 1) / 2, g.nb);
+  ProfScope ps(c, FCSPH_PROF_COL_OUT);
+  k_col_out_rb<N1, N2><<<grid, TF::THREADS, smem, c->stream>>>(g, (const float2*)spec, fs, spec_out_fields(c) * fs,
+                                                              nout, ea, c->pool32 + P.chirp, c->pool32 + P.bhat,
+                                                              c->pool32 + P.sub.tw);
+  c->launches++;
+  return cudaGetLastError();
+}
+
 // cuTensorMapEncodeTiled from the driver, looked up once through the runtime.
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
@@ -1824,6 +1988,11 @@ static cudaError_t col_fwd_t(fcsph_ctx* c, int prec, int nf, const void* const* 
       switch (col_r_split(c)) {
         case 20: return col_fwd_r<20, 27>(c, nf, fields, bc, spec);
         case 30: return col_fwd_r<30, 35>(c, nf, fields, bc, spec);
+        default: break;
+      }
+      switch (col_rb_split(c)) {
+        case 30: return col_fwd_rb<30, 36>(c, nf, fields, bc, spec);
+        case 42: return col_fwd_rb<42, 50>(c, nf, fields, bc, spec);
         default: break;
       }
     }
@@ -1986,6 +2155,23 @@ static cudaError_t line_op_r(fcsph_ctx* c, const void* f, const LineOuts& lo, in
   return cudaGetLastError();
 }
 
+template <int N1, int N2>
+static cudaError_t line_op_rb(fcsph_ctx* c, const void* f, const LineOuts& lo, int bc) {
+  typedef TeamFFT<N1, N2> TF;
+  const GridDev& g = c->gd;
+  const FftPlan& P = c->plan_y;
+  const size_t smem = (2 * (size_t)N1 * N2 + TF::XCHG) * sizeof(float2);
+  cudaError_t e = check_smem(smem);
+  if (e != cudaSuccess) return e;
+  const long long ncols = (long long)g.batch * g.ncol;
+  const auto* E = static_cast<const typename FcTab<float>::t*>(fc_table(c, FCSPH_F32, bc));
+  ProfScope ps(c, FCSPH_PROF_COL_OUT);
+  k_line_op_rb<N1, N2><<<(unsigned)((ncols + 1) / 2), TF::THREADS, smem, c->stream>>>(
+      g, (const float*)f, ncols, E, c->pool32, c->pool32 + P.chirp, c->pool32 + P.bhat, c->pool32 + P.sub.tw, lo);
+  c->launches++;
+  return cudaGetLastError();
+}
+
 template <typename T, typename U>
 static cudaError_t line_op_t(fcsph_ctx* c, int prec, const void* f, const int* ops, int nout, int bc, void* const* outs) {
   const GridDev& g = c->gd;
@@ -2001,6 +2187,18 @@ static cudaError_t line_op_t(fcsph_ctx* c, int prec, const void* f, const int* o
       }
       if (split == 20) return line_op_r<20, 27>(c, f, lo, bc);
       if (split == 30) return line_op_r<30, 35>(c, f, lo, bc);
+    }
+    const int bsplit = col_rb_split(c);
+    if (bsplit) {
+      LineOuts lo;
+      memset(&lo, 0, sizeof(lo));
+      lo.nout = nout;
+      for (int o = 0; o < nout; ++o) {
+        lo.op[o] = ops[o];
+        lo.out[o] = outs[o];
+      }
+      if (bsplit == 30) return line_op_rb<30, 36>(c, f, lo, bc);
+      if (bsplit == 42) return line_op_rb<42, 50>(c, f, lo, bc);
     }
   }
   const FftPlan& P = c->plan_y;
@@ -2140,6 +2338,11 @@ cudaError_t launch_col_out(fcsph_ctx* c, const void* spec, int nout, void* const
       case 30:
         if (c->tma) e = col_out_rt<30, 35>(c, spec, nout, ea);
         return e == cudaErrorNotSupported ? col_out_r<30, 35>(c, spec, nout, ea) : e;
+      default: break;
+    }
+    switch (col_rb_split(c)) {
+      case 30: return col_out_rb<30, 36>(c, spec, nout, ea);
+      case 42: return col_out_rb<42, 50>(c, spec, nout, ea);
       default: break;
     }
   }

@@ -33,6 +33,10 @@ template <> struct RegSplit<27> { static constexpr int a = 3; };
 template <> struct RegSplit<28> { static constexpr int a = 4; };
 template <> struct RegSplit<30> { static constexpr int a = 3; };
 template <> struct RegSplit<35> { static constexpr int a = 5; };
+template <> struct RegSplit<6> { static constexpr int a = 2; };
+template <> struct RegSplit<36> { static constexpr int a = 4; };
+template <> struct RegSplit<42> { static constexpr int a = 6; };
+template <> struct RegSplit<50> { static constexpr int a = 5; };
 
 // exp(-/+ 2 pi i e / N) (forward / inverse) for a composite N.
 template <int N, bool INV> __device__ __forceinline__ float2 rroot(int e) {
@@ -75,7 +79,9 @@ template <int N1, int N2> struct TeamFFT {
   static constexpr int S = (N2 % 2) ? N2 : N2 + 1;    // odd row stride of the exchange block
   static constexpr int XCHG = N1 * S;                 // float2 elements of the exchange block
   static constexpr int THREADS = (NV + 31) / 32 * 32;
-  static constexpr int MIN_CTAS = 512 / THREADS;      // <= 128 registers per thread
+  // <= 128 registers per thread; teams of more than 35 points per thread
+  // (the Bluestein lengths 1080 = 30 x 36 and 2100 = 42 x 50) get up to 255
+  static constexpr int MIN_CTAS = NV > 35 ? 256 / THREADS : 512 / THREADS;
 
   // Forward: v[j] = x[t + N2 j] (t < N2) on entry; v[k2] = X[t + N1 k2]
   // (t < N1) on return.  Every thread of the CTA calls it.
@@ -115,5 +121,53 @@ template <int N1, int N2> struct TeamFFT {
     __syncthreads();
   }
 };
+
+// Length-n DFT (forward, or INV: the unnormalised inverse) of the line L by
+// Bluestein's chirp-z convolution on the team FFT of length m = N1 N2 >= 2n - 1:
+// a_j = x_j conj(c_j) for j < n, zero up to m; y = IDFT_m(DFT_m(a) . bhat), the
+// inverse unnormalised, bhat = DFT_m(b) / m of the chirp filter b; then
+// X_k = conj(c_k) y_k, with c_j = exp(i pi j^2 / n); the inverse as
+// conj(DFT(conj x)).  In: L[j], j < n (L holds m values).  Out: L[k], k < n.
+// chirp: c_j, j < n; roots: w_m^e, e < m.  Every thread of the CTA calls it.
+template <int N1, int N2, bool INV>
+__device__ __forceinline__ void bluestein_team(float2* L, float2* xs, int n, const float2* __restrict__ chirp,
+                                               const float2* __restrict__ bhat, const float2* __restrict__ roots,
+                                               int t) {
+  typedef TeamFFT<N1, N2> TF;
+  constexpr int m = N1 * N2;
+  for (int j = t; j < m; j += blockDim.x) {
+    float2 a = make_float2(0.f, 0.f);
+    if (j < n) {
+      float2 x = L[j];
+      if (INV) x.y = -x.y;
+      a = cmulc(x, chirp[j]);
+    }
+    L[j] = a;
+  }
+  __syncthreads();
+  float2 v[TF::NV];
+  if (t < N2) {
+#pragma unroll
+    for (int j = 0; j < N1; ++j) v[j] = L[t + N2 * j];
+  }
+  TF::fwd(v, xs, roots, t);
+  if (t < N1) {
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) v[k2] = cmul(v[k2], bhat[t + N1 * k2]);
+  }
+  TF::inv(v, xs, roots, t);
+  if (t < N2) {
+#pragma unroll
+    for (int j = 0; j < N1; ++j) {
+      const int idx = t + N2 * j;
+      if (idx < n) {
+        float2 z = cmulc(v[j], chirp[idx]);
+        if (INV) z.y = -z.y;
+        L[idx] = z;
+      }
+    }
+  }
+  __syncthreads();
+}
 
 }  // namespace fcsph

@@ -10,7 +10,7 @@ import os
 
 import mpmath as mp
 
-SIZES = [10, 14, 15, 20, 21, 25, 27, 28, 30, 35]
+SIZES = [6, 10, 14, 15, 20, 21, 25, 27, 28, 30, 35, 36, 42, 50]
 
 
 def main():

@@ -108,12 +108,14 @@ def test_fp32_register_rows_3d_channel_step():
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("nx,ny,n_cont", [(16, 1024, 26), (15, 512, 28), (64, 512, 28)])
+@pytest.mark.parametrize("nx,ny,n_cont", [(16, 1024, 26), (15, 512, 28), (64, 512, 28),
+                                         (16, 1024, 25), (15, 512, 25), (64, 512, 25)])
 def test_fp32_register_columns_spectral_op(nx, ny, n_cont):
     """The register column FFT of FP32 contexts (fcsph_regfft.cuh: 1050 = 30 x 35
-    and 540 = 20 x 27 extended points): forward pass with FC and inverse pass
-    into FP32 outputs, against the FP64 oracle; an odd nx leaves the last
-    column pair half empty."""
+    and 540 = 20 x 27 extended points, and Bluestein's convolution on the team
+    FFT for 1049 (m = 2100 = 42 x 50) and 537 (m = 1080 = 30 x 36)): forward
+    pass with FC and inverse pass into FP32 outputs, against the FP64 oracle;
+    an odd nx leaves the last column pair half empty."""
     torch = torch_cuda()
     b = binding()
     batch = 2
@@ -143,10 +145,11 @@ def test_fp32_register_columns_spectral_op(nx, ny, n_cont):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("ny,n_cont", [(1024, 26), (512, 28)])
+@pytest.mark.parametrize("ny,n_cont", [(1024, 26), (512, 28), (1024, 25), (512, 25)])
 def test_fp32_register_line_op(ny, n_cont):
     """line_op of FP32 contexts on the register team FFT (1050 and 540 extended
-    points), an odd number of lines, against the FP64 oracle."""
+    points directly, 1049 and 537 by Bluestein's convolution on it), an odd
+    number of lines, against the FP64 oracle."""
     torch = torch_cuda()
     b = binding()
     from oracle.symbols import symbol_closed
@@ -167,7 +170,10 @@ def test_fp32_register_line_op(ny, n_cont):
         for o, r in zip(outs, refs):
             worst = max(worst, rel_l2(o[0, i].double().cpu().numpy(), r[0]))
     print(f"register line_op ny={ny} C={n_cont}: worst FP32 rel L2 {worst:.2e}")
-    assert worst < 1e-4
+    # Bluestein lengths run two FP32 transforms of length m ~ 2n plus two chirp
+    # products per transform: about twice the rounding of a direct transform
+    # (measured 1.3e-4 at 1049 points, under 1e-4 at the direct lengths)
+    assert worst < (2e-4 if n_cont == 25 else 1e-4)
 
 
 @pytest.mark.gpu
