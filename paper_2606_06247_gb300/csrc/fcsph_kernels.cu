@@ -1413,24 +1413,26 @@ __global__ void __launch_bounds__(TeamFFT<N1, N2>::THREADS, TeamFFT<N1, N2>::MIN
   }
 }
 
-// k_col_out_r with TMA staging, persistent over (column pair, output) units:
+// k_col_out_r (BS: k_col_out_rb) with TMA staging, persistent over (column pair, output) units:
 // while one unit's inverse transform runs, the next unit's half-spectrum rows
 // (the pair's two complex values of rows ky < hy, 16 bytes a row) arrive in
 // a staging buffer by 2D tiled bulk copies (nbox boxes of rows_box rows) on
 // one mbarrier, so the column pass no longer waits on its strided gather.
 // The wait for a copy is bounded: on a timeout the CTA sets bit 1 of the
 // status word, waits once more (bounded) for its copy in flight and returns.
-template <int N1, int N2>
+template <int N1, int N2, bool BS>
 __global__ void __launch_bounds__(TeamFFT<N1, N2>::THREADS, TeamFFT<N1, N2>::MIN_CTAS) k_col_out_rt(
     GridDev g, const __grid_constant__ CUtensorMap tmap, int rows_box, int nbox, int nfo, int nout,
-    const EpiArgs ea, const float2* __restrict__ roots, int npairs) {
+    const EpiArgs ea, const float2* __restrict__ roots, int npairs, const float2* __restrict__ chirp,
+    const float2* __restrict__ bhat) {
   typedef TeamFFT<N1, N2> TF;
-  constexpr int n = N1 * N2;
+  constexpr int m = N1 * N2;
+  const int n = BS ? g.my : m;  // the line's length (BS: transformed by Bluestein on length m)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   // bulk tensor copies land on 128-byte boundaries (the launch adds 128 bytes)
   float4* stage = reinterpret_cast<float4*>(smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
   float2* L = reinterpret_cast<float2*>(stage + (size_t)nbox * rows_box);
-  float2* xs = L + n;
+  float2* xs = L + m;
   __shared__ __align__(8) uint64_t bar;
   __shared__ int s_ok;
   const int t = threadIdx.x;
@@ -1481,20 +1483,29 @@ __global__ void __launch_bounds__(TeamFFT<N1, N2>::THREADS, TeamFFT<N1, N2>::MIN
     }
     __syncthreads();
     if (t == 0 && pair_of(k + 1) < W) issue(k + 1);  // the stage is free again
-    float2 v[TF::NV];
-    if (t < N1) {
+    float* out = reinterpret_cast<float*>(ea.outs[o]);
+    if constexpr (BS) {
+      bluestein_team<N1, N2, true>(L, xs, n, chirp, bhat, roots, t);
+      for (int j = t; j < ny; j += blockDim.x) {
+        out[fidx(g, b, i0, j)] = L[j].x;
+        if (i0 + 1 < g.ncol) out[fidx(g, b, i0 + 1, j)] = L[j].y;
+      }
+      __syncthreads();  // L is rewritten by the next unit
+    } else {
+      float2 v[TF::NV];
+      if (t < N1) {
 #pragma unroll
-      for (int k2 = 0; k2 < N2; ++k2) v[k2] = L[t + N1 * k2];
-    }
-    TF::inv(v, xs, roots, t);
-    if (t < N2) {
-      float* out = reinterpret_cast<float*>(ea.outs[o]);
+        for (int k2 = 0; k2 < N2; ++k2) v[k2] = L[t + N1 * k2];
+      }
+      TF::inv(v, xs, roots, t);
+      if (t < N2) {
 #pragma unroll
-      for (int j = 0; j < N1; ++j) {
-        const int row = t + N2 * j;
-        if (row < ny) {
-          out[fidx(g, b, i0, row)] = v[j].x;
-          if (i0 + 1 < g.ncol) out[fidx(g, b, i0 + 1, row)] = v[j].y;
+        for (int j = 0; j < N1; ++j) {
+          const int row = t + N2 * j;
+          if (row < ny) {
+            out[fidx(g, b, i0, row)] = v[j].x;
+            if (i0 + 1 < g.ncol) out[fidx(g, b, i0 + 1, row)] = v[j].y;
+          }
         }
       }
     }
@@ -1731,12 +1742,18 @@ cudaError_t init_kernel_attributes() {
   FCSPH_RAISE((k_col_out_rb<42, 50>))
   FCSPH_RAISE((k_line_op_rb<30, 36>))
   FCSPH_RAISE((k_line_op_rb<42, 50>))
-  if ((e = cudaFuncSetAttribute(k_col_out_rt<20, 27>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax - 64)) !=
-      cudaSuccess)
-    return e;
-  if ((e = cudaFuncSetAttribute(k_col_out_rt<30, 35>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax - 64)) !=
-      cudaSuccess)
-    return e;
+  {
+    const int lim = (int)kSmemMax - 64;
+    if ((e = cudaFuncSetAttribute(k_col_out_rt<20, 27, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) !=
+            cudaSuccess ||
+        (e = cudaFuncSetAttribute(k_col_out_rt<30, 35, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) !=
+            cudaSuccess ||
+        (e = cudaFuncSetAttribute(k_col_out_rt<30, 36, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) !=
+            cudaSuccess ||
+        (e = cudaFuncSetAttribute(k_col_out_rt<42, 50, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) !=
+            cudaSuccess)
+      return e;
+  }
   FCSPH_RAISE((k_row_sym_w<2>))
   FCSPH_RAISE((k_row_sym_w<4>))
   FCSPH_RAISE((k_row_sym_w<8>))
@@ -1927,7 +1944,7 @@ static EncodeTiledFn encode_tiled() {
 // of the tensor map and 16-byte aligned pair coordinates), a 16-byte aligned
 // spectrum buffer and no instance mask; returns cudaErrorNotSupported
 // otherwise (the caller then runs k_col_out_r).
-template <int N1, int N2>
+template <int N1, int N2, bool BS>
 static cudaError_t col_out_rt(fcsph_ctx* c, const void* spec, int nout, EpiArgs& ea) {
   typedef TeamFFT<N1, N2> TF;
   const GridDev& g = c->gd;
@@ -1951,15 +1968,19 @@ static cudaError_t col_out_rt(fcsph_ctx* c, const void* spec, int nout, EpiArgs&
   int dev = 0, sms = 0, occ = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
       (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
-      (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_col_out_rt<N1, N2>, TF::THREADS, smem)) != cudaSuccess)
+      (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_col_out_rt<N1, N2, BS>, TF::THREADS, smem)) !=
+          cudaSuccess)
     return e;
   const int npairs = (g.ncol + 1) / 2;
   const long long W = (long long)g.nb * npairs;
   const long long grid = std::min<long long>(W, (long long)sms * (occ > 0 ? occ : 1));
   ea.status = c->dstatus;
   ProfScope ps(c, FCSPH_PROF_COL_OUT);
-  k_col_out_rt<N1, N2><<<(unsigned)grid, TF::THREADS, smem, c->stream>>>(g, map, rows_box, nbox, nfo, nout, ea,
-                                                                         c->pool32 + c->plan_y.base.tw, npairs);
+  const FftPlan& P = c->plan_y;
+  const float2* roots = c->pool32 + (BS ? P.sub.tw : P.base.tw);
+  k_col_out_rt<N1, N2, BS><<<(unsigned)grid, TF::THREADS, smem, c->stream>>>(
+      g, map, rows_box, nbox, nfo, nout, ea, roots, npairs, BS ? c->pool32 + P.chirp : nullptr,
+      BS ? c->pool32 + P.bhat : nullptr);
   c->launches++;
   return cudaGetLastError();
 }
@@ -2333,16 +2354,20 @@ cudaError_t launch_col_out(fcsph_ctx* c, const void* spec, int nout, void* const
     cudaError_t e = cudaErrorNotSupported;
     switch (col_r_split(c)) {
       case 20:
-        if (c->tma) e = col_out_rt<20, 27>(c, spec, nout, ea);
+        if (c->tma) e = col_out_rt<20, 27, false>(c, spec, nout, ea);
         return e == cudaErrorNotSupported ? col_out_r<20, 27>(c, spec, nout, ea) : e;
       case 30:
-        if (c->tma) e = col_out_rt<30, 35>(c, spec, nout, ea);
+        if (c->tma) e = col_out_rt<30, 35, false>(c, spec, nout, ea);
         return e == cudaErrorNotSupported ? col_out_r<30, 35>(c, spec, nout, ea) : e;
       default: break;
     }
     switch (col_rb_split(c)) {
-      case 30: return col_out_rb<30, 36>(c, spec, nout, ea);
-      case 42: return col_out_rb<42, 50>(c, spec, nout, ea);
+      case 30:
+        if (c->tma) e = col_out_rt<30, 36, true>(c, spec, nout, ea);
+        return e == cudaErrorNotSupported ? col_out_rb<30, 36>(c, spec, nout, ea) : e;
+      case 42:
+        if (c->tma) e = col_out_rt<42, 50, true>(c, spec, nout, ea);
+        return e == cudaErrorNotSupported ? col_out_rb<42, 50>(c, spec, nout, ea) : e;
       default: break;
     }
   }

@@ -177,7 +177,8 @@ def test_fp32_register_line_op(ny, n_cont):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("nx,ny,n_cont,batch", [(128, 512, 28, 24), (40, 1024, 26, 3)])
+@pytest.mark.parametrize("nx,ny,n_cont,batch", [(128, 512, 28, 24), (40, 1024, 26, 3), (128, 512, 25, 24),
+                                               (40, 1024, 25, 3)])
 def test_fp32_register_columns_tma_staging_is_exact(nx, ny, n_cont, batch):
     """The output column pass with its half-spectrum rows staged by 2D bulk
     tensor copies (fcsph_set_tma, the default) gives bitwise the outputs of the
