@@ -71,6 +71,8 @@ def parse():
     ap.add_argument("--fc-cont", default="25",
                     help="uneven/serve: FC continuation length of every size class, an integer or 'smooth' (per size "
                          "the length nearest 25 in [20, 40] whose extended line the engine transforms directly)")
+    ap.add_argument("--plane-cont", type=int, default=26,
+                    help="--profile-case --workload planes: FC continuation length (26: n_e = 1050; 25: 1049)")
     ap.add_argument("--profile-case", action="store_true",
                     help="no timing: 2 eager RK3 steps of the cavity, or (--workload planes) 3 spectral_op calls "
                          "on --batch planes of 1024^2, for ncu captures on a small batch")
@@ -1010,7 +1012,7 @@ def run_profile_case(args):
     """Two eager RK3 steps of the workload with every kernel launched on its own
     (no graph), for kernel-level captures; prints the launch count.  With
     --workload planes: three spectral_op calls (DX, DY, LAP) on `batch` planes
-    of 1024^2 (n_cont 26, FP32, default CTA widths)."""
+    of 1024^2 (n_cont --plane-cont, FP32, default CTA widths)."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -1023,7 +1025,8 @@ def run_profile_case(args):
         base = inputs.band_limited_planes(4, n, n, seed=12346, n_modes=64, max_mode=64)
         f = torch.tensor(np.tile(base, ((B + 3) // 4, 1, 1))[:B], dtype=torch.float32, device="cuda")
         outs = [torch.empty_like(f) for _ in range(3)]
-        ctx = b.Context(n, n, n / (n - 1), 1.0, batch=B, n_cont=26, family="G4", h_over_dx=1.3, prec="f32")
+        ctx = b.Context(n, n, n / (n - 1), 1.0, batch=B, n_cont=args.plane_cont, family="G4", h_over_dx=1.3,
+                        prec="f32")
         for _ in range(3):
             ctx.spectral_op(f, ["DX", "DY", "LAP"], outs)
         ctx.sync()
