@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--slots", type=int, default=8, help="uneven/serve: slots (batch) per size class")
     ap.add_argument("--server", default="native", choices=["native", "python"],
                     help="uneven/serve: the library's scheduler (fcsph_batch_*) or the Python one")
+    ap.add_argument("--size-priorities", action="store_true",
+                    help="uneven/serve (native scheduler): larger size classes on higher-priority streams")
     ap.add_argument("--persistent", action="store_true",
                     help="uneven/serve (native scheduler, 2D requests): every tick steps all size classes in one "
                          "persistent launch instead of one graph per class; with --profile-case: two cavity "
@@ -678,6 +680,8 @@ def run_serving(args):
         if args.server != "native":
             raise SystemExit("--persistent needs the native scheduler")
         srv = ServerCls(prec=args.prec, capacity=args.slots, fc_cont=fc_cont, persistent=True)
+    elif args.size_priorities:
+        srv = ServerCls(prec=args.prec, capacity=args.slots, fc_cont=fc_cont, size_priorities=True)
     else:
         srv = ServerCls(prec=args.prec, capacity=args.slots, fc_cont=fc_cont)
     rs = reqs()
@@ -719,7 +723,8 @@ def run_serving(args):
         "steps": steps, "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
         "config": {"workload": desc, "precision": args.prec, "slots_per_size_class": args.slots, "fc_cont": args.fc_cont,
-                   "scheduler": args.server + (" persistent" if args.persistent else "")},
+                   "scheduler": args.server + (" persistent" if args.persistent else "")
+                   + (" size-priorities" if args.size_priorities else "")},
         "latency_ms": {"p50": served["step_latency_ms_p50"], "p99": served["step_latency_ms_p99"]},
         "served": served, "serial_plain_fp64": serial,
         "error_vs_fp64": err_summary, "per_instance": per_inst,

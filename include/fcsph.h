@@ -285,6 +285,12 @@ fcsph_status fcsph_batch_run(fcsph_batch* batch, int block, int* in_flight);
  * batching of uneven sizes is this library's serving layer; the paper has no
  * counterpart. */
 fcsph_status fcsph_batch_set_persistent(fcsph_batch* batch, int on, double wait_limit_s);
+/* Stream priorities by class size (on = 1; default off): classes created
+ * from now on step on streams of high priority when an instance has at least
+ * 512^2 nodes, middle priority from 256^2, low below, so that the longest
+ * steps (which set the tail of the step latency) are scheduled first when
+ * classes compete for the GPU.  Results are unchanged.  No device work. */
+fcsph_status fcsph_batch_set_size_priorities(fcsph_batch* batch, int on);
 /* Fault injection for tests of the bounded wait (persistent mode): in the
  * next launch the last work item waits for a count that never comes, so its
  * wait runs out after wait_limit_s.  Plants nothing on the device that could

@@ -127,6 +127,7 @@ def _load():
         "fcsph_batch_last_error": [P, ctypes.c_char_p, S],
         "fcsph_batch_set_persistent": [P, I, D],
         "fcsph_batch_inject_stall": [P],
+        "fcsph_batch_set_size_priorities": [P, I],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -469,6 +470,10 @@ class Batch:
     def set_persistent(self, on=True, wait_limit_s=1.0):
         """fcsph_batch_set_persistent: every tick steps all classes in one persistent launch."""
         self._ck(lib.fcsph_batch_set_persistent(self.h, 1 if on else 0, float(wait_limit_s)))
+
+    def set_size_priorities(self, on=True):
+        """fcsph_batch_set_size_priorities: larger classes on higher-priority streams."""
+        self._ck(lib.fcsph_batch_set_size_priorities(self.h, 1 if on else 0))
 
     def inject_stall(self):
         """fcsph_batch_inject_stall: the next persistent launch has one wait that runs out (tests)."""

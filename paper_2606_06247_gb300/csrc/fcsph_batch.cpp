@@ -74,6 +74,7 @@ struct fcsph_batch {
   std::map<long long, Req> reqs;
   long long next_id = 1;
   std::string err;
+  bool size_priorities = false;  // class streams prioritised by class size (fcsph_batch_set_size_priorities)
   // persistent mode: one launch steps every class (fcsph_batch_set_persistent)
   bool persistent = false;
   double wait_s = 1.0;
@@ -173,7 +174,18 @@ fcsph_status create_class(fcsph_batch* b, int kind, int n, int family, Class** o
     destroy_class(c);
     return st;
   };
-  cudaError_t e = cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking);
+  // with size priorities on, the classes with the most nodes per instance run
+  // on the highest-priority streams (their steps are the longest, and set the
+  // tail of the step latency), the smallest on the lowest
+  int prio = 0;
+  if (b->size_priorities) {
+    int least = 0, greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) == cudaSuccess) {
+      const size_t cells = c->cells();
+      prio = cells >= (size_t)512 * 512 ? greatest : (cells >= (size_t)256 * 256 ? (least + greatest) / 2 : least);
+    }
+  }
+  cudaError_t e = cudaStreamCreateWithPriority(&c->st, cudaStreamNonBlocking, prio);
   if (e != cudaSuccess) return cleanup(bcuda(b, e, "fcsph_batch: stream"));
   if ((e = cudaEventCreate(&c->e0)) != cudaSuccess || (e = cudaEventCreate(&c->e1)) != cudaSuccess)
     return cleanup(bcuda(b, e, "fcsph_batch: events"));
@@ -603,6 +615,12 @@ fcsph_status fcsph_batch_set_persistent(fcsph_batch* b, int on, double wait_limi
   b->persistent = on != 0;
   b->wait_s = wait_limit_s;
   b->plan_gen = -1;
+  return FCSPH_OK;
+}
+
+fcsph_status fcsph_batch_set_size_priorities(fcsph_batch* b, int on) {
+  if (!b) return bfail(nullptr, FCSPH_EINVAL, "fcsph_batch_set_size_priorities: null batch");
+  b->size_priorities = on != 0;
   return FCSPH_OK;
 }
 

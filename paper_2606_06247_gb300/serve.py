@@ -300,8 +300,10 @@ class NativeServer:
     the batch and collects results and step latencies (same interface as
     Server)."""
 
-    def __init__(self, prec="f64", capacity=8, mem_budget=None, device=None, fc_cont=25, persistent=False):
-        """persistent: every tick steps all classes in one persistent launch (2D requests; FP64 / FP32x2)."""
+    def __init__(self, prec="f64", capacity=8, mem_budget=None, device=None, fc_cont=25, persistent=False,
+                 size_priorities=False):
+        """persistent: every tick steps all classes in one persistent launch (2D requests; FP64 / FP32x2).
+        size_priorities: larger classes step on higher-priority streams."""
         self.prec = prec
         self.capacity = capacity
         self.fc_cont = fc_cont
@@ -309,6 +311,8 @@ class NativeServer:
                              n_cont=fc_cont)
         if persistent:
             self.batch.set_persistent(True)
+        if size_priorities:
+            self.batch.set_size_priorities(True)
         self.live = {}     # library id -> Request
         self.done = []
 

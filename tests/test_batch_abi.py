@@ -52,3 +52,4 @@ def test_persistent_mode_arguments_are_checked_before_any_device_call():
     L = b.lib
     assert L.fcsph_batch_set_persistent(None, 1, 1.0) == 1
     assert L.fcsph_batch_inject_stall(None) == 1
+    assert L.fcsph_batch_set_size_priorities(None, 1) == 1

@@ -131,3 +131,25 @@ def test_per_instance_time_step(prec):
         np.testing.assert_array_equal(a[0], x[0])
         np.testing.assert_array_equal(a[1], y[1])
     assert np.abs(big[0][1] - small[0][1]).max() > 1e-9
+
+
+@pytest.mark.gpu
+def test_size_priorities_leave_results_unchanged():
+    """fcsph_batch_set_size_priorities only reorders the classes' streams on the
+    GPU: every request's result is bitwise the one without priorities."""
+    torch_cuda()
+    b = binding()
+    reqs = [("cavity", 64, 400.0, 3), ("channel", 32, 50.0, 4), ("cavity", 48, 1000.0, 3)]
+    ref, _ = _serve(b, reqs, "f32x2")
+    bt = b.Batch(prec="f32x2", slots=4, mem_budget=0.0)
+    bt.set_size_priorities(True)
+    ids = [bt.add(*r) for r in reqs]
+    for _ in range(100000):
+        bt.run(block=True)
+        if all(bt.poll(i)["state"] == "done" for i in ids):
+            break
+    for i, r, a in zip(ids, reqs, ref):
+        got = bt.result(i, r[0], r[1])
+        for f in got:
+            np.testing.assert_array_equal(got[f], a[f])
+    bt.close()
