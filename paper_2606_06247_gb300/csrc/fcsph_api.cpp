@@ -273,6 +273,15 @@ fcsph_status fcsph_create(const fcsph_grid* grid, const fcsph_fc* fc, const fcsp
   g.dx = g.x_walls ? grid->lx / (g.nx - 1) : grid->lx / g.nx;
   g.dy = grid->ly / (g.ny - 1);
   g.h = kernel->h_over_dx * g.dx;
+  g.ckx_d = 2.0 * 3.14159265358979323846 / (g.mx * g.dx);
+  g.cky_d = 2.0 * 3.14159265358979323846 / (g.my * g.dy);
+  g.ckz_d = 2.0 * 3.14159265358979323846 / (g.nz * g.dz);
+  g.hh_d = g.h * g.h * 0.25;
+  g.ckx_f = (float)g.ckx_d;
+  g.cky_f = (float)g.cky_d;
+  g.ckz_f = (float)g.ckz_d;
+  g.hh_f = (float)g.hh_d;
+  g.inv_my_f = (float)(1.0 / g.my);
   g.family = kernel->family;
 
   Pool pool;

@@ -151,6 +151,12 @@ struct GridDev {
   // several such groups on parallel branches of its graph; every other call
   // covers the whole batch (b0 = 0, nb = batch).
   int b0 = 0, nb = 0;
+  // FP32 constants of the register passes, computed once on the host in FP64
+  // and rounded (the same values the kernels would get, without per-thread
+  // FP64 divisions): 2 pi / (mx dx), 2 pi / (my dy), 2 pi / (nz dz), h^2 / 4, 1 / my
+  float ckx_f = 0.f, cky_f = 0.f, ckz_f = 0.f, hh_f = 0.f, inv_my_f = 0.f;
+  // the same in FP64, for the kernels of every precision
+  double ckx_d = 0.0, cky_d = 0.0, ckz_d = 0.0, hh_d = 0.0;
 };
 
 // CTAs of an instance left out of the step return at once (uniform per CTA,

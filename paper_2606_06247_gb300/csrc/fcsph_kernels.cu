@@ -390,9 +390,7 @@ __device__ __forceinline__ void row_sym_body(const GridDev& g, const typename CT
   V* X = fft_any<T, false>(A, B, nin * Rr, ls, P, pool);
   V* Cq = (X == A) ? B : A;
   V* D = nin >= 2 ? Cq + (size_t)Rr * ls : B + (size_t)Rr * ls;
-  const T ckx = (T)(2.0 * 3.14159265358979323846 / (mx * g.dx));
-  const T cky = (T)(2.0 * 3.14159265358979323846 / (g.my * g.dy));
-  const T ckz = (T)(2.0 * 3.14159265358979323846 / (nz * g.dz));
+  const T ckx = (T)g.ckx_d, cky = (T)g.cky_d, ckz = (T)g.ckz_d;  // 2 pi / (mx dx), 2 pi / (my dy), 2 pi / (nz dz)
   const T tscale = (T)scale;
   for (int o = 0; o < nout; ++o) {
     for (int r = 0; r < Rr; ++r) {
@@ -523,9 +521,7 @@ __global__ void __launch_bounds__(128, 3) k_row_sym_w(GridDev g, const float2* _
   __syncwarp();
   const int l = lane / M, k1 = lane - (lane / M) * M;
   const int q = q0 + l < nq ? q0 + l : q0;
-  const float ckx = (float)(2.0 * 3.14159265358979323846 / (mx * g.dx));
-  const float cky = (float)(2.0 * 3.14159265358979323846 / (g.my * g.dy));
-  const float ckz = (float)(2.0 * 3.14159265358979323846 / (nz * g.dz));
+  const float ckx = g.ckx_f, cky = g.cky_f, ckz = g.ckz_f;
   const int ky = q / nz, kq = q - (q / nz) * nz;
   const int kzeta = (2 * kq <= nz) ? kq : kq - nz;
   const float kyw = cky * (float)ky, kz = ckz * (float)kzeta;
@@ -607,8 +603,7 @@ __global__ void __launch_bounds__(NT, LineMinCtas<T, NT>::v) k_line_op(GridDev g
   __syncthreads();
   V* R = fft_any<T, false>(X, Cq, Pp, ls, P, pool);
   V* W1 = (R == X) ? Cq : X;
-  const T hh = (T)(g.h * g.h * 0.25);
-  const T cky = (T)(2.0 * 3.14159265358979323846 / (my * g.dy));
+  const T hh = (T)g.hh_d, cky = (T)g.cky_d;  // h^2 / 4, 2 pi / (my dy)
   const T tscale = (T)(1.0 / my);
   for (int o = 0; o < lo.nout; ++o) {
     const int op = lo.op[o];
@@ -693,9 +688,7 @@ __global__ void __launch_bounds__(TeamFFT<N1, N2>::THREADS, TeamFFT<N1, N2>::MIN
 #pragma unroll
     for (int k2 = 0; k2 < N2; ++k2) L[t + N1 * k2] = x[k2];
   }
-  const float hh = (float)(g.h * g.h * 0.25);
-  const float cky = (float)(2.0 * 3.14159265358979323846 / (n * g.dy));
-  const float tscale = (float)(1.0 / n);
+  const float hh = g.hh_f, cky = g.cky_f, tscale = g.inv_my_f;  // n = my
   const float ky0 = cky * (float)t;
   for (int o = 0; o < lo.nout; ++o) {
     const int op = lo.op[o];
@@ -934,6 +927,14 @@ __device__ __forceinline__ void col_inv_body(const GridDev& g, const typename CT
   const int i0 = bx * 2 * Pp;
   const int ny = g.ny;
   const bool ppe = (EPI == EPI_PPE_SOLVE || EPI == EPI_PPE_RESID || EPI == EPI_PPE_ADD);
+  // the instance's step parameters and the epilogue factors, once per CTA:
+  // inside the point loops the compiler would reload them after every store
+  // and repeat the FP64 divisions per point
+  const double nu_b = ea.s.nu_inst ? ea.s.nu_inst[b] : ea.s.nu;
+  const double fx_b = ea.s.fx_inst ? ea.s.fx_inst[b] : ea.s.fx;
+  const double dt_b = ea.s.dt_inst ? ea.s.dt_inst[b] : ea.s.dt;
+  const double div_c = EPI == EPI_DIV ? ea.s.rho / (ea.s.a * dt_b) : 0.0;   // rho / (a dt)
+  const double corr_c = EPI == EPI_CORR ? ea.s.a * dt_b / ea.s.rho : 0.0;  // a dt / rho
   for (int o = 0; o < nout; ++o) {
     V* R;
     if (ppe) {
@@ -987,10 +988,10 @@ __device__ __forceinline__ void col_inv_body(const GridDev& g, const typename CT
           } else if (term < nt - 1) {
             *a += ea.vel[term][id] * val;
           } else {
-            const double nu = ea.s.nu_inst ? ea.s.nu_inst[b] : ea.s.nu;
+            const double nu = nu_b;
             const double F = *a - nu * val;
-            const double f = comp == 0 ? (ea.s.fx_inst ? ea.s.fx_inst[b] : ea.s.fx) : (comp == 1 ? ea.s.fy : ea.s.fz);
-            const double dt = ea.s.dt_inst ? ea.s.dt_inst[b] : ea.s.dt;
+            const double f = comp == 0 ? fx_b : (comp == 1 ? ea.s.fy : ea.s.fz);
+            const double dt = dt_b;
             double cs = ea.vel[comp][id] + dt * (-ea.s.g * F - ea.s.z * ea.Fp[comp][id] + ea.s.a * f);
             // y walls: the tangential x velocity takes the wall speeds, the others 0
             if (j == 0) cs = comp == 0 ? ea.s.u_bottom : 0.0;
@@ -1002,12 +1003,12 @@ __device__ __forceinline__ void col_inv_body(const GridDev& g, const typename CT
             *a = cs;
           }
         } else if (EPI == EPI_DIV) {
-          nv = ea.s.rho / (ea.s.a * (ea.s.dt_inst ? ea.s.dt_inst[b] : ea.s.dt)) * val;
+          nv = div_c * val;
           ea.bvec[id] = nv;
           slot = 0;
         } else if (EPI == EPI_CORR) {
           // output o: d phi / d(axis o) -> component o
-          const double c = ea.s.a * (ea.s.dt_inst ? ea.s.dt_inst[b] : ea.s.dt) / ea.s.rho;
+          const double c = corr_c;
           double cn = ea.vs[o][id] - c * val;
           if (j == 0) cn = o == 0 ? ea.s.u_bottom : 0.0;
           if (j == ny - 1) cn = o == 0 ? ea.s.u_top : 0.0;
@@ -1381,9 +1382,7 @@ __global__ void __launch_bounds__(TeamFFT<N1, N2>::THREADS, TeamFFT<N1, N2>::MIN
   fc_append<float>(L, 1, m, ny, g.n_cont, g.n_match, E);
   __syncthreads();
   bluestein_team<N1, N2, false>(L, xs, n, chirp, bhat, roots, t);
-  const float hh = (float)(g.h * g.h * 0.25);
-  const float cky = (float)(2.0 * 3.14159265358979323846 / (n * g.dy));
-  const float tscale = (float)(1.0 / n);
+  const float hh = g.hh_f, cky = g.cky_f, tscale = g.inv_my_f;  // n = my
   for (int o = 0; o < lo.nout; ++o) {
     const int op = lo.op[o];
     for (int k = t; k < n; k += blockDim.x) {
