@@ -1015,7 +1015,8 @@ def run_channel3d(args):
 
 def run_profile_case(args):
     """Two eager RK3 steps of the workload with every kernel launched on its own
-    (no graph), for kernel-level captures; prints the launch count.  With
+    (no graph), for kernel-level captures, in the launch shape --tiling /
+    --cta-threads give (else the context's default); prints the launch count.  With
     --workload planes: three spectral_op calls (DX, DY, LAP) on `batch` planes
     of 1024^2 (n_cont --plane-cont, FP32, default CTA widths)."""
     import torch
@@ -1040,6 +1041,10 @@ def run_profile_case(args):
         return
     ctx = b.Context(N, N, 1.0, 1.0, x_walls=True, batch=B, n_match=N_MATCH, n_cont=N_CONT, family=FAMILY,
                     h_over_dx=HDX, prec=args.prec, refine=args.refine if args.prec == "f32" else 0)
+    if args.tiling:  # the launch shape of the bench line being profiled
+        ctx.set_tiling(*[int(x) for x in args.tiling.split(",")])
+    if args.cta_threads:
+        ctx.set_cta_threads(*[int(x) for x in args.cta_threads.split(",")])
     z = torch.zeros((B, N, N), dtype=torch.float64, device="cuda")
     u, v, p, fu, fv = [z.clone() for _ in range(5)]
     if args.persistent:  # two steps, each one launch of the persistent kernel

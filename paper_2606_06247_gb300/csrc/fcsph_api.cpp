@@ -1100,37 +1100,43 @@ fcsph_status fcsph_autotune(fcsph_ctx* c, const fcsph_step_params* prm, int step
   if (e == cudaSuccess) e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
   if (e != cudaSuccess) st = cuda_fail(c, e, "autotune setup");
-  for (int ri = 0; ri < 3 && st == FCSPH_OK; ++ri)
-    for (int ci = 0; ci < 3 && st == FCSPH_OK; ++ci) {
-      if (tiling_smem(c, cand[ri], cand[ci]) > tiling_smem_limit()) continue;
-      if ((st = fcsph_set_tiling(c, cand[ri], cand[ci])) != FCSPH_OK) break;
-      if ((st = isph_step(c, &s, 1, prm)) != FCSPH_OK) break;  // warm-up (and graph capture)
-      if ((e = cudaEventRecord(e0, c->stream)) != cudaSuccess) { st = cuda_fail(c, e, "autotune event"); break; }
-      if ((st = isph_step(c, &s, steps, prm)) != FCSPH_OK) break;
-      if ((e = cudaEventRecord(e1, c->stream)) != cudaSuccess) { st = cuda_fail(c, e, "autotune event"); break; }
-      if ((e = cudaEventSynchronize(e1)) != cudaSuccess) { st = cuda_fail(c, e, "autotune sync"); break; }
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (best < 0.f || ms < best) {
-        best = ms;
-        best_r = cand[ri];
-        best_c = cand[ci];
+  // ms of `steps` steps in the context's current launch shape (after one
+  // untimed step, which also captures the step graph); < 0 on failure
+  auto time_steps = [&]() -> float {
+    if ((st = isph_step(c, &s, 1, prm)) != FCSPH_OK) return -1.f;
+    if ((e = cudaEventRecord(e0, c->stream)) != cudaSuccess) { st = cuda_fail(c, e, "autotune event"); return -1.f; }
+    if ((st = isph_step(c, &s, steps, prm)) != FCSPH_OK) return -1.f;
+    if ((e = cudaEventRecord(e1, c->stream)) != cudaSuccess) { st = cuda_fail(c, e, "autotune event"); return -1.f; }
+    if ((e = cudaEventSynchronize(e1)) != cudaSuccess) { st = cuda_fail(c, e, "autotune sync"); return -1.f; }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    return ms;
+  };
+  // tiling (lines per CTA) at the current CTA widths
+  auto sweep_tiling = [&]() {
+    for (int ri = 0; ri < 3 && st == FCSPH_OK; ++ri)
+      for (int ci = 0; ci < 3 && st == FCSPH_OK; ++ci) {
+        if (tiling_smem(c, cand[ri], cand[ci]) > tiling_smem_limit()) continue;
+        if ((st = fcsph_set_tiling(c, cand[ri], cand[ci])) != FCSPH_OK) break;
+        const float ms = time_steps();
+        if (st != FCSPH_OK) break;
+        if (best < 0.f || ms < best) {
+          best = ms;
+          best_r = cand[ri];
+          best_c = cand[ci];
+        }
       }
-    }
-  if (st == FCSPH_OK) st = fcsph_set_tiling(c, best_r, best_c);
+    if (st == FCSPH_OK) st = fcsph_set_tiling(c, best_r, best_c);
+  };
+  sweep_tiling();
   // then the CTA widths at the chosen tiling
   int best_rt = c->row_threads, best_ct = c->col_threads;
   const int widths[3] = {32, 64, 128};
   for (int ri = 0; ri < 3 && st == FCSPH_OK; ++ri)
     for (int ci = 0; ci < 3 && st == FCSPH_OK; ++ci) {
       if ((st = fcsph_set_cta_threads(c, widths[ri], widths[ci])) != FCSPH_OK) break;
-      if ((st = isph_step(c, &s, 1, prm)) != FCSPH_OK) break;
-      if ((e = cudaEventRecord(e0, c->stream)) != cudaSuccess) { st = cuda_fail(c, e, "autotune event"); break; }
-      if ((st = isph_step(c, &s, steps, prm)) != FCSPH_OK) break;
-      if ((e = cudaEventRecord(e1, c->stream)) != cudaSuccess) { st = cuda_fail(c, e, "autotune event"); break; }
-      if ((e = cudaEventSynchronize(e1)) != cudaSuccess) { st = cuda_fail(c, e, "autotune sync"); break; }
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
+      const float ms = time_steps();
+      if (st != FCSPH_OK) break;
       if (ms < best) {
         best = ms;
         best_rt = widths[ri];
@@ -1138,19 +1144,18 @@ fcsph_status fcsph_autotune(fcsph_ctx* c, const fcsph_step_params* prm, int step
       }
     }
   if (st == FCSPH_OK) st = fcsph_set_cta_threads(c, best_rt, best_ct);
+  // the tiling once more at those widths: lines per CTA and CTA width trade
+  // against each other (two column pairs per 64-thread CTA fill as many
+  // warps per SM as one pair per 32-thread CTA, with half the CTAs)
+  if (st == FCSPH_OK && (best_rt != 32 || best_ct != 32)) sweep_tiling();
   // then the instance groups of the step graph at that tiling and width
   int best_g = c->groups;
   const int gcand[3] = {1, 2, 4};
   for (int gi = 0; gi < 3 && st == FCSPH_OK; ++gi) {
     if (gcand[gi] > c->gd.batch) continue;
     if ((st = fcsph_set_step_groups(c, gcand[gi])) != FCSPH_OK) break;
-    if ((st = isph_step(c, &s, 1, prm)) != FCSPH_OK) break;
-    if ((e = cudaEventRecord(e0, c->stream)) != cudaSuccess) { st = cuda_fail(c, e, "autotune event"); break; }
-    if ((st = isph_step(c, &s, steps, prm)) != FCSPH_OK) break;
-    if ((e = cudaEventRecord(e1, c->stream)) != cudaSuccess) { st = cuda_fail(c, e, "autotune event"); break; }
-    if ((e = cudaEventSynchronize(e1)) != cudaSuccess) { st = cuda_fail(c, e, "autotune sync"); break; }
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
+    const float ms = time_steps();
+    if (st != FCSPH_OK) break;
     if (ms < best) {
       best = ms;
       best_g = gcand[gi];
@@ -1160,13 +1165,8 @@ fcsph_status fcsph_autotune(fcsph_ctx* c, const fcsph_step_params* prm, int step
   // then one persistent launch per step instead of the graph (2D FP64 / FP32x2)
   if (st == FCSPH_OK && c->gd.nz == 1 && c->prec.fft_prec != FCSPH_F32) {
     bool keep = false;
-    if ((st = fcsph_set_step_persistent(c, 1)) == FCSPH_OK && (st = isph_step(c, &s, 1, prm)) == FCSPH_OK) {
-      if ((e = cudaEventRecord(e0, c->stream)) != cudaSuccess) st = cuda_fail(c, e, "autotune event");
-      if (st == FCSPH_OK) st = isph_step(c, &s, steps, prm);
-      if (st == FCSPH_OK && (e = cudaEventRecord(e1, c->stream)) != cudaSuccess) st = cuda_fail(c, e, "autotune event");
-      if (st == FCSPH_OK && (e = cudaEventSynchronize(e1)) != cudaSuccess) st = cuda_fail(c, e, "autotune sync");
-      float ms = 0.f;
-      if (st == FCSPH_OK) cudaEventElapsedTime(&ms, e0, e1);
+    if ((st = fcsph_set_step_persistent(c, 1)) == FCSPH_OK) {
+      const float ms = time_steps();
       if (st == FCSPH_OK && ms < best) {
         best = ms;
         keep = true;

@@ -901,6 +901,15 @@ __device__ void prefetch_field_cols(const GridDev& g, int b, int i0, int Pp, con
   }
 }
 
+// The FP64 field the fused forward of a column pass transforms: its f-th new
+// field, which the epilogue has written to global memory.
+__device__ __forceinline__ const double* fwd_field(const EpiArgs& ea, int EPI, int f) {
+  if (EPI == EPI_MOM) return ea.vs[f];
+  if (EPI == EPI_CORR) return ea.vo[f];
+  if (EPI == EPI_DIV) return ea.bvec;
+  return ea.phi;  // PPE_SOLVE, PPE_ADD
+}
+
 // The epilogue kind is a runtime argument (uniform across the grid): one
 // instantiation per precision keeps the build small.
 //
@@ -908,20 +917,21 @@ __device__ void prefetch_field_cols(const GridDev& g, int b, int i0, int Pp, con
 // inverse transforms run one at a time: gather the half spectrum of output o
 // into packed lines Z, inverse FFT (scratch S), then the epilogue consumes
 // output o.  Per-point FP64 values that later outputs or the fused forward
-// need live in `acc` (nacc double2 lines of ny per pair: the two columns in
-// .x / .y): the momentum terms accumulate there (u.grad + nu lap per
-// component), the other epilogues leave the new field there.  The fused
-// forward then transforms acc[f] (f < fwd_nf) with Z and S as its lines.
+// need stay in global memory, in the arrays the epilogue writes anyway (and
+// in L2 between the passes over one CTA's columns): the momentum terms
+// accumulate u.grad + nu lap of each component in its u* array (overwritten
+// by u* at the last term), and the fused forward transforms fwd_field(f)
+// (f < fwd_nf), the new fields of this pass, with Z and S as its lines.
+// Shared memory then holds only the lines: 2 Pp ls values.
 template <typename T>
 __device__ __forceinline__ void col_inv_body(const GridDev& g, const typename CT<T>::t* spec, size_t fstride,
-                                             size_t bstride, int nout, int nacc, const FftPlan& P,
+                                             size_t bstride, int nout, const FftPlan& P,
                                              const typename CT<T>::t* pool, const EpiArgs& ea, int Pp, int ls,
                                              const int EPI, int bx, int by) {
   typedef typename CT<T>::t V;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* Z = reinterpret_cast<V*>(smem_raw);
   V* S = Z + (size_t)Pp * ls;
-  double2* acc = reinterpret_cast<double2*>(S + (size_t)Pp * ls);
   const int b = by + g.b0;
   if (inactive(g, b)) return;
   const int i0 = bx * 2 * Pp;
@@ -959,7 +969,6 @@ __device__ __forceinline__ void col_inv_body(const GridDev& g, const typename CT
     for (int p = 0; p < Pp; ++p)
     for (int j = threadIdx.x; j < ny; j += blockDim.x) {
       const V z = R[(size_t)p * ls + j];
-      double2* A = acc + (size_t)p * ny + j;  // + f * Pp * ny for field f
 #pragma unroll
       for (int w = 0; w < 2; ++w) {
         const int i = i0 + 2 * p + w;
@@ -975,14 +984,12 @@ __device__ __forceinline__ void col_inv_body(const GridDev& g, const typename CT
           continue;
         }
         const double val = (double)zv;
-        double nv = 0.0;
-        int slot = -1;
         if (EPI == EPI_MOM) {
           // output comp * nt + term: d/dx, d/dy, (d/dz,) lap of component comp;
-          // F_comp = u . grad(comp) - nu lap(comp) accumulates in acc[comp]
+          // F_comp = u . grad(comp) - nu lap(comp) accumulates in u*_comp
           const int nt = ea.mom_terms;
           const int comp = o / nt, term = o - comp * nt;
-          double* a = w ? &A[(size_t)comp * Pp * ny].y : &A[(size_t)comp * Pp * ny].x;
+          double* a = ea.vs[comp] + id;
           if (term == 0) {
             *a = ea.vel[0][id] * val;
           } else if (term < nt - 1) {
@@ -998,14 +1005,11 @@ __device__ __forceinline__ void col_inv_body(const GridDev& g, const typename CT
             if (j == ny - 1) cs = comp == 0 ? ea.s.u_top : 0.0;
             if (g.x_walls && (i == 0 || i == g.nx - 1)) cs = 0.0;
             ea.Fp[comp][id] = F;
-            ea.vs[comp][id] = cs;
-            if (!isfinite(cs)) atomicOr(ea.status, 1);
             *a = cs;
+            if (!isfinite(cs)) atomicOr(ea.status, 1);
           }
         } else if (EPI == EPI_DIV) {
-          nv = div_c * val;
-          ea.bvec[id] = nv;
-          slot = 0;
+          ea.bvec[id] = div_c * val;
         } else if (EPI == EPI_CORR) {
           // output o: d phi / d(axis o) -> component o
           const double c = corr_c;
@@ -1015,42 +1019,30 @@ __device__ __forceinline__ void col_inv_body(const GridDev& g, const typename CT
           if (g.x_walls && (i == 0 || i == g.nx - 1)) cn = 0.0;
           ea.vo[o][id] = cn;
           if (!isfinite(cn)) atomicOr(ea.status, 1);
-          nv = cn;
-          slot = o;
         } else if (EPI == EPI_PPE_SOLVE) {
           if (ea.phi_double)
             reinterpret_cast<double*>(ea.phi_any)[id] = val;
           else
             reinterpret_cast<float*>(ea.phi_any)[id] = (float)val;
           if (ea.phi) ea.phi[id] = val;
-          nv = val;
-          slot = 0;
         } else if (EPI == EPI_PPE_RESID) {
           ea.phi[id] = ea.bvec[id] - val;  // r = b - L phi
         } else if (EPI == EPI_PPE_ADD) {
-          nv = ea.phi[id] + val;
-          ea.phi[id] = nv;
-          slot = 0;
-        }
-        if (slot >= 0 && slot < nacc) {
-          double2* a = A + (size_t)slot * Pp * ny;
-          if (w)
-            a->y = nv;
-          else
-            a->x = nv;
+          ea.phi[id] = ea.phi[id] + val;
         }
       }
     }
     __syncthreads();
   }
   for (int f = 0; f < ea.fwd_nf; ++f) {
-    // fields beyond nx (ragged last pair) are zero
+    // the new field f as this CTA's threads stored it above (a thread reads
+    // back its own points; columns beyond nx, a ragged last pair, are zero)
+    const double* a = fwd_field(ea, EPI, f);
     for (int p = 0; p < Pp; ++p) {
       const int i = i0 + 2 * p;
-      const double2* a = acc + ((size_t)f * Pp + p) * ny;
       V* L = Z + (size_t)p * ls;
       for (int j = threadIdx.x; j < ny; j += blockDim.x)
-        L[j] = mk<V>(i < g.ncol ? a[j].x : 0.0, i + 1 < g.ncol ? a[j].y : 0.0);
+        L[j] = mk<V>(i < g.ncol ? a[fidx(g, b, i, j)] : 0.0, i + 1 < g.ncol ? a[fidx(g, b, i + 1, j)] : 0.0);
     }
     __syncthreads();
     col_forward_store<T>(Z, S, Pp, ls, g, i0, reinterpret_cast<const typename FcTab<T>::t*>(ea.fwdE), ea.fwdP, pool,
@@ -1061,12 +1053,12 @@ __device__ __forceinline__ void col_inv_body(const GridDev& g, const typename CT
 
 template <typename T, int NT>
 __global__ void __launch_bounds__(NT, MinCtas<T, NT>::v) k_col_inv(GridDev g, const typename CT<T>::t* __restrict__ spec,
-                                                         size_t fstride, size_t bstride, int nout, int nacc,
+                                                         size_t fstride, size_t bstride, int nout,
                                                          const __grid_constant__ FftPlan P,
                                                          const typename CT<T>::t* __restrict__ pool,
                                                          const __grid_constant__ EpiArgs ea, int Pp, int ls,
                                                          const int EPI) {
-  col_inv_body<T>(g, spec, fstride, bstride, nout, nacc, P, pool, ea, Pp, ls, EPI, blockIdx.x, blockIdx.y);
+  col_inv_body<T>(g, spec, fstride, bstride, nout, P, pool, ea, Pp, ls, EPI, blockIdx.x, blockIdx.y);
 }
 
 // ---------------------------------------------------------------------------
@@ -1108,7 +1100,7 @@ struct PassDesc {
   double scale;
   int apply;
   // column inverse
-  int nout, nacc, epi;
+  int nout, epi;
   EpiArgs ea;
 };
 
@@ -1151,7 +1143,7 @@ template <typename T> __device__ __noinline__ void item_row_sym(const PassDesc& 
 }
 template <typename T> __device__ __noinline__ void item_col_inv(const PassDesc& __restrict__ d, int bx, int b) {
   typedef typename CT<T>::t V;
-  col_inv_body<T>(d.g, (const V*)d.spec, d.fstride, d.bstride, d.nout, d.nacc, d.P, (const V*)d.pool, d.ea, d.Pp, d.ls,
+  col_inv_body<T>(d.g, (const V*)d.spec, d.fstride, d.bstride, d.nout, d.P, (const V*)d.pool, d.ea, d.Pp, d.ls,
                   d.epi, bx, b);
 }
 template <typename T> __device__ __noinline__ void item_row_ppe(const PassDesc& __restrict__ d, int bx, int b) {
@@ -1806,7 +1798,7 @@ size_t tiling_smem(const fcsph_ctx* c, int row_lines, int col_pairs) {
   const size_t cb = c->prec.fft_prec == FCSPH_F32 ? sizeof(float2) : sizeof(double2);
   const size_t row = (c->gd.nz > 1 ? 6 : 4) * (size_t)row_lines * c->plan_x.line_len() * cb;
   const size_t ppe = 2 * (size_t)row_lines * c->plan_px.line_len() * cb;
-  const size_t col = (size_t)col_pairs * (2 * (size_t)col_ls(c) * cb + (c->gd.nz > 1 ? 3 : 2) * (size_t)c->gd.ny * sizeof(double2));
+  const size_t col = (size_t)col_pairs * 2 * (size_t)col_ls(c) * cb;
   size_t m = row > ppe ? row : ppe;
   return m > col ? m : col;
 }
@@ -2294,16 +2286,17 @@ static cudaError_t col_inv_common(fcsph_ctx* c, int epi, const void* spec, int n
   int ls = P.line_len();
   if (ea.fwd_nf > 0 && ea.fwdP.line_len() > ls) ls = ea.fwdP.line_len();
   const int Pp = c->col_pairs;
-  // FP64 per-point values kept across outputs: the two momentum components,
-  // else the fields of the fused forward
-  const int nacc = ea.fwd_nf;
-  const size_t smem = ((size_t)2 * ls * sizeof(typename CT<T>::t) + (size_t)nacc * g.ny * sizeof(double2)) * Pp;
+  // the lines only: FP64 values kept across outputs stay in global memory
+  const size_t smem = (size_t)2 * ls * sizeof(typename CT<T>::t) * Pp;
   const size_t fs = (size_t)g.rows * g.ncol;
   const size_t bs = (epi >= EPI_PPE_SOLVE ? 1 : spec_out_fields(c)) * fs;  // spec_ppe or spec_out
   dim3 grid((g.ncol + 2 * Pp - 1) / (2 * Pp), g.nb);
   const typename CT<T>::t* pool = PoolOf<T>::get(c);
   if (epi < EPI_OUT || epi > EPI_PPE_ADD) return cudaErrorInvalidValue;
   if (ea.fwd_nf > 3 || (epi == EPI_MOM && nout != ea.fwd_nf * ea.mom_terms)) return cudaErrorInvalidValue;
+  // the fused forward of a PPE pass reads the FP64 potential
+  if (ea.fwd_nf > 0 && (epi == EPI_PPE_SOLVE || epi == EPI_PPE_ADD) && ea.phi == nullptr) return cudaErrorInvalidValue;
+  if (ea.fwd_nf > 0 && (epi == EPI_OUT || epi == EPI_PPE_RESID)) return cudaErrorInvalidValue;
   ea.status = c->dstatus;
   cudaError_t e = check_smem(smem);
   if (e != cudaSuccess) return e;
@@ -2316,7 +2309,6 @@ static cudaError_t col_inv_common(fcsph_ctx* c, int epi, const void* spec, int n
     d.fstride = fs;
     d.bstride = bs;
     d.nout = nout;
-    d.nacc = nacc;
     d.epi = epi;
     d.ea = ea;
     return rec_push<T>(c, d);
@@ -2326,7 +2318,7 @@ static cudaError_t col_inv_common(fcsph_ctx* c, int epi, const void* spec, int n
   ProfScope ps(c, kinds[epi]);
   return with_width(c->col_threads, [&](auto w) {
     constexpr int NT = decltype(w)::value;
-    k_col_inv<T, NT><<<grid, NT, smem, c->stream>>>(g, (const typename CT<T>::t*)spec, fs, bs, nout, nacc, P, pool,
+    k_col_inv<T, NT><<<grid, NT, smem, c->stream>>>(g, (const typename CT<T>::t*)spec, fs, bs, nout, P, pool,
                                                     ea, Pp, ls, epi);
     c->launches++;
     return cudaGetLastError();
