@@ -407,15 +407,15 @@ fcsph_status fcsph_set_tma(fcsph_ctx* ctx, int on);
 fcsph_status fcsph_set_tracing(fcsph_ctx* ctx, int on);
 fcsph_status fcsph_get_step_persistent(const fcsph_ctx* ctx, int* on);
 
-/* Autotuner: times `steps` isph_step calls with *prm for every tiling with
- * row_lines, col_pairs in {1, 2, 4} that fits, on a zero state the call
- * allocates and frees (5 fields of the context's batch), then keeps the
- * fastest (2D: 5 fields, 3D: 7); then it times every pair of CTA widths in
- * {32, 64, 128} at that tiling and keeps the fastest; then the instance
- * groups 1, 2, 4 (at most the batch) of the step graph at that tiling and
- * width, and keeps the fastest; then (2D FP64 / FP32x2) the persistent step,
- * kept if faster still.  best_ms_out (nullable, host): its milliseconds per
- * step.
+/* Autotuner: times `steps` isph_step calls with *prm on a zero state the
+ * call allocates and frees (2D: 5 fields of the context's batch, 3D: 7).
+ * First the row-pass shape: every rows-per-CTA in {1, 2, 4} with every row
+ * CTA width in {32, 64, 128}, keeping the fastest; then the column-pass shape
+ * the same way (column pairs per CTA x column CTA width); shapes whose shared
+ * memory does not fit are skipped.  Then the instance groups 1, 2, 4, 8 (at
+ * most the batch) of the step graph in that shape, keeping the fastest; then
+ * (2D FP64 / FP32x2) the persistent step, kept if faster still.  best_ms_out
+ * (nullable, host): its milliseconds per step.
  * Synchronises the context's stream.  Engineering choice of this library;
  * the paper has no counterpart. */
 fcsph_status fcsph_autotune(fcsph_ctx* ctx, const fcsph_step_params* prm, int steps, double* best_ms_out);

@@ -1112,46 +1112,38 @@ fcsph_status fcsph_autotune(fcsph_ctx* c, const fcsph_step_params* prm, int step
     cudaEventElapsedTime(&ms, e0, e1);
     return ms;
   };
-  // tiling (lines per CTA) at the current CTA widths
-  auto sweep_tiling = [&]() {
-    for (int ri = 0; ri < 3 && st == FCSPH_OK; ++ri)
-      for (int ci = 0; ci < 3 && st == FCSPH_OK; ++ci) {
-        if (tiling_smem(c, cand[ri], cand[ci]) > tiling_smem_limit()) continue;
-        if ((st = fcsph_set_tiling(c, cand[ri], cand[ci])) != FCSPH_OK) break;
-        const float ms = time_steps();
-        if (st != FCSPH_OK) break;
-        if (best < 0.f || ms < best) {
-          best = ms;
-          best_r = cand[ri];
-          best_c = cand[ci];
-        }
-      }
-    if (st == FCSPH_OK) st = fcsph_set_tiling(c, best_r, best_c);
-  };
-  sweep_tiling();
-  // then the CTA widths at the chosen tiling
+  // The row passes and the column passes are separate kernels: their shapes
+  // (lines per CTA x CTA width) are swept one family at a time, each over all
+  // nine pairs, since lines per CTA and width trade against each other (two
+  // lines on a 64-thread CTA fill as many warps per SM as one line on a
+  // 32-thread CTA, with half the CTAs).
   int best_rt = c->row_threads, best_ct = c->col_threads;
   const int widths[3] = {32, 64, 128};
-  for (int ri = 0; ri < 3 && st == FCSPH_OK; ++ri)
-    for (int ci = 0; ci < 3 && st == FCSPH_OK; ++ci) {
-      if ((st = fcsph_set_cta_threads(c, widths[ri], widths[ci])) != FCSPH_OK) break;
-      const float ms = time_steps();
-      if (st != FCSPH_OK) break;
-      if (ms < best) {
-        best = ms;
-        best_rt = widths[ri];
-        best_ct = widths[ci];
-      }
+  auto try_shape = [&](int r, int cp, int rt, int ct) -> bool {
+    if (tiling_smem(c, r, cp) > tiling_smem_limit()) return false;
+    if ((st = fcsph_set_tiling(c, r, cp)) != FCSPH_OK) return false;
+    if ((st = fcsph_set_cta_threads(c, rt, ct)) != FCSPH_OK) return false;
+    const float ms = time_steps();
+    if (st != FCSPH_OK) return false;
+    if (best < 0.f || ms < best) {
+      best = ms;
+      best_r = r;
+      best_c = cp;
+      best_rt = rt;
+      best_ct = ct;
     }
+    return true;
+  };
+  for (int li = 0; li < 3 && st == FCSPH_OK; ++li)  // rows per CTA x row width
+    for (int wi = 0; wi < 3 && st == FCSPH_OK; ++wi) try_shape(cand[li], best_c, widths[wi], best_ct);
+  for (int li = 0; li < 3 && st == FCSPH_OK; ++li)  // column pairs per CTA x column width
+    for (int wi = 0; wi < 3 && st == FCSPH_OK; ++wi) try_shape(best_r, cand[li], best_rt, widths[wi]);
+  if (st == FCSPH_OK) st = fcsph_set_tiling(c, best_r, best_c);
   if (st == FCSPH_OK) st = fcsph_set_cta_threads(c, best_rt, best_ct);
-  // the tiling once more at those widths: lines per CTA and CTA width trade
-  // against each other (two column pairs per 64-thread CTA fill as many
-  // warps per SM as one pair per 32-thread CTA, with half the CTAs)
-  if (st == FCSPH_OK && (best_rt != 32 || best_ct != 32)) sweep_tiling();
   // then the instance groups of the step graph at that tiling and width
   int best_g = c->groups;
-  const int gcand[3] = {1, 2, 4};
-  for (int gi = 0; gi < 3 && st == FCSPH_OK; ++gi) {
+  const int gcand[4] = {1, 2, 4, 8};
+  for (int gi = 0; gi < 4 && st == FCSPH_OK; ++gi) {
     if (gcand[gi] > c->gd.batch) continue;
     if ((st = fcsph_set_step_groups(c, gcand[gi])) != FCSPH_OK) break;
     const float ms = time_steps();
