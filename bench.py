@@ -420,7 +420,7 @@ def run_ours(args):
         if args.groups:
             ctx.set_step_groups(args.groups)
     else:
-        ctx.autotune(steps=2, **prm)
+        ctx.autotune(steps=4, **prm)
     dtype_name = {"f64": "f64", "f32x2": "f32x2", "f32": "f32"}[args.prec]
     st = state()
     total_ms, per_ms, launches, clocks = timed(ctx, st, args.steps, args.warmup)
@@ -521,7 +521,7 @@ def run_ours(args):
         for pr in ("f64", "f32x2", "f32"):
             c2 = ctx if pr == args.prec else make(pr, 0)
             if pr != args.prec:
-                c2.autotune(steps=2, **prm)
+                c2.autotune(steps=4, **prm)
                 st2 = state()
                 n2 = max(2, args.steps // 2)
                 t2, _, _, _ = timed(c2, st2, n2, 1)

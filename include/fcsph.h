@@ -411,9 +411,11 @@ fcsph_status fcsph_get_step_persistent(const fcsph_ctx* ctx, int* on);
  * call allocates and frees (2D: 5 fields of the context's batch, 3D: 7).
  * First the row-pass shape: every rows-per-CTA in {1, 2, 4} with every row
  * CTA width in {32, 64, 128}, keeping the fastest; then the column-pass shape
- * the same way (column pairs per CTA x column CTA width); shapes whose shared
- * memory does not fit are skipped.  Then the instance groups 1, 2, 4, 8 (at
- * most the batch) of the step graph in that shape, keeping the fastest; then
+ * the same way (column pairs per CTA in {1, 2, 4, 8} x column CTA width);
+ * shapes whose shared memory does not fit are skipped.  Then the instance
+ * groups 1, 2, 3, 4, 6, 8 (at most the batch) of the step graph in that
+ * shape, keeping the fastest; the column sweep and the groups sweep then run
+ * once more at the chosen groups; then
  * (2D FP64 / FP32x2) the persistent step, kept if faster still.  best_ms_out
  * (nullable, host): its milliseconds per step.
  * Synchronises the context's stream.  Engineering choice of this library;

@@ -1136,24 +1136,35 @@ fcsph_status fcsph_autotune(fcsph_ctx* c, const fcsph_step_params* prm, int step
   };
   for (int li = 0; li < 3 && st == FCSPH_OK; ++li)  // rows per CTA x row width
     for (int wi = 0; wi < 3 && st == FCSPH_OK; ++wi) try_shape(cand[li], best_c, widths[wi], best_ct);
-  for (int li = 0; li < 3 && st == FCSPH_OK; ++li)  // column pairs per CTA x column width
-    for (int wi = 0; wi < 3 && st == FCSPH_OK; ++wi) try_shape(best_r, cand[li], best_rt, widths[wi]);
-  if (st == FCSPH_OK) st = fcsph_set_tiling(c, best_r, best_c);
-  if (st == FCSPH_OK) st = fcsph_set_cta_threads(c, best_rt, best_ct);
-  // then the instance groups of the step graph at that tiling and width
+  const int ccand[4] = {1, 2, 4, 8};  // a column pair's lines take half a row's shared memory
+  auto sweep_cols = [&]() {  // column pairs per CTA x column width
+    for (int li = 0; li < 4 && st == FCSPH_OK; ++li)
+      for (int wi = 0; wi < 3 && st == FCSPH_OK; ++wi) try_shape(best_r, ccand[li], best_rt, widths[wi]);
+    if (st == FCSPH_OK) st = fcsph_set_tiling(c, best_r, best_c);
+    if (st == FCSPH_OK) st = fcsph_set_cta_threads(c, best_rt, best_ct);
+  };
+  // the instance groups of the step graph in the current shape
   int best_g = c->groups;
-  const int gcand[4] = {1, 2, 4, 8};
-  for (int gi = 0; gi < 4 && st == FCSPH_OK; ++gi) {
-    if (gcand[gi] > c->gd.batch) continue;
-    if ((st = fcsph_set_step_groups(c, gcand[gi])) != FCSPH_OK) break;
-    const float ms = time_steps();
-    if (st != FCSPH_OK) break;
-    if (ms < best) {
-      best = ms;
-      best_g = gcand[gi];
+  const int gcand[6] = {1, 2, 3, 4, 6, 8};
+  auto sweep_groups = [&]() {
+    for (int gi = 0; gi < 6 && st == FCSPH_OK; ++gi) {
+      if (gcand[gi] > c->gd.batch) continue;
+      if ((st = fcsph_set_step_groups(c, gcand[gi])) != FCSPH_OK) break;
+      const float ms = time_steps();
+      if (st != FCSPH_OK) break;
+      if (ms < best) {
+        best = ms;
+        best_g = gcand[gi];
+      }
     }
+    if (st == FCSPH_OK) st = fcsph_set_step_groups(c, best_g);
+  };
+  // the column shape and the groups interact (how the partial waves of one
+  // group's launches overlap the next group's): two rounds of each
+  for (int round = 0; round < 2 && st == FCSPH_OK; ++round) {
+    sweep_cols();
+    sweep_groups();
   }
-  if (st == FCSPH_OK) st = fcsph_set_step_groups(c, best_g);
   // then one persistent launch per step instead of the graph (2D FP64 / FP32x2)
   if (st == FCSPH_OK && c->gd.nz == 1 && c->prec.fft_prec != FCSPH_F32) {
     bool keep = false;
