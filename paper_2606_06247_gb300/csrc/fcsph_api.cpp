@@ -311,11 +311,11 @@ fcsph_status fcsph_create(const fcsph_grid* grid, const fcsph_fc* fc, const fcsp
       if (c->plan_y.line_len() >= kWideLine) c->col_threads = 128;
     } else {
       // shared memory of the momentum passes, the largest of each kind: one
-      // row CTA (2 nc lines) and one column-pair CTA (2 lines + the FP64
-      // accumulators of nc components)
+      // row CTA (2 nc lines) and one column-pair CTA (2 lines; its FP64
+      // values stay in global memory)
       const size_t cb = 16, nc = g.nz > 1 ? 3 : 2;
       c->row_threads = std::max(c->row_threads, smem_width(2 * nc * c->plan_x.line_len() * cb));
-      c->col_threads = std::max(c->col_threads, smem_width(2 * (size_t)c->plan_y.line_len() * cb + nc * g.ny * 16));
+      c->col_threads = std::max(c->col_threads, smem_width(2 * (size_t)c->plan_y.line_len() * cb));
     }
   }
   {
