@@ -180,9 +180,10 @@ def test_cta_widths_are_checked():
         assert small.get_cta_threads() == (64, 32)
     big = b.Context(1024, 1024, 1024 / 1023, 1.0, batch=1, prec="f32")
     assert big.get_cta_threads() == (64, 128)      # FP32, lines of >= 768 points
-    # FP32-pair 540-point lines: ~34 KB per one-warp CTA, 6 fit an SM; 2 warps reach 12
+    # FP32-pair 540-point lines: a row CTA holds 4 lines (~35 KB), 6 fit an SM, so 2 warps reach 12; a
+    # column pair holds 2 (~17 KB, its FP64 values stay in global memory), 13 fit, so one warp does
     long = b.Context(512, 512, 1.0, 1.0, x_walls=True, batch=32, n_cont=28, prec="f32x2")
-    assert long.get_cta_threads() == (64, 64)
+    assert long.get_cta_threads() == (64, 32)
 
 
 @pytest.mark.gpu
