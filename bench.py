@@ -745,19 +745,13 @@ def plane_kernel_bytes(kind, P, nx, ny, hy, nout=3):
     return {"col_fwd": F + S, "row_op": S + nout * S, "col_out": nout * S + nout * F}.get(kind, 0)
 
 
-# spectral_op chunk sizes swept by the plane microbenchmark (0: every pass over all planes)
-PLANE_CHUNKS = (0, 2, 4, 8, 16)
-
-
 def measure_planes(steps, warmup, sweep_widths=True):
     """FC-extended operator microbench on 256 planes of 1024 x 1024 (x periodic,
     walls in y), FP32 fields, d/dx, d/dy and the Laplacian per call, for
     n_cont = 25 (n_e = 1049, Bluestein) and 26 (n_e = 1050).  Algorithmic bytes
     per call: 4 B in + 3 x 4 B out per node; per pass: each kernel's own
     reads and writes (plane_kernel_bytes), from CUDA events on the launching
-    stream around every eager launch, summed per call.  The CTA widths and the
-    spectral_op chunk size (planes per chunk of the three passes) are swept
-    first and the fastest kept."""
+    stream around every eager launch."""
     import numpy as np
     import torch
     from paper_2606_06247_gb300 import binding as b
@@ -788,37 +782,25 @@ def measure_planes(steps, warmup, sweep_widths=True):
                 sweep[f"{w[0]},{w[1]}"] = call_ms(ctx, 2)
             best_w = min(sweep, key=sweep.get)
             ctx.set_cta_threads(*[int(x) for x in best_w.split(",")])
-        # spectral_op schedule: all planes per pass, or chunks of planes whose spectra can stay in L2
-        chunk_sweep = {}
-        for ch in PLANE_CHUNKS:
-            ctx.set_op_chunk(ch)
-            call_ms(ctx, 1)
-            chunk_sweep[str(ch)] = call_ms(ctx, 2)
-        chunk = int(min(chunk_sweep, key=chunk_sweep.get))
-        ctx.set_op_chunk(chunk)
         call_ms(ctx, max(3, warmup))
         ms = call_ms(ctx, max(3, steps))
         gbs = P * n * n * 16 / (ms * 1e-3) / 1e9
-        # per-pass durations (eager, events on the launching stream), summed per call over the chunks
-        ncalls = 3
+        # per-pass durations (eager, events on the launching stream)
         ctx.set_profiling(True)
-        for _ in range(ncalls):
+        for _ in range(3):
             ctx.spectral_op(f, ["DX", "DY", "LAP"], outs)
         prof = ctx.get_profile()
         ctx.set_profiling(False)
         hy = (n + n_cont) // 2 + 1
         passes = {}
-        launches = 0
         for k, (tms, cnt) in prof.items():
             by = plane_kernel_bytes(k, P, n, n, hy)
-            avg = tms / ncalls
-            launches += cnt // ncalls
-            passes[k] = {"avg_ms": avg, "launches": cnt // ncalls, "alg_bytes": by, "alg_GBps": by / (avg * 1e-3) / 1e9,
+            avg = tms / cnt
+            passes[k] = {"avg_ms": avg, "alg_bytes": by, "alg_GBps": by / (avg * 1e-3) / 1e9,
                          "frac_of_hbm": by / (avg * 1e-3) / 1e9 / peaks["hbm_gbs"]}
         res[f"n_cont={n_cont} (n_e={n + n_cont})"] = {
-            "ms_per_call": ms, "alg_GBps": gbs, "frac_of_hbm": gbs / peaks["hbm_gbs"], "launches_per_call": launches,
-            "cta_threads": list(ctx.get_cta_threads()), "width_sweep_ms": sweep, "op_chunk": chunk,
-            "chunk_sweep_ms": chunk_sweep, "passes": passes}
+            "ms_per_call": ms, "alg_GBps": gbs, "frac_of_hbm": gbs / peaks["hbm_gbs"], "launches_per_call": 3,
+            "cta_threads": list(ctx.get_cta_threads()), "width_sweep_ms": sweep, "passes": passes}
         del ctx
         torch.cuda.empty_cache()
     del f, outs

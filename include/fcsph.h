@@ -398,18 +398,6 @@ fcsph_status fcsph_set_step_persistent(fcsph_ctx* ctx, int on);
  * counterpart. */
 fcsph_status fcsph_set_tma(fcsph_ctx* ctx, int on);
 
-/* spectral_op schedule: instances = 0 (the default) runs each of its passes
- * (column forward, row, column output) over the whole batch; instances = k > 0
- * runs all passes for instances [0, k), then [k, 2k), and so on, so that a
- * chunk's intermediate spectra can stay in the L2 cache from the pass that
- * writes them to the pass that reads them (for batches whose spectra exceed
- * L2).  More launches per call; results are bitwise identical either way.
- * FCSPH_EINVAL for a null context or instances < 0.  get: the current value
- * (non-null pointer, host).  Engineering choice of this library; the paper
- * has no counterpart. */
-fcsph_status fcsph_set_op_chunk(fcsph_ctx* ctx, int instances);
-fcsph_status fcsph_get_op_chunk(const fcsph_ctx* ctx, int* instances);
-
 /* Tracing (on = 1; default off): NVTX ranges ("fcsph <call>" around every
  * call of this header that takes the context, "fcsph <pass>" around every
  * kernel launch, named as the FCSPH_PROF_* kinds) for a profiler's timeline

@@ -112,8 +112,6 @@ def _load():
         "fcsph_set_step_groups": [P, I],
         "fcsph_set_step_persistent": [P, I],
         "fcsph_set_tma": [P, I],
-        "fcsph_set_op_chunk": [P, I],
-        "fcsph_get_op_chunk": [P, ctypes.POINTER(I)],
         "fcsph_set_tracing": [P, I],
         "fcsph_get_step_persistent": [P, ctypes.POINTER(I)],
         "fcsph_get_step_groups": [P, ctypes.POINTER(I)],
@@ -368,15 +366,6 @@ class Context:
     def set_tma(self, on=True):
         """fcsph_set_tma: bulk-copy (TMA) staging of the FP32 register column passes."""
         self._ck(lib.fcsph_set_tma(self.h, 1 if on else 0))
-
-    def set_op_chunk(self, instances):
-        """fcsph_set_op_chunk: spectral_op runs its passes chunk by chunk of `instances` (0: whole batch)."""
-        self._ck(lib.fcsph_set_op_chunk(self.h, int(instances)))
-
-    def get_op_chunk(self):
-        v = ctypes.c_int()
-        self._ck(lib.fcsph_get_op_chunk(self.h, ctypes.byref(v)))
-        return v.value
 
     def get_step_persistent(self):
         v = ctypes.c_int()

@@ -477,30 +477,14 @@ fcsph_status spectral_op(fcsph_ctx* c, const void* f, unsigned op_mask, int bc, 
     }
   const int p = c->prec.fft_prec;
   const void* fl[1] = {f};
-  // All passes over the whole batch, or (op_chunk) chunk by chunk of
-  // instances, so that a chunk's spectra can stay in L2 from the pass that
-  // writes them to the pass that reads them.  The kernels take the chunk as
-  // an instance offset and count; every instance's arithmetic is the same.
-  const int b0 = c->gd.b0, nb = c->gd.nb;
-  const int chunk = (c->op_chunk > 0 && c->op_chunk < nb) ? c->op_chunk : nb;
-  fcsph_status st = FCSPH_OK;
-  for (int s = 0; s < nb && st == FCSPH_OK; s += chunk) {
-    c->gd.b0 = b0 + s;
-    c->gd.nb = std::min(chunk, nb - s);
-    st = [&]() -> fcsph_status {
-      FCSPH_CK(launch_col_fwd(c, p, 1, fl, p != FCSPH_F32, bc, c->spec_in, 0), "spectral_op fwd");
-      FCSPH_CK(launch_zpass(c, p, c->spec_in, 1, in_bstride(c), c->gd.hy, 0), "spectral_op z fwd");
-      FCSPH_CK(launch_row_sym(c, p, c->spec_in, c->spec_out, ops, 1.0 / ((double)c->gd.mx * c->gd.my * c->gd.nz),
-                              bc, FCSPH_PROF_ROW_OP),
-               "spectral_op row");
-      FCSPH_CK(launch_zpass(c, p, c->spec_out, ops.nout, out_bstride(c), c->gd.hy, 1), "spectral_op z inv");
-      FCSPH_CK(launch_col_out(c, c->spec_out, ops.nout, outs), "spectral_op inv");
-      return FCSPH_OK;
-    }();
-  }
-  c->gd.b0 = b0;
-  c->gd.nb = nb;
-  return st;
+  FCSPH_CK(launch_col_fwd(c, p, 1, fl, p != FCSPH_F32, bc, c->spec_in, 0), "spectral_op fwd");
+  FCSPH_CK(launch_zpass(c, p, c->spec_in, 1, in_bstride(c), c->gd.hy, 0), "spectral_op z fwd");
+  FCSPH_CK(launch_row_sym(c, p, c->spec_in, c->spec_out, ops, 1.0 / ((double)c->gd.mx * c->gd.my * c->gd.nz), bc,
+                          FCSPH_PROF_ROW_OP),
+           "spectral_op row");
+  FCSPH_CK(launch_zpass(c, p, c->spec_out, ops.nout, out_bstride(c), c->gd.hy, 1), "spectral_op z inv");
+  FCSPH_CK(launch_col_out(c, c->spec_out, ops.nout, outs), "spectral_op inv");
+  return FCSPH_OK;
 }
 
 fcsph_status line_op(fcsph_ctx* c, const void* f, unsigned op_mask, int bc, void* const* outs) {
@@ -977,18 +961,6 @@ fcsph_status fcsph_set_tracing(fcsph_ctx* c, int on) {
 fcsph_status fcsph_set_tma(fcsph_ctx* c, int on) {
   if (!c) return fail(nullptr, FCSPH_EINVAL, "fcsph_set_tma: null context");
   c->tma = on ? 1 : 0;
-  return FCSPH_OK;
-}
-
-fcsph_status fcsph_set_op_chunk(fcsph_ctx* c, int instances) {
-  if (!c || instances < 0) return fail(c, FCSPH_EINVAL, "fcsph_set_op_chunk: bad argument");
-  c->op_chunk = instances;
-  return FCSPH_OK;
-}
-
-fcsph_status fcsph_get_op_chunk(const fcsph_ctx* c, int* instances) {
-  if (!c || !instances) return fail(nullptr, FCSPH_EINVAL, "fcsph_get_op_chunk: bad argument");
-  *instances = c->op_chunk;
   return FCSPH_OK;
 }
 

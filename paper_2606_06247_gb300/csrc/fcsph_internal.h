@@ -197,7 +197,6 @@ struct fcsph_ctx {
   PersistRec* rec = nullptr;    // set: the step's launchers record pass descriptors instead of launching
   int persist = 0;              // isph_step (use_graph = 1) as one persistent launch per step
   int tma = 1;                  // FP32 column passes stage their loads with bulk async copies (TMA)
-  int op_chunk = 0;             // spectral_op: instances per chunk of its passes (0: the whole batch)
   PersistPlan* pplan = nullptr; // its plan, valid for pplan_key
   std::vector<double> pplan_key;
   std::vector<cudaStream_t> grp_streams;  // one capture stream per group
