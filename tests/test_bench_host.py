@@ -1,7 +1,8 @@
 """Host logic of bench.py that needs no GPU: the device-code hash that keys
 the recorded DRAM counters (comment edits keep it, code edits change it),
 the lookup that reports null for stale or missing counters, the per-launch
-cost model's scaling, and the whole-job rate over ranks."""
+cost model's scaling, the whole-job rate over ranks, and the reference
+arm's JSON line (the FP64 oracle on the host cores)."""
 import os
 import shutil
 
@@ -73,3 +74,28 @@ def test_hardware_peaks_and_plane_pass_bytes():
     assert passes["col_fwd"] > P * n * n * 4 and passes["col_out"] > P * n * n * 12
     assert sum(passes.values()) > P * n * n * 16
     assert bench.STEP_BYTES_PER_UPDATE == {"f32": 72, "f32x2": 72, "f64": 112}
+
+
+def test_reference_arm_prints_the_contract_line():
+    """`bench.py --impl reference` times the FP64 oracle on the host cores
+    (one bounded RK3 step here) and prints one JSON line with the keys the
+    reference arm carries: the same metric and workload as the GPU arm, a
+    cpu_baseline of kind oracle, and an e2e block with no host-device bytes."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "0"], capture_output=True, text=True, timeout=600, cwd=root)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference"
+    assert d["metric"].startswith("particle-updates/s per ISPH step")
+    assert d["unit"] == "particle-updates/s" and d["higher_is_better"] is True
+    assert d["value"] > 0 and d["steps"] == 1 and d["n_gpus"] == 1
+    assert d["config"]["batch"] == 32 and d["config"]["nx"] == 256 and d["config"]["ny"] == 256
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
